@@ -1,0 +1,270 @@
+"""FP64 CPU oracle of the HGKS step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+may import this package.  The product path in ``paper_2005_08736_gb300`` never
+imports it, and the oracle shares no code with that path: it is a plain C++
+restatement of the scheme of Cao, Pan & Xu (arXiv:2005.08736), Sec. 2.1 and
+Sec. 3, compiled here with g++ and loaded through ctypes.
+
+Every function here is argument marshalling; the arithmetic is in
+``hgks_oracle.cpp``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hgks_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libhgks_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RECON_LINEAR, RECON_WENO_JS, RECON_WENO_Z = 0, 1, 2
+FLUX_SMOOTH, FLUX_FULL = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (-O2, OpenMP, no FP contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OracleConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("x0", ctypes.c_double), ("lx", ctypes.c_double),
+        ("y0", ctypes.c_double), ("ly", ctypes.c_double),
+        ("z0", ctypes.c_double), ("lz", ctypes.c_double),
+        ("y_stretch", ctypes.c_int), ("stretch_b", ctypes.c_double),
+        ("bc_y", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+        ("visc_law", ctypes.c_int),
+        ("mu_ref", ctypes.c_double), ("T_ref", ctypes.c_double), ("visc_exp", ctypes.c_double),
+        ("T_wall", ctypes.c_double), ("force_x", ctypes.c_double),
+        ("recon", ctypes.c_int), ("flux", ctypes.c_int),
+        ("tau_num_C", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            pd = ctypes.POINTER(ctypes.c_double)
+            L.oracle_create.restype = vp
+            L.oracle_create.argtypes = [ctypes.POINTER(OracleConfig)]
+            L.oracle_destroy.argtypes = [vp]
+            L.oracle_set_state.argtypes = [vp, pd]
+            L.oracle_get_state.argtypes = [vp, pd]
+            L.oracle_step.restype = d
+            L.oracle_step.argtypes = [vp, i, d]
+            L.oracle_time.restype = d
+            L.oracle_time.argtypes = [vp]
+            L.oracle_cfl_dt.restype = d
+            L.oracle_cfl_dt.argtypes = [vp]
+            L.oracle_rhs.argtypes = [vp, d, pd, pd]
+            L.oracle_widths.argtypes = [vp, i, pd]
+            L.oracle_padded.argtypes = [vp, pd]
+            L.oracle_moments.argtypes = [d, d, d, d, d, pd, pd, pd, pd, pd, pd]
+            L.oracle_slope.argtypes = [pd, d, pd, pd]
+            L.oracle_kinetic.argtypes = [pd, pd, d, pd, pd]
+            L.oracle_compat.argtypes = [pd, pd, d, pd]
+            L.oracle_time_integrals.argtypes = [d, d, pd]
+            L.oracle_s2o4_stage1.restype = d
+            L.oracle_s2o4_stage1.argtypes = [d, d, d, d]
+            L.oracle_s2o4_stage2.restype = d
+            L.oracle_s2o4_stage2.argtypes = [d, d, d, d, d]
+            L.oracle_weno5_right.restype = d
+            L.oracle_weno5_right.argtypes = [pd, i]
+            L.oracle_weno5_left.restype = d
+            L.oracle_weno5_left.argtypes = [pd, i]
+            L.oracle_tangential.argtypes = [pd, i, pd, pd]
+            L.oracle_flux_point.argtypes = [ctypes.POINTER(OracleConfig), pd, d, pd, pd]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+@dataclass
+class Config:
+    """Problem statement of the scheme (oracle side): grid, gas, viscosity, modes."""
+    nx: int
+    ny: int
+    nz: int
+    lx: float = 2 * np.pi
+    ly: float = 2 * np.pi
+    lz: float = 2 * np.pi
+    x0: float = 0.0
+    y0: float = 0.0
+    z0: float = 0.0
+    y_stretch: int = 0
+    stretch_b: float = 2.0
+    bc_y: int = 0
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    visc_law: int = 0
+    mu_ref: float = 1.0 / 1600.0
+    T_ref: float = 1.0
+    visc_exp: float = 0.76
+    T_wall: float = 1.0
+    force_x: float = 0.0
+    recon: int = RECON_LINEAR
+    flux: int = FLUX_SMOOTH
+    tau_num_C: float = 0.0
+    cfl: float = 0.5
+
+    def c_struct(self) -> OracleConfig:
+        return OracleConfig(**{k: getattr(self, k) for k, _ in OracleConfig._fields_})
+
+
+class Solver:
+    """The oracle's HGKS solver: conservative cell averages [5][nz][ny][nx], FP64."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        self._c = cfg.c_struct()
+        self._h = lib().oracle_create(ctypes.byref(self._c))
+        self.shape = (5, cfg.nz, cfg.ny, cfg.nx)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_destroy(h)
+            self._h = None
+
+    def set_state(self, cons) -> None:
+        a = _f64(cons)
+        assert a.shape == self.shape
+        lib().oracle_set_state(self._h, _p(a))
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.shape)
+        lib().oracle_get_state(self._h, _p(out))
+        return out
+
+    def step(self, nsteps: int = 1, dt: float = 0.0) -> float:
+        return lib().oracle_step(self._h, int(nsteps), float(dt))
+
+    @property
+    def t(self) -> float:
+        return lib().oracle_time(self._h)
+
+    def cfl_dt(self) -> float:
+        return lib().oracle_cfl_dt(self._h)
+
+    def rhs(self, dt: float):
+        L = np.empty(self.shape)
+        dL = np.empty(self.shape)
+        lib().oracle_rhs(self._h, float(dt), _p(L), _p(dL))
+        return L, dL
+
+    def widths(self, d: int) -> np.ndarray:
+        n = (self.cfg.nx, self.cfg.ny, self.cfg.nz)[d]
+        out = np.empty(n)
+        lib().oracle_widths(self._h, d, _p(out))
+        return out
+
+    def padded(self) -> np.ndarray:
+        c = self.cfg
+        out = np.empty((5, c.nz + 6, c.ny + 6, c.nx + 6))
+        lib().oracle_padded(self._h, _p(out))
+        return out
+
+
+# ---- single pieces -------------------------------------------------------------
+
+def moments(U, V, W, lam, K):
+    out = [np.empty(10) for _ in range(5)] + [np.empty(4)]
+    lib().oracle_moments(float(U), float(V), float(W), float(lam), float(K), *[_p(o) for o in out])
+    return dict(uf=out[0], up=out[1], un=out[2], v=out[3], w=out[4], xi=out[5])
+
+
+def slope(Q, gamma, b):
+    a = np.empty(5)
+    lib().oracle_slope(_p(_f64(Q)), float(gamma), _p(_f64(b)), _p(a))
+    return a
+
+
+def kinetic(Q, dQ, gamma):
+    a = np.empty((3, 5))
+    A = np.empty(5)
+    lib().oracle_kinetic(_p(_f64(Q)), _p(_f64(dQ)), float(gamma), _p(a), _p(A))
+    return a, A
+
+
+def compat(Ql, Qr, gamma):
+    out = np.empty(5)
+    lib().oracle_compat(_p(_f64(Ql)), _p(_f64(Qr)), float(gamma), _p(out))
+    return out
+
+
+def time_integrals(T, tau):
+    q = np.empty(6)
+    lib().oracle_time_integrals(float(T), float(tau), _p(q))
+    return q
+
+
+def s2o4_stage1(Qn, L0, dL0, dt):
+    return lib().oracle_s2o4_stage1(float(Qn), float(L0), float(dL0), float(dt))
+
+
+def s2o4_stage2(Qn, L0, dL0, dL1, dt):
+    return lib().oracle_s2o4_stage2(float(Qn), float(L0), float(dL0), float(dL1), float(dt))
+
+
+def weno5_right(q, mode):
+    return lib().oracle_weno5_right(_p(_f64(q)), int(mode))
+
+
+def weno5_left(q, mode):
+    return lib().oracle_weno5_left(_p(_f64(q)), int(mode))
+
+
+def tangential(f, mode):
+    val = np.empty(2)
+    der = np.empty(2)
+    lib().oracle_tangential(_p(_f64(f)), int(mode), _p(val), _p(der))
+    return val, der
+
+
+def flux_point(cfg: Config, st, dt):
+    """st: [3][4][5] = states (l, r, 0) x (value, d/dn, d/dt1, d/dt2) x vars, local frame."""
+    c = cfg.c_struct()
+    F = np.empty(5)
+    dF = np.empty(5)
+    lib().oracle_flux_point(ctypes.byref(c), _p(_f64(st)), float(dt), _p(F), _p(dF))
+    return F, dF
+
+
+def conservative(prim, gamma):
+    """Conservative variables from primitive (rho, u, v, w, p) [5, ...] (oracle side)."""
+    prim = np.asarray(prim, dtype=np.float64)
+    rho, u, v, w, p = prim
+    return np.stack([rho, rho * u, rho * v, rho * w,
+                     p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)])

@@ -1,0 +1,99 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds problem set-up only (initial fields of the paper's test
+cases and of the convergence test); it contains none of the scheme's
+arithmetic.  Every generator returns FP64 numpy arrays of primitive variables
+(rho, u, v, w, p) laid out as [5][nz][ny][nx] (x fastest), sampled at cell
+centres, unless stated otherwise.
+
+Workloads (Cao, Pan & Xu, arXiv:2005.08736):
+  * Taylor-Green vortex, Sec. 3.1.
+  * Decaying compressible isotropic turbulence, Sec. 3.4, Eq. (9)-(10).
+  * Turbulent channel flow, Sec. 3.3 (tanh-stretched y, laminar profile + noise).
+  * Advected density wave: an exact Euler solution used for convergence tests.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def centres(n: int, length: float, origin: float = 0.0) -> np.ndarray:
+    """Cell centres of a uniform grid of n cells on [origin, origin + length]."""
+    return origin + (np.arange(n) + 0.5) * (length / n)
+
+
+def channel_faces(ny: int, b: float = 2.0) -> np.ndarray:
+    """Face positions y_j, j = 0..ny, of the tanh mapping of Sec. 3.3:
+    y = tanh(b (eta / (1.5 pi) - 1)) / tanh(b), eta uniform on [0, 3 pi]."""
+    eta = 3.0 * math.pi * np.arange(ny + 1) / ny
+    return np.tanh(b * (eta / (1.5 * math.pi) - 1.0)) / math.tanh(b)
+
+
+def taylor_green(n: int, mach: float = 0.1, V0: float = 1.0, rho0: float = 1.0,
+                 gamma: float = 1.4, uniform_T: bool = False) -> np.ndarray:
+    """Taylor-Green vortex on the periodic box [0, 2 pi]^3 (Sec. 3.1, L = 1).
+
+    u = V0 sin x cos y cos z, v = -V0 cos x sin y cos z, w = 0,
+    p = p0 + rho0 V0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2), p0 = rho0 c0^2 / gamma,
+    c0 = V0 / Ma.  rho = rho0 by default; uniform_T=True takes rho = p / T0
+    with T0 = p0 / rho0 instead.
+    """
+    x = centres(n, 2 * math.pi)
+    z3, y3, x3 = np.meshgrid(x, x, x, indexing="ij")
+    c0 = V0 / mach
+    p0 = rho0 * c0 * c0 / gamma
+    u = V0 * np.sin(x3) * np.cos(y3) * np.cos(z3)
+    v = -V0 * np.cos(x3) * np.sin(y3) * np.cos(z3)
+    w = np.zeros_like(u)
+    p = p0 + rho0 * V0 * V0 / 16.0 * (np.cos(2 * x3) + np.cos(2 * y3)) * (np.cos(2 * z3) + 2.0)
+    rho = p / (p0 / rho0) if uniform_T else np.full_like(u, rho0)
+    return np.stack([rho, u, v, w, p])
+
+
+def taylor_green_reference(mach: float = 0.1, V0: float = 1.0, rho0: float = 1.0,
+                           gamma: float = 1.4):
+    """Reference state (rho, (u, v, w), p) of the Taylor-Green set-up."""
+    c0 = V0 / mach
+    return rho0, (0.0, 0.0, 0.0), rho0 * c0 * c0 / gamma
+
+
+def density_wave_cons(n: int, amp: float = 0.2, gamma: float = 1.4, t: float = 0.0,
+                      U: float = 1.0, p: float = 1.0) -> np.ndarray:
+    """Exact cell averages of the conservative variables of the advected wave
+    rho = 1 + amp sin(x + y + z - 3 U t), u = v = w = U, p const, on [0, 2 pi]^3.
+
+    The cell average of sin(x + y + z) over a cube of side h centred at c is
+    sin(c_x + c_y + c_z) (sin(h/2) / (h/2))^3.
+    """
+    h = 2 * math.pi / n
+    x = centres(n, 2 * math.pi)
+    z3, y3, x3 = np.meshgrid(x, x, x, indexing="ij")
+    s = (math.sin(h / 2) / (h / 2)) ** 3
+    rho = 1.0 + amp * s * np.sin(x3 + y3 + z3 - 3 * U * t)
+    E = p / (gamma - 1.0) + 1.5 * U * U * rho
+    return np.stack([rho, U * rho, U * rho, U * rho, E])
+
+
+def random_smooth(n: tuple[int, int, int], seed: int, amp: float = 0.05,
+                  rho0: float = 1.0, p0: float = 1.0, kmax: int = 3) -> np.ndarray:
+    """A seeded smooth periodic primitive field: a few random low Fourier modes
+    of relative amplitude `amp` around (rho0, 0, 0, 0, p0); shape (nx, ny, nz)."""
+    nx, ny, nz = n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = 2 * math.pi * (np.arange(nx) + 0.5) / nx
+    y = 2 * math.pi * (np.arange(ny) + 0.5) / ny
+    z = 2 * math.pi * (np.arange(nz) + 0.5) / nz
+    z3, y3, x3 = np.meshgrid(z, y, x, indexing="ij")
+    out = []
+    for var, base in enumerate((rho0, 0.0, 0.0, 0.0, p0)):
+        f = np.zeros_like(x3)
+        for _ in range(4):
+            k = rng.integers(-kmax, kmax + 1, size=3)
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.uniform(-1, 1)
+            f += a * np.sin(k[0] * x3 + k[1] * y3 + k[2] * z3 + ph)
+        scale = base if base != 0.0 else 1.0
+        out.append(base + amp * scale * f / 4.0)
+    return np.stack(out)

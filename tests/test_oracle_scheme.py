@@ -1,0 +1,189 @@
+"""Whole-scheme pins of the oracle (CPU only).
+
+* Free-stream preservation and exact discrete conservation on periodic grids.
+* Convergence order of the semi-discrete operator L and of dL/dt on an
+  advected density wave, an exact Euler solution.
+* Mirror symmetry of a channel with isothermal walls and the wall ghost cells.
+* The printed time steps of the Taylor-Green runs (Sec. 3.2 table) and the
+  printed channel grid spacings (Sec. 3.3 table), from tests/golden/.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_08736_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+MODES = [(oracle.RECON_LINEAR, oracle.FLUX_SMOOTH), (oracle.RECON_WENO_Z, oracle.FLUX_FULL)]
+
+
+def solver(n, **kw):
+    nx, ny, nz = n if isinstance(n, tuple) else (n, n, n)
+    return oracle.Solver(oracle.Config(nx, ny, nz, **kw))
+
+
+@pytest.mark.parametrize("recon,flux", MODES)
+def test_free_stream_is_preserved_bitwise(recon, flux):
+    s = solver((8, 7, 6), recon=recon, flux=flux, tau_num_C=1.0)
+    prim = np.zeros((5, 6, 7, 8))
+    prim[0], prim[1], prim[2], prim[3], prim[4] = 1.3, 0.4, -0.25, 0.1, 2.0
+    Q = oracle.conservative(prim, 1.4)
+    s.set_state(Q)
+    s.step(2)
+    assert np.array_equal(s.state(), Q)
+
+
+@pytest.mark.parametrize("recon,flux", MODES)
+def test_periodic_totals_are_conserved(recon, flux):
+    s = solver((10, 8, 9), recon=recon, flux=flux, tau_num_C=1.0, mu_ref=0.01)
+    prim = inputs.random_smooth((10, 8, 9), seed=11, amp=0.1)
+    Q = oracle.conservative(prim, 1.4)
+    s.set_state(Q)
+    s.step(3)
+    Q1 = s.state()
+    assert not np.allclose(Q1, Q)
+    tot0, tot1 = Q.sum(axis=(1, 2, 3)), Q1.sum(axis=(1, 2, 3))
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * np.abs(Q).sum(axis=(1, 2, 3)))
+
+
+def wave_error(n, recon, flux, aligned):
+    """Max error of L and dL/dt against the exact cell-averaged time derivatives."""
+    U, amp, gamma = 1.0, 0.2, 1.4
+    h = 2 * math.pi / n
+    x = inputs.centres(n, 2 * math.pi)
+    z3, y3, x3 = np.meshgrid(x, x, x, indexing="ij")
+    if aligned:   # rho = 1 + amp sin(x), u = U, v = w = 0
+        ph, sx, c = x3, math.sin(h / 2) / (h / 2), 1.0
+        Q = np.stack([1 + amp * sx * np.sin(ph), U * (1 + amp * sx * np.sin(ph)), 0 * ph, 0 * ph,
+                      1 / (gamma - 1) + 0.5 * U * U * (1 + amp * sx * np.sin(ph))])
+        vel = np.array([U, 0, 0])
+        s = sx
+    else:         # rho = 1 + amp sin(x + y + z), u = v = w = U
+        Q = inputs.density_wave_cons(n, amp, gamma, U=U)
+        ph = x3 + y3 + z3
+        c = 3.0
+        vel = np.array([U, U, U])
+        s = (math.sin(h / 2) / (h / 2)) ** 3
+    sv = solver(n, recon=recon, flux=flux, mu_ref=0.0, tau_num_C=0.0, prandtl=1.0)
+    sv.set_state(Q)
+    L, dL = sv.rhs(1e-3)
+    rho_t = -c * U * amp * s * np.cos(ph)
+    rho_tt = -(c * U) ** 2 * amp * s * np.sin(ph)
+    ke = 0.5 * float(vel @ vel)
+    exact_t = np.stack([rho_t, vel[0] * rho_t, vel[1] * rho_t, vel[2] * rho_t, ke * rho_t])
+    exact_tt = np.stack([rho_tt, vel[0] * rho_tt, vel[1] * rho_tt, vel[2] * rho_tt, ke * rho_tt])
+    return np.abs(L - exact_t).max(), np.abs(dL - exact_tt).max()
+
+
+def orders(errs):
+    e = np.array(errs)
+    return np.log2(e[:-1] / e[1:])
+
+
+def test_linear_smooth_operator_is_fifth_order_on_oblique_wave():
+    errs = [wave_error(n, 0, 0, aligned=False) for n in (8, 16, 32)]
+    oL = orders([e[0] for e in errs])
+    odL = orders([e[1] for e in errs])
+    assert oL[-1] > 4.6, (errs, oL)
+    assert odL[-1] > 3.6, (errs, odL)
+
+
+def test_wenoz_full_operator_orders():
+    # Aligned wave: tangential reconstruction is exact, the normal WENO-Z
+    # gives fifth order.  Oblique wave: the quadratic tangential
+    # reconstruction of the WENO mode (Remark 1) limits the order to three.
+    al = [wave_error(n, 2, 1, aligned=True) for n in (16, 32, 64)]
+    assert orders([e[0] for e in al])[-1] > 4.6, al
+    ob = [wave_error(n, 2, 1, aligned=False) for n in (8, 16, 32)]
+    assert orders([e[0] for e in ob])[-1] > 2.7, ob
+
+
+def channel_state(nx, ny, nz, seed):
+    """A y-mirror-symmetric wall-bounded state on the stretched channel grid."""
+    yf = inputs.channel_faces(ny)
+    yc = 0.5 * (yf[1:] + yf[:-1])
+    rng = np.random.default_rng(seed)
+    prim = np.zeros((5, nz, ny, nx))
+    half = rng.normal(size=(5, nz, ny // 2, nx)) * 0.05
+    sym = np.concatenate([half[:, :, ::-1], half], axis=2)  # even in y
+    prim[0] = 1.0 + sym[0]
+    prim[1] = 1.5 * (1 - yc[None, :, None] ** 2) + sym[1]
+    prim[2] = np.concatenate([-half[2, :, ::-1], half[2]], axis=1)  # odd in y
+    prim[3] = sym[3]
+    prim[4] = 71.43 * (1.0 + sym[4])
+    return prim
+
+
+def test_channel_walls_keep_mirror_symmetry():
+    nx, ny, nz = 6, 12, 6
+    kw = dict(ly=2.0, y0=-1.0, y_stretch=1, stretch_b=2.0, bc_y=1, T_wall=71.43,
+              mu_ref=0.0541 / 180, force_x=2.93e-3, cfl=0.5)
+    s = solver((nx, ny, nz), **kw)
+    s.set_state(oracle.conservative(channel_state(nx, ny, nz, 1), 1.4))
+    s.step(2)
+    Q = s.state()
+    mirror = Q[:, :, ::-1, :].copy()
+    mirror[2] *= -1
+    assert np.allclose(Q, mirror, rtol=1e-12, atol=1e-12)
+
+
+def test_wall_ghost_cells():
+    nx, ny, nz, Tw = 6, 8, 6, 71.43
+    s = solver((nx, ny, nz), ly=2.0, y0=-1.0, y_stretch=1, bc_y=1, T_wall=Tw)
+    prim = channel_state(nx, ny, nz, 2)
+    s.set_state(oracle.conservative(prim, 1.4))
+    P = s.padded()
+    G = 3
+    rho = P[0]
+    u = P[1:4] / rho
+    p = 0.4 * (P[4] - 0.5 * rho * (u ** 2).sum(axis=0))
+    T = p / rho
+    for m in range(G):
+        lo_g, lo_i = G - 1 - m, G + m
+        hi_g, hi_i = G + ny + m, G + ny - 1 - m
+        for g, i in ((lo_g, lo_i), (hi_g, hi_i)):
+            sl = (slice(G, G + nz), slice(G, G + nx))
+            assert np.allclose(u[:, sl[0], g, sl[1]], -u[:, sl[0], i, sl[1]], atol=1e-13)
+            assert np.allclose(p[sl[0], g, sl[1]], p[sl[0], i, sl[1]], rtol=1e-13)
+            assert np.allclose(0.5 * (T[sl[0], g, sl[1]] + T[sl[0], i, sl[1]]), Tw, rtol=1e-13)
+
+
+def test_periodic_ghost_cells_wrap_including_corners():
+    s = solver((7, 6, 5))
+    prim = inputs.random_smooth((7, 6, 5), seed=3)
+    Q = oracle.conservative(prim, 1.4)
+    s.set_state(Q)
+    P = s.padded()
+    idx = [np.arange(-3, n + 3) % n for n in (5, 6, 7)]
+    ref = Q[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+    assert np.array_equal(P, ref)
+
+
+def test_taylor_green_time_steps_match_printed_table():
+    # Sec. 3.2 prints dt for TG1-TG3; with CFL 0.4 and dt = CFL min dx/(|u|+c)
+    # the 128^3 value is reproduced (the larger grids scale as 1/n).
+    rows = json.load(open(GOLDEN))["tg_time_steps"]["rows"]
+    s = solver(128, cfl=0.4)
+    s.set_state(oracle.conservative(inputs.taylor_green(128), 1.4))
+    dt = s.cfl_dt()
+    for r in rows:
+        assert dt * 128 / r["n"] == pytest.approx(r["dt"], rel=2e-3)
+
+
+def test_channel_grid_matches_printed_table():
+    rows = json.load(open(GOLDEN))["channel_grids"]["rows"]
+    re_tau = 180.0
+    for r in rows:
+        n = r["n"]
+        s = solver((n, n, n), lx=2 * math.pi, ly=2.0, y0=-1.0, lz=math.pi, y_stretch=1,
+                   stretch_b=2.0, bc_y=1)
+        dy = s.widths(1)
+        # The printed minimum is the wall-to-first-centre distance (half a cell).
+        assert 0.5 * dy.min() * re_tau == pytest.approx(r["dyplus_min"], abs=0.006)
+        assert dy.max() * re_tau == pytest.approx(r["dyplus_max"], abs=0.006)
+        assert s.widths(0)[0] * re_tau == pytest.approx(r["dxplus"], rel=2e-3)
+        assert s.widths(2)[0] * re_tau == pytest.approx(r["dzplus"], rel=2e-3)
