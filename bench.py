@@ -1,0 +1,324 @@
+"""Throughput of the HGKS S2O4 step on the GPU (Mcell-updates/s).
+
+Workload: the Taylor-Green vortex of Cao, Pan & Xu (arXiv:2005.08736,
+Sec. 3.1) on a 256^3 periodic grid -- Ma 0.1, Re 1600, gamma 1.4, Pr 0.72 --
+with linear-weight WENO5 and the smooth BGK flux (the paper's setting for this
+flow), CFL 0.5, FP32 arithmetic with deviation storage and FP64 reductions.
+One "step" is one full S2O4 time step (CFL reduction, two stages of ghost
+fill, reconstruction, Gauss-point flux and update).  The same step in FP64 is
+timed beside it, with the FP32-vs-FP64 error after the timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the
+domain-decomposed multi-GPU path is not built); value = sum over ranks.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.09 s/step
+METRIC = "Mcell-updates/s per S2O4 step"
+LAUNCHES_PER_STEP = 23  # cfl, dt, 2 x (3 ghost + 3 x (face fields + flux) + update), time
+# Executed FP32 operations (add, mul, 2 x fma) per Gauss point of the flux
+# kernel, counted by ncu on TG 64^3 (profiles/flux_kernel_taylor_green.md);
+# None until counted.
+FLOPS_PER_GAUSS_POINT = {"stage1": None, "stage2": None}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample(steps: int, n: int = 32):
+    """The FP64 oracle on a bounded sample: TG n^3, `steps` steps; (Mcell-upd/s, seconds)."""
+    import oracle
+    from paper_2005_08736_gb300 import inputs
+    s = oracle.Solver(oracle.Config(n, n, n, recon=0, flux=0, prandtl=0.72, mu_ref=1 / 1600,
+                                    cfl=0.5))
+    s.set_state(oracle.conservative(inputs.taylor_green(n), 1.4))
+    t0 = time.perf_counter()
+    s.step(steps)
+    el = time.perf_counter() - t0
+    return n ** 3 * steps / el / 1e6, el
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = 32
+    oracle_sample(1, n)  # load and warm the library
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state beyond the library load
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, el = oracle_sample(1, n)
+        rates.append(r)
+        times.append(el)
+    value = n ** 3 * args.steps / sum(times) / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mcell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(),
+        "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"FP64 CPU oracle, one step of Taylor-Green {n}^3 per timed step "
+                                   f"(same physics and scheme as the {N_GRID}^3 workload)"},
+        "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict():
+    return {"workload": f"taylor-green-{N_GRID}^3 fp32 linear-WENO5 smooth-GKS S2O4",
+            "model": "HGKS", "grid": [N_GRID] * 3, "precision": "fp32", "recon": "linear",
+            "flux": "smooth", "cfl": 0.5, "mach": 0.1, "reynolds": 1600, "prandtl": 0.72,
+            "global_batch": 1, "seq_len": None, "parallelism": "replicas",
+            "l2": "inputs larger than L2: the FP32 state alone is 335 MB per step"}
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_2005_08736_gb300 import build as cuda_build
+    from paper_2005_08736_gb300 import inputs
+    from paper_2005_08736_gb300.solver import Simulation, taylor_green_config
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        cuda_build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        dist.barrier()
+        cuda_build.build()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prim = inputs.taylor_green(N_GRID)
+    cfg = taylor_green_config(N_GRID, args.precision)
+    sim = Simulation(cfg)
+    sim.init_primitive(prim)
+    stream = sim.stream
+    for _ in range(args.warmup):
+        sim.step(1, sync=False)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        sim.step(args.steps, sync=False)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(stop) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cfg.cells / (ms * 1e-3) / 1e6
+    t_reached = sim.step(0)  # sync + non-physical check
+
+    # Kernel classes of one step (CUDA events around each launch).
+    prof = sim.profile_step()
+    if args.quick:
+        sim.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "Mcell-updates/s",
+                              "ms_per_step": ms, "grid": N_GRID, "precision": args.precision,
+                              "kernel_ms_per_step": prof, "quick": True}), flush=True)
+        return
+
+    # FP64 step of the same workload, and the FP32-vs-FP64 error after the same steps.
+    k64 = max(2, min(args.steps, 4))
+    sim64 = Simulation(taylor_green_config(N_GRID, "fp64"))
+    sim64.init_primitive(prim)
+    sim64.step(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(sim64.stream)
+    sim64.step(k64, sync=False)
+    e1.record(sim64.stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / k64
+    # Error of FP32 against FP64 after 1 + k64 steps from the same initial state.
+    simA = Simulation(taylor_green_config(N_GRID, "fp32"))
+    simA.init_primitive(prim)
+    simA.step(1 + k64)
+    a32, a64 = simA.state(), sim64.state()
+    err = max(float(np.abs(a32[v] - a64[v]).max() / np.abs(a64[v]).max()) for v in range(5))
+    ek32, ek64 = simA.diagnostics()["Ek"], sim64.diagnostics()["Ek"]
+    simA.close()
+    sim64.close()
+
+    # End to end through the C ABI with host buffers: per step the FP64
+    # primitive state is copied in from pinned host memory, one step runs and
+    # the FP64 diagnostics are read back.
+    host = torch.from_numpy(np.ascontiguousarray(prim)).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.init_primitive(host)
+        sim.step(1, sync=False)
+        sim.diagnostics()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    barrier()
+    sim.close()
+    e2e_value = world * cfg.cells / e2e_s / 1e6
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = load_peaks()
+    sm_clock = clocks.summary()
+    faces = 3 * (N_GRID + 1) * N_GRID * N_GRID
+    flux_ms = prof["flux_stage1"] / 3.0  # average launch duration of the dominant kernel
+    f1 = FLOPS_PER_GAUSS_POINT["stage1"]
+    sms, lanes = 152, 128
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = sms * lanes * 2 * clock_mhz * 1e6 / 1e12
+    achieved = (f1 * 4 * faces / 3) / (flux_ms * 1e-3) / 1e12 if f1 else None
+    roofline = {"bound": "alu", "kernel": "k_gauss_flux (stage 1, FP32)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops if achieved else None, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (nominal)",
+                "launch_ms": flux_ms, "kernel_ms_per_step": prof}
+    cpu_rate, cpu_s = oracle_sample(2)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_MCUPS_256, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(),
+        "fp64": {"value": world * cfg.cells / (ms64 * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                 "ms_per_step": ms64, "steps": k64},
+        "fp32_speedup_over_fp64": ms64 / ms,
+        "fp32_error": {"rel_linf_vs_fp64_gpu": err, "steps": 1 + k64,
+                       "Ek_rel_diff": abs(ek32 - ek64) / ek64},
+        "t_reached": t_reached,
+        "roofline": roofline,
+        "cpu_baseline": {"value": cpu_rate, "unit": "Mcell-updates/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"FP64 CPU oracle, 2 steps of Taylor-Green 32^3 "
+                                   f"({cpu_s:.1f} s), same physics and scheme"},
+        "e2e": {"value": e2e_value, "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": int(prim.nbytes), "d2h_bytes_per_step": 96},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": sm_clock,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=256, help="grid size (profiling cases)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--quick", action="store_true",
+                    help="time the step only (no FP64 leg, e2e or CPU baseline); for profiling")
+    args = ap.parse_args()
+    global N_GRID
+    N_GRID = args.grid
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * hgks.h -- C ABI of a GB300 (sm_103a) implementation of one time step of the
+ * high-order gas-kinetic scheme (HGKS) of Cao, Pan & Xu, "High-order
+ * gas-kinetic scheme with parallel computation for direct numerical
+ * simulation of turbulent flows" (arXiv:2005.08736).
+ *
+ * The problem is stated as in the paper:
+ *   - gas: specific-heat ratio gamma and internal degrees of freedom
+ *     N = (5 - 3 gamma)/(gamma - 1) (Sec. 2.1, after Eq. (2)); Prandtl number
+ *     (Sec. 3.1); gas constant R = 1, so p = rho T;
+ *   - viscosity: constant (Sec. 3.1, 3.3) or mu = mu_ref (T/T_ref)^visc_exp
+ *     (Sec. 3.4);
+ *   - an orthogonal Cartesian grid, uniform or with the tanh stretching of
+ *     Sec. 3.3 in y; boundaries periodic, or isothermal no-slip walls at both
+ *     ends of y (Sec. 3.3); optional streamwise body force f_x (Sec. 3.3);
+ *   - reconstruction: WENO5 with linear weights, WENO-JS or WENO-Z
+ *     (Sec. 2.1, Remark 1); flux: the simplified smooth BGK flux or the full
+ *     second-order flux of Eq. (5); collision time tau = mu/p plus, for the
+ *     full flux, C |p_l - p_r|/(p_l + p_r) dt (Sec. 3 opening);
+ *   - time stepping: the two-stage fourth-order scheme of Eq. (6) with the
+ *     linear flux fit of Eq. (7); dt = cfl * min over cells and directions of
+ *     width / (|u_d| + c).
+ *
+ * Conventions for every call:
+ *   - Field arrays crossing the ABI are FP64, laid out [5][nz][ny][nx]
+ *     (x fastest).  Primitive arrays hold (rho, u, v, w, p); conservative
+ *     arrays hold (rho, rho u, rho v, rho w, rho E).
+ *   - Pointers passed in are borrowed for the duration of the call only.
+ *     "is_host" selects host (pageable or pinned) or device memory.
+ *   - All GPU work runs on the CUDA stream given to hgks_create.  A call
+ *     returns after enqueuing its work unless it reads results back to the
+ *     host or is asked to synchronise.
+ *   - Every function returns an hgks_status; HGKS_OK is 0.  No error is
+ *     reported by any other route; hgks_last_error gives a message.
+ */
+#ifndef HGKS_H
+#define HGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HGKS_OK = 0,
+  HGKS_E_INVAL = 1,        /* invalid argument or configuration */
+  HGKS_E_NOMEM = 2,        /* device allocation failed */
+  HGKS_E_CUDA = 3,         /* a CUDA call failed */
+  HGKS_E_NONPHYSICAL = 4,  /* rho <= 0, p <= 0 or NaN in the state after a step */
+  HGKS_E_TIMEOUT = 5,      /* reserved: a bounded device wait expired */
+  HGKS_E_UNSUPPORTED = 6   /* a valid request this build does not implement */
+} hgks_status;
+
+typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_WALL_ISOTHERMAL = 1 } hgks_bc;
+typedef enum { HGKS_RECON_LINEAR = 0, HGKS_RECON_WENO_JS = 1, HGKS_RECON_WENO_Z = 2 } hgks_recon;
+typedef enum { HGKS_FLUX_SMOOTH = 0, HGKS_FLUX_FULL = 1 } hgks_flux;
+typedef enum { HGKS_VISC_CONST = 0, HGKS_VISC_POWER = 1 } hgks_visc;
+typedef enum { HGKS_FP64 = 0, HGKS_FP32 = 1 } hgks_prec;
+
+typedef struct {
+  int nx, ny, nz;                  /* interior cells; >= 6 on every axis */
+  double x0, lx, y0, ly, z0, lz;   /* origin and extent of the box */
+  int y_stretch;                   /* 0 uniform y; 1 tanh mapping of Sec. 3.3 (ly = 2) */
+  double stretch_b;                /* b_g of the mapping */
+  int bc_y;                        /* hgks_bc for both y ends; x and z are periodic */
+  double gamma, prandtl;           /* gamma > 1; Pr > 0 */
+  int visc;                        /* hgks_visc */
+  double mu_ref, T_ref, visc_exp;  /* mu = mu_ref (T/T_ref)^visc_exp, or mu_ref */
+  double T_wall, force_x;          /* wall temperature; streamwise body force */
+  int recon, flux;                 /* hgks_recon, hgks_flux */
+  double tau_num_C;                /* C of the numerical collision time (full flux) */
+  double cfl;                      /* > 0 */
+  int prec;                        /* hgks_prec: arithmetic and storage type */
+  double rho_ref, p_ref;           /* reference state at rest; the state is stored as its
+                                      deviation from it (must be > 0) */
+} hgks_config;
+
+typedef struct hgks_ctx hgks_ctx;  /* opaque; owns every device buffer it uses */
+
+/* Fill *cfg with the Taylor-Green settings of Sec. 3.1 on an n^3 grid
+ * (gamma 1.4, Pr 0.72, mu = 1/1600, Ma 0.1, periodic [0, 2 pi]^3, linear
+ * weights and smooth flux, CFL 0.5, FP32).  Never fails for n >= 6. */
+hgks_status hgks_default_config(hgks_config* cfg, int n);
+
+/* Validate cfg, allocate the context's device buffers and bind it to the
+ * CUDA stream `stream` (a cudaStream_t).  NULL gives the context a
+ * non-blocking stream of its own (the legacy default stream cannot be
+ * captured into a CUDA graph); work on it is then ordered with the caller's
+ * streams only through the synchronising calls.  On success *out owns the context.  E_INVAL for a bad config
+ * (n < 6, gamma <= 1, Pr <= 0, cfl <= 0, reference <= 0, unknown enum),
+ * E_NOMEM when a device allocation fails, E_CUDA for other CUDA errors. */
+hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out);
+
+/* Release every resource of ctx (synchronises its stream first).  NULL is OK. */
+hgks_status hgks_destroy(hgks_ctx* ctx);
+
+/* Set the state from primitive cell values (rho, u, v, w, p), FP64
+ * [5][nz][ny][nx]; resets t and the step count to 0. */
+hgks_status hgks_init_state(hgks_ctx* ctx, const double* prim, int is_host);
+
+/* Same from conservative cell averages. */
+hgks_status hgks_init_conservative(hgks_ctx* ctx, const double* cons, int is_host);
+
+/* Copy the conservative state (FP64 [5][nz][ny][nx]) out; synchronises when
+ * is_host != 0. */
+hgks_status hgks_get_state(hgks_ctx* ctx, double* cons_out, int is_host);
+
+/* Advance nsteps S2O4 steps (Eq. (6)).  dt > 0 fixes the step; dt <= 0 takes
+ * the CFL step each time (computed on the device).  One step is captured as
+ * a CUDA graph on first use and replayed.  With sync != 0 the call waits,
+ * checks the state (E_NONPHYSICAL if rho <= 0, p <= 0 or NaN somewhere; the
+ * state is then that of the failed step) and writes the time reached to
+ * *t_out (may be NULL).  With sync == 0 it returns after enqueuing. */
+hgks_status hgks_step(hgks_ctx* ctx, int nsteps, double dt, int sync, double* t_out);
+
+typedef struct {
+  double t, dt;          /* time reached and last step */
+  double mass, mom[3], energy;  /* totals sum Q |Omega_c| */
+  double Ek;             /* (1/(rho_ref |Omega|)) sum rho |U|^2/2 |Omega_c| (Sec. 3.1) */
+  double rho_min, p_min;
+  long long step;
+} hgks_diag;
+
+/* FP64 reductions of the current state (synchronises). */
+hgks_status hgks_diagnostics(hgks_ctx* ctx, hgks_diag* out);
+
+/* Profiling aid (not on the hot path): advance ONE step without the graph,
+ * with CUDA events around every kernel launch on the context's stream, and
+ * write the summed device time in milliseconds of each kernel class to
+ * ms_out[0..nclass-1] (nclass >= 6): 0 CFL reduction and dt, 1 ghost-cell
+ * fills, 2 face fields (3 directions x 2 stages), 3 Gauss-point flux of
+ * stage 1 (3 launches), 4 Gauss-point flux of stage 2 (3 launches),
+ * 5 update (2 launches).  dt as in hgks_step.  Synchronises. */
+hgks_status hgks_profile_step(hgks_ctx* ctx, double dt, double* ms_out, int nclass);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next
+ * call on ctx.  ctx may be NULL for errors of hgks_create. */
+const char* hgks_last_error(const hgks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGKS_H */

@@ -1,0 +1,103 @@
+"""ctypes binding of the C ABI in include/hgks.h (argument marshalling only).
+
+Every step of the scheme runs in the CUDA kernels of libhgks.so; this module
+only converts Python values to the C structs and pointers of the ABI.  It
+raises if the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhgks.so")
+
+HGKS_OK, HGKS_E_INVAL, HGKS_E_NOMEM, HGKS_E_CUDA, HGKS_E_NONPHYSICAL, HGKS_E_TIMEOUT, \
+    HGKS_E_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONPHYSICAL",
+                5: "E_TIMEOUT", 6: "E_UNSUPPORTED"}
+
+# Entry points declared in include/hgks.h.
+EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_state",
+           "hgks_init_conservative", "hgks_get_state", "hgks_step", "hgks_diagnostics",
+           "hgks_profile_step", "hgks_last_error"]
+KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
+
+
+class HgksConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("x0", ctypes.c_double), ("lx", ctypes.c_double),
+        ("y0", ctypes.c_double), ("ly", ctypes.c_double),
+        ("z0", ctypes.c_double), ("lz", ctypes.c_double),
+        ("y_stretch", ctypes.c_int), ("stretch_b", ctypes.c_double),
+        ("bc_y", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+        ("visc", ctypes.c_int),
+        ("mu_ref", ctypes.c_double), ("T_ref", ctypes.c_double), ("visc_exp", ctypes.c_double),
+        ("T_wall", ctypes.c_double), ("force_x", ctypes.c_double),
+        ("recon", ctypes.c_int), ("flux", ctypes.c_int),
+        ("tau_num_C", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("prec", ctypes.c_int),
+        ("rho_ref", ctypes.c_double), ("p_ref", ctypes.c_double),
+    ]
+
+
+class HgksDiag(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("dt", ctypes.c_double),
+        ("mass", ctypes.c_double), ("mom", ctypes.c_double * 3), ("energy", ctypes.c_double),
+        ("Ek", ctypes.c_double), ("rho_min", ctypes.c_double), ("p_min", ctypes.c_double),
+        ("step", ctypes.c_longlong),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HgksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libhgks.so (built by paper_2005_08736_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library {p} is missing; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(p)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        pd = ctypes.POINTER(ctypes.c_double)
+        pcfg = ctypes.POINTER(HgksConfig)
+        L.hgks_default_config.argtypes = [pcfg, i]
+        L.hgks_create.argtypes = [pcfg, vp, ctypes.POINTER(vp)]
+        L.hgks_destroy.argtypes = [vp]
+        L.hgks_init_state.argtypes = [vp, vp, i]
+        L.hgks_init_conservative.argtypes = [vp, vp, i]
+        L.hgks_get_state.argtypes = [vp, vp, i]
+        L.hgks_step.argtypes = [vp, i, d, i, pd]
+        L.hgks_diagnostics.argtypes = [vp, ctypes.POINTER(HgksDiag)]
+        L.hgks_profile_step.argtypes = [vp, d, pd, i]
+        L.hgks_last_error.argtypes = [vp]
+        L.hgks_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "hgks_last_error":
+                getattr(L, name).restype = i
+        _lib = L
+        return L
+
+
+def check(status: int, ctx=None) -> None:
+    if status != HGKS_OK:
+        msg = load().hgks_last_error(ctx)
+        raise HgksError(status, msg.decode() if msg else "")

@@ -1,0 +1,83 @@
+// Internal interface between the host runtime (hgks_api.cu) and the kernel
+// translation units (kernels_f32.cu, kernels_f64.cu).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/hgks.h"
+
+namespace hgks {
+
+struct GridDev;
+
+// Device buffers and derived launch data of one context.
+struct Engine {
+  hgks_config cfg;
+  cudaStream_t stream = nullptr;
+  int n[3];
+  int p[3];
+  long long P = 0;  // padded cells per variable
+  long long N = 0;  // interior cells
+  void* q = nullptr;     // padded state Q^n (deviation), 5 * P
+  void* qs = nullptr;    // padded state Q*, 5 * P
+  void* inc = nullptr;   // stage-1 increment, 5 * N
+  void* comp = nullptr;  // FP32 compensation, 5 * N (null for FP64)
+  void* ff = nullptr;    // face fields of one direction
+  void* fd[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction, 10 * faces
+  void* w[3] = {nullptr, nullptr, nullptr};   // cell widths incl. ghosts, n + 6
+  double* scal = nullptr;                      // [0] dt, [1] t, [2] step
+  unsigned long long* dtmin = nullptr;
+  int* flag = nullptr;
+  double* part = nullptr;      // diagnostic partials
+  double* diag_out = nullptr;  // 8 doubles
+  double* io = nullptr;        // FP64 staging buffer, 5 * N
+  int diag_blocks = 0;
+  int cfl_blocks = 0;
+};
+
+// Kernel classes timed by hgks_profile_step (order of its output array).
+enum KernelClass {
+  KC_CFL = 0,        // CFL reduction and dt
+  KC_GHOST = 1,      // ghost-cell fills
+  KC_FACE = 2,       // face fields, all directions and stages
+  KC_FLUX1 = 3,      // Gauss-point flux, stage 1 (F and dF)
+  KC_FLUX2 = 4,      // Gauss-point flux, stage 2
+  KC_UPDATE = 5,     // divergence + S2O4 update
+  KC_COUNT = 6
+};
+
+// Optional CUDA-event probe around kernel launches (profiling only; null in
+// the captured step).
+struct Probe {
+  static constexpr int kMax = 64;
+  cudaEvent_t start[kMax], stop[kMax];
+  int cls[kMax];
+  int n = 0;
+  void begin(cudaStream_t s, int c) {
+    if (n >= kMax) return;
+    cls[n] = c;
+    cudaEventRecord(start[n], s);
+  }
+  void end(cudaStream_t s) {
+    if (n >= kMax) return;
+    cudaEventRecord(stop[n], s);
+    ++n;
+  }
+};
+
+// Kernel sequences, implemented per floating type in kernels_f32.cu / kernels_f64.cu.
+template <class T> cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe = nullptr);
+template <class T> cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe = nullptr);
+template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
+template <class T> cudaError_t enqueue_diag(const Engine& e);
+template <class T> cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative);
+template <class T> cudaError_t enqueue_to_fp64(const Engine& e, double* dst);
+cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed);
+cudaError_t enqueue_advance_time(const Engine& e);
+
+// Sizes (in elements) of the per-direction face buffers.
+long long face_field_elems(const Engine& e, int d);
+long long face_flux_elems(const Engine& e, int d);
+int face_field_count(const Engine& e);
+
+}  // namespace hgks

@@ -1,0 +1,169 @@
+// Kernel sequences of one S2O4 stage and of the reductions, per floating
+// type.  Included once by kernels_f32.cu and once by kernels_f64.cu.
+#pragma once
+
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace hgks {
+
+inline GridDev grid_of(const Engine& e) {
+  GridDev g;
+  for (int c = 0; c < 3; ++c) {
+    g.n[c] = e.n[c];
+    g.p[c] = e.p[c];
+  }
+  g.P = e.P;
+  g.N = e.N;
+  return g;
+}
+
+template <class T>
+Gas<T> gas_of(const hgks_config& c) {
+  Gas<T> g;
+  g.gamma = T(c.gamma);
+  g.gm1 = T(c.gamma - 1.0);
+  g.K = T((5.0 - 3.0 * c.gamma) / (c.gamma - 1.0));
+  g.pr_fix = T(1.0 / c.prandtl - 1.0);
+  g.visc_law = c.visc;
+  g.mu_ref = T(c.mu_ref);
+  g.T_ref_inv = T(1.0 / c.T_ref);
+  g.visc_exp = T(c.visc_exp);
+  g.tau_num_C = c.flux == HGKS_FLUX_FULL ? T(c.tau_num_C) : T(0);
+  g.rho_r = T(c.rho_ref);
+  g.p_r = T(c.p_ref);
+  g.h_r = T(c.gamma / (c.gamma - 1.0) * c.p_ref);
+  return g;
+}
+
+inline unsigned blocks_for(long long n, int threads) {
+  return unsigned((n + threads - 1) / threads);
+}
+
+template <class T>
+cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe) {
+  T* q = static_cast<T*>(qbuf);
+  const GridDev g = grid_of(e);
+  const int th = 256;
+  if (probe) probe->begin(e.stream, KC_GHOST);
+  k_ghost_x<T><<<blocks_for(6LL * g.n[1] * g.n[2], th), th, 0, e.stream>>>(q, g);
+  k_ghost_y<T><<<blocks_for(6LL * g.p[0] * g.n[2], th), th, 0, e.stream>>>(
+      q, g, e.cfg.bc_y == HGKS_BC_WALL_ISOTHERMAL, gas_of<T>(e.cfg), T(e.cfg.T_wall));
+  k_ghost_z<T><<<blocks_for(6LL * g.p[0] * g.p[1], th), th, 0, e.stream>>>(q, g);
+  if (probe) probe->end(e.stream);
+  return cudaGetLastError();
+}
+
+template <class T, int MODE, int FLUX>
+void launch_direction(const Engine& e, const T* q, int d, int stage, Probe* probe) {
+  const GridDev g = grid_of(e);
+  FaceArgs<T> fa;
+  fa.q = q;
+  fa.ff = static_cast<T*>(e.ff);
+  fa.w = static_cast<const T*>(e.w[d]);
+  fa.g = g;
+  fa.box = face_box(g, d, 2);
+  fa.d = d;
+  fa.gas = gas_of<T>(e.cfg);
+  if (probe) probe->begin(e.stream, KC_FACE);
+  k_face_fields<T, MODE, FLUX><<<blocks_for(fa.box.size, 256), 256, 0, e.stream>>>(fa);
+  if (probe) probe->end(e.stream);
+  GaussArgs<T> ga;
+  ga.ff = fa.ff;
+  ga.fd = static_cast<T*>(e.fd[d]);
+  ga.w1 = static_cast<const T*>(e.w[(d + 1) % 3]);
+  ga.w2 = static_cast<const T*>(e.w[(d + 2) % 3]);
+  ga.scal = e.scal;
+  ga.g = g;
+  ga.box = fa.box;
+  ga.fbox = face_box(g, d, 0);
+  ga.d = d;
+  ga.want_F = stage == 1;
+  ga.gas = fa.gas;
+  if (probe) probe->begin(e.stream, stage == 1 ? KC_FLUX1 : KC_FLUX2);
+  k_gauss_flux<T, MODE, FLUX><<<blocks_for(4 * ga.fbox.size, 128), 128, 0, e.stream>>>(ga);
+  if (probe) probe->end(e.stream);
+}
+
+template <class T, int MODE, int FLUX>
+void launch_all_directions(const Engine& e, const T* q, int stage, Probe* probe) {
+  for (int d = 0; d < 3; ++d) launch_direction<T, MODE, FLUX>(e, q, d, stage, probe);
+}
+
+template <class T>
+cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
+  T* qin = static_cast<T*>(stage == 1 ? e.q : e.qs);
+  cudaError_t err = enqueue_ghosts<T>(e, qin, probe);
+  if (err != cudaSuccess) return err;
+  const int mode = e.cfg.recon, flux = e.cfg.flux;
+#define HGKS_DISPATCH(M, F) \
+  if (mode == M && flux == F) launch_all_directions<T, M, F>(e, qin, stage, probe);
+  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0)
+  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1)
+#undef HGKS_DISPATCH
+  UpdateArgs<T> ua;
+  ua.q = static_cast<T*>(e.q);
+  ua.qs = static_cast<T*>(e.qs);
+  ua.inc = static_cast<T*>(e.inc);
+  ua.comp = static_cast<T*>(e.comp);
+  ua.fx = static_cast<const T*>(e.fd[0]);
+  ua.fy = static_cast<const T*>(e.fd[1]);
+  ua.fz = static_cast<const T*>(e.fd[2]);
+  ua.wx = static_cast<const T*>(e.w[0]);
+  ua.wy = static_cast<const T*>(e.w[1]);
+  ua.wz = static_cast<const T*>(e.w[2]);
+  ua.scal = e.scal;
+  ua.g = grid_of(e);
+  ua.force_x = T(e.cfg.force_x);
+  ua.rho_r = T(e.cfg.rho_ref);
+  if (probe) probe->begin(e.stream, KC_UPDATE);
+  if (stage == 1)
+    k_update<T, 1><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua);
+  else
+    k_update<T, 2><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua);
+  if (probe) probe->end(e.stream);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t enqueue_cfl(const Engine& e, const void* qbuf) {
+  k_cfl<T><<<e.cfl_blocks, 256, 0, e.stream>>>(
+      static_cast<const T*>(qbuf), grid_of(e), static_cast<const T*>(e.w[0]),
+      static_cast<const T*>(e.w[1]), static_cast<const T*>(e.w[2]), e.cfg.rho_ref, e.cfg.p_ref,
+      e.cfg.gamma, e.dtmin, e.flag);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t enqueue_diag(const Engine& e) {
+  k_diag<T><<<e.diag_blocks, 256, 0, e.stream>>>(
+      static_cast<const T*>(e.q), grid_of(e), static_cast<const T*>(e.w[0]),
+      static_cast<const T*>(e.w[1]), static_cast<const T*>(e.w[2]), e.cfg.rho_ref, e.cfg.p_ref,
+      e.cfg.gamma, e.part);
+  k_diag_final<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, e.diag_out);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative) {
+  k_from_prim<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
+      src, static_cast<T*>(e.q), grid_of(e), e.cfg.rho_ref, e.cfg.p_ref, e.cfg.gamma, conservative);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t enqueue_to_fp64(const Engine& e, double* dst) {
+  k_to_cons<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
+      static_cast<const T*>(e.q), dst, grid_of(e), e.cfg.rho_ref, e.cfg.p_ref, e.cfg.gamma);
+  return cudaGetLastError();
+}
+
+#define HGKS_INSTANTIATE(T)                                                  \
+  template cudaError_t enqueue_ghosts<T>(const Engine&, void*, Probe*);      \
+  template cudaError_t enqueue_rhs_and_update<T>(const Engine&, int, Probe*); \
+  template cudaError_t enqueue_cfl<T>(const Engine&, const void*);           \
+  template cudaError_t enqueue_diag<T>(const Engine&);                       \
+  template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
+  template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);
+
+}  // namespace hgks

@@ -1,0 +1,419 @@
+// Host runtime behind include/hgks.h: validation, device buffers, the grid
+// metrics, and the captured CUDA graph of one S2O4 step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "kernels.cuh"
+
+struct hgks_ctx {
+  hgks::Engine e;
+  bool own_stream = false;
+  std::string err;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+hgks_status fail(hgks_ctx* c, hgks_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return s;
+}
+
+hgks_status cuda_fail(hgks_ctx* c, cudaError_t e, const char* where) {
+  const hgks_status s = (e == cudaErrorMemoryAllocation) ? HGKS_E_NOMEM : HGKS_E_CUDA;
+  return fail(c, s, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HGKS_CHECK(c, expr)                                        \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return cuda_fail((c), _e, #expr);       \
+  } while (0)
+
+size_t elem_size(const hgks_config& c) { return c.prec == HGKS_FP32 ? 4 : 8; }
+
+std::string validate(const hgks_config& c) {
+  if (c.nx < 6 || c.ny < 6 || c.nz < 6) return "every axis needs at least 6 cells";
+  if (!(c.gamma > 1.0)) return "gamma must exceed 1";
+  if (!(c.prandtl > 0.0)) return "Prandtl number must be positive";
+  if (!(c.cfl > 0.0)) return "cfl must be positive";
+  if (!(c.lx > 0.0) || !(c.ly > 0.0) || !(c.lz > 0.0)) return "box extents must be positive";
+  if (!(c.rho_ref > 0.0) || !(c.p_ref > 0.0)) return "reference density and pressure must be positive";
+  if (!(c.mu_ref >= 0.0)) return "mu_ref must be non-negative";
+  if (c.visc != HGKS_VISC_CONST && c.visc != HGKS_VISC_POWER) return "unknown viscosity law";
+  if (c.visc == HGKS_VISC_POWER && !(c.T_ref > 0.0)) return "T_ref must be positive";
+  if (c.recon < 0 || c.recon > 2) return "unknown reconstruction";
+  if (c.flux < 0 || c.flux > 1) return "unknown flux";
+  if (c.prec < 0 || c.prec > 1) return "unknown precision";
+  if (c.bc_y != HGKS_BC_PERIODIC && c.bc_y != HGKS_BC_WALL_ISOTHERMAL) return "unknown y boundary";
+  if (c.bc_y == HGKS_BC_WALL_ISOTHERMAL && !(c.T_wall > 0.0)) return "wall temperature must be positive";
+  if (c.y_stretch && c.bc_y != HGKS_BC_WALL_ISOTHERMAL) return "the tanh mapping needs wall boundaries";
+  if (c.y_stretch && !(c.stretch_b > 0.0)) return "stretch_b must be positive";
+  if (!(c.tau_num_C >= 0.0)) return "tau_num_C must be non-negative";
+  return "";
+}
+
+// Cell widths along each axis including 3 ghost cells per side: uniform, or
+// the y mapping of Sec. 3.3 with ghost widths mirrored across the walls.
+std::vector<double> widths(const hgks_config& c, int d) {
+  const int n = d == 0 ? c.nx : (d == 1 ? c.ny : c.nz);
+  const double L = d == 0 ? c.lx : (d == 1 ? c.ly : c.lz);
+  std::vector<double> w(n + 6, L / n);
+  if (d == 1 && c.y_stretch) {
+    const double pi = 3.14159265358979323846;
+    std::vector<double> yf(n + 1);
+    for (int j = 0; j <= n; ++j) {
+      const double eta = 3.0 * pi * j / n;
+      yf[j] = c.y0 + 0.5 * c.ly * (1.0 + std::tanh(c.stretch_b * (eta / (1.5 * pi) - 1.0)) /
+                                             std::tanh(c.stretch_b));
+    }
+    for (int j = 0; j < n; ++j) w[j + 3] = yf[j + 1] - yf[j];
+    for (int m = 0; m < 3; ++m) {
+      w[2 - m] = w[3 + m];
+      w[3 + n + m] = w[3 + n - 1 - m];
+    }
+  }
+  return w;
+}
+
+template <class T>
+cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) {
+  std::vector<T> tw(w.begin(), w.end());
+  return cudaMemcpyAsync(e.w[d], tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, e.stream);
+}
+
+void free_all(hgks::Engine& e) {
+  void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.ff, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
+                  e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+cudaError_t enqueue_stage_pair(hgks::Engine& e, double dt_fixed, hgks::Probe* probe = nullptr) {
+  cudaError_t err;
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  if (probe) probe->begin(e.stream, hgks::KC_CFL);
+  err = f32 ? hgks::enqueue_cfl<float>(e, e.q) : hgks::enqueue_cfl<double>(e, e.q);
+  if (err != cudaSuccess) return err;
+  err = hgks::enqueue_set_dt(e, dt_fixed);
+  if (probe) probe->end(e.stream);
+  if (err != cudaSuccess) return err;
+  for (int stage = 1; stage <= 2; ++stage) {
+    err = f32 ? hgks::enqueue_rhs_and_update<float>(e, stage, probe)
+              : hgks::enqueue_rhs_and_update<double>(e, stage, probe);
+    if (err != cudaSuccess) return err;
+  }
+  return hgks::enqueue_advance_time(e);
+}
+
+hgks_status capture_step(hgks_ctx* c, double dt_fixed) {
+  hgks::Engine& e = c->e;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  HGKS_CHECK(c, cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t err = enqueue_stage_pair(e, dt_fixed);
+  const cudaError_t end = cudaStreamEndCapture(e.stream, &g);
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, err, "capturing the step");
+  }
+  HGKS_CHECK(c, end);
+  const cudaError_t inst = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  HGKS_CHECK(c, inst);
+  c->graph_dt = dt_fixed;
+  return HGKS_OK;
+}
+
+}  // namespace
+
+namespace hgks {
+
+static __global__ void k_reset_scalars(double* scal, unsigned long long* dtmin, int* flag) {
+  if (threadIdx.x != 0) return;
+  scal[0] = 0.0;
+  scal[1] = 0.0;
+  scal[2] = 0.0;
+  *dtmin = (unsigned long long)__double_as_longlong(1e300);
+  *flag = 0;
+}
+
+cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed) {
+  k_set_dt<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.cfg.cfl, dt_fixed);
+  return cudaGetLastError();
+}
+cudaError_t enqueue_advance_time(const Engine& e) {
+  k_advance_time<<<1, 32, 0, e.stream>>>(e.scal);
+  return cudaGetLastError();
+}
+
+}  // namespace hgks
+
+extern "C" {
+
+hgks_status hgks_default_config(hgks_config* cfg, int n) {
+  if (!cfg) return HGKS_E_INVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  const double pi = 3.14159265358979323846;
+  cfg->nx = cfg->ny = cfg->nz = n;
+  cfg->lx = cfg->ly = cfg->lz = 2.0 * pi;
+  cfg->stretch_b = 2.0;
+  cfg->bc_y = HGKS_BC_PERIODIC;
+  cfg->gamma = 1.4;
+  cfg->prandtl = 0.72;
+  cfg->visc = HGKS_VISC_CONST;
+  cfg->mu_ref = 1.0 / 1600.0;
+  cfg->T_ref = 1.0;
+  cfg->visc_exp = 0.76;
+  cfg->T_wall = 1.0;
+  cfg->recon = HGKS_RECON_LINEAR;
+  cfg->flux = HGKS_FLUX_SMOOTH;
+  cfg->tau_num_C = 0.0;
+  cfg->cfl = 0.5;
+  cfg->prec = HGKS_FP32;
+  cfg->rho_ref = 1.0;
+  cfg->p_ref = 100.0 / 1.4;  // rho0 c0^2 / gamma with c0 = V0 / Ma = 10
+  return n >= 6 ? HGKS_OK : HGKS_E_INVAL;
+}
+
+hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, HGKS_E_INVAL, "null argument");
+  *out = nullptr;
+  const std::string why = validate(*cfg);
+  if (!why.empty()) return fail(nullptr, HGKS_E_INVAL, why);
+  hgks_ctx* c = new hgks_ctx();
+  hgks::Engine& e = c->e;
+  e.cfg = *cfg;
+  e.stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  if (!e.stream) {
+    // The legacy default stream cannot be captured into a graph: use a stream
+    // of the context's own.
+    const cudaError_t se = cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking);
+    if (se != cudaSuccess) {
+      delete c;
+      return cuda_fail(nullptr, se, "cudaStreamCreateWithFlags");
+    }
+    c->own_stream = true;
+  }
+  e.n[0] = cfg->nx;
+  e.n[1] = cfg->ny;
+  e.n[2] = cfg->nz;
+  for (int d = 0; d < 3; ++d) e.p[d] = e.n[d] + 6;
+  e.P = (long long)e.p[0] * e.p[1] * e.p[2];
+  e.N = (long long)e.n[0] * e.n[1] * e.n[2];
+  const size_t es = elem_size(*cfg);
+  long long ff_max = 0;
+  for (int d = 0; d < 3; ++d) {
+    const long long v = hgks::face_field_elems(e, d);
+    if (v > ff_max) ff_max = v;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (sms <= 0) sms = 152;
+  e.cfl_blocks = sms * 4;
+  e.diag_blocks = sms * 4;
+  auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes); };
+  cudaError_t err = cudaSuccess;
+  if (err == cudaSuccess) err = alloc(&e.q, 5 * e.P * es);
+  if (err == cudaSuccess) err = alloc(&e.qs, 5 * e.P * es);
+  if (err == cudaSuccess) err = alloc(&e.inc, 5 * e.N * es);
+  if (err == cudaSuccess && cfg->prec == HGKS_FP32) err = alloc(&e.comp, 5 * e.N * es);
+  if (err == cudaSuccess) err = alloc(&e.ff, ff_max * es);
+  for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.fd[d], hgks::face_flux_elems(e, d) * es);
+  for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.w[d], (e.n[d] + 6) * es);
+  if (err == cudaSuccess) err = alloc((void**)&e.scal, 4 * sizeof(double));
+  if (err == cudaSuccess) err = alloc((void**)&e.dtmin, sizeof(unsigned long long));
+  if (err == cudaSuccess) err = alloc((void**)&e.flag, sizeof(int));
+  if (err == cudaSuccess) err = alloc((void**)&e.part, 8 * sizeof(double) * e.diag_blocks);
+  if (err == cudaSuccess) err = alloc((void**)&e.diag_out, 8 * sizeof(double));
+  if (err == cudaSuccess) err = alloc((void**)&e.io, 5 * e.N * sizeof(double));
+  if (err != cudaSuccess) {
+    const hgks_status s = cuda_fail(nullptr, err, "hgks_create allocation");
+    free_all(e);
+    if (c->own_stream) cudaStreamDestroy(e.stream);
+    delete c;
+    return s;
+  }
+  // Zero the padded buffers once so that unused ghost corners stay finite.
+  err = cudaMemsetAsync(e.q, 0, 5 * e.P * es, e.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(e.qs, 0, 5 * e.P * es, e.stream);
+  if (err == cudaSuccess && e.comp) err = cudaMemsetAsync(e.comp, 0, 5 * e.N * es, e.stream);
+  for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
+    const std::vector<double> w = widths(*cfg, d);
+    err = cfg->prec == HGKS_FP32 ? upload_widths<float>(e, d, w) : upload_widths<double>(e, d, w);
+  }
+  if (err == cudaSuccess) {
+    hgks::k_reset_scalars<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.flag);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(e.stream);
+  if (err != cudaSuccess) {
+    const hgks_status s = cuda_fail(nullptr, err, "hgks_create initialisation");
+    free_all(e);
+    if (c->own_stream) cudaStreamDestroy(e.stream);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return HGKS_OK;
+}
+
+hgks_status hgks_destroy(hgks_ctx* c) {
+  if (!c) return HGKS_OK;
+  cudaStreamSynchronize(c->e.stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  free_all(c->e);
+  if (c->own_stream) cudaStreamDestroy(c->e.stream);
+  delete c;
+  return HGKS_OK;
+}
+
+static hgks_status init_common(hgks_ctx* c, const double* src, int is_host, int conservative) {
+  if (!c || !src) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  const double* dsrc = src;
+  if (is_host) {
+    HGKS_CHECK(c, cudaMemcpyAsync(e.io, src, 5 * e.N * sizeof(double), cudaMemcpyHostToDevice, e.stream));
+    dsrc = e.io;
+  }
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_from_fp64<float>(e, dsrc, conservative)
+                    : hgks::enqueue_from_fp64<double>(e, dsrc, conservative));
+  if (e.comp) HGKS_CHECK(c, cudaMemsetAsync(e.comp, 0, 5 * e.N * sizeof(float), e.stream));
+  hgks::k_reset_scalars<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.flag);
+  HGKS_CHECK(c, cudaGetLastError());
+  if (is_host) HGKS_CHECK(c, cudaStreamSynchronize(e.stream));  // the host buffer is borrowed
+  return HGKS_OK;
+}
+
+hgks_status hgks_init_state(hgks_ctx* c, const double* prim, int is_host) {
+  return init_common(c, prim, is_host, 0);
+}
+hgks_status hgks_init_conservative(hgks_ctx* c, const double* cons, int is_host) {
+  return init_common(c, cons, is_host, 1);
+}
+
+hgks_status hgks_get_state(hgks_ctx* c, double* out, int is_host) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  double* dst = is_host ? e.io : out;
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_to_fp64<float>(e, dst) : hgks::enqueue_to_fp64<double>(e, dst));
+  if (is_host) {
+    HGKS_CHECK(c, cudaMemcpyAsync(out, e.io, 5 * e.N * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+    HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  }
+  return HGKS_OK;
+}
+
+hgks_status hgks_step(hgks_ctx* c, int nsteps, double dt, int sync, double* t_out) {
+  if (!c) return fail(c, HGKS_E_INVAL, "null context");
+  if (nsteps < 0) return fail(c, HGKS_E_INVAL, "nsteps must be non-negative");
+  hgks::Engine& e = c->e;
+  const double dt_fixed = dt > 0.0 ? dt : 0.0;
+  if (nsteps > 0 && (!c->graph || c->graph_dt != dt_fixed)) {
+    const hgks_status s = capture_step(c, dt_fixed);
+    if (s != HGKS_OK) return s;
+  }
+  for (int n = 0; n < nsteps; ++n) HGKS_CHECK(c, cudaGraphLaunch(c->graph, e.stream));
+  if (!sync) return HGKS_OK;
+  // Check the state reached: the CFL kernel flags rho <= 0, p <= 0 and NaN.
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_cfl<float>(e, e.q) : hgks::enqueue_cfl<double>(e, e.q));
+  double scal[3];
+  int flag = 0;
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(&flag, e.flag, sizeof(int), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  if (t_out) *t_out = scal[1];
+  if (flag) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "non-physical state (rho <= 0, p <= 0 or NaN) by step %lld",
+                  (long long)scal[2]);
+    return fail(c, HGKS_E_NONPHYSICAL, buf);
+  }
+  return HGKS_OK;
+}
+
+hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_diag<float>(e) : hgks::enqueue_diag<double>(e));
+  double r[8], scal[3];
+  HGKS_CHECK(c, cudaMemcpyAsync(r, e.diag_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  const double vol = e.cfg.lx * e.cfg.ly * e.cfg.lz;
+  out->t = scal[1];
+  out->dt = scal[0];
+  out->step = (long long)scal[2];
+  out->mass = r[0];
+  out->mom[0] = r[1];
+  out->mom[1] = r[2];
+  out->mom[2] = r[3];
+  out->energy = r[4];
+  out->Ek = r[5] / (e.cfg.rho_ref * vol);
+  out->rho_min = r[6];
+  out->p_min = r[7];
+  return HGKS_OK;
+}
+
+hgks_status hgks_profile_step(hgks_ctx* c, double dt, double* ms_out, int nclass) {
+  if (!c || !ms_out || nclass < hgks::KC_COUNT) return fail(c, HGKS_E_INVAL, "bad argument");
+  hgks::Engine& e = c->e;
+  hgks::Probe probe;
+  for (int i = 0; i < hgks::Probe::kMax; ++i) {
+    HGKS_CHECK(c, cudaEventCreate(&probe.start[i]));
+    HGKS_CHECK(c, cudaEventCreate(&probe.stop[i]));
+  }
+  const cudaError_t err = enqueue_stage_pair(e, dt > 0.0 ? dt : 0.0, &probe);
+  cudaError_t sync = cudaStreamSynchronize(e.stream);
+  for (int k = 0; k < nclass; ++k) ms_out[k] = 0.0;
+  for (int i = 0; i < probe.n && sync == cudaSuccess; ++i) {
+    float ms = 0.f;
+    sync = cudaEventElapsedTime(&ms, probe.start[i], probe.stop[i]);
+    ms_out[probe.cls[i]] += ms;
+  }
+  for (int i = 0; i < hgks::Probe::kMax; ++i) {
+    cudaEventDestroy(probe.start[i]);
+    cudaEventDestroy(probe.stop[i]);
+  }
+  HGKS_CHECK(c, err);
+  HGKS_CHECK(c, sync);
+  return HGKS_OK;
+}
+
+const char* hgks_last_error(const hgks_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
+
+namespace hgks {
+
+long long face_field_elems(const Engine& e, int d) {
+  long long s = 1;
+  for (int c = 0; c < 3; ++c) s *= (c == d) ? e.n[c] + 1 : e.n[c] + 4;
+  return s * 5 * face_field_count(e);
+}
+long long face_flux_elems(const Engine& e, int d) {
+  long long s = 1;
+  for (int c = 0; c < 3; ++c) s *= (c == d) ? e.n[c] + 1 : e.n[c];
+  return s * 10;
+}
+int face_field_count(const Engine& e) { return e.cfg.flux == HGKS_FLUX_FULL ? 6 : 2; }
+
+}  // namespace hgks

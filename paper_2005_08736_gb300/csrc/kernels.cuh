@@ -1,0 +1,621 @@
+// Kernels of one S2O4 step of the high-order gas-kinetic scheme (Cao, Pan &
+// Xu, arXiv:2005.08736), templated on the storage/arithmetic type T.
+//
+// State layout in HBM: structure of arrays, 5 planes (rho, rho U, rho V,
+// rho W, rho E) of (nx+6)(ny+6)(nz+6) cells, x fastest, 3 ghost layers on
+// every side, holding deviations from the reference state at rest.
+//
+// Per stage and sweep direction d (tangential directions t1 = d+1, t2 = d+2
+// mod 3):
+//   k_face_fields  one thread per face and tangential row (2 ghost rows on
+//                  each side): WENO5 end values, normal slopes, the
+//                  compatibility state Q0 and its normal slope, in the local
+//                  frame (normal momentum first);
+//   k_gauss_flux   one thread per Gauss point (4 per face): tangential
+//                  reconstruction to the point, the BGK flux there, and a
+//                  4-lane shuffle sum with weights 1/4 into the face flux;
+// then k_update forms L = -(1/|Omega|) sum F (Eq. (4)) and the S2O4 stage
+// (Eq. (6)).
+#pragma once
+
+#include <cstdint>
+
+#include "recon.cuh"
+
+namespace hgks {
+
+constexpr int kGhost = 3;
+
+struct GridDev {
+  int n[3];       // interior cells
+  int p[3];       // padded extents n + 6
+  long long P;    // padded cells per variable
+  long long N;    // interior cells
+};
+
+__host__ __device__ __forceinline__ long long pad_index(const GridDev& g, int x, int y, int z) {
+  return ((long long)(z + kGhost) * g.p[1] + (y + kGhost)) * g.p[0] + (x + kGhost);
+}
+
+// Extents and offsets of the face-field box of direction d: faces 0..n_d
+// along d, tangential rows -2..n+1 along the two other axes.
+struct FaceBox {
+  int r[3], o[3];
+  long long size;
+};
+__host__ __device__ __forceinline__ FaceBox face_box(const GridDev& g, int d, int tang_halo) {
+  FaceBox b;
+  for (int c = 0; c < 3; ++c) {
+    if (c == d) {
+      b.r[c] = g.n[c] + 1;
+      b.o[c] = 0;
+    } else {
+      b.r[c] = g.n[c] + 2 * tang_halo;
+      b.o[c] = -tang_halo;
+    }
+  }
+  b.size = (long long)b.r[0] * b.r[1] * b.r[2];
+  return b;
+}
+
+// ------------------------------------------------------------- ghost cells ---
+
+// x ghosts (periodic) for interior y, z.
+template <class T>
+__global__ void k_ghost_x(T* __restrict__ q, GridDev g) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = 6LL * g.n[1] * g.n[2];
+  if (tid >= total) return;
+  const int m = int(tid % 6);
+  const long long r = tid / 6;
+  const int y = int(r % g.n[1]), z = int(r / g.n[1]);
+  const int x = m < 3 ? -1 - m : g.n[0] + (m - 3);
+  const int src = m < 3 ? g.n[0] - 1 - m : m - 3;
+  const long long dst = pad_index(g, x, y, z), s = pad_index(g, src, y, z);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
+}
+
+// y ghosts for all x (ghosts included) and interior z: periodic, or the
+// isothermal no-slip wall (Sec. 3.3): the ghost mirrors interior cell m with
+// velocity negated, equal pressure and T_g = 2 T_w - T_m (floored at T_w/2).
+template <class T>
+__global__ void k_ghost_y(T* __restrict__ q, GridDev g, int wall, Gas<T> gas, T T_wall) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = 6LL * g.p[0] * g.n[2];
+  if (tid >= total) return;
+  const int x = int(tid % g.p[0]) - kGhost;
+  const long long r = tid / g.p[0];
+  const int m = int(r % 6), z = int(r / 6);
+  const int y = m < 3 ? -1 - m : g.n[1] + (m - 3);
+  const long long dst = pad_index(g, x, y, z);
+  if (!wall) {
+    const int src = m < 3 ? g.n[1] - 1 - m : m - 3;
+    const long long s = pad_index(g, x, src, z);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
+    return;
+  }
+  const int src = m < 3 ? m : g.n[1] - 1 - (m - 3);
+  const long long s = pad_index(g, x, src, z);
+  T dq[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dq[v] = q[v * g.P + s];
+  const Prim<T> st = prim_of(dq, gas);
+  T Tg = T(2) * T_wall - st.theta;
+  if (Tg < T(0.5) * T_wall) Tg = T(0.5) * T_wall;
+  const T rg = st.p / Tg;
+  const T ke = T(0.5) * rg * (st.U * st.U + st.V * st.V + st.W * st.W);
+  q[0 * g.P + dst] = rg - gas.rho_r;
+  q[1 * g.P + dst] = -rg * st.U;
+  q[2 * g.P + dst] = -rg * st.V;
+  q[3 * g.P + dst] = -rg * st.W;
+  q[4 * g.P + dst] = st.dp / gas.gm1 + ke;
+}
+
+// z ghosts (periodic) for all x, y including ghosts.
+template <class T>
+__global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long plane = (long long)g.p[0] * g.p[1];
+  const long long total = 6LL * plane;
+  if (tid >= total) return;
+  const long long xy = tid % plane;
+  const int m = int(tid / plane);
+  const int z = m < 3 ? -1 - m : g.n[2] + (m - 3);
+  const int src = m < 3 ? g.n[2] - 1 - m : m - 3;
+  const long long dst = (long long)(z + kGhost) * plane + xy;
+  const long long s = (long long)(src + kGhost) * plane + xy;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
+}
+
+// ------------------------------------------------------------- face fields ---
+
+// Local-frame component of variable i for sweep direction d.
+__host__ __device__ __forceinline__ int global_var(int d, int i) {
+  if (i == 0 || i == 4) return i;
+  return 1 + (d + i - 1) % 3;
+}
+
+template <class T>
+struct FaceArgs {
+  const T* __restrict__ q;   // padded state
+  T* __restrict__ ff;        // face fields [NF*5][box]
+  const T* __restrict__ w;   // widths along d, offset kGhost
+  GridDev g;
+  FaceBox box;
+  int d;
+  Gas<T> gas;
+};
+
+// Fields: smooth flux -> 0: Q0, 1: dQ0/dn; full flux -> 0: Q_l, 1: Q_r,
+// 2: dQ_l/dn, 3: dQ_r/dn, 4: Q0, 5: dQ0/dn.
+template <class T, int MODE, int FLUX>
+__global__ void __launch_bounds__(256) k_face_fields(FaceArgs<T> a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= a.box.size) return;
+  int c[3];
+  c[0] = int(tid % a.box.r[0]) + a.box.o[0];
+  const long long r1 = tid / a.box.r[0];
+  c[1] = int(r1 % a.box.r[1]) + a.box.o[1];
+  c[2] = int(r1 / a.box.r[1]) + a.box.o[2];
+  const int d = a.d;
+  const int f = c[d];
+  long long sd = 1;
+  if (d >= 1) sd *= a.g.p[0];
+  if (d >= 2) sd *= a.g.p[1];
+  c[d] = f - 3;
+  const long long base = pad_index(a.g, c[0], c[1], c[2]);
+  const T hl = a.w[f - 1 + kGhost], hr = a.w[f + kGhost];
+  T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T* qv = a.q + global_var(d, i) * a.g.P + base;
+    const T q0 = qv[0], q1 = qv[sd], q2 = qv[2 * sd], q3 = qv[3 * sd], q4 = qv[4 * sd],
+            q5 = qv[5 * sd];
+    T Li, Ri, Lr, Rr;
+    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);  // cell f-1
+    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);  // cell f
+    Ql[i] = Ri;
+    Qr[i] = Lr;
+    // Normal slopes of the quadratic through both end values and the average.
+    Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) / hl;
+    Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) / hr;
+    // Equilibrium slope: derivative at the face of the cubic matching four averages.
+    D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) / (T(6) * (hl + hr));
+  }
+  T Q0[5];
+  compat_dev(Ql, Qr, a.gas, Q0);
+  const long long S = a.box.size;
+  T* out = a.ff + tid;
+  if (FLUX == FLUX_SMOOTH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      out[(0 * 5 + i) * S] = Q0[i];
+      out[(1 * 5 + i) * S] = D0[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      out[(0 * 5 + i) * S] = Ql[i];
+      out[(1 * 5 + i) * S] = Qr[i];
+      out[(2 * 5 + i) * S] = Dl[i];
+      out[(3 * 5 + i) * S] = Dr[i];
+      out[(4 * 5 + i) * S] = Q0[i];
+      out[(5 * 5 + i) * S] = D0[i];
+    }
+  }
+}
+
+// ------------------------------------------------------- Gauss-point flux ---
+
+template <class T>
+struct GaussArgs {
+  const T* __restrict__ ff;
+  T* __restrict__ fd;          // face fluxes [10][fbox]: F then dF, global frame
+  const T* __restrict__ w1;    // widths along t1 (offset kGhost)
+  const T* __restrict__ w2;    // widths along t2
+  const double* __restrict__ scal;  // device scalars: [0] = dt
+  GridDev g;
+  FaceBox box;   // face-field box (tangential halo 2)
+  FaceBox fbox;  // face-flux box (no tangential halo)
+  int d;
+  int want_F;    // 0 in the second S2O4 stage: only dF is used
+  Gas<T> gas;
+};
+
+// Value, d/dt1 and d/dt2 (or the value only) of one face-field component at
+// Gauss point (m1, m2), from the 5x5 face averages around the face.
+template <int MODE, bool DERIV, class T>
+__device__ __forceinline__ void gauss_recon(const T* __restrict__ f, long long s1, long long s2,
+                                            int m1, int m2, T& val, T& d1, T& d2) {
+  T rv[5], rd[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const T* row = f + (r - 2) * s2;
+    T v[2], dd[2];
+    tangential<MODE>(row[-2 * s1], row[-s1], row[0], row[s1], row[2 * s1], v, dd);
+    rv[r] = m1 ? v[1] : v[0];
+    rd[r] = m1 ? dd[1] : dd[0];
+  }
+  T v[2], dd[2];
+  tangential<MODE>(rv[0], rv[1], rv[2], rv[3], rv[4], v, dd);
+  val = m2 ? v[1] : v[0];
+  if (DERIV) {
+    d2 = m2 ? dd[1] : dd[0];
+    tangential<MODE>(rd[0], rd[1], rd[2], rd[3], rd[4], v, dd);
+    d1 = m2 ? v[1] : v[0];
+  }
+}
+
+template <int MODE, class T>
+__device__ __forceinline__ void gauss_state(const T* __restrict__ ff, long long S, long long at,
+                                            long long s1, long long s2, int fv, int fs, int m1,
+                                            int m2, T h1, T h2, PointState<T>& st) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    T v, d1, d2, dn, u1, u2;
+    gauss_recon<MODE, true>(ff + (fv * 5 + i) * S + at, s1, s2, m1, m2, v, d1, d2);
+    gauss_recon<MODE, false>(ff + (fs * 5 + i) * S + at, s1, s2, m1, m2, dn, u1, u2);
+    st.q[i] = v;
+    st.dq[0][i] = dn;
+    st.dq[1][i] = d1 / h1;
+    st.dq[2][i] = d2 / h2;
+  }
+}
+
+template <class T, int MODE, int FLUX>
+__global__ void __launch_bounds__(128) k_gauss_flux(GaussArgs<T> a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long face = tid >> 2;
+  const int gp = int(tid & 3);
+  const bool active = face < a.fbox.size;
+  const long long fc = active ? face : 0;
+  int c[3];
+  c[0] = int(fc % a.fbox.r[0]);
+  const long long r1 = fc / a.fbox.r[0];
+  c[1] = int(r1 % a.fbox.r[1]);
+  c[2] = int(r1 / a.fbox.r[1]);
+  const int d = a.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  // Position in the face-field box and strides of the tangential axes there.
+  const long long at = (long long)(c[0] - a.box.o[0]) +
+                       (long long)a.box.r[0] * ((c[1] - a.box.o[1]) + (long long)a.box.r[1] * (c[2] - a.box.o[2]));
+  long long st[3] = {1, a.box.r[0], (long long)a.box.r[0] * a.box.r[1]};
+  const long long s1 = st[t1], s2 = st[t2];
+  const T h1 = a.w1[c[t1] + kGhost], h2 = a.w2[c[t2] + kGhost];
+  const int m1 = gp & 1, m2 = gp >> 1;
+  const T dt = T(a.scal[0]);
+  const long long S = a.box.size;
+  T F[5], dF[5];
+  if (FLUX == FLUX_SMOOTH) {
+    PointState<T> s0;
+    gauss_state<MODE>(a.ff, S, at, s1, s2, 0, 1, m1, m2, h1, h2, s0);
+    flux_smooth(s0, a.gas, a.want_F != 0, F, dF);
+    if (!a.want_F) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) F[i] = T(0);
+    }
+  } else {
+    PointState<T> sl, sr, s0;
+    gauss_state<MODE>(a.ff, S, at, s1, s2, 0, 2, m1, m2, h1, h2, sl);
+    gauss_state<MODE>(a.ff, S, at, s1, s2, 1, 3, m1, m2, h1, h2, sr);
+    gauss_state<MODE>(a.ff, S, at, s1, s2, 4, 5, m1, m2, h1, h2, s0);
+    flux_full(sl, sr, s0, a.gas, dt, F, dF);
+  }
+  // Sum over the four Gauss points of the face (consecutive lanes), weight 1/4.
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    F[i] += __shfl_xor_sync(0xffffffffu, F[i], 1);
+    F[i] += __shfl_xor_sync(0xffffffffu, F[i], 2);
+    dF[i] += __shfl_xor_sync(0xffffffffu, dF[i], 1);
+    dF[i] += __shfl_xor_sync(0xffffffffu, dF[i], 2);
+  }
+  if (!active || gp != 0) return;
+  const long long FS = a.fbox.size;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int v = global_var(d, i);
+    a.fd[v * FS + face] = T(0.25) * F[i];
+    a.fd[(5 + v) * FS + face] = T(0.25) * dF[i];
+  }
+}
+
+// ------------------------------------------------------------------ update ---
+
+template <class T>
+struct UpdateArgs {
+  T* __restrict__ q;          // Q^n (padded); overwritten with Q^{n+1} in stage 2
+  T* __restrict__ qs;         // Q* (padded), written in stage 1
+  T* __restrict__ inc;        // dt L(Q^n) + dt^2/6 dL(Q^n), interior
+  T* __restrict__ comp;       // compensation of the FP32 accumulation (or null)
+  const T* __restrict__ fx;
+  const T* __restrict__ fy;
+  const T* __restrict__ fz;
+  const T* __restrict__ wx;
+  const T* __restrict__ wy;
+  const T* __restrict__ wz;
+  const double* __restrict__ scal;
+  GridDev g;
+  T force_x;
+  T rho_r;
+};
+
+// Stage 1: L, dL of Q^n; Q* = Q^n + dt/2 L + dt^2/8 dL; inc = dt L + dt^2/6 dL.
+// Stage 2: dL of Q*; Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), then the body force.
+template <class T, int STAGE>
+__global__ void __launch_bounds__(256) k_update(UpdateArgs<T> a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= a.g.N) return;
+  const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
+  const int x = int(tid % nx);
+  const long long r = tid / nx;
+  const int y = int(r % ny), z = int(r / ny);
+  const long long SX = (long long)(nx + 1) * ny * nz, SY = (long long)nx * (ny + 1) * nz,
+                  SZ = (long long)nx * ny * (nz + 1);
+  const long long ix = ((long long)z * ny + y) * (nx + 1) + x;
+  const long long iy = ((long long)z * (ny + 1) + y) * nx + x;
+  const long long iz = ((long long)z * ny + y) * nx + x;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const T ix_w = T(1) / a.wx[x + kGhost], iy_w = T(1) / a.wy[y + kGhost], iz_w = T(1) / a.wz[z + kGhost];
+  const T dt = T(a.scal[0]);
+  const long long pi = pad_index(a.g, x, y, z);
+  T dL[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const int o = 5 + v;
+    dL[v] = -((a.fx[o * SX + ix + 1] - a.fx[o * SX + ix]) * ix_w +
+              (a.fy[o * SY + iy + sy] - a.fy[o * SY + iy]) * iy_w +
+              (a.fz[o * SZ + iz + sz] - a.fz[o * SZ + iz]) * iz_w);
+  }
+  if (STAGE == 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const T L = -((a.fx[v * SX + ix + 1] - a.fx[v * SX + ix]) * ix_w +
+                    (a.fy[v * SY + iy + sy] - a.fy[v * SY + iy]) * iy_w +
+                    (a.fz[v * SZ + iz + sz] - a.fz[v * SZ + iz]) * iz_w);
+      const T qn = a.q[v * a.g.P + pi];
+      a.qs[v * a.g.P + pi] = qn + T(0.5) * dt * L + T(0.125) * dt * dt * dL[v];
+      a.inc[v * a.g.N + tid] = dt * L + dt * dt / T(6) * dL[v];
+    }
+  } else {
+    T qn[5], dq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qn[v] = a.q[v * a.g.P + pi];
+      dq[v] = a.inc[v * a.g.N + tid] + dt * dt / T(3) * dL[v];
+    }
+    if (a.force_x != T(0)) {
+      // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
+      // (rho E) += dt/2 ((rho U)^{n+1} + (rho U)^n) f_x; the reference is at rest.
+      const T rho_n = a.rho_r + qn[0];
+      dq[1] += T(0.5) * dt * (T(2) * rho_n + dq[0]) * a.force_x;
+      dq[4] += T(0.5) * dt * (T(2) * qn[1] + dq[1]) * a.force_x;
+    }
+    if (a.comp) {
+      // Compensated (Kahan) accumulation of Q^{n+1} = Q^n + dq.
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const T y = dq[v] - a.comp[v * a.g.N + tid];
+        const T t = qn[v] + y;
+        a.comp[v * a.g.N + tid] = (t - qn[v]) - y;
+        a.q[v * a.g.P + pi] = t;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.q[v * a.g.P + pi] = qn[v] + dq[v];
+    }
+  }
+}
+
+// -------------------------------------------------------------- reductions ---
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CFL time-step bound min over cells and directions of width/(|u_d| + c)
+// (FP64), with a flag for non-physical states (rho <= 0, p <= 0, NaN).
+// Positive doubles order like their bit patterns, so the block minima are
+// combined with a 64-bit atomicMin on the bits.
+template <class T>
+__global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
+                                             const T* __restrict__ wx, const T* __restrict__ wy,
+                                             const T* __restrict__ wz, double rho_r, double p_r,
+                                             double gamma, unsigned long long* __restrict__ dtmin,
+                                             int* __restrict__ flag) {
+  double best = 1e300;
+  int bad = 0;
+  const int nx = g.n[0], ny = g.n[1];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = int(c % nx);
+    const long long r = c / nx;
+    const int y = int(r % ny), z = int(r / ny);
+    const long long pi = pad_index(g, x, y, z);
+    const double rho = rho_r + double(q[pi]);
+    const double mx = q[g.P + pi], my = q[2 * g.P + pi], mz = q[3 * g.P + pi];
+    const double dE = q[4 * g.P + pi];
+    const double ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
+    const double p = p_r + (gamma - 1.0) * (dE - ke);
+    if (!(rho > 0.0) || !(p > 0.0)) {
+      bad = 1;
+      continue;
+    }
+    const double cs = sqrt(gamma * p / rho);
+    best = fmin(best, double(wx[x + kGhost]) / (fabs(mx / rho) + cs));
+    best = fmin(best, double(wy[y + kGhost]) / (fabs(my / rho) + cs));
+    best = fmin(best, double(wz[z + kGhost]) / (fabs(mz / rho) + cs));
+  }
+  best = warp_min(best);
+  __shared__ double sm[32];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  if (bad) atomicOr(&sbad, 1);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 1e300;
+    v = warp_min(v);
+    if (threadIdx.x == 0) {
+      atomicMin(dtmin, (unsigned long long)__double_as_longlong(v));
+      if (sbad) atomicOr(flag, 1);
+    }
+  }
+}
+
+// Scalars: [0] dt, [1] t, [2] steps taken.  dt_fixed > 0 overrides the CFL step.
+static __global__ void k_set_dt(double* scal, unsigned long long* dtmin, double cfl, double dt_fixed) {
+  if (threadIdx.x != 0) return;
+  scal[0] = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)*dtmin);
+  *dtmin = (unsigned long long)__double_as_longlong(1e300);
+}
+static __global__ void k_advance_time(double* scal) {
+  if (threadIdx.x != 0) return;
+  scal[1] += scal[0];
+  scal[2] += 1.0;
+}
+
+// FP64 partial sums per block: mass, momentum (3), energy, kinetic energy,
+// and minima of rho and p; cell volume weights from the widths.
+template <class T>
+__global__ void __launch_bounds__(256) k_diag(const T* __restrict__ q, GridDev g,
+                                              const T* __restrict__ wx, const T* __restrict__ wy,
+                                              const T* __restrict__ wz, double rho_r, double p_r,
+                                              double gamma, double* __restrict__ part) {
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  double rmin = 1e300, pmin = 1e300;
+  const int nx = g.n[0], ny = g.n[1];
+  const double E_r = p_r / (gamma - 1.0);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = int(c % nx);
+    const long long r = c / nx;
+    const int y = int(r % ny), z = int(r / ny);
+    const long long pi = pad_index(g, x, y, z);
+    const double vol = double(wx[x + kGhost]) * double(wy[y + kGhost]) * double(wz[z + kGhost]);
+    const double rho = rho_r + double(q[pi]);
+    const double mx = q[g.P + pi], my = q[2 * g.P + pi], mz = q[3 * g.P + pi];
+    const double E = E_r + double(q[4 * g.P + pi]);
+    const double ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
+    s[0] += rho * vol;
+    s[1] += mx * vol;
+    s[2] += my * vol;
+    s[3] += mz * vol;
+    s[4] += E * vol;
+    s[5] += ke * vol;
+    rmin = fmin(rmin, rho);
+    pmin = fmin(pmin, (gamma - 1.0) * (E - ke));
+  }
+  __shared__ double sm[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double v = warp_sum(s[k]);
+    if (lane == 0) sm[k][wid] = v;
+  }
+  rmin = warp_min(rmin);
+  pmin = warp_min(pmin);
+  if (lane == 0) {
+    sm[6][wid] = rmin;
+    sm[7][wid] = pmin;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double v = lane < nw ? sm[k][lane] : (k < 6 ? 0.0 : 1e300);
+      v = k < 6 ? warp_sum(v) : warp_min(v);
+      if (lane == 0) part[blockIdx.x * 8 + k] = v;
+    }
+  }
+}
+
+// Deterministic final reduction of the per-block partials (one block).
+static __global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  __shared__ double sm[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double s[8] = {0, 0, 0, 0, 0, 0, 1e300, 1e300};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[k] += part[b * 8 + k];
+    s[6] = fmin(s[6], part[b * 8 + 6]);
+    s[7] = fmin(s[7], part[b * 8 + 7]);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double v = k < 6 ? warp_sum(s[k]) : warp_min(s[k]);
+    if (lane == 0) sm[k][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double v = lane < nw ? sm[k][lane] : (k < 6 ? 0.0 : 1e300);
+      v = k < 6 ? warp_sum(v) : warp_min(v);
+      if (lane == 0) out[k] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------- state in/out ---
+
+// FP64 primitive (rho, u, v, w, p) [5][N] -> deviation conservative (padded interior).
+template <class T>
+__global__ void k_from_prim(const double* __restrict__ prim, T* __restrict__ q, GridDev g,
+                            double rho_r, double p_r, double gamma, int conservative) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const int nx = g.n[0], ny = g.n[1];
+  const int x = int(c % nx);
+  const long long r = c / nx;
+  const int y = int(r % ny), z = int(r / ny);
+  const long long pi = pad_index(g, x, y, z);
+  double Q[5];
+  if (conservative) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Q[v] = prim[v * g.N + c];
+  } else {
+    const double rho = prim[c], u = prim[g.N + c], v = prim[2 * g.N + c], w = prim[3 * g.N + c],
+                 p = prim[4 * g.N + c];
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = rho * w;
+    Q[4] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+  }
+  q[pi] = T(Q[0] - rho_r);
+  q[g.P + pi] = T(Q[1]);
+  q[2 * g.P + pi] = T(Q[2]);
+  q[3 * g.P + pi] = T(Q[3]);
+  q[4 * g.P + pi] = T(Q[4] - p_r / (gamma - 1.0));
+}
+
+template <class T>
+__global__ void k_to_cons(const T* __restrict__ q, double* __restrict__ out, GridDev g,
+                          double rho_r, double p_r, double gamma) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const int nx = g.n[0], ny = g.n[1];
+  const int x = int(c % nx);
+  const long long r = c / nx;
+  const int y = int(r % ny), z = int(r / ny);
+  const long long pi = pad_index(g, x, y, z);
+  out[c] = rho_r + double(q[pi]);
+  out[g.N + c] = double(q[g.P + pi]);
+  out[2 * g.N + c] = double(q[2 * g.P + pi]);
+  out[3 * g.N + c] = double(q[3 * g.P + pi]);
+  out[4 * g.N + c] = p_r / (gamma - 1.0) + double(q[4 * g.P + pi]);
+}
+
+}  // namespace hgks

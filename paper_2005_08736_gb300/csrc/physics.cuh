@@ -1,0 +1,406 @@
+// Device arithmetic of the high-order gas-kinetic scheme (HGKS) of Cao, Pan &
+// Xu (arXiv:2005.08736), templated on the floating type T (float or double).
+//
+// All conservative states handled here are DEVIATIONS from a reference state
+// at rest, dQ = Q - Q_ref with Q_ref = (rho_r, 0, 0, 0, p_r/(gamma-1)).  Every
+// quantity whose magnitude is set by the reference pressure (pressure,
+// enthalpy flux, the Euler momentum flux) is formed from deviations, so that
+// FP32 keeps the low-Mach variations instead of rounding them against p_r.
+//
+// Units: R = 1, p = rho T, lambda = rho / (2 p), theta = 1 / (2 lambda) = T.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace hgks {
+
+// Problem constants passed by value to every kernel.
+template <class T>
+struct Gas {
+  T gamma, gm1;     // gamma, gamma - 1
+  T K;              // internal degrees of freedom N = (5 - 3 gamma)/(gamma - 1), Sec. 2.1
+  T pr_fix;         // 1/Pr - 1 (Prandtl fix of the energy flux)
+  int visc_law;     // 0 constant, 1 power law
+  T mu_ref, T_ref_inv, visc_exp;
+  T tau_num_C;      // C of the numerical collision time, Sec. 3 opening
+  T rho_r, p_r;     // reference state at rest
+  T h_r;            // rho_r E_r + p_r = gamma/(gamma-1) p_r
+};
+
+template <class T> __device__ __forceinline__ T tsqrt(T x);
+template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <class T> __device__ __forceinline__ T texp(T x);
+template <> __device__ __forceinline__ float texp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
+template <class T> __device__ __forceinline__ T texpm1(T x);
+template <> __device__ __forceinline__ float texpm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double texpm1<double>(double x) { return expm1(x); }
+template <class T> __device__ __forceinline__ T terf(T x);
+template <> __device__ __forceinline__ float terf<float>(float x) { return erff(x); }
+template <> __device__ __forceinline__ double terf<double>(double x) { return erf(x); }
+template <class T> __device__ __forceinline__ T tpow(T x, T y);
+template <> __device__ __forceinline__ float tpow<float>(float x, float y) { return powf(x, y); }
+template <> __device__ __forceinline__ double tpow<double>(double x, double y) { return pow(x, y); }
+template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+template <class T>
+struct Prim {
+  T rho, U, V, W;  // density, local-frame velocity
+  T dp, p;         // pressure deviation and pressure
+  T lam, theta;    // lambda = rho/(2p), theta = 1/(2 lambda)
+};
+
+// Primitive variables of the state Q_ref + dq (local frame).
+template <class T>
+__device__ __forceinline__ Prim<T> prim_of(const T dq[5], const Gas<T>& g) {
+  Prim<T> s;
+  s.rho = g.rho_r + dq[0];
+  const T inv = T(1) / s.rho;
+  s.U = dq[1] * inv;
+  s.V = dq[2] * inv;
+  s.W = dq[3] * inv;
+  // p - p_r = (gamma-1) (dE - |m|^2 / (2 rho)); the reference is at rest.
+  s.dp = g.gm1 * (dq[4] - T(0.5) * (dq[1] * s.U + dq[2] * s.V + dq[3] * s.W));
+  s.p = g.p_r + s.dp;
+  s.theta = s.p * inv;
+  s.lam = T(0.5) / s.theta;
+  return s;
+}
+
+// Normalised moments <.> = (1/rho) int g (.) dXi of a Maxwellian.  u may be
+// taken over the whole line or over a half line; v, w over the whole line.
+template <class T>
+struct Mom {
+  T u[7], v[7], w[7];
+  T xi1, xi2;  // <xi^2> = K theta, <xi^4> = K (K+2) theta^2
+};
+
+template <class T>
+__device__ __forceinline__ void gauss_recursion(T* m, T U, T theta) {
+  // <c^(n+2)> = U <c^(n+1)> + (n+1) theta <c^n>, on the line and on half lines.
+#pragma unroll
+  for (int n = 0; n < 5; ++n) m[n + 2] = U * m[n + 1] + T(n + 1) * theta * m[n];
+}
+
+// half: 0 whole line, +1 u > 0, -1 u < 0.
+template <class T>
+__device__ __forceinline__ void moments(const Prim<T>& s, const Gas<T>& g, int half, Mom<T>& m) {
+  if (half == 0) {
+    m.u[0] = T(1);
+    m.u[1] = s.U;
+  } else {
+    // <u^0>_{u>0} = erfc(-sqrt(lam) U)/2, <u^1>_{u>0} = U <u^0> + exp(-lam U^2)/(2 sqrt(pi lam)).
+    const T x = tsqrt(s.lam) * s.U;
+    const T e = texp(-x * x) * T(0.28209479177387814) / tsqrt(s.lam);  // 1/(2 sqrt(pi))
+    const T sg = T(half);
+    m.u[0] = T(0.5) * (T(1) + sg * terf(x));
+    m.u[1] = s.U * m.u[0] + sg * e;
+  }
+  gauss_recursion(m.u, s.U, s.theta);
+  m.v[0] = T(1);
+  m.v[1] = s.V;
+  gauss_recursion(m.v, s.V, s.theta);
+  m.w[0] = T(1);
+  m.w[1] = s.W;
+  gauss_recursion(m.w, s.W, s.theta);
+  m.xi1 = g.K * s.theta;
+  m.xi2 = g.K * (g.K + T(2)) * s.theta * s.theta;
+}
+
+// <u^a v^b w^c>
+template <int A, int B, int C, class T>
+__device__ __forceinline__ T mm(const Mom<T>& m) {
+  return m.u[A] * m.v[B] * m.w[C];
+}
+
+// <u^a v^b w^c psi>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2)
+template <int A, int B, int C, class T>
+__device__ __forceinline__ void mom_psi(const Mom<T>& m, T out[5]) {
+  const T m0 = mm<A, B, C>(m);
+  out[0] = m0;
+  out[1] = mm<A + 1, B, C>(m);
+  out[2] = mm<A, B + 1, C>(m);
+  out[3] = mm<A, B, C + 1>(m);
+  out[4] = T(0.5) * (mm<A + 2, B, C>(m) + mm<A, B + 2, C>(m) + mm<A, B, C + 2>(m) + m0 * m.xi1);
+}
+
+// <(a.psi) u^a v^b w^c psi>, a.psi = a0 + a1 u + a2 v + a3 w + a4 (u^2+v^2+w^2+xi^2)/2.
+template <int A, int B, int C, class T>
+__device__ __forceinline__ void mom_apsi(const Mom<T>& m, const T a[5], T out[5]) {
+  T t0[5], t1[5], t2[5], t3[5], tu[5], tv[5], tw[5];
+  mom_psi<A, B, C>(m, t0);
+  mom_psi<A + 1, B, C>(m, t1);
+  mom_psi<A, B + 1, C>(m, t2);
+  mom_psi<A, B, C + 1>(m, t3);
+  mom_psi<A + 2, B, C>(m, tu);
+  mom_psi<A, B + 2, C>(m, tv);
+  mom_psi<A, B, C + 2>(m, tw);
+  // <xi^2 u^a v^b w^c psi>: xi^2 multiplies every component, and psi_4 adds xi^4/2.
+  const T m0 = mm<A, B, C>(m);
+  T tx[5];
+  tx[0] = m.xi1 * m0;
+  tx[1] = m.xi1 * mm<A + 1, B, C>(m);
+  tx[2] = m.xi1 * mm<A, B + 1, C>(m);
+  tx[3] = m.xi1 * mm<A, B, C + 1>(m);
+  tx[4] = T(0.5) * (m.xi1 * (mm<A + 2, B, C>(m) + mm<A, B + 2, C>(m) + mm<A, B, C + 2>(m)) +
+                    m.xi2 * m0);
+  const T h = T(0.5) * a[4];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    out[i] = a[0] * t0[i] + a[1] * t1[i] + a[2] * t2[i] + a[3] * t3[i] +
+             h * (tu[i] + tv[i] + tw[i] + tx[i]);
+}
+
+// Solution a of <a.psi psi> = b (moment matrix of the Maxwellian, K internal
+// degrees of freedom), in closed form.
+template <class T>
+__device__ __forceinline__ void slope_solve(const Prim<T>& s, const Gas<T>& g, const T b[5],
+                                            T a[5]) {
+  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+  const T k3t = (g.K + T(3)) * s.theta;
+  const T l2 = T(2) * s.lam;
+  a[4] = (l2 * l2 / (g.K + T(3))) *
+         (T(2) * (b[4] - s.U * b[1] - s.V * b[2] - s.W * b[3]) + (q2 - k3t) * b[0]);
+  a[3] = l2 * (b[3] - s.W * b[0]) - s.W * a[4];
+  a[2] = l2 * (b[2] - s.V * b[0]) - s.V * a[4];
+  a[1] = l2 * (b[1] - s.U * b[0]) - s.U * a[4];
+  a[0] = b[0] - s.U * a[1] - s.V * a[2] - s.W * a[3] - T(0.5) * a[4] * (q2 + k3t);
+}
+
+// Spatial slopes a_n, a_t1, a_t2 from the derivatives of the state, and the
+// time coefficient A from <a_n u + a_t1 v + a_t2 w + A> = 0 (Sec. 2.1).
+template <class T>
+__device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Mom<T>& mf, const Gas<T>& g,
+                                             const T dq[3][5], T a[3][5], T A[5]) {
+  const T inv = T(1) / s.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T b[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) b[i] = dq[d][i] * inv;
+    slope_solve(s, g, b, a[d]);
+  }
+  T r0[5], r1[5], r2[5], rhs[5];
+  mom_apsi<1, 0, 0>(mf, a[0], r0);
+  mom_apsi<0, 1, 0>(mf, a[1], r1);
+  mom_apsi<0, 0, 1>(mf, a[2], r2);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) rhs[i] = -(r0[i] + r1[i] + r2[i]);
+  slope_solve(s, g, rhs, A);
+}
+
+// <u (a_n.psi u + a_t1.psi v + a_t2.psi w) psi>
+template <class T>
+__device__ __forceinline__ void mom_u_adotu(const Mom<T>& m, const T a[3][5], T out[5]) {
+  T r0[5], r1[5], r2[5];
+  mom_apsi<2, 0, 0>(m, a[0], r0);
+  mom_apsi<1, 1, 0>(m, a[1], r1);
+  mom_apsi<1, 0, 1>(m, a[2], r2);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) out[i] = r0[i] + r1[i] + r2[i];
+}
+
+// rho <u psi> - E(Q_ref): the Euler flux of the state minus that of the
+// reference state (0, p_r, 0, 0, 0), formed from deviations.
+template <class T>
+__device__ __forceinline__ void euler_flux_dev(const Prim<T>& s, const T dq[5], const Gas<T>& g,
+                                               T out[5]) {
+  const T m = s.rho * s.U;
+  out[0] = m;
+  out[1] = m * s.U + s.dp;
+  out[2] = m * s.V;
+  out[3] = m * s.W;
+  out[4] = s.U * (g.h_r + dq[4] + s.dp);
+}
+
+// Collision time tau = mu(T)/p at the interface (Sec. 3 opening).
+template <class T>
+__device__ __forceinline__ T collision_time(const Prim<T>& s, const Gas<T>& g) {
+  T mu = g.mu_ref;
+  if (g.visc_law == 1) mu = g.mu_ref * tpow(s.theta * g.T_ref_inv, g.visc_exp);
+  return mu / s.p;
+}
+
+// Heat flux of the non-equilibrium part -tau (a.u + A) g0 in the frame of g0:
+// <h (a_n.psi u + a_t1.psi v + a_t2.psi w + A.psi)>, h = c_u (|c|^2 + xi^2)/2,
+// reduced with the central moments H1 = <c_u^2 s>/2 = (K+5) theta^2 / 2 and
+// H2 = <c_u^2 s^2>/2 = (K+5)(K+7) theta^3 / 2, s = |c|^2 + xi^2.
+template <class T>
+__device__ __forceinline__ T heat_moment(const Prim<T>& s, const Gas<T>& g, const T a[3][5],
+                                         const T A[5]) {
+  const T t2 = s.theta * s.theta;
+  const T H1 = T(0.5) * (g.K + T(5)) * t2;
+  const T H2 = T(0.5) * (g.K + T(5)) * (g.K + T(7)) * t2 * s.theta;
+  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+  const T b0 = a[0][0] + a[0][1] * s.U + a[0][2] * s.V + a[0][3] * s.W + T(0.5) * a[0][4] * q2;
+  const T bu = s.U * (a[0][1] + a[0][4] * s.U) + s.V * (a[1][1] + a[1][4] * s.U) +
+               s.W * (a[2][1] + a[2][4] * s.U) + (A[1] + A[4] * s.U);
+  return H1 * (b0 + bu) + T(0.5) * H2 * a[0][4];
+}
+
+// One reconstructed state at a Gauss point: deviation value and derivatives
+// along n, t1, t2 (local frame, physical units).
+template <class T>
+struct PointState {
+  T q[5];
+  T dq[3][5];
+};
+
+// Simplified smooth flux (Sec. 2.1, Remark 1): f = g0 [1 - tau (a.u + A) + t A],
+// F = rho0 [<u psi> - tau (<u (a.u) psi> + <u A psi>)], dF = rho0 <u A psi>.
+// Returns F - E(Q_ref) and dF.  want_F = false skips F (second S2O4 stage).
+template <class T>
+__device__ __forceinline__ void flux_smooth(const PointState<T>& st0, const Gas<T>& g, bool want_F,
+                                            T F[5], T dF[5]) {
+  const Prim<T> s = prim_of(st0.q, g);
+  Mom<T> m;
+  moments(s, g, 0, m);
+  T a[3][5], A[5];
+  slopes_and_A(s, m, g, st0.dq, a, A);
+  T uA[5];
+  mom_apsi<1, 0, 0>(m, A, uA);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dF[i] = s.rho * uA[i];
+  if (!want_F) return;
+  const T tau = collision_time(s, g);
+  T E[5], ua[5];
+  euler_flux_dev(s, st0.q, g, E);
+  mom_u_adotu(m, a, ua);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) F[i] = E[i] - tau * s.rho * (ua[i] + uA[i]);
+  F[4] -= g.pr_fix * tau * s.rho * heat_moment(s, g, a, A);
+}
+
+// Coefficients of the linear fit F(t) = F + dF t (Eq. (7)) of the six
+// time-integrated terms of Eq. (5), in closed form with y = 1 - exp(-dt/(2 tau)),
+// r = tau/dt: term k contributes Fq[k] V_k to F and dFq[k] V_k to dF.
+template <class T>
+__device__ __forceinline__ void fit_coefficients(T tau, T dt, T Fq[6], T dFq[6]) {
+  const T y = -texpm1(-dt / (T(2) * tau));
+  const T eh = T(1) - y;
+  const T r = tau / dt;
+  const T S = y * (T(2) + y);  // 3 - 4 e^{-dt/2tau} + e^{-dt/tau}
+  const T D = y * y;           // (1 - e^{-dt/2tau})^2
+  Fq[0] = T(1) - r * S;
+  Fq[3] = r * S;
+  dFq[0] = T(4) * r * D / dt;
+  dFq[3] = -dFq[0];
+  Fq[1] = tau * (T(2) * r * S - D);
+  Fq[4] = -tau - Fq[1];
+  dFq[1] = T(4) * tau / dt * (eh * y - T(2) * r * D);
+  dFq[4] = -dFq[1];
+  Fq[2] = -tau * (T(1) - r * S);
+  Fq[5] = -tau * r * S;
+  dFq[2] = T(1) - T(4) * r * r * D;
+  dFq[5] = T(4) * r * r * D;
+}
+
+// Full second-order flux (Eq. (5)) with the Heaviside factor H(u) on g_l and
+// 1 - H(u) on g_r, integrated over [0, dt] and [0, dt/2] and fitted linearly
+// (Eq. (7)).  Returns F - E(Q_ref) and dF.
+template <class T>
+__device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointState<T>& str,
+                                          const PointState<T>& st0, const Gas<T>& g, T dt,
+                                          T F[5], T dF[5]) {
+  T V[6][5];
+  T tau;
+  T q0h[5];  // heat-flux data of g0 for the Prandtl fix
+  T heat0;
+  {
+    const Prim<T> s = prim_of(st0.q, g);
+    Mom<T> m;
+    moments(s, g, 0, m);
+    T a[3][5], A[5];
+    slopes_and_A(s, m, g, st0.dq, a, A);
+    euler_flux_dev(s, st0.q, g, V[0]);
+    T ua[5], uA[5];
+    mom_u_adotu(m, a, ua);
+    mom_apsi<1, 0, 0>(m, A, uA);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      V[1][i] = s.rho * ua[i];
+      V[2][i] = s.rho * uA[i];
+    }
+    tau = collision_time(s, g);
+    heat0 = s.rho * heat_moment(s, g, a, A);
+    (void)q0h;
+  }
+  T pl, pr;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const PointState<T>& st = side == 0 ? stl : str;
+    const Prim<T> s = prim_of(st.q, g);
+    Mom<T> mf, mh;
+    moments(s, g, 0, mf);
+    T a[3][5], A[5];
+    slopes_and_A(s, mf, g, st.dq, a, A);
+    moments(s, g, side == 0 ? +1 : -1, mh);
+    T u0[5], ua[5], uA[5];
+    mom_psi<1, 0, 0>(mh, u0);
+    mom_u_adotu(mh, a, ua);
+    mom_apsi<1, 0, 0>(mh, A, uA);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const T v3 = s.rho * u0[i], v4 = s.rho * ua[i], v5 = s.rho * uA[i];
+      if (side == 0) {
+        V[3][i] = v3;
+        V[4][i] = v4;
+        V[5][i] = v5;
+      } else {
+        V[3][i] += v3;
+        V[4][i] += v4;
+        V[5][i] += v5;
+      }
+    }
+    if (side == 0) pl = s.p; else pr = s.p;
+  }
+  V[3][1] -= g.p_r;  // the half-space sum minus the reference Euler flux
+  tau += g.tau_num_C * tabs((pl - pr) / (pl + pr)) * dt;
+  T Fq[6], dFq[6];
+  fit_coefficients(tau, dt, Fq, dFq);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    T f = T(0), df = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      f += Fq[k] * V[k][i];
+      df += dFq[k] * V[k][i];
+    }
+    F[i] = f;
+    dF[i] = df;
+  }
+  F[4] -= g.pr_fix * tau * heat0;
+}
+
+// Equilibrium state of the compatibility condition, Q0 = int_{u>0} psi g_l +
+// int_{u<0} psi g_r, as a deviation: Q0 - Q_ref = (dQl + dQr)/2 + (S_l - S_r)/2
+// with S = int sign(u) psi g = rho (D0, D1, V D0, W D0, (D2 + D0 (V^2+W^2+(K+2) theta))/2),
+// D0 = erf(sqrt(lam) U), D1 = U D0 + exp(-lam U^2)/sqrt(pi lam), D2 = U D1 + theta D0.
+template <class T>
+__device__ __forceinline__ void sign_moments(const T dq[5], const Gas<T>& g, T S[5]) {
+  const Prim<T> s = prim_of(dq, g);
+  const T sl = tsqrt(s.lam);
+  const T x = sl * s.U;
+  const T D0 = terf(x);
+  const T D1 = s.U * D0 + texp(-x * x) * T(0.5641895835477563) / sl;  // 1/sqrt(pi)
+  const T D2 = s.U * D1 + s.theta * D0;
+  S[0] = s.rho * D0;
+  S[1] = s.rho * D1;
+  S[2] = s.rho * s.V * D0;
+  S[3] = s.rho * s.W * D0;
+  S[4] = T(0.5) * s.rho * (D2 + D0 * (s.V * s.V + s.W * s.W + (g.K + T(2)) * s.theta));
+}
+
+template <class T>
+__device__ __forceinline__ void compat_dev(const T dql[5], const T dqr[5], const Gas<T>& g,
+                                           T dq0[5]) {
+  T Sl[5], Sr[5];
+  sign_moments(dql, g, Sl);
+  sign_moments(dqr, g, Sr);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dq0[i] = T(0.5) * (dql[i] + dqr[i]) + T(0.5) * (Sl[i] - Sr[i]);
+}
+
+}  // namespace hgks

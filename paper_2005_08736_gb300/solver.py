@@ -1,0 +1,159 @@
+"""Python API over the C ABI: a GPU HGKS simulation on one device.
+
+PyTorch provides the device memory for field transfers and the CUDA stream
+the library runs on; every step of the scheme runs in the library's CUDA
+kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, fields
+
+import numpy as np
+import torch
+
+from . import _lib
+
+RECON = {"linear": 0, "weno-js": 1, "weno-z": 2}
+FLUX = {"smooth": 0, "full": 1}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+@dataclass
+class Config:
+    """Problem statement (mirrors hgks_config of include/hgks.h)."""
+    nx: int
+    ny: int
+    nz: int
+    x0: float = 0.0
+    lx: float = 2 * math.pi
+    y0: float = 0.0
+    ly: float = 2 * math.pi
+    z0: float = 0.0
+    lz: float = 2 * math.pi
+    y_stretch: int = 0
+    stretch_b: float = 2.0
+    bc_y: int = 0
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    visc: int = 0
+    mu_ref: float = 1.0 / 1600.0
+    T_ref: float = 1.0
+    visc_exp: float = 0.76
+    T_wall: float = 1.0
+    force_x: float = 0.0
+    recon: int = 0
+    flux: int = 0
+    tau_num_C: float = 0.0
+    cfl: float = 0.5
+    prec: int = 1
+    rho_ref: float = 1.0
+    p_ref: float = 100.0 / 1.4
+
+    def c_struct(self) -> _lib.HgksConfig:
+        return _lib.HgksConfig(**{f.name: getattr(self, f.name) for f in fields(self)})
+
+    @property
+    def shape(self):
+        return (5, self.nz, self.ny, self.nx)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def taylor_green_config(n: int, prec: str = "fp32", recon: str = "linear", flux: str = "smooth",
+                        **kw) -> Config:
+    """Taylor-Green vortex of Sec. 3.1: Ma 0.1, Re 1600 (mu = 1/1600), gamma 1.4."""
+    c = Config(n, n, n, prec=PREC[prec], recon=RECON[recon], flux=FLUX[flux],
+               tau_num_C=1.0 if flux == "full" else 0.0)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+class Simulation:
+    """One HGKS context on the current CUDA device."""
+
+    def __init__(self, cfg: Config, stream: torch.cuda.Stream | None = None):
+        self.lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.cfg = cfg
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._c = cfg.c_struct()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.hgks_create(ctypes.byref(self._c), ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hgks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, status):
+        _lib.check(status, self.h)
+
+    def _fp64_arg(self, a):
+        """(pointer, is_host, keep-alive) for an FP64 [5][nz][ny][nx] array."""
+        if isinstance(a, torch.Tensor):
+            assert a.dtype == torch.float64 and tuple(a.shape) == self.cfg.shape
+            a = a.contiguous()
+            if a.is_cuda:
+                # Order the caller's producer stream before the library's stream.
+                self.stream.wait_stream(torch.cuda.current_stream(a.device))
+                return ctypes.c_void_p(a.data_ptr()), 0, a
+            return ctypes.c_void_p(a.data_ptr()), 1, a
+        arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        assert arr.shape == self.cfg.shape
+        return ctypes.c_void_p(arr.ctypes.data), 1, arr
+
+    def init_primitive(self, prim) -> None:
+        p, host, keep = self._fp64_arg(prim)
+        self._call(self.lib.hgks_init_state(self.h, p, host))
+        if not host:
+            keep.record_stream(self.stream)
+
+    def init_conservative(self, cons) -> None:
+        p, host, keep = self._fp64_arg(cons)
+        self._call(self.lib.hgks_init_conservative(self.h, p, host))
+        if not host:
+            keep.record_stream(self.stream)
+
+    def step(self, nsteps: int = 1, dt: float = 0.0, sync: bool = True) -> float | None:
+        t = ctypes.c_double(0.0)
+        self._call(self.lib.hgks_step(self.h, int(nsteps), float(dt), int(sync), ctypes.byref(t)))
+        return t.value if sync else None
+
+    def state(self, device: bool = False):
+        """Conservative state, FP64 [5][nz][ny][nx] (numpy, or a CUDA tensor)."""
+        if device:
+            out = torch.empty(self.cfg.shape, dtype=torch.float64, device=self.device)
+            self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 0))
+            out.record_stream(self.stream)
+            torch.cuda.current_stream(self.device).wait_stream(self.stream)
+            return out
+        out = np.empty(self.cfg.shape)
+        self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.ctypes.data), 1))
+        return out
+
+    def profile_step(self, dt: float = 0.0) -> dict:
+        """Advance one step with CUDA events per kernel class; device ms per class."""
+        ms = (ctypes.c_double * len(_lib.KERNEL_CLASSES))()
+        self._call(self.lib.hgks_profile_step(self.h, float(dt), ms, len(ms)))
+        return dict(zip(_lib.KERNEL_CLASSES, list(ms)))
+
+    def diagnostics(self) -> dict:
+        d = _lib.HgksDiag()
+        self._call(self.lib.hgks_diagnostics(self.h, ctypes.byref(d)))
+        return dict(t=d.t, dt=d.dt, mass=d.mass, mom=tuple(d.mom), energy=d.energy, Ek=d.Ek,
+                    rho_min=d.rho_min, p_min=d.p_min, step=d.step)

@@ -1,0 +1,89 @@
+"""The C ABI library loads and exports every entry point include/*.h declares;
+struct layouts agree between C and the ctypes binding; configuration errors
+are rejected on the host (CPU only: no kernel runs here)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2005_08736_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            src = open(os.path.join(INCLUDE, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(hgks_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert "hgks_step" in names and "hgks_create" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(hgks_\w+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+    assert sorted(_lib.EXPORTS) == sorted(n for n in names if n in _lib.EXPORTS)
+
+
+def test_struct_layouts_match_the_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "hgks.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(hgks_config), offsetof(hgks_config, prec),
+         offsetof(hgks_config, p_ref), sizeof(hgks_diag), offsetof(hgks_diag, step));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", INCLUDE, c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(_lib.HgksConfig), _lib.HgksConfig.prec.offset,
+                    _lib.HgksConfig.p_ref.offset, ctypes.sizeof(_lib.HgksDiag),
+                    _lib.HgksDiag.step.offset]
+
+
+@pytest.mark.parametrize("field,value", [("nx", 5), ("gamma", 1.0), ("prandtl", 0.0), ("cfl", -1.0),
+                                         ("recon", 7), ("flux", 2), ("prec", 3), ("p_ref", 0.0),
+                                         ("bc_y", 4), ("y_stretch", 1)])
+def test_invalid_configurations_are_rejected_before_any_device_work(lib, field, value):
+    cfg = _lib.HgksConfig()
+    assert lib.hgks_default_config(ctypes.byref(cfg), 16) == _lib.HGKS_OK
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.hgks_create(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.HGKS_E_INVAL
+    assert not h.value
+    assert lib.hgks_last_error(None)
+
+
+def test_default_config_is_the_taylor_green_setting(lib):
+    cfg = _lib.HgksConfig()
+    assert lib.hgks_default_config(ctypes.byref(cfg), 32) == _lib.HGKS_OK
+    assert (cfg.nx, cfg.gamma, cfg.prandtl, cfg.cfl) == (32, 1.4, 0.72, 0.5)
+    assert cfg.mu_ref == pytest.approx(1 / 1600)
+    assert cfg.p_ref == pytest.approx(100 / 1.4)
+    assert lib.hgks_default_config(ctypes.byref(cfg), 5) == _lib.HGKS_E_INVAL
