@@ -287,7 +287,7 @@ __device__ __forceinline__ void fit_coefficients(T tau, T dt, T Fq[6], T dFq[6])
   Fq[3] = r * S;
   dFq[0] = T(4) * r * D / dt;
   dFq[3] = -dFq[0];
-  Fq[1] = tau * (T(2) * r * S - D);
+  Fq[1] = tau * (T(2) * r * S + D - T(2));
   Fq[4] = -tau - Fq[1];
   dFq[1] = T(4) * tau / dt * (eh * y - T(2) * r * D);
   dFq[4] = -dFq[1];
