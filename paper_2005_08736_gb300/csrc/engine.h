@@ -22,7 +22,6 @@ struct Engine {
   void* qs = nullptr;    // padded state Q*, 5 * P
   void* inc = nullptr;   // stage-1 increment, 5 * N
   void* comp = nullptr;  // FP32 compensation, 5 * N (null for FP64)
-  void* ff = nullptr;    // face fields of one direction
   void* fd[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction, 10 * faces
   void* w[3] = {nullptr, nullptr, nullptr};   // cell widths incl. ghosts, n + 6
   double* scal = nullptr;                      // [0] dt, [1] t, [2] step
@@ -33,15 +32,16 @@ struct Engine {
   double* io = nullptr;        // FP64 staging buffer, 5 * N
   int diag_blocks = 0;
   int cfl_blocks = 0;
+  int sms = 152;  // multiprocessors of the device
 };
 
 // Kernel classes timed by hgks_profile_step (order of its output array).
 enum KernelClass {
   KC_CFL = 0,        // CFL reduction and dt
   KC_GHOST = 1,      // ghost-cell fills
-  KC_FACE = 2,       // face fields, all directions and stages
-  KC_FLUX1 = 3,      // Gauss-point flux, stage 1 (F and dF)
-  KC_FLUX2 = 4,      // Gauss-point flux, stage 2
+  KC_FACE = 2,       // unused (face fields are fused into the sweep)
+  KC_FLUX1 = 3,      // sweep kernels of stage 1 (face fields, reconstruction, flux)
+  KC_FLUX2 = 4,      // sweep kernels of stage 2
   KC_UPDATE = 5,     // divergence + S2O4 update
   KC_COUNT = 6
 };
@@ -76,8 +76,6 @@ cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed);
 cudaError_t enqueue_advance_time(const Engine& e);
 
 // Sizes (in elements) of the per-direction face buffers.
-long long face_field_elems(const Engine& e, int d);
 long long face_flux_elems(const Engine& e, int d);
-int face_field_count(const Engine& e);
 
 }  // namespace hgks

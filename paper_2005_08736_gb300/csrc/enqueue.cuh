@@ -4,6 +4,7 @@
 
 #include "engine.h"
 #include "kernels.cuh"
+#include "sweep.cuh"
 
 namespace hgks {
 
@@ -54,40 +55,53 @@ cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe) {
   return cudaGetLastError();
 }
 
-template <class T, int MODE, int FLUX>
-void launch_direction(const Engine& e, const T* q, int d, int stage, Probe* probe) {
+// Tile of the sweep kernel per precision and flux: TP x TS faces, sized so
+// that the shared-memory staging fits and every tile gives 1, 2 or 4 threads
+// per face.
+template <class T, int FLUX> struct SweepTile { static constexpr int TP = 16, TS = 8; };
+template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8; };
+
+template <class T, int MODE, int FLUX, int STAGE>
+cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
+  constexpr int TP = SweepTile<T, FLUX>::TP, TS = SweepTile<T, FLUX>::TS;
   const GridDev g = grid_of(e);
-  FaceArgs<T> fa;
-  fa.q = q;
-  fa.ff = static_cast<T*>(e.ff);
-  fa.w = static_cast<const T*>(e.w[d]);
-  fa.g = g;
-  fa.box = face_box(g, d, 2);
-  fa.d = d;
-  fa.gas = gas_of<T>(e.cfg);
-  if (probe) probe->begin(e.stream, KC_FACE);
-  k_face_fields<T, MODE, FLUX><<<blocks_for(fa.box.size, 256), 256, 0, e.stream>>>(fa);
-  if (probe) probe->end(e.stream);
-  GaussArgs<T> ga;
-  ga.ff = fa.ff;
-  ga.fd = static_cast<T*>(e.fd[d]);
-  ga.w1 = static_cast<const T*>(e.w[(d + 1) % 3]);
-  ga.w2 = static_cast<const T*>(e.w[(d + 2) % 3]);
-  ga.scal = e.scal;
-  ga.g = g;
-  ga.box = fa.box;
-  ga.fbox = face_box(g, d, 0);
-  ga.d = d;
-  ga.want_F = stage == 1;
-  ga.gas = fa.gas;
-  if (probe) probe->begin(e.stream, stage == 1 ? KC_FLUX1 : KC_FLUX2);
-  k_gauss_flux<T, MODE, FLUX><<<blocks_for(4 * ga.fbox.size, 128), 128, 0, e.stream>>>(ga);
-  if (probe) probe->end(e.stream);
+  SweepArgs<T> a;
+  a.q = q;
+  a.fd = static_cast<T*>(e.fd[d]);
+  a.wn = static_cast<const T*>(e.w[d]);
+  a.wt1 = static_cast<const T*>(e.w[(d + 1) % 3]);
+  a.wt2 = static_cast<const T*>(e.w[(d + 2) % 3]);
+  a.scal = e.scal;
+  a.g = g;
+  a.d = d;
+  a.gas = gas_of<T>(e.cfg);
+  const int P = d == 0 ? 1 : 0, S = d == 2 ? 1 : 2;
+  const int gx = (g.n[P] + TP - 1) / TP, gy = (g.n[S] + TS - 1) / TS;
+  // Chunk the march along d so that the grid holds several waves of CTAs.
+  const int layers = g.n[d] + 1;
+  const int want_chunks = (4 * e.sms + gx * gy - 1) / (gx * gy);
+  int chunk = (layers + want_chunks - 1) / want_chunks;
+  if (chunk < 8) chunk = 8;
+  a.chunk = chunk;
+  const int gz = (layers + chunk - 1) / chunk;
+  constexpr size_t smem = sweep_smem_bytes<T, FLUX, TP, TS>();
+  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<dim3(gx, gy, gz), 256, smem, e.stream>>>(a);
+  return cudaGetLastError();
 }
 
 template <class T, int MODE, int FLUX>
-void launch_all_directions(const Engine& e, const T* q, int stage, Probe* probe) {
-  for (int d = 0; d < 3; ++d) launch_direction<T, MODE, FLUX>(e, q, d, stage, probe);
+cudaError_t launch_all_directions(const Engine& e, const T* q, int stage, Probe* probe) {
+  for (int d = 0; d < 3; ++d) {
+    if (probe) probe->begin(e.stream, stage == 1 ? KC_FLUX1 : KC_FLUX2);
+    const cudaError_t err = stage == 1 ? launch_sweep<T, MODE, FLUX, 1>(e, q, d)
+                                       : launch_sweep<T, MODE, FLUX, 2>(e, q, d);
+    if (probe) probe->end(e.stream);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
 }
 
 template <class T>
@@ -97,10 +111,11 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   if (err != cudaSuccess) return err;
   const int mode = e.cfg.recon, flux = e.cfg.flux;
 #define HGKS_DISPATCH(M, F) \
-  if (mode == M && flux == F) launch_all_directions<T, M, F>(e, qin, stage, probe);
+  if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe);
   HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0)
   HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1)
 #undef HGKS_DISPATCH
+  if (err != cudaSuccess) return err;
   UpdateArgs<T> ua;
   ua.q = static_cast<T*>(e.q);
   ua.qs = static_cast<T*>(e.qs);

@@ -91,7 +91,7 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 }
 
 void free_all(hgks::Engine& e) {
-  void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.ff, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
+  void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -214,14 +214,10 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   e.P = (long long)e.p[0] * e.p[1] * e.p[2];
   e.N = (long long)e.n[0] * e.n[1] * e.n[2];
   const size_t es = elem_size(*cfg);
-  long long ff_max = 0;
-  for (int d = 0; d < 3; ++d) {
-    const long long v = hgks::face_field_elems(e, d);
-    if (v > ff_max) ff_max = v;
-  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   if (sms <= 0) sms = 152;
+  e.sms = sms;
   e.cfl_blocks = sms * 4;
   e.diag_blocks = sms * 4;
   auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes); };
@@ -230,7 +226,6 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   if (err == cudaSuccess) err = alloc(&e.qs, 5 * e.P * es);
   if (err == cudaSuccess) err = alloc(&e.inc, 5 * e.N * es);
   if (err == cudaSuccess && cfg->prec == HGKS_FP32) err = alloc(&e.comp, 5 * e.N * es);
-  if (err == cudaSuccess) err = alloc(&e.ff, ff_max * es);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.fd[d], hgks::face_flux_elems(e, d) * es);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.w[d], (e.n[d] + 6) * es);
   if (err == cudaSuccess) err = alloc((void**)&e.scal, 4 * sizeof(double));
@@ -404,16 +399,10 @@ const char* hgks_last_error(const hgks_ctx* c) {
 
 namespace hgks {
 
-long long face_field_elems(const Engine& e, int d) {
-  long long s = 1;
-  for (int c = 0; c < 3; ++c) s *= (c == d) ? e.n[c] + 1 : e.n[c] + 4;
-  return s * 5 * face_field_count(e);
-}
 long long face_flux_elems(const Engine& e, int d) {
   long long s = 1;
   for (int c = 0; c < 3; ++c) s *= (c == d) ? e.n[c] + 1 : e.n[c];
   return s * 10;
 }
-int face_field_count(const Engine& e) { return e.cfg.flux == HGKS_FLUX_FULL ? 6 : 2; }
 
 }  // namespace hgks

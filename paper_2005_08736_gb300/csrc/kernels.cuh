@@ -5,17 +5,10 @@
 // rho W, rho E) of (nx+6)(ny+6)(nz+6) cells, x fastest, 3 ghost layers on
 // every side, holding deviations from the reference state at rest.
 //
-// Per stage and sweep direction d (tangential directions t1 = d+1, t2 = d+2
-// mod 3):
-//   k_face_fields  one thread per face and tangential row (2 ghost rows on
-//                  each side): WENO5 end values, normal slopes, the
-//                  compatibility state Q0 and its normal slope, in the local
-//                  frame (normal momentum first);
-//   k_gauss_flux   one thread per Gauss point (4 per face): tangential
-//                  reconstruction to the point, the BGK flux there, and a
-//                  4-lane shuffle sum with weights 1/4 into the face flux;
-// then k_update forms L = -(1/|Omega|) sum F (Eq. (4)) and the S2O4 stage
-// (Eq. (6)).
+// Per stage, the fused sweep kernel (sweep.cuh) writes the face fluxes of
+// each direction; k_update then forms L = -(1/|Omega|) sum F (Eq. (4)) and
+// the S2O4 stage (Eq. (6)).  Ghost fills, the CFL and diagnostic reductions
+// and the state conversions are here too.
 #pragma once
 
 #include <cstdint>
@@ -130,195 +123,11 @@ __global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
   for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
 }
 
-// ------------------------------------------------------------- face fields ---
-
-// Local-frame component of variable i for sweep direction d.
+// Global conservative-variable index of local-frame component i for sweep
+// direction d (local frame: normal momentum first, then t1, t2).
 __host__ __device__ __forceinline__ int global_var(int d, int i) {
   if (i == 0 || i == 4) return i;
   return 1 + (d + i - 1) % 3;
-}
-
-template <class T>
-struct FaceArgs {
-  const T* __restrict__ q;   // padded state
-  T* __restrict__ ff;        // face fields [NF*5][box]
-  const T* __restrict__ w;   // widths along d, offset kGhost
-  GridDev g;
-  FaceBox box;
-  int d;
-  Gas<T> gas;
-};
-
-// Fields: smooth flux -> 0: Q0, 1: dQ0/dn; full flux -> 0: Q_l, 1: Q_r,
-// 2: dQ_l/dn, 3: dQ_r/dn, 4: Q0, 5: dQ0/dn.
-template <class T, int MODE, int FLUX>
-__global__ void __launch_bounds__(256) k_face_fields(FaceArgs<T> a) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= a.box.size) return;
-  int c[3];
-  c[0] = int(tid % a.box.r[0]) + a.box.o[0];
-  const long long r1 = tid / a.box.r[0];
-  c[1] = int(r1 % a.box.r[1]) + a.box.o[1];
-  c[2] = int(r1 / a.box.r[1]) + a.box.o[2];
-  const int d = a.d;
-  const int f = c[d];
-  long long sd = 1;
-  if (d >= 1) sd *= a.g.p[0];
-  if (d >= 2) sd *= a.g.p[1];
-  c[d] = f - 3;
-  const long long base = pad_index(a.g, c[0], c[1], c[2]);
-  const T hl = a.w[f - 1 + kGhost], hr = a.w[f + kGhost];
-  T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const T* qv = a.q + global_var(d, i) * a.g.P + base;
-    const T q0 = qv[0], q1 = qv[sd], q2 = qv[2 * sd], q3 = qv[3 * sd], q4 = qv[4 * sd],
-            q5 = qv[5 * sd];
-    T Li, Ri, Lr, Rr;
-    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);  // cell f-1
-    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);  // cell f
-    Ql[i] = Ri;
-    Qr[i] = Lr;
-    // Normal slopes of the quadratic through both end values and the average.
-    Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) / hl;
-    Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) / hr;
-    // Equilibrium slope: derivative at the face of the cubic matching four averages.
-    D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) / (T(6) * (hl + hr));
-  }
-  T Q0[5];
-  compat_dev(Ql, Qr, a.gas, Q0);
-  const long long S = a.box.size;
-  T* out = a.ff + tid;
-  if (FLUX == FLUX_SMOOTH) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      out[(0 * 5 + i) * S] = Q0[i];
-      out[(1 * 5 + i) * S] = D0[i];
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      out[(0 * 5 + i) * S] = Ql[i];
-      out[(1 * 5 + i) * S] = Qr[i];
-      out[(2 * 5 + i) * S] = Dl[i];
-      out[(3 * 5 + i) * S] = Dr[i];
-      out[(4 * 5 + i) * S] = Q0[i];
-      out[(5 * 5 + i) * S] = D0[i];
-    }
-  }
-}
-
-// ------------------------------------------------------- Gauss-point flux ---
-
-template <class T>
-struct GaussArgs {
-  const T* __restrict__ ff;
-  T* __restrict__ fd;          // face fluxes [10][fbox]: F then dF, global frame
-  const T* __restrict__ w1;    // widths along t1 (offset kGhost)
-  const T* __restrict__ w2;    // widths along t2
-  const double* __restrict__ scal;  // device scalars: [0] = dt
-  GridDev g;
-  FaceBox box;   // face-field box (tangential halo 2)
-  FaceBox fbox;  // face-flux box (no tangential halo)
-  int d;
-  int want_F;    // 0 in the second S2O4 stage: only dF is used
-  Gas<T> gas;
-};
-
-// Value, d/dt1 and d/dt2 (or the value only) of one face-field component at
-// Gauss point (m1, m2), from the 5x5 face averages around the face.
-template <int MODE, bool DERIV, class T>
-__device__ __forceinline__ void gauss_recon(const T* __restrict__ f, long long s1, long long s2,
-                                            int m1, int m2, T& val, T& d1, T& d2) {
-  T rv[5], rd[5];
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    const T* row = f + (r - 2) * s2;
-    T v[2], dd[2];
-    tangential<MODE>(row[-2 * s1], row[-s1], row[0], row[s1], row[2 * s1], v, dd);
-    rv[r] = m1 ? v[1] : v[0];
-    rd[r] = m1 ? dd[1] : dd[0];
-  }
-  T v[2], dd[2];
-  tangential<MODE>(rv[0], rv[1], rv[2], rv[3], rv[4], v, dd);
-  val = m2 ? v[1] : v[0];
-  if (DERIV) {
-    d2 = m2 ? dd[1] : dd[0];
-    tangential<MODE>(rd[0], rd[1], rd[2], rd[3], rd[4], v, dd);
-    d1 = m2 ? v[1] : v[0];
-  }
-}
-
-template <int MODE, class T>
-__device__ __forceinline__ void gauss_state(const T* __restrict__ ff, long long S, long long at,
-                                            long long s1, long long s2, int fv, int fs, int m1,
-                                            int m2, T h1, T h2, PointState<T>& st) {
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    T v, d1, d2, dn, u1, u2;
-    gauss_recon<MODE, true>(ff + (fv * 5 + i) * S + at, s1, s2, m1, m2, v, d1, d2);
-    gauss_recon<MODE, false>(ff + (fs * 5 + i) * S + at, s1, s2, m1, m2, dn, u1, u2);
-    st.q[i] = v;
-    st.dq[0][i] = dn;
-    st.dq[1][i] = d1 / h1;
-    st.dq[2][i] = d2 / h2;
-  }
-}
-
-template <class T, int MODE, int FLUX>
-__global__ void __launch_bounds__(128) k_gauss_flux(GaussArgs<T> a) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long face = tid >> 2;
-  const int gp = int(tid & 3);
-  const bool active = face < a.fbox.size;
-  const long long fc = active ? face : 0;
-  int c[3];
-  c[0] = int(fc % a.fbox.r[0]);
-  const long long r1 = fc / a.fbox.r[0];
-  c[1] = int(r1 % a.fbox.r[1]);
-  c[2] = int(r1 / a.fbox.r[1]);
-  const int d = a.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  // Position in the face-field box and strides of the tangential axes there.
-  const long long at = (long long)(c[0] - a.box.o[0]) +
-                       (long long)a.box.r[0] * ((c[1] - a.box.o[1]) + (long long)a.box.r[1] * (c[2] - a.box.o[2]));
-  long long st[3] = {1, a.box.r[0], (long long)a.box.r[0] * a.box.r[1]};
-  const long long s1 = st[t1], s2 = st[t2];
-  const T h1 = a.w1[c[t1] + kGhost], h2 = a.w2[c[t2] + kGhost];
-  const int m1 = gp & 1, m2 = gp >> 1;
-  const T dt = T(a.scal[0]);
-  const long long S = a.box.size;
-  T F[5], dF[5];
-  if (FLUX == FLUX_SMOOTH) {
-    PointState<T> s0;
-    gauss_state<MODE>(a.ff, S, at, s1, s2, 0, 1, m1, m2, h1, h2, s0);
-    flux_smooth(s0, a.gas, a.want_F != 0, F, dF);
-    if (!a.want_F) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) F[i] = T(0);
-    }
-  } else {
-    PointState<T> sl, sr, s0;
-    gauss_state<MODE>(a.ff, S, at, s1, s2, 0, 2, m1, m2, h1, h2, sl);
-    gauss_state<MODE>(a.ff, S, at, s1, s2, 1, 3, m1, m2, h1, h2, sr);
-    gauss_state<MODE>(a.ff, S, at, s1, s2, 4, 5, m1, m2, h1, h2, s0);
-    flux_full(sl, sr, s0, a.gas, dt, F, dF);
-  }
-  // Sum over the four Gauss points of the face (consecutive lanes), weight 1/4.
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    F[i] += __shfl_xor_sync(0xffffffffu, F[i], 1);
-    F[i] += __shfl_xor_sync(0xffffffffu, F[i], 2);
-    dF[i] += __shfl_xor_sync(0xffffffffu, dF[i], 1);
-    dF[i] += __shfl_xor_sync(0xffffffffu, dF[i], 2);
-  }
-  if (!active || gp != 0) return;
-  const long long FS = a.fbox.size;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int v = global_var(d, i);
-    a.fd[v * FS + face] = T(0.25) * F[i];
-    a.fd[(5 + v) * FS + face] = T(0.25) * dF[i];
-  }
 }
 
 // ------------------------------------------------------------------ update ---
@@ -421,46 +230,47 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// CFL time-step bound min over cells and directions of width/(|u_d| + c)
-// (FP64), with a flag for non-physical states (rho <= 0, p <= 0, NaN).
-// Positive doubles order like their bit patterns, so the block minima are
-// combined with a 64-bit atomicMin on the bits.
+// CFL time-step bound min over cells and directions of width/(|u_d| + c),
+// with a flag for non-physical states (rho <= 0, p <= 0, NaN).  The per-cell
+// arithmetic runs in T; the minimum is combined in FP64: positive doubles
+// order like their bit patterns, so block minima meet in a 64-bit atomicMin.
 template <class T>
 __global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
                                              const T* __restrict__ wx, const T* __restrict__ wy,
                                              const T* __restrict__ wz, double rho_r, double p_r,
                                              double gamma, unsigned long long* __restrict__ dtmin,
                                              int* __restrict__ flag) {
-  double best = 1e300;
+  T best = T(1e30);
   int bad = 0;
   const int nx = g.n[0], ny = g.n[1];
+  const T tr = T(rho_r), tp = T(p_r), tg = T(gamma), tg1 = T(gamma - 1.0);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
        c += (long long)gridDim.x * blockDim.x) {
     const int x = int(c % nx);
     const long long r = c / nx;
     const int y = int(r % ny), z = int(r / ny);
     const long long pi = pad_index(g, x, y, z);
-    const double rho = rho_r + double(q[pi]);
-    const double mx = q[g.P + pi], my = q[2 * g.P + pi], mz = q[3 * g.P + pi];
-    const double dE = q[4 * g.P + pi];
-    const double ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
-    const double p = p_r + (gamma - 1.0) * (dE - ke);
-    if (!(rho > 0.0) || !(p > 0.0)) {
+    const T rho = tr + q[pi];
+    const T mx = q[g.P + pi], my = q[2 * g.P + pi], mz = q[3 * g.P + pi];
+    const T inv = T(1) / rho;
+    const T ke = T(0.5) * (mx * mx + my * my + mz * mz) * inv;
+    const T p = tp + tg1 * (q[4 * g.P + pi] - ke);
+    if (!(rho > T(0)) || !(p > T(0))) {
       bad = 1;
       continue;
     }
-    const double cs = sqrt(gamma * p / rho);
-    best = fmin(best, double(wx[x + kGhost]) / (fabs(mx / rho) + cs));
-    best = fmin(best, double(wy[y + kGhost]) / (fabs(my / rho) + cs));
-    best = fmin(best, double(wz[z + kGhost]) / (fabs(mz / rho) + cs));
+    const T cs = tsqrt(tg * p * inv);
+    best = fmin(best, wx[x + kGhost] / (tabs(mx * inv) + cs));
+    best = fmin(best, wy[y + kGhost] / (tabs(my * inv) + cs));
+    best = fmin(best, wz[z + kGhost] / (tabs(mz * inv) + cs));
   }
-  best = warp_min(best);
+  double bd = warp_min(double(best));
   __shared__ double sm[32];
   __shared__ int sbad;
   if (threadIdx.x == 0) sbad = 0;
   __syncthreads();
   if (bad) atomicOr(&sbad, 1);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = bd;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 1e300;

@@ -169,28 +169,6 @@ __device__ __forceinline__ void slope_solve(const Prim<T>& s, const Gas<T>& g, c
   a[0] = b[0] - s.U * a[1] - s.V * a[2] - s.W * a[3] - T(0.5) * a[4] * (q2 + k3t);
 }
 
-// Spatial slopes a_n, a_t1, a_t2 from the derivatives of the state, and the
-// time coefficient A from <a_n u + a_t1 v + a_t2 w + A> = 0 (Sec. 2.1).
-template <class T>
-__device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Mom<T>& mf, const Gas<T>& g,
-                                             const T dq[3][5], T a[3][5], T A[5]) {
-  const T inv = T(1) / s.rho;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    T b[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) b[i] = dq[d][i] * inv;
-    slope_solve(s, g, b, a[d]);
-  }
-  T r0[5], r1[5], r2[5], rhs[5];
-  mom_apsi<1, 0, 0>(mf, a[0], r0);
-  mom_apsi<0, 1, 0>(mf, a[1], r1);
-  mom_apsi<0, 0, 1>(mf, a[2], r2);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) rhs[i] = -(r0[i] + r1[i] + r2[i]);
-  slope_solve(s, g, rhs, A);
-}
-
 // <u (a_n.psi u + a_t1.psi v + a_t2.psi w) psi>
 template <class T>
 __device__ __forceinline__ void mom_u_adotu(const Mom<T>& m, const T a[3][5], T out[5]) {
@@ -215,31 +193,6 @@ __device__ __forceinline__ void euler_flux_dev(const Prim<T>& s, const T dq[5], 
   out[4] = s.U * (g.h_r + dq[4] + s.dp);
 }
 
-// Collision time tau = mu(T)/p at the interface (Sec. 3 opening).
-template <class T>
-__device__ __forceinline__ T collision_time(const Prim<T>& s, const Gas<T>& g) {
-  T mu = g.mu_ref;
-  if (g.visc_law == 1) mu = g.mu_ref * tpow(s.theta * g.T_ref_inv, g.visc_exp);
-  return mu / s.p;
-}
-
-// Heat flux of the non-equilibrium part -tau (a.u + A) g0 in the frame of g0:
-// <h (a_n.psi u + a_t1.psi v + a_t2.psi w + A.psi)>, h = c_u (|c|^2 + xi^2)/2,
-// reduced with the central moments H1 = <c_u^2 s>/2 = (K+5) theta^2 / 2 and
-// H2 = <c_u^2 s^2>/2 = (K+5)(K+7) theta^3 / 2, s = |c|^2 + xi^2.
-template <class T>
-__device__ __forceinline__ T heat_moment(const Prim<T>& s, const Gas<T>& g, const T a[3][5],
-                                         const T A[5]) {
-  const T t2 = s.theta * s.theta;
-  const T H1 = T(0.5) * (g.K + T(5)) * t2;
-  const T H2 = T(0.5) * (g.K + T(5)) * (g.K + T(7)) * t2 * s.theta;
-  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
-  const T b0 = a[0][0] + a[0][1] * s.U + a[0][2] * s.V + a[0][3] * s.W + T(0.5) * a[0][4] * q2;
-  const T bu = s.U * (a[0][1] + a[0][4] * s.U) + s.V * (a[1][1] + a[1][4] * s.U) +
-               s.W * (a[2][1] + a[2][4] * s.U) + (A[1] + A[4] * s.U);
-  return H1 * (b0 + bu) + T(0.5) * H2 * a[0][4];
-}
-
 // One reconstructed state at a Gauss point: deviation value and derivatives
 // along n, t1, t2 (local frame, physical units).
 template <class T>
@@ -248,29 +201,120 @@ struct PointState {
   T dq[3][5];
 };
 
+// Directional derivative of the Euler flux along local axis J at the state s
+// (H = rho E + p) in the direction dQ: J_J(Q) dQ.
+template <int J, class T>
+__device__ __forceinline__ void euler_jvp(const Prim<T>& s, T H, const T dQ[5], const Gas<T>& g,
+                                          T out[5]) {
+  const T inv = T(1) / s.rho;
+  const T U[3] = {s.U, s.V, s.W};
+  const T du[3] = {(dQ[1] - U[0] * dQ[0]) * inv, (dQ[2] - U[1] * dQ[0]) * inv,
+                   (dQ[3] - U[2] * dQ[0]) * inv};
+  const T dp = g.gm1 * (dQ[4] - U[0] * dQ[1] - U[1] * dQ[2] - U[2] * dQ[3] +
+                        T(0.5) * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]) * dQ[0]);
+  const T mJ = s.rho * U[J];
+  out[0] = dQ[1 + J];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[1 + i] = dQ[1 + J] * U[i] + mJ * du[i];
+  out[1 + J] += dp;
+  out[4] = du[J] * H + U[J] * (dQ[4] + dp);
+}
+
+// Time derivative of the conservative state of the equilibrium,
+// Q_t = rho <A psi> = -rho sum_d <(a_d.psi) u_d psi> = -sum_d J_d(Q) dQ/dx_d:
+// each moment of (a.psi) g is the derivative of the Maxwellian's moment along
+// the parameter change that a encodes.
+template <class T>
+__device__ __forceinline__ void state_time_derivative(const Prim<T>& s, T H, const T dq[3][5],
+                                                      const Gas<T>& g, T Qt[5]) {
+  T j0[5], j1[5], j2[5];
+  euler_jvp<0>(s, H, dq[0], g, j0);
+  euler_jvp<1>(s, H, dq[1], g, j1);
+  euler_jvp<2>(s, H, dq[2], g, j2);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Qt[i] = -(j0[i] + j1[i] + j2[i]);
+}
+
+// Spatial slopes a_n, a_t1, a_t2 from <a_d.psi psi> = (dQ/dx_d)/rho, and the
+// time coefficient A from <(a_n u + a_t1 v + a_t2 w + A) psi> = 0 (Sec. 2.1),
+// i.e. <A psi> = Q_t / rho.
+template <class T>
+__device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Gas<T>& g, const T q[5],
+                                             const T dq[3][5], T a[3][5], T A[5]) {
+  const T inv = T(1) / s.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T b[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) b[i] = dq[d][i] * inv;
+    slope_solve(s, g, b, a[d]);
+  }
+  T Qt[5];
+  state_time_derivative(s, g.h_r + q[4] + s.dp, dq, g, Qt);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Qt[i] *= inv;
+  slope_solve(s, g, Qt, A);
+}
+
+// Non-equilibrium flux of the smooth BGK solution, -tau rho (<u (a.u) psi> +
+// <u A psi>), in its exact closed form: the Navier-Stokes viscous flux of the
+// BGK model with mu = tau p, stress mu (grad U + grad U^T) - 2 mu/(K+3) div U I
+// (bulk viscosity 2K/(3(K+3)) mu, Sec. 3.1), and heat flux -mu c_p dT/dn
+// with c_p = (K+5)/2; `heat_scale` multiplies the heat flux (1/Pr for the
+// Prandtl fix).
+template <class T>
+__device__ __forceinline__ void ns_viscous_flux(const Prim<T>& s, const T dq[3][5], const Gas<T>& g,
+                                                T mu, T heat_scale, T Fv[5]) {
+  const T inv = T(1) / s.rho;
+  const T U[3] = {s.U, s.V, s.W};
+  // du[j][i] = d u_i / d x_j (local frame) for the entries the normal row needs.
+  T du0[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) du0[i] = (dq[0][1 + i] - U[i] * dq[0][0]) * inv;
+  const T du10 = (dq[1][1] - U[0] * dq[1][0]) * inv, du11 = (dq[1][2] - U[1] * dq[1][0]) * inv;
+  const T du20 = (dq[2][1] - U[0] * dq[2][0]) * inv, du22 = (dq[2][3] - U[2] * dq[2][0]) * inv;
+  const T divU = du0[0] + du11 + du22;
+  const T q2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+  const T dp0 = g.gm1 * (dq[0][4] - U[0] * dq[0][1] - U[1] * dq[0][2] - U[2] * dq[0][3] +
+                         T(0.5) * q2 * dq[0][0]);
+  const T dT0 = (dp0 - s.theta * dq[0][0]) * inv;
+  const T s00 = mu * (T(2) * du0[0] - T(2) / (g.K + T(3)) * divU);
+  const T s01 = mu * (du0[1] + du10);
+  const T s02 = mu * (du0[2] + du20);
+  Fv[0] = T(0);
+  Fv[1] = -s00;
+  Fv[2] = -s01;
+  Fv[3] = -s02;
+  Fv[4] = -(s00 * U[0] + s01 * U[1] + s02 * U[2]) - heat_scale * mu * T(0.5) * (g.K + T(5)) * dT0;
+}
+
+template <class T>
+__device__ __forceinline__ T viscosity(const Prim<T>& s, const Gas<T>& g) {
+  if (g.visc_law == 1) return g.mu_ref * tpow(s.theta * g.T_ref_inv, g.visc_exp);
+  return g.mu_ref;
+}
+
 // Simplified smooth flux (Sec. 2.1, Remark 1): f = g0 [1 - tau (a.u + A) + t A],
-// F = rho0 [<u psi> - tau (<u (a.u) psi> + <u A psi>)], dF = rho0 <u A psi>.
-// Returns F - E(Q_ref) and dF.  want_F = false skips F (second S2O4 stage).
+// F = rho0 [<u psi> - tau (<u (a.u) psi> + <u A psi>)], dF = rho0 <u A psi>,
+// with tau = mu/p (Sec. 3).  Evaluated through the exact identities
+// rho0 <u psi> = Euler flux, -tau rho0 (<u(a.u)psi> + <u A psi>) = BGK
+// Navier-Stokes viscous flux, rho0 <u A psi> = J_n(Q0) Q_t.  The Prandtl fix
+// scales the heat flux by 1/Pr.  Returns F - E(Q_ref) and dF; want_F = false
+// skips F (second S2O4 stage).
 template <class T>
 __device__ __forceinline__ void flux_smooth(const PointState<T>& st0, const Gas<T>& g, bool want_F,
                                             T F[5], T dF[5]) {
   const Prim<T> s = prim_of(st0.q, g);
-  Mom<T> m;
-  moments(s, g, 0, m);
-  T a[3][5], A[5];
-  slopes_and_A(s, m, g, st0.dq, a, A);
-  T uA[5];
-  mom_apsi<1, 0, 0>(m, A, uA);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) dF[i] = s.rho * uA[i];
+  const T H = g.h_r + st0.q[4] + s.dp;
+  T Qt[5];
+  state_time_derivative(s, H, st0.dq, g, Qt);
+  euler_jvp<0>(s, H, Qt, g, dF);
   if (!want_F) return;
-  const T tau = collision_time(s, g);
-  T E[5], ua[5];
+  T E[5], Fv[5];
   euler_flux_dev(s, st0.q, g, E);
-  mom_u_adotu(m, a, ua);
+  ns_viscous_flux(s, st0.dq, g, viscosity(s, g), g.pr_fix + T(1), Fv);
 #pragma unroll
-  for (int i = 0; i < 5; ++i) F[i] = E[i] - tau * s.rho * (ua[i] + uA[i]);
-  F[4] -= g.pr_fix * tau * s.rho * heat_moment(s, g, a, A);
+  for (int i = 0; i < 5; ++i) F[i] = E[i] + Fv[i];
 }
 
 // Coefficients of the linear fit F(t) = F + dF t (Eq. (7)) of the six
@@ -305,37 +349,36 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
                                           const PointState<T>& st0, const Gas<T>& g, T dt,
                                           T F[5], T dF[5]) {
   T V[6][5];
-  T tau;
-  T q0h[5];  // heat-flux data of g0 for the Prandtl fix
-  T heat0;
+  T tau, mu0, dT0, p0;
   {
+    // Equilibrium part: V0 = rho0 <u psi> (Euler flux), V2 = rho0 <u A psi> =
+    // J_n Q_t, V1 = rho0 <u (a.u) psi> = -(viscous flux with mu = p, Pr = 1) - V2.
     const Prim<T> s = prim_of(st0.q, g);
-    Mom<T> m;
-    moments(s, g, 0, m);
-    T a[3][5], A[5];
-    slopes_and_A(s, m, g, st0.dq, a, A);
+    const T H = g.h_r + st0.q[4] + s.dp;
     euler_flux_dev(s, st0.q, g, V[0]);
-    T ua[5], uA[5];
-    mom_u_adotu(m, a, ua);
-    mom_apsi<1, 0, 0>(m, A, uA);
+    T Qt[5], Fv[5];
+    state_time_derivative(s, H, st0.dq, g, Qt);
+    euler_jvp<0>(s, H, Qt, g, V[2]);
+    ns_viscous_flux(s, st0.dq, g, s.p, T(1), Fv);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      V[1][i] = s.rho * ua[i];
-      V[2][i] = s.rho * uA[i];
-    }
-    tau = collision_time(s, g);
-    heat0 = s.rho * heat_moment(s, g, a, A);
-    (void)q0h;
+    for (int i = 0; i < 5; ++i) V[1][i] = -Fv[i] - V[2][i];
+    mu0 = viscosity(s, g);
+    p0 = s.p;
+    tau = mu0 / s.p;
+    // Normal temperature derivative for the Prandtl fix of the heat flux.
+    const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+    const T dp0 = g.gm1 * (st0.dq[0][4] - s.U * st0.dq[0][1] - s.V * st0.dq[0][2] -
+                           s.W * st0.dq[0][3] + T(0.5) * q2 * st0.dq[0][0]);
+    dT0 = (dp0 - s.theta * st0.dq[0][0]) / s.rho;
   }
   T pl, pr;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     const PointState<T>& st = side == 0 ? stl : str;
     const Prim<T> s = prim_of(st.q, g);
-    Mom<T> mf, mh;
-    moments(s, g, 0, mf);
+    Mom<T> mh;
     T a[3][5], A[5];
-    slopes_and_A(s, mf, g, st.dq, a, A);
+    slopes_and_A(s, g, st.q, st.dq, a, A);
     moments(s, g, side == 0 ? +1 : -1, mh);
     T u0[5], ua[5], uA[5];
     mom_psi<1, 0, 0>(mh, u0);
@@ -371,7 +414,9 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
     F[i] = f;
     dF[i] = df;
   }
-  F[4] -= g.pr_fix * tau * heat0;
+  // Prandtl fix: (1/Pr - 1) times the heat flux -tau rho0 <h (a.u + A)> =
+  // -tau p0 c_p dT/dn of the equilibrium part (tau includes the numerical term).
+  F[4] -= g.pr_fix * tau * p0 * (T(0.5) * (g.K + T(5))) * dT0;
 }
 
 // Equilibrium state of the compatibility condition, Q0 = int_{u>0} psi g_l +

@@ -1,0 +1,252 @@
+// Fused sweep kernel: for one direction d and one S2O4 stage, the face
+// fields, the tangential reconstruction to the 2x2 Gauss points and the BGK
+// flux there, for a 2D tile of faces marching along the normal.
+//
+// Tile: TP x TS faces in the transverse plane, P = the faster-varying
+// transverse axis in memory, S = the slower one; the CTA marches through a
+// chunk of faces f0..f1-1 along d (face f lies between cells f-1 and f).
+// Per face layer:
+//   phase 1  one thread per transverse point of the tile plus a halo of 2:
+//            the six cells f-3..f+2 along d (L1-cached loads), WENO5 end
+//            values of cells f-1 and f, the normal slopes, the compatibility
+//            state Q0 and its normal slope -> face fields in shared memory;
+//   phase 2  the tangential pass along t1 = d+1 for every point of the tile
+//            (halo 2 along t2): values at the two t1 Gauss abscissae, and
+//            t1-derivatives of the state fields -> shared memory;
+//   phase 3  the tangential pass along t2 = d+2 and the flux at each Gauss
+//            point; TPF threads per face, each with 4/TPF Gauss points,
+//            summed with weights 1/4 into the face flux, written to HBM.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace hgks {
+
+template <class T>
+struct SweepArgs {
+  const T* __restrict__ q;     // padded state (deviation)
+  T* __restrict__ fd;          // face fluxes [10][fbox]: F then dF, global frame
+  const T* __restrict__ wn;    // widths along d (offset kGhost)
+  const T* __restrict__ wt1;   // widths along t1
+  const T* __restrict__ wt2;   // widths along t2
+  const double* __restrict__ scal;
+  GridDev g;
+  int d;
+  int chunk;
+  Gas<T> gas;
+};
+
+template <int FLUX>
+struct SweepLayout {
+  static constexpr int NV = FLUX == FLUX_FULL ? 15 : 5;  // state field components
+  static constexpr int NFF = 2 * NV;                     // + their normal slopes
+  static constexpr int NT1 = 4 * NV + 2 * NV;            // t1 pass outputs
+};
+
+template <class T, int FLUX, int TP, int TS>
+constexpr size_t sweep_smem_bytes() {
+  constexpr int NH = (TP + 4) * (TS + 4);
+  constexpr int TPF = 256 / (TP * TS);
+  return sizeof(T) * ((SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH +
+                      (TPF - 1) * 10 * TP * TS);
+}
+
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
+  constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
+  constexpr int NV = SweepLayout<FLUX>::NV;
+  constexpr int NFF = SweepLayout<FLUX>::NFF;
+  constexpr int NFACE = TP * TS;
+  constexpr int TPF = 256 / NFACE;  // threads per face in phase 3
+  constexpr int GPF = 4 / TPF;      // Gauss points per thread
+  static_assert(TPF * NFACE == 256 && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ff = reinterpret_cast<T*>(smem_raw);  // [NFF][NH]
+  T* tb = ff + NFF * NH;                   // [NT1][NH]
+  T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
+
+  const int d = a.d;
+  const int P = d == 0 ? 1 : 0;
+  const int S = d == 2 ? 1 : 2;
+  const int t1 = (d + 1) % 3;
+  const bool t1P = (t1 == P);
+  const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
+  const int p0 = blockIdx.x * TP, s0 = blockIdx.y * TS;
+  const int f0 = blockIdx.z * a.chunk;
+  const int f1 = min(f0 + a.chunk, nd + 1);
+  const long long sd = d == 0 ? 1LL : (d == 1 ? (long long)a.g.p[0] : (long long)a.g.p[0] * a.g.p[1]);
+  const int tid = threadIdx.x;
+
+  // Phase-1 role: one transverse point of the halo'd tile.
+  const bool h_on = tid < NH;
+  const int hp = tid % HP, hs = tid / HP;
+  const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+  const bool h_valid = h_on && Pc <= nP + 1 && Sc <= nS + 1;
+  long long hbase = 0;
+  if (h_valid) {
+    int c[3];
+    c[d] = 0;
+    c[P] = Pc;
+    c[S] = Sc;
+    hbase = pad_index(a.g, c[0], c[1], c[2]);
+  }
+  int gv[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) gv[i] = global_var(d, i);
+
+  // Phase-3 role: one face and GPF Gauss points of it.
+  const int face = tid % NFACE, sub = tid / NFACE;
+  const int ip = face % TP, is = face / TP;
+  const bool f_valid = (p0 + ip < nP) && (s0 + is < nS);
+  const int cP = min(p0 + ip, nP - 1), cS = min(s0 + is, nS - 1);
+  const int ct1 = t1P ? cP : cS, ct2 = t1P ? cS : cP;
+  const T h1 = a.wt1[ct1 + kGhost], h2 = a.wt2[ct2 + kGhost];
+  const int at3 = (is + 2) * HP + (ip + 2);
+  const int st2 = t1P ? HP : 1;
+  const T dt = T(a.scal[0]);
+  const long long FS = (long long)(a.g.n[0] + (d == 0)) * (a.g.n[1] + (d == 1)) * (a.g.n[2] + (d == 2));
+  long long fout = 0;
+  {
+    int c[3];
+    c[d] = 0;
+    c[P] = cP;
+    c[S] = cS;
+    fout = ((long long)c[2] * (a.g.n[1] + (d == 1)) + c[1]) * (a.g.n[0] + (d == 0)) + c[0];
+  }
+  const long long fstep = d == 0 ? 1LL : (d == 1 ? (long long)a.g.n[0] : (long long)a.g.n[0] * a.g.n[1]);
+
+  for (int f = f0; f < f1; ++f) {
+    // ---------------- phase 1: face fields of the layer f ----------------
+    if (h_valid) {
+      const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
+      const long long cb = hbase + (long long)(f - 3) * sd;
+      T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const T* qv = a.q + gv[i] * a.g.P + cb;
+        const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd),
+                q3 = __ldg(qv + 3 * sd), q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
+        T Li, Ri, Lr, Rr;
+        weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
+        weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+        Ql[i] = Ri;
+        Qr[i] = Lr;
+        Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) / hl;
+        Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) / hr;
+        D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) / (T(6) * (hl + hr));
+      }
+      T Q0[5];
+      compat_dev(Ql, Qr, a.gas, Q0);
+      if constexpr (FLUX == FLUX_SMOOTH) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          ff[i * NH + tid] = Q0[i];
+          ff[(5 + i) * NH + tid] = D0[i];
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          ff[i * NH + tid] = Ql[i];
+          ff[(5 + i) * NH + tid] = Qr[i];
+          ff[(10 + i) * NH + tid] = Q0[i];
+          ff[(15 + i) * NH + tid] = Dl[i];
+          ff[(20 + i) * NH + tid] = Dr[i];
+          ff[(25 + i) * NH + tid] = D0[i];
+        }
+      }
+    } else if (h_on) {
+#pragma unroll 1
+      for (int k = 0; k < NFF; ++k) ff[k * NH + tid] = T(0);
+    }
+    __syncthreads();
+
+    // ---------------- phase 2: tangential pass along t1 ----------------
+    {
+      const int items = t1P ? TP * HS : HP * TS;
+      const int st1 = t1P ? 1 : HP;
+      for (int it = tid; it < items; it += 256) {
+        const int hp2 = t1P ? 2 + it % TP : it % HP;
+        const int hs2 = t1P ? it / TP : 2 + it / HP;
+        const int at = hs2 * HP + hp2;
+#pragma unroll 1
+        for (int k = 0; k < NV; ++k) {
+          const T* src = ff + k * NH + at;
+          T v[2], dd[2];
+          tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+          tb[(4 * k + 0) * NH + at] = v[0];
+          tb[(4 * k + 1) * NH + at] = v[1];
+          tb[(4 * k + 2) * NH + at] = dd[0];
+          tb[(4 * k + 3) * NH + at] = dd[1];
+        }
+#pragma unroll 1
+        for (int k = 0; k < NV; ++k) {
+          const T* src = ff + (NV + k) * NH + at;
+          T v[2];
+          tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
+          tb[(4 * NV + 2 * k + 0) * NH + at] = v[0];
+          tb[(4 * NV + 2 * k + 1) * NH + at] = v[1];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase 3: tangential pass along t2 and flux ----------------
+    T Fs[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) Fs[i] = T(0);
+#pragma unroll 1
+    for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
+      const int m1 = g & 1, m2 = g >> 1;
+      PointState<T> st[FLUX == FLUX_FULL ? 3 : 1];
+#pragma unroll
+      for (int s = 0; s < (FLUX == FLUX_FULL ? 3 : 1); ++s) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          const int k = 5 * s + i;
+          const T* sv = tb + (4 * k + m1) * NH + at3;
+          const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+          const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+          T v[2], dd[2];
+          tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+          st[s].q[i] = v[m2];
+          st[s].dq[2][i] = dd[m2] / h2;
+          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
+          st[s].dq[1][i] = v[m2] / h1;
+          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
+          st[s].dq[0][i] = v[m2];
+        }
+      }
+      T F[5], dF[5];
+      if constexpr (FLUX == FLUX_SMOOTH) {
+        flux_smooth(st[0], a.gas, STAGE == 1, F, dF);
+      } else {
+        flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
+      }
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        if (STAGE == 1) Fs[i] += F[i];
+        Fs[5 + i] += dF[i];
+      }
+    }
+    if (TPF > 1 && sub > 0) {
+#pragma unroll
+      for (int i = 0; i < 10; ++i) part[((sub - 1) * 10 + i) * NFACE + face] = Fs[i];
+    }
+    if (TPF > 1) __syncthreads();
+    if (sub == 0 && f_valid) {
+#pragma unroll
+      for (int r = 1; r < TPF; ++r)
+#pragma unroll
+        for (int i = 0; i < 10; ++i) Fs[i] += part[((r - 1) * 10 + i) * NFACE + face];
+      const long long o = fout + (long long)f * fstep;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        a.fd[gv[i] * FS + o] = T(0.25) * Fs[i];
+        a.fd[(5 + gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace hgks
