@@ -47,7 +47,8 @@ template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x
 
 template <class T>
 struct Prim {
-  T rho, U, V, W;  // density, local-frame velocity
+  T rho, inv_rho;  // density and its reciprocal
+  T U, V, W;       // local-frame velocity
   T dp, p;         // pressure deviation and pressure
   T lam, theta;    // lambda = rho/(2p), theta = 1/(2 lambda)
 };
@@ -58,6 +59,7 @@ __device__ __forceinline__ Prim<T> prim_of(const T dq[5], const Gas<T>& g) {
   Prim<T> s;
   s.rho = g.rho_r + dq[0];
   const T inv = T(1) / s.rho;
+  s.inv_rho = inv;
   s.U = dq[1] * inv;
   s.V = dq[2] * inv;
   s.W = dq[3] * inv;
@@ -206,7 +208,7 @@ struct PointState {
 template <int J, class T>
 __device__ __forceinline__ void euler_jvp(const Prim<T>& s, T H, const T dQ[5], const Gas<T>& g,
                                           T out[5]) {
-  const T inv = T(1) / s.rho;
+  const T inv = s.inv_rho;
   const T U[3] = {s.U, s.V, s.W};
   const T du[3] = {(dQ[1] - U[0] * dQ[0]) * inv, (dQ[2] - U[1] * dQ[0]) * inv,
                    (dQ[3] - U[2] * dQ[0]) * inv};
@@ -241,7 +243,7 @@ __device__ __forceinline__ void state_time_derivative(const Prim<T>& s, T H, con
 template <class T>
 __device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Gas<T>& g, const T q[5],
                                              const T dq[3][5], T a[3][5], T A[5]) {
-  const T inv = T(1) / s.rho;
+  const T inv = s.inv_rho;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     T b[5];
@@ -265,7 +267,7 @@ __device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Gas<T>& g, 
 template <class T>
 __device__ __forceinline__ void ns_viscous_flux(const Prim<T>& s, const T dq[3][5], const Gas<T>& g,
                                                 T mu, T heat_scale, T Fv[5]) {
-  const T inv = T(1) / s.rho;
+  const T inv = s.inv_rho;
   const T U[3] = {s.U, s.V, s.W};
   // du[j][i] = d u_i / d x_j (local frame) for the entries the normal row needs.
   T du0[3];
@@ -369,7 +371,7 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
     const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
     const T dp0 = g.gm1 * (st0.dq[0][4] - s.U * st0.dq[0][1] - s.V * st0.dq[0][2] -
                            s.W * st0.dq[0][3] + T(0.5) * q2 * st0.dq[0][0]);
-    dT0 = (dp0 - s.theta * st0.dq[0][0]) / s.rho;
+    dT0 = (dp0 - s.theta * st0.dq[0][0]) * s.inv_rho;
   }
   T pl, pr;
 #pragma unroll
@@ -429,7 +431,7 @@ __device__ __forceinline__ void sign_moments(const T dq[5], const Gas<T>& g, T S
   const T sl = tsqrt(s.lam);
   const T x = sl * s.U;
   const T D0 = terf(x);
-  const T D1 = s.U * D0 + texp(-x * x) * T(0.5641895835477563) / sl;  // 1/sqrt(pi)
+  const T D1 = s.U * D0 + texp(-x * x) * T(0.5641895835477563) * tsqrt(s.theta + s.theta);  // 1/sqrt(pi lam)
   const T D2 = s.U * D1 + s.theta * D0;
   S[0] = s.rho * D0;
   S[1] = s.rho * D1;

@@ -51,8 +51,14 @@ constexpr size_t sweep_smem_bytes() {
                       (TPF - 1) * 10 * TP * TS);
 }
 
+// Resident CTAs per SM the register budget is sized for: the smooth FP32
+// sweep fits three (shared memory allows three as well), the others one or two.
+template <class T, int FLUX> struct SweepOccupancy { static constexpr int value = 1; };
+template <> struct SweepOccupancy<float, FLUX_SMOOTH> { static constexpr int value = 3; };
+template <> struct SweepOccupancy<double, FLUX_SMOOTH> { static constexpr int value = 2; };
+
 template <class T, int MODE, int FLUX, int STAGE, int TP, int TS>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(SweepArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
   constexpr int NV = SweepLayout<FLUX>::NV;
   constexpr int NFF = SweepLayout<FLUX>::NFF;
@@ -100,7 +106,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
   const bool f_valid = (p0 + ip < nP) && (s0 + is < nS);
   const int cP = min(p0 + ip, nP - 1), cS = min(s0 + is, nS - 1);
   const int ct1 = t1P ? cP : cS, ct2 = t1P ? cS : cP;
-  const T h1 = a.wt1[ct1 + kGhost], h2 = a.wt2[ct2 + kGhost];
+  const T rh1 = T(1) / a.wt1[ct1 + kGhost], rh2 = T(1) / a.wt2[ct2 + kGhost];
   const int at3 = (is + 2) * HP + (ip + 2);
   const int st2 = t1P ? HP : 1;
   const T dt = T(a.scal[0]);
@@ -119,6 +125,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
     // ---------------- phase 1: face fields of the layer f ----------------
     if (h_valid) {
       const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
+      const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
       const long long cb = hbase + (long long)(f - 3) * sd;
       T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
 #pragma unroll
@@ -131,9 +138,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
         weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
         Ql[i] = Ri;
         Qr[i] = Lr;
-        Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) / hl;
-        Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) / hr;
-        D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) / (T(6) * (hl + hr));
+        Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
+        Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
+        D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
       }
       T Q0[5];
       compat_dev(Ql, Qr, a.gas, Q0);
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
         const int at = hs2 * HP + hp2;
-#pragma unroll 1
+#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
         for (int k = 0; k < NV; ++k) {
           const T* src = ff + k * NH + at;
           T v[2], dd[2];
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
           tb[(4 * k + 2) * NH + at] = dd[0];
           tb[(4 * k + 3) * NH + at] = dd[1];
         }
-#pragma unroll 1
+#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
         for (int k = 0; k < NV; ++k) {
           const T* src = ff + (NV + k) * NH + at;
           T v[2];
@@ -194,38 +201,74 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
     T Fs[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) Fs[i] = T(0);
+    if constexpr (FLUX == FLUX_SMOOTH && TPF <= 2) {
+      // One pass along t2 gives both t2 abscissae: each thread takes one (or
+      // both) t1 abscissae m1 and evaluates the flux at (m1, 0) and (m1, 1).
 #pragma unroll 1
-    for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
-      const int m1 = g & 1, m2 = g >> 1;
-      PointState<T> st[FLUX == FLUX_FULL ? 3 : 1];
-#pragma unroll
-      for (int s = 0; s < (FLUX == FLUX_FULL ? 3 : 1); ++s) {
+      for (int m1 = (TPF == 2 ? sub : 0); m1 < (TPF == 2 ? sub + 1 : 2); ++m1) {
+        PointState<T> st[2];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-          const int k = 5 * s + i;
-          const T* sv = tb + (4 * k + m1) * NH + at3;
-          const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-          const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-          T v[2], dd[2];
+          const T* sv = tb + (4 * i + m1) * NH + at3;
+          const T* sdv = tb + (4 * i + 2 + m1) * NH + at3;
+          const T* ss = tb + (4 * NV + 2 * i + m1) * NH + at3;
+          T v[2], dd[2], vd[2], vs[2];
           tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-          st[s].q[i] = v[m2];
-          st[s].dq[2][i] = dd[m2] / h2;
-          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
-          st[s].dq[1][i] = v[m2] / h1;
-          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
-          st[s].dq[0][i] = v[m2];
+          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
+          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
+#pragma unroll
+          for (int m2 = 0; m2 < 2; ++m2) {
+            st[m2].q[i] = v[m2];
+            st[m2].dq[0][i] = vs[m2];
+            st[m2].dq[1][i] = vd[m2] * rh1;
+            st[m2].dq[2][i] = dd[m2] * rh2;
+          }
+        }
+#pragma unroll
+        for (int m2 = 0; m2 < 2; ++m2) {
+          T F[5], dF[5];
+          flux_smooth(st[m2], a.gas, STAGE == 1, F, dF);
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            if (STAGE == 1) Fs[i] += F[i];
+            Fs[5 + i] += dF[i];
+          }
         }
       }
-      T F[5], dF[5];
-      if constexpr (FLUX == FLUX_SMOOTH) {
-        flux_smooth(st[0], a.gas, STAGE == 1, F, dF);
-      } else {
-        flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
-      }
+    } else {
+#pragma unroll 1
+      for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
+        const int m1 = g & 1, m2 = g >> 1;
+        PointState<T> st[FLUX == FLUX_FULL ? 3 : 1];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        if (STAGE == 1) Fs[i] += F[i];
-        Fs[5 + i] += dF[i];
+        for (int s = 0; s < (FLUX == FLUX_FULL ? 3 : 1); ++s) {
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            const int k = 5 * s + i;
+            const T* sv = tb + (4 * k + m1) * NH + at3;
+            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+            T v[2], dd[2];
+            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+            st[s].q[i] = v[m2];
+            st[s].dq[2][i] = dd[m2] * rh2;
+            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
+            st[s].dq[1][i] = v[m2] * rh1;
+            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
+            st[s].dq[0][i] = v[m2];
+          }
+        }
+        T F[5], dF[5];
+        if constexpr (FLUX == FLUX_SMOOTH) {
+          flux_smooth(st[0], a.gas, STAGE == 1, F, dF);
+        } else {
+          flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          if (STAGE == 1) Fs[i] += F[i];
+          Fs[5 + i] += dF[i];
+        }
       }
     }
     if (TPF > 1 && sub > 0) {
