@@ -58,12 +58,16 @@ cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe) {
 // Tile of the sweep kernel per precision and flux: TP x TS faces, sized so
 // that the shared-memory staging fits and every tile gives 1, 2 or 4 threads
 // per face.
-template <class T, int FLUX> struct SweepTile { static constexpr int TP = 16, TS = 8; };
-template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8; };
+// NL face layers share one face-field pass (phase 1).
+template <class T, int FLUX> struct SweepTile { static constexpr int TP = 16, TS = 8, NL = 4; };
+template <> struct SweepTile<float, FLUX_FULL> { static constexpr int TP = 16, TS = 8, NL = 2; };
+template <> struct SweepTile<double, FLUX_SMOOTH> { static constexpr int TP = 16, TS = 8, NL = 2; };
+template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NL = 2; };
 
 template <class T, int MODE, int FLUX, int STAGE>
 cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   constexpr int TP = SweepTile<T, FLUX>::TP, TS = SweepTile<T, FLUX>::TS;
+  constexpr int NL = SweepTile<T, FLUX>::NL;
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
   a.q = q;
@@ -81,11 +85,12 @@ cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   const int layers = g.n[d] + 1;
   const int want_chunks = (4 * e.sms + gx * gy - 1) / (gx * gy);
   int chunk = (layers + want_chunks - 1) / want_chunks;
-  if (chunk < 8) chunk = 8;
+  if (chunk < 2 * NL) chunk = 2 * NL;
+  chunk = (chunk + NL - 1) / NL * NL;
   a.chunk = chunk;
   const int gz = (layers + chunk - 1) / chunk;
-  constexpr size_t smem = sweep_smem_bytes<T, FLUX, TP, TS>();
-  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS>;
+  constexpr size_t smem = sweep_smem_bytes<T, FLUX, TP, TS, NL>();
+  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<dim3(gx, gy, gz), 256, smem, e.stream>>>(a);

@@ -43,11 +43,11 @@ struct SweepLayout {
   static constexpr int NT1 = 4 * NV + 2 * NV;            // t1 pass outputs
 };
 
-template <class T, int FLUX, int TP, int TS>
+template <class T, int FLUX, int TP, int TS, int NL>
 constexpr size_t sweep_smem_bytes() {
   constexpr int NH = (TP + 4) * (TS + 4);
   constexpr int TPF = 256 / (TP * TS);
-  return sizeof(T) * ((SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH +
+  return sizeof(T) * ((NL * SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH +
                       (TPF - 1) * 10 * TP * TS);
 }
 
@@ -57,7 +57,7 @@ template <class T, int FLUX> struct SweepOccupancy { static constexpr int value 
 template <> struct SweepOccupancy<float, FLUX_SMOOTH> { static constexpr int value = 3; };
 template <> struct SweepOccupancy<double, FLUX_SMOOTH> { static constexpr int value = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS>
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
 __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(SweepArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
   constexpr int NV = SweepLayout<FLUX>::NV;
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   constexpr int GPF = 4 / TPF;      // Gauss points per thread
   static_assert(TPF * NFACE == 256 && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ff = reinterpret_cast<T*>(smem_raw);  // [NFF][NH]
-  T* tb = ff + NFF * NH;                   // [NT1][NH]
+  T* ffb = reinterpret_cast<T*>(smem_raw);  // [NL][NFF][NH]
+  T* tb = ffb + NL * NFF * NH;              // [NT1][NH]
   T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
 
   const int d = a.d;
@@ -83,19 +83,6 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   const long long sd = d == 0 ? 1LL : (d == 1 ? (long long)a.g.p[0] : (long long)a.g.p[0] * a.g.p[1]);
   const int tid = threadIdx.x;
 
-  // Phase-1 role: one transverse point of the halo'd tile.
-  const bool h_on = tid < NH;
-  const int hp = tid % HP, hs = tid / HP;
-  const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
-  const bool h_valid = h_on && Pc <= nP + 1 && Sc <= nS + 1;
-  long long hbase = 0;
-  if (h_valid) {
-    int c[3];
-    c[d] = 0;
-    c[P] = Pc;
-    c[S] = Sc;
-    hbase = pad_index(a.g, c[0], c[1], c[2]);
-  }
   int gv[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) gv[i] = global_var(d, i);
@@ -121,52 +108,71 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   }
   const long long fstep = d == 0 ? 1LL : (d == 1 ? (long long)a.g.n[0] : (long long)a.g.n[0] * a.g.n[1]);
 
-  for (int f = f0; f < f1; ++f) {
-    // ---------------- phase 1: face fields of the layer f ----------------
-    if (h_valid) {
-      const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
-      const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
-      const long long cb = hbase + (long long)(f - 3) * sd;
-      T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        const T* qv = a.q + gv[i] * a.g.P + cb;
-        const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd),
-                q3 = __ldg(qv + 3 * sd), q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
-        T Li, Ri, Lr, Rr;
-        weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
-        weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
-        Ql[i] = Ri;
-        Qr[i] = Lr;
-        Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
-        Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
-        D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
-      }
-      T Q0[5];
-      compat_dev(Ql, Qr, a.gas, Q0);
-      if constexpr (FLUX == FLUX_SMOOTH) {
+  for (int fb = f0; fb < f1; fb += NL) {
+    // ---------------- phase 1: face fields of layers fb .. fb+NL-1 ----------------
+    // Items (layer, transverse point of the tile plus a halo of 2).  For d = x
+    // consecutive threads take consecutive layers, so that the loads along x
+    // are coalesced; otherwise consecutive transverse points along P (= x).
+    for (int it = tid; it < NL * NH; it += 256) {
+      const int l = d == 0 ? it % NL : it / NH;
+      const int h = d == 0 ? it / NL : it % NH;
+      const int f = fb + l;
+      const int hp = h % HP, hs = h / HP;
+      const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+      T* ff = ffb + l * NFF * NH;
+      if (f < f1 && Pc <= nP + 1 && Sc <= nS + 1) {
+        int c[3];
+        c[d] = f - 3;
+        c[P] = Pc;
+        c[S] = Sc;
+        const long long cb = pad_index(a.g, c[0], c[1], c[2]);
+        const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
+        const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
+        T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-          ff[i * NH + tid] = Q0[i];
-          ff[(5 + i) * NH + tid] = D0[i];
+          const T* qv = a.q + gv[i] * a.g.P + cb;
+          const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd),
+                  q3 = __ldg(qv + 3 * sd), q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
+          T Li, Ri, Lr, Rr;
+          weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
+          weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+          Ql[i] = Ri;
+          Qr[i] = Lr;
+          Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
+          Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
+          D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
+        }
+        T Q0[5];
+        compat_dev(Ql, Qr, a.gas, Q0);
+        if constexpr (FLUX == FLUX_SMOOTH) {
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            ff[i * NH + h] = Q0[i];
+            ff[(5 + i) * NH + h] = D0[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            ff[i * NH + h] = Ql[i];
+            ff[(5 + i) * NH + h] = Qr[i];
+            ff[(10 + i) * NH + h] = Q0[i];
+            ff[(15 + i) * NH + h] = Dl[i];
+            ff[(20 + i) * NH + h] = Dr[i];
+            ff[(25 + i) * NH + h] = D0[i];
+          }
         }
       } else {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          ff[i * NH + tid] = Ql[i];
-          ff[(5 + i) * NH + tid] = Qr[i];
-          ff[(10 + i) * NH + tid] = Q0[i];
-          ff[(15 + i) * NH + tid] = Dl[i];
-          ff[(20 + i) * NH + tid] = Dr[i];
-          ff[(25 + i) * NH + tid] = D0[i];
-        }
-      }
-    } else if (h_on) {
 #pragma unroll 1
-      for (int k = 0; k < NFF; ++k) ff[k * NH + tid] = T(0);
+        for (int k = 0; k < NFF; ++k) ff[k * NH + h] = T(0);
+      }
     }
     __syncthreads();
 
+#pragma unroll 1
+  for (int l = 0; l < NL && fb + l < f1; ++l) {
+    const int f = fb + l;
+    const T* ff = ffb + l * NFF * NH;
     // ---------------- phase 2: tangential pass along t1 ----------------
     {
       const int items = t1P ? TP * HS : HP * TS;
@@ -289,6 +295,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
       }
     }
     __syncthreads();
+  }
   }
 }
 
