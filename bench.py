@@ -35,10 +35,14 @@ N_GRID = 256
 PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.09 s/step
 METRIC = "Mcell-updates/s per S2O4 step"
 LAUNCHES_PER_STEP = 23  # cfl, dt, 2 x (3 ghost + 3 x (face fields + flux) + update), time
-# Executed FP32 operations (add, mul, 2 x fma) per Gauss point of the flux
-# kernel, counted by ncu on TG 64^3 (profiles/flux_kernel_taylor_green.md);
-# None until counted.
-FLOPS_PER_GAUSS_POINT = {"stage1": None, "stage2": None}
+# Executed FP32 operations (fadd + fmul + 2 ffma) per face of the stage-1
+# sweep kernel (FP32, linear WENO5, smooth flux), mean of the three directions,
+# counted by ncu on Taylor-Green 128^3 (profiles/k_sweep_fp32_smooth_taylor_green_128.md);
+# the tiles are the same at 256^3, so the count per face carries over.
+FLOPS_PER_FACE_STAGE1 = 2707.0
+# DRAM bytes (read + write) per face of the same kernel in that capture, mean
+# of the three directions; scaled to a 256^3 launch by its face count.
+DRAM_BYTES_PER_FACE_STAGE1 = (163.8 + 143.9 + 48.8 + 39.8 + 49.0 + 39.0) * 1e6 / 3 / (129 * 128 * 128)
 
 
 def load_peaks():
@@ -258,18 +262,21 @@ def run_ours(args, rank: int, world: int):
 
     peaks = load_peaks()
     sm_clock = clocks.summary()
-    faces = 3 * (N_GRID + 1) * N_GRID * N_GRID
+    faces_per_launch = (N_GRID + 1) * N_GRID * N_GRID
     flux_ms = prof["flux_stage1"] / 3.0  # average launch duration of the dominant kernel
-    f1 = FLOPS_PER_GAUSS_POINT["stage1"]
     sms, lanes = 152, 128
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = sms * lanes * 2 * clock_mhz * 1e6 / 1e12
-    achieved = (f1 * 4 * faces / 3) / (flux_ms * 1e-3) / 1e12 if f1 else None
-    roofline = {"bound": "alu", "kernel": "k_gauss_flux (stage 1, FP32)",
+    achieved = FLOPS_PER_FACE_STAGE1 * faces_per_launch / (flux_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_sweep stage 1 (FP32, linear WENO5, smooth flux)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops if achieved else None, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (nominal)",
-                "launch_ms": flux_ms, "kernel_ms_per_step": prof}
+                "frac": achieved / peak_tflops,
+                "traffic": DRAM_BYTES_PER_FACE_STAGE1 * faces_per_launch,
+                "flops_per_launch": FLOPS_PER_FACE_STAGE1 * faces_per_launch,
+                "peak_source": f"nominal: 152 SMs x 128 FP32 lanes x 2 flops x {clock_mhz:.0f} MHz",
+                "launch_ms": flux_ms, "kernel_ms_per_step": prof,
+                "hbm_frac": DRAM_BYTES_PER_FACE_STAGE1 * faces_per_launch / (flux_ms * 1e-3)
+                / (peaks.get("hbm_gbs", 6802.0) * 1e9)}
     cpu_rate, cpu_s = oracle_sample(2)
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
