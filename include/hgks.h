@@ -132,6 +132,27 @@ hgks_status hgks_diagnostics(hgks_ctx* ctx, hgks_diag* out);
  * 5 update (2 launches).  dt as in hgks_step.  Synchronises. */
 hgks_status hgks_profile_step(hgks_ctx* ctx, double dt, double* ms_out, int nclass);
 
+/* Advance nsteps S2O4 steps of the conservative state cons_inout (DEVICE
+ * pointer, FP64 [5][nz][ny][nx]) in place, without allocating any device
+ * memory.  This is for callers that cannot call cudaMalloc (a host framework
+ * that owns all device allocations, a context whose memory footprint must
+ * not grow, a path that must not synchronise the device as an allocation
+ * may).  No counterpart in the paper: it is the step of hgks_step with its
+ * working buffers in one scratch array of fixed size (about 15 MiB) that is
+ * part of the library image; every GPU that loads the library holds it until
+ * the process exits.  Limits: at most 32 cells on every axis (larger grids
+ * return E_UNSUPPORTED); cfg must be valid (else E_INVAL).  dt > 0 fixes the
+ * step, dt <= 0 takes the CFL step.  Work is enqueued on `stream` (a
+ * cudaStream_t; NULL is the legacy default stream) and the call returns
+ * without waiting; no non-physical-state check is made.  The first call on a
+ * device looks up the scratch array's device address with that device
+ * current; make it before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and corrupt each other.  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_inout, int nsteps, double dt,
+                              void* stream);
+
 /* Message of the last failed call on ctx ("" if none); valid until the next
  * call on ctx.  ctx may be NULL for errors of hgks_create. */
 const char* hgks_last_error(const hgks_ctx* ctx);

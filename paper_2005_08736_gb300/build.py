@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhgks.so")
-SOURCES = ["hgks_api.cu", "kernels_f32.cu", "kernels_f64.cu"]
+SOURCES = ["hgks_api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

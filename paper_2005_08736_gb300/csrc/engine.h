@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "../../include/hgks.h"
 
 namespace hgks {
@@ -72,8 +74,12 @@ template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
 template <class T> cudaError_t enqueue_diag(const Engine& e);
 template <class T> cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative);
 template <class T> cudaError_t enqueue_to_fp64(const Engine& e, double* dst);
+cudaError_t enqueue_reset_scalars(const Engine& e);
 cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed);
 cudaError_t enqueue_advance_time(const Engine& e);
+
+// Empty string if cfg is a valid problem statement, else the reason.
+std::string validate_config(const hgks_config& cfg);
 
 // Sizes (in elements) of the per-direction face buffers.
 long long face_flux_elems(const Engine& e, int d);

@@ -40,7 +40,9 @@ hgks_status cuda_fail(hgks_ctx* c, cudaError_t e, const char* where) {
 
 size_t elem_size(const hgks_config& c) { return c.prec == HGKS_FP32 ? 4 : 8; }
 
-std::string validate(const hgks_config& c) {
+}  // namespace
+
+std::string hgks::validate_config(const hgks_config& c) {
   if (c.nx < 6 || c.ny < 6 || c.nz < 6) return "every axis needs at least 6 cells";
   if (!(c.gamma > 1.0)) return "gamma must exceed 1";
   if (!(c.prandtl > 0.0)) return "Prandtl number must be positive";
@@ -60,6 +62,8 @@ std::string validate(const hgks_config& c) {
   if (!(c.tau_num_C >= 0.0)) return "tau_num_C must be non-negative";
   return "";
 }
+
+namespace {
 
 // Cell widths along each axis including 3 ghost cells per side: uniform, or
 // the y mapping of Sec. 3.3 with ghost widths mirrored across the walls.
@@ -149,6 +153,11 @@ static __global__ void k_reset_scalars(double* scal, unsigned long long* dtmin, 
   *flag = 0;
 }
 
+cudaError_t enqueue_reset_scalars(const Engine& e) {
+  k_reset_scalars<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.flag);
+  return cudaGetLastError();
+}
+
 cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed) {
   k_set_dt<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.cfg.cfl, dt_fixed);
   return cudaGetLastError();
@@ -190,7 +199,7 @@ hgks_status hgks_default_config(hgks_config* cfg, int n) {
 hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   if (!cfg || !out) return fail(nullptr, HGKS_E_INVAL, "null argument");
   *out = nullptr;
-  const std::string why = validate(*cfg);
+  const std::string why = hgks::validate_config(*cfg);
   if (!why.empty()) return fail(nullptr, HGKS_E_INVAL, why);
   hgks_ctx* c = new hgks_ctx();
   hgks::Engine& e = c->e;
