@@ -123,6 +123,19 @@ typedef struct {
 /* FP64 reductions of the current state (synchronises). */
 hgks_status hgks_diagnostics(hgks_ctx* ctx, hgks_diag* out);
 
+/* Adjoint of one S2O4 step (no counterpart in the paper): with the context's
+ * state at Q^n (set it with hgks_init_conservative, e.g. from a checkpoint)
+ * and dt the forward step's dt (frozen, > 0), write
+ *   adj_out = (dQ^{n+1}/dQ^n)^T adj_in,
+ * the vector-Jacobian product of the step map Q^n -> Q^{n+1} of Eq. (6) in
+ * the context's scheme and precision.  adj_in, adj_out: DEVICE FP64 arrays
+ * [5][nz][ny][nx] of cotangents of the conservative variables (may not
+ * alias).  The state is left unchanged.  Conventions where the scheme is not
+ * differentiable: d|x|/dx = sign(x), sign(0) = 0.  Periodic boundaries and no
+ * body force only (else E_UNSUPPORTED).  Allocates its work buffers on the
+ * first call.  Enqueued on the context's stream; does not synchronise. */
+hgks_status hgks_adjoint_step(hgks_ctx* ctx, double dt, const double* adj_in, double* adj_out);
+
 /* Profiling aid (not on the hot path): advance ONE step without the graph,
  * with CUDA events around every kernel launch on the context's stream, and
  * write the summed device time in milliseconds of each kernel class to

@@ -1,0 +1,477 @@
+// Adjoint (vector-Jacobian product) of one stage evaluation of the HGKS
+// operator: given cotangents w_L, w_dL of L(Q) and dL(Q)/dt on the cells,
+// accumulate sum_c (w_L . dL_c/dQ + w_dL . d(dL_c)/dQ) into a padded cotangent
+// buffer.  There is no counterpart in the paper (its scheme has no adjoint);
+// the step's adjoint is assembled from two such evaluations in hgks_api.cu.
+//
+// The kernel mirrors the forward sweep (sweep.cuh) tile by tile and layer by
+// layer.  For each face layer it first recomputes the face fields and the t1
+// pass into shared memory, then runs the reverse:
+//   R3  per Gauss point: the cotangent of the face flux from the divergence
+//       (Eq. (4)), the vector-Jacobian product of the flux at the point, and
+//       the transposed t2 pass, accumulated into shared memory;
+//   R2  the transposed t1 pass into face-field cotangents;
+//   R1  per transverse point: the compatibility state, the normal slopes and
+//       the WENO5 pairs transposed, scattered into the cells f-3 .. f+2 with
+//       atomics.
+// The Jacobians of the point-wise nonlinear maps (flux, compatibility state,
+// WENO5 end values and tangential polynomials) are formed by forward-mode dual
+// numbers through the same device functions as the forward sweep, one input
+// direction at a time.  Ghost cells collect cotangents like interior cells;
+// k_fold_ghosts returns them to their periodic images afterwards.
+#pragma once
+
+#include "dual.cuh"
+#include "sweep.cuh"
+
+namespace hgks {
+
+// cot[j] += sum_m gv[m] dv[m]/df_j + gd[m] dd[m]/df_j for the tangential
+// polynomial of the five averages f.
+template <int MODE, class T>
+__device__ __forceinline__ void tangential_vjp(const T f[5], const T gv[2], const T gd[2],
+                                               T cot[5]) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    Dual<T> x[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) x[k] = Dual<T>(f[k], T(k == j ? 1 : 0));
+    Dual<T> v[2], dd[2];
+    tangential<MODE>(x[0], x[1], x[2], x[3], x[4], v, dd);
+    cot[j] += gv[0] * v[0].d + gv[1] * v[1].d + gd[0] * dd[0].d + gd[1] * dd[1].d;
+  }
+}
+
+// cot[j] += gL dqL/dq_j + gR dqR/dq_j for the WENO5 end values of the centre cell.
+template <int MODE, class T>
+__device__ __forceinline__ void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5]) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    Dual<T> x[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) x[k] = Dual<T>(q[k], T(k == j ? 1 : 0));
+    Dual<T> L, R;
+    weno5_pair<MODE>(x[0], x[1], x[2], x[3], x[4], L, R);
+    cot[j] += gL * L.d + gR * R.d;
+  }
+}
+
+// (cl, cr) += J^T g0 for the compatibility state Q0(Q_l, Q_r).
+template <class T>
+__device__ __forceinline__ void compat_vjp(const T ql[5], const T qr[5], const T g0[5],
+                                           const Gas<T>& gas, T cl[5], T cr[5]) {
+  const Gas<Dual<T>> gd = dual_gas(gas);
+#pragma unroll 1
+  for (int j = 0; j < 10; ++j) {
+    Dual<T> xl[5], xr[5], out[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      xl[k] = Dual<T>(ql[k], T(j == k ? 1 : 0));
+      xr[k] = Dual<T>(qr[k], T(j == 5 + k ? 1 : 0));
+    }
+    compat_dev(xl, xr, gd, out);
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s += g0[i] * out[i].d;
+    if (j < 5) cl[j] += s; else cr[j - 5] += s;
+  }
+}
+
+// Cotangents of the reconstructed Gauss-point states (value and the three
+// derivatives of each of NS states) from the flux cotangents (gF, gdF).
+template <class T, int FLUX>
+__device__ __forceinline__ void flux_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
+                                         bool want_F, const T gF[5], const T gdF[5],
+                                         PointState<T>* cot) {
+  constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
+  const Gas<Dual<T>> gd = dual_gas(gas);
+#pragma unroll 1
+  for (int j = 0; j < 20 * NS; ++j) {
+    PointState<Dual<T>> x[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        x[s].q[i] = Dual<T>(st[s].q[i], T(j == 20 * s + i ? 1 : 0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          x[s].dq[c][i] = Dual<T>(st[s].dq[c][i], T(j == 20 * s + 5 + 5 * c + i ? 1 : 0));
+      }
+    Dual<T> F[5], dF[5];
+    if constexpr (FLUX == FLUX_SMOOTH) {
+      flux_smooth(x[0], gd, want_F, F, dF);
+      if (!want_F)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) F[i] = Dual<T>(T(0));
+    } else {
+      flux_full(x[0], x[NS > 1 ? 1 : 0], x[NS > 2 ? 2 : 0], gd, Dual<T>(dt), F, dF);
+    }
+    T sdot = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) sdot += gF[i] * F[i].d + gdF[i] * dF[i].d;
+    const int s = j / 20, r = j % 20;
+    if (r < 5) cot[s].q[r] += sdot;
+    else cot[s].dq[(r - 5) / 5][(r - 5) % 5] += sdot;
+  }
+}
+
+template <class T>
+struct AdjArgs {
+  const T* __restrict__ q;      // padded state (deviation) with ghost cells filled
+  const T* __restrict__ wL;     // cotangent of L, [5][N] (null: zero)
+  const T* __restrict__ wdL;    // cotangent of dL/dt, [5][N]
+  T* __restrict__ acc;          // padded cotangent of the state, [5][P], accumulated
+  const T* __restrict__ wn;
+  const T* __restrict__ wt1;
+  const T* __restrict__ wt2;
+  const double* __restrict__ scal;
+  GridDev g;
+  int d;
+  int chunk;
+  Gas<T> gas;
+};
+
+template <class T, int FLUX, int TP, int TS>
+constexpr size_t adj_smem_bytes() {
+  constexpr int NH = (TP + 4) * (TS + 4);
+  return sizeof(T) * 2 * (SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH;
+}
+
+template <class T, int MODE, int FLUX, int TP, int TS, int NT>
+__global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
+  constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
+  constexpr int NV = SweepLayout<FLUX>::NV;
+  constexpr int NFF = SweepLayout<FLUX>::NFF;
+  constexpr int NT1 = SweepLayout<FLUX>::NT1;
+  constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
+  constexpr int NFACE = TP * TS;
+  constexpr int TPF = NT / NFACE;
+  constexpr int GPF = 4 / TPF;
+  static_assert(TPF * NFACE == NT && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ff = reinterpret_cast<T*>(smem_raw);  // [NFF][NH] face fields
+  T* tb = ff + NFF * NH;                   // [NT1][NH] t1 pass
+  T* tbc = tb + NT1 * NH;                  // [NT1][NH] cotangents of the t1 pass
+  T* ffc = tbc + NT1 * NH;                 // [NFF][NH] cotangents of the face fields
+
+  const int d = a.d;
+  const SweepAxes ax = sweep_axes(d, a.g);
+  const int P = ax.P, S = ax.S;
+  const bool t1P = ax.t1P;
+  const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
+  const int p0 = blockIdx.x * TP, s0 = blockIdx.y * TS;
+  const int f0 = blockIdx.z * a.chunk;
+  const int f1 = min(f0 + a.chunk, nd + 1);
+  const int tid = threadIdx.x;
+  const T dt = T(a.scal[0]);
+
+  const int face = tid % NFACE, sub = tid / NFACE;
+  const int ip = face % TP, is = face / TP;
+  const bool f_valid = (p0 + ip < nP) && (s0 + is < nS);
+  const int cP = min(p0 + ip, nP - 1), cS = min(s0 + is, nS - 1);
+  const int ct1 = t1P ? cP : cS, ct2 = t1P ? cS : cP;
+  const T rh1 = T(1) / a.wt1[ct1 + kGhost], rh2 = T(1) / a.wt2[ct2 + kGhost];
+  const int at3 = (is + 2) * HP + (ip + 2);
+  const int st2 = t1P ? HP : 1;
+  const int st1 = t1P ? 1 : HP;
+
+  for (int f = f0; f < f1; ++f) {
+    // ---------------- forward: face fields, t1 pass ----------------
+    for (int h = tid; h < NH; h += NT) {
+      const int hp = h % HP, hs = h / HP;
+      const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+      if (Pc <= nP + 1 && Sc <= nS + 1) {
+        face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc, Sc, h, ff);
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < NFF; ++k) ff[k * NH + h] = T(0);
+      }
+#pragma unroll 1
+      for (int k = 0; k < NFF; ++k) ffc[k * NH + h] = T(0);
+    }
+    for (int i = tid; i < NT1 * NH; i += NT) tbc[i] = T(0);
+    __syncthreads();
+    {
+      const int items = t1P ? TP * HS : HP * TS;
+      for (int it = tid; it < items; it += NT) {
+        const int hp2 = t1P ? 2 + it % TP : it % HP;
+        const int hs2 = t1P ? it / TP : 2 + it / HP;
+        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1);
+      }
+    }
+    __syncthreads();
+
+    // ---------------- R3: flux VJP and transposed t2 pass ----------------
+    if (f_valid) {
+      // Face-flux cotangents from L_c = -(F_{c+1/2} - F_{c-1/2}) / h_c: the face
+      // f is the right face of cell f-1 and the left face of cell f.
+      T gF[5], gdF[5];
+      {
+        T cF[5] = {0, 0, 0, 0, 0}, cdF[5] = {0, 0, 0, 0, 0};
+        int c[3];
+        c[P] = cP;
+        c[S] = cS;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int cell = f - 1 + side;
+          if (cell < 0 || cell >= nd) continue;
+          c[d] = cell;
+          const long long ci = ((long long)c[2] * a.g.n[1] + c[1]) * a.g.n[0] + c[0];
+          const T sgn = side == 0 ? T(-1) : T(1);
+          const T r = sgn / a.wn[cell + kGhost];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            if (a.wL) cF[v] += r * a.wL[v * a.g.N + ci];
+            cdF[v] += r * a.wdL[v * a.g.N + ci];
+          }
+        }
+        // Local frame; the face flux is the 1/4-weighted Gauss sum.
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          gF[i] = T(0.25) * cF[ax.gv[i]];
+          gdF[i] = T(0.25) * cdF[ax.gv[i]];
+        }
+      }
+#pragma unroll 1
+      for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
+        const int m1 = g & 1, m2 = g >> 1;
+        PointState<T> st[NS], ct[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            const int k = 5 * s + i;
+            const T* sv = tb + (4 * k + m1) * NH + at3;
+            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+            T v[2], dd[2];
+            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+            st[s].q[i] = v[m2];
+            st[s].dq[2][i] = dd[m2] * rh2;
+            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
+            st[s].dq[1][i] = v[m2] * rh1;
+            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
+            st[s].dq[0][i] = v[m2];
+            ct[s].q[i] = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ct[s].dq[c][i] = T(0);
+          }
+        flux_vjp<T, FLUX>(st, a.gas, dt, a.wL != nullptr, gF, gdF, ct);
+        // Transposed t2 pass into the t1-pass cotangents.
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll 1
+          for (int i = 0; i < 5; ++i) {
+            const int k = 5 * s + i;
+            const int rows[3] = {4 * k + m1, 4 * k + 2 + m1, 4 * NV + 2 * k + m1};
+            T gvv[3][2] = {{0, 0}, {0, 0}, {0, 0}}, gdd[2] = {0, 0};
+            gvv[0][m2] = ct[s].q[i];
+            gdd[m2] = ct[s].dq[2][i] * rh2;
+            gvv[1][m2] = ct[s].dq[1][i] * rh1;
+            gvv[2][m2] = ct[s].dq[0][i];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const T* src = tb + rows[r] * NH + at3;
+              const T fv[5] = {src[-2 * st2], src[-st2], src[0], src[st2], src[2 * st2]};
+              T cot[5] = {0, 0, 0, 0, 0};
+              const T zero2[2] = {0, 0};
+              tangential_vjp<MODE>(fv, gvv[r], r == 0 ? gdd : zero2, cot);
+              T* dst = tbc + rows[r] * NH + at3;
+#pragma unroll
+              for (int j = 0; j < 5; ++j) atomicAdd(dst + (j - 2) * st2, cot[j]);
+            }
+          }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- R2: transposed t1 pass ----------------
+    {
+      const int items = t1P ? TP * HS : HP * TS;
+      for (int it = tid; it < items; it += NT) {
+        const int hp2 = t1P ? 2 + it % TP : it % HP;
+        const int hs2 = t1P ? it / TP : 2 + it / HP;
+        const int at = hs2 * HP + hp2;
+#pragma unroll 1
+        for (int k = 0; k < 2 * NV; ++k) {
+          const bool value_field = k < NV;
+          const T* src = ff + k * NH + at;
+          const T fv[5] = {src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1]};
+          T gv2[2], gd2[2];
+          if (value_field) {
+            gv2[0] = tbc[(4 * k + 0) * NH + at];
+            gv2[1] = tbc[(4 * k + 1) * NH + at];
+            gd2[0] = tbc[(4 * k + 2) * NH + at];
+            gd2[1] = tbc[(4 * k + 3) * NH + at];
+          } else {
+            gv2[0] = tbc[(4 * NV + 2 * (k - NV) + 0) * NH + at];
+            gv2[1] = tbc[(4 * NV + 2 * (k - NV) + 1) * NH + at];
+            gd2[0] = gd2[1] = T(0);
+          }
+          if (gv2[0] == T(0) && gv2[1] == T(0) && gd2[0] == T(0) && gd2[1] == T(0)) continue;
+          T cot[5] = {0, 0, 0, 0, 0};
+          tangential_vjp<MODE>(fv, gv2, gd2, cot);
+          T* dst = ffc + k * NH + at;
+#pragma unroll
+          for (int j = 0; j < 5; ++j) atomicAdd(dst + (j - 2) * st1, cot[j]);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- R1: face fields -> cells ----------------
+    for (int h = tid; h < NH; h += NT) {
+      const int hp = h % HP, hs = h / HP;
+      const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+      if (Pc > nP + 1 || Sc > nS + 1) continue;
+      T gQl[5], gQr[5], gQ0[5], gDl[5], gDr[5], gD0[5];
+      bool any = false;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        if constexpr (FLUX == FLUX_SMOOTH) {
+          gQl[i] = gQr[i] = gDl[i] = gDr[i] = T(0);
+          gQ0[i] = ffc[i * NH + h];
+          gD0[i] = ffc[(5 + i) * NH + h];
+        } else {
+          gQl[i] = ffc[i * NH + h];
+          gQr[i] = ffc[(5 + i) * NH + h];
+          gQ0[i] = ffc[(10 + i) * NH + h];
+          gDl[i] = ffc[(15 + i) * NH + h];
+          gDr[i] = ffc[(20 + i) * NH + h];
+          gD0[i] = ffc[(25 + i) * NH + h];
+        }
+        any = any || gQl[i] != T(0) || gQr[i] != T(0) || gQ0[i] != T(0) || gDl[i] != T(0) ||
+              gDr[i] != T(0) || gD0[i] != T(0);
+      }
+      if (!any) continue;
+      int c[3];
+      c[d] = f - 3;
+      c[P] = Pc;
+      c[S] = Sc;
+      const long long cb = pad_index(a.g, c[0], c[1], c[2]);
+      const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
+      const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
+      T qc[5][6], Ql[5], Qr[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const T* qv = a.q + ax.gv[i] * a.g.P + cb;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qc[i][k] = qv[k * ax.sd];
+        T Li, Ri, Lr, Rr;
+        weno5_pair<MODE>(qc[i][0], qc[i][1], qc[i][2], qc[i][3], qc[i][4], Li, Ri);
+        weno5_pair<MODE>(qc[i][1], qc[i][2], qc[i][3], qc[i][4], qc[i][5], Lr, Rr);
+        Ql[i] = Ri;
+        Qr[i] = Lr;
+      }
+      compat_vjp(Ql, Qr, gQ0, a.gas, gQl, gQr);
+#pragma unroll 1
+      for (int i = 0; i < 5; ++i) {
+        T gq[6] = {0, 0, 0, 0, 0, 0};
+        // Slopes: Dl = (4 Ri + 2 Li - 6 q2)/hl, Dr = -(4 Lr + 2 Rr - 6 q3)/hr,
+        // D0 = (q1 - 15 q2 + 15 q3 - q4) / (6 (hl + hr)).
+        const T gRi = gQl[i] + T(4) * rhl * gDl[i], gLi = T(2) * rhl * gDl[i];
+        const T gLr = gQr[i] - T(4) * rhr * gDr[i], gRr = -T(2) * rhr * gDr[i];
+        gq[2] -= T(6) * rhl * gDl[i];
+        gq[3] += T(6) * rhr * gDr[i];
+        gq[1] += r6 * gD0[i];
+        gq[2] -= T(15) * r6 * gD0[i];
+        gq[3] += T(15) * r6 * gD0[i];
+        gq[4] -= r6 * gD0[i];
+        weno5_pair_vjp<MODE>(&qc[i][0], gLi, gRi, &gq[0]);
+        weno5_pair_vjp<MODE>(&qc[i][1], gLr, gRr, &gq[1]);
+        T* accv = a.acc + ax.gv[i] * a.g.P + cb;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (gq[k] != T(0)) atomicAdd(accv + k * ax.sd, gq[k]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Returns the cotangents collected on ghost cells to their periodic images,
+// in the reverse order of the ghost fill (z, then y, then x).  Wall
+// boundaries are not handled (the adjoint rejects them).
+template <class T>
+__global__ void k_fold_ghosts_z(T* __restrict__ acc, GridDev g) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long plane = (long long)g.p[0] * g.p[1];
+  if (tid >= 6 * plane) return;
+  const long long xy = tid % plane;
+  const int m = int(tid / plane);
+  const int z = m < 3 ? -1 - m : g.n[2] + (m - 3);
+  const int src = m < 3 ? g.n[2] - 1 - m : m - 3;
+  const long long gi = (long long)(z + kGhost) * plane + xy;
+  const long long si = (long long)(src + kGhost) * plane + xy;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    acc[v * g.P + si] += acc[v * g.P + gi];
+    acc[v * g.P + gi] = T(0);
+  }
+}
+template <class T>
+__global__ void k_fold_ghosts_y(T* __restrict__ acc, GridDev g) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= 6LL * g.p[0] * g.n[2]) return;
+  const int x = int(tid % g.p[0]) - kGhost;
+  const long long r = tid / g.p[0];
+  const int m = int(r % 6), z = int(r / 6);
+  const int y = m < 3 ? -1 - m : g.n[1] + (m - 3);
+  const int src = m < 3 ? g.n[1] - 1 - m : m - 3;
+  const long long gi = pad_index(g, x, y, z), si = pad_index(g, x, src, z);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    acc[v * g.P + si] += acc[v * g.P + gi];
+    acc[v * g.P + gi] = T(0);
+  }
+}
+template <class T>
+__global__ void k_fold_ghosts_x(T* __restrict__ acc, GridDev g) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= 6LL * g.n[1] * g.n[2]) return;
+  const int m = int(tid % 6);
+  const long long r = tid / 6;
+  const int y = int(r % g.n[1]), z = int(r / g.n[1]);
+  const int x = m < 3 ? -1 - m : g.n[0] + (m - 3);
+  const int src = m < 3 ? g.n[0] - 1 - m : m - 3;
+  const long long gi = pad_index(g, x, y, z), si = pad_index(g, src, y, z);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    acc[v * g.P + si] += acc[v * g.P + gi];
+    acc[v * g.P + gi] = T(0);
+  }
+}
+
+// Elementwise pieces of the step's adjoint (interior cells, [5][N]):
+// mode 0: wdL = c1 * lam                      (the Q* evaluation; wL = 0)
+// mode 1: wL = dt lam + dt/2 mu, wdL = dt^2/6 lam + dt^2/8 mu, mu = acc
+// mode 2: out = lam + mu_star + acc           (FP64 result)
+template <class T>
+__global__ void k_adj_combine(int mode, const double* __restrict__ lam, const T* __restrict__ acc,
+                              T* __restrict__ mu_star, T* __restrict__ wL, T* __restrict__ wdL,
+                              double* __restrict__ out, const double* __restrict__ scal, GridDev g) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const double dt = scal[0];
+  const int nx = g.n[0], ny = g.n[1];
+  const int x = int(c % nx);
+  const long long r = c / nx;
+  const int y = int(r % ny), z = int(r / ny);
+  const long long pi = pad_index(g, x, y, z);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double l = lam[v * g.N + c];
+    if (mode == 0) {
+      wdL[v * g.N + c] = T(dt * dt / 3.0 * l);
+    } else if (mode == 1) {
+      const double m = double(acc[v * g.P + pi]);
+      mu_star[v * g.N + c] = T(m);
+      wL[v * g.N + c] = T(dt * l + 0.5 * dt * m);
+      wdL[v * g.N + c] = T(dt * dt / 6.0 * l + dt * dt / 8.0 * m);
+    } else {
+      out[v * g.N + c] = l + double(mu_star[v * g.N + c]) + double(acc[v * g.P + pi]);
+    }
+  }
+}
+
+}  // namespace hgks

@@ -32,6 +32,10 @@ struct Engine {
   double* part = nullptr;      // diagnostic partials
   double* diag_out = nullptr;  // 8 doubles
   double* io = nullptr;        // FP64 staging buffer, 5 * N
+  void* adj_acc = nullptr;  // adjoint: padded cotangent accumulator, 5 * P
+  void* adj_mu = nullptr;   // adjoint: cotangent of Q*, 5 * N
+  void* adj_wL = nullptr;   // adjoint: cotangents of L and dL/dt, 5 * N each
+  void* adj_wdL = nullptr;
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
@@ -74,6 +78,10 @@ template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
 template <class T> cudaError_t enqueue_diag(const Engine& e);
 template <class T> cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative);
 template <class T> cudaError_t enqueue_to_fp64(const Engine& e, double* dst);
+// Adjoint of one S2O4 step at the state e.q with the step dt already in
+// e.scal[0]: adj_out = (dQ^{n+1}/dQ^n)^T adj_in (FP64 device arrays, [5][N]).
+template <class T> cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in,
+                                                    double* adj_out);
 cudaError_t enqueue_reset_scalars(const Engine& e);
 cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed);
 cudaError_t enqueue_advance_time(const Engine& e);

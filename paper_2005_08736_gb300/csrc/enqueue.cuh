@@ -5,6 +5,7 @@
 #include "engine.h"
 #include "kernels.cuh"
 #include "sweep.cuh"
+#include "adjoint.cuh"
 
 namespace hgks {
 
@@ -178,12 +179,102 @@ cudaError_t enqueue_to_fp64(const Engine& e, double* dst) {
   return cudaGetLastError();
 }
 
+// Tiles of the adjoint sweep: four shared-memory planes (face fields, t1 pass
+// and their cotangents) must fit one CTA.
+template <class T, int FLUX> struct AdjTile { static constexpr int TP = 16, TS = 8, NT = 256; };
+template <> struct AdjTile<float, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NT = 256; };
+template <> struct AdjTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 4, NT = 128; };
+
+template <class T, int MODE, int FLUX>
+cudaError_t launch_adjoint_sweeps(const Engine& e, const T* q, const T* wL, const T* wdL) {
+  constexpr int TP = AdjTile<T, FLUX>::TP, TS = AdjTile<T, FLUX>::TS, NT = AdjTile<T, FLUX>::NT;
+  const GridDev g = grid_of(e);
+  constexpr size_t smem = adj_smem_bytes<T, FLUX, TP, TS>();
+  auto kern = k_sweep_adj<T, MODE, FLUX, TP, TS, NT>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  for (int d = 0; d < 3; ++d) {
+    AdjArgs<T> a;
+    a.q = q;
+    a.wL = wL;
+    a.wdL = wdL;
+    a.acc = static_cast<T*>(e.adj_acc);
+    a.wn = static_cast<const T*>(e.w[d]);
+    a.wt1 = static_cast<const T*>(e.w[(d + 1) % 3]);
+    a.wt2 = static_cast<const T*>(e.w[(d + 2) % 3]);
+    a.scal = e.scal;
+    a.g = g;
+    a.d = d;
+    a.gas = gas_of<T>(e.cfg);
+    const int P = d == 0 ? 1 : 0, S = d == 2 ? 1 : 2;
+    const int gx = (g.n[P] + TP - 1) / TP, gy = (g.n[S] + TS - 1) / TS;
+    const int layers = g.n[d] + 1;
+    const int want_chunks = (4 * e.sms + gx * gy - 1) / (gx * gy);
+    int chunk = (layers + want_chunks - 1) / want_chunks;
+    if (chunk < 1) chunk = 1;
+    a.chunk = chunk;
+    const int gz = (layers + chunk - 1) / chunk;
+    kern<<<dim3(gx, gy, gz), NT, smem, e.stream>>>(a);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  T* acc = static_cast<T*>(e.adj_acc);
+  k_fold_ghosts_z<T><<<blocks_for(6LL * g.p[0] * g.p[1], 256), 256, 0, e.stream>>>(acc, g);
+  k_fold_ghosts_y<T><<<blocks_for(6LL * g.p[0] * g.n[2], 256), 256, 0, e.stream>>>(acc, g);
+  k_fold_ghosts_x<T><<<blocks_for(6LL * g.n[1] * g.n[2], 256), 256, 0, e.stream>>>(acc, g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t dispatch_adjoint_sweeps(const Engine& e, const T* q, const T* wL, const T* wdL) {
+  const int mode = e.cfg.recon, flux = e.cfg.flux;
+#define HGKS_ADJ(M, F) \
+  if (mode == M && flux == F) return launch_adjoint_sweeps<T, M, F>(e, q, wL, wdL);
+  HGKS_ADJ(0, 0) HGKS_ADJ(1, 0) HGKS_ADJ(2, 0)
+  HGKS_ADJ(0, 1) HGKS_ADJ(1, 1) HGKS_ADJ(2, 1)
+#undef HGKS_ADJ
+  return cudaErrorInvalidValue;
+}
+
+template <class T>
+cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* adj_out) {
+  const GridDev g = grid_of(e);
+  T* acc = static_cast<T*>(e.adj_acc);
+  T* mu = static_cast<T*>(e.adj_mu);
+  T* wL = static_cast<T*>(e.adj_wL);
+  T* wdL = static_cast<T*>(e.adj_wdL);
+  const size_t accb = 5 * (size_t)e.P * sizeof(T);
+  // Q* = Q^n + dt/2 L + dt^2/8 dL (also fills the ghost cells of Q^n).
+  cudaError_t err = enqueue_rhs_and_update<T>(e, 1);
+  if (err != cudaSuccess) return err;
+  err = enqueue_ghosts<T>(e, e.qs);
+  if (err != cudaSuccess) return err;
+  // mu* = (d dL(Q*)/dQ*)^T (dt^2/3 lam).
+  err = cudaMemsetAsync(acc, 0, accb, e.stream);
+  if (err != cudaSuccess) return err;
+  k_adj_combine<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(0, adj_in, acc, mu, wL, wdL, nullptr,
+                                                               e.scal, g);
+  err = dispatch_adjoint_sweeps<T>(e, static_cast<const T*>(e.qs), nullptr, wdL);
+  if (err != cudaSuccess) return err;
+  // Cotangents of L(Q^n) and dL(Q^n), then their VJP at Q^n.
+  k_adj_combine<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(1, adj_in, acc, mu, wL, wdL, nullptr,
+                                                               e.scal, g);
+  err = cudaMemsetAsync(acc, 0, accb, e.stream);
+  if (err != cudaSuccess) return err;
+  err = dispatch_adjoint_sweeps<T>(e, static_cast<const T*>(e.q), wL, wdL);
+  if (err != cudaSuccess) return err;
+  k_adj_combine<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(2, adj_in, acc, mu, wL, wdL, adj_out,
+                                                               e.scal, g);
+  return cudaGetLastError();
+}
+
 #define HGKS_INSTANTIATE(T)                                                  \
   template cudaError_t enqueue_ghosts<T>(const Engine&, void*, Probe*);      \
   template cudaError_t enqueue_rhs_and_update<T>(const Engine&, int, Probe*); \
   template cudaError_t enqueue_cfl<T>(const Engine&, const void*);           \
   template cudaError_t enqueue_diag<T>(const Engine&);                       \
   template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
-  template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);
+  template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);           \
+  template cudaError_t enqueue_adjoint_step<T>(const Engine&, const double*, double*);
 
 }  // namespace hgks

@@ -96,7 +96,8 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 
 void free_all(hgks::Engine& e) {
   void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
-                  e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io};
+                  e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
+                  e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -372,6 +373,27 @@ hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
   out->Ek = r[5] / (e.cfg.rho_ref * vol);
   out->rho_min = r[6];
   out->p_min = r[7];
+  return HGKS_OK;
+}
+
+hgks_status hgks_adjoint_step(hgks_ctx* c, double dt, const double* adj_in, double* adj_out) {
+  if (!c || !adj_in || !adj_out) return fail(c, HGKS_E_INVAL, "null argument");
+  if (!(dt > 0.0)) return fail(c, HGKS_E_INVAL, "the adjoint needs the forward step dt > 0");
+  hgks::Engine& e = c->e;
+  if (e.cfg.bc_y != HGKS_BC_PERIODIC)
+    return fail(c, HGKS_E_UNSUPPORTED, "the adjoint supports periodic boundaries only");
+  if (e.cfg.force_x != 0.0) return fail(c, HGKS_E_UNSUPPORTED, "the adjoint has no body force");
+  const size_t es = elem_size(e.cfg);
+  if (!e.adj_acc) {
+    HGKS_CHECK(c, cudaMalloc(&e.adj_acc, 5 * e.P * es));
+    HGKS_CHECK(c, cudaMalloc(&e.adj_mu, 5 * e.N * es));
+    HGKS_CHECK(c, cudaMalloc(&e.adj_wL, 5 * e.N * es));
+    HGKS_CHECK(c, cudaMalloc(&e.adj_wdL, 5 * e.N * es));
+  }
+  HGKS_CHECK(c, hgks::enqueue_set_dt(e, dt));
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_adjoint_step<float>(e, adj_in, adj_out)
+                    : hgks::enqueue_adjoint_step<double>(e, adj_in, adj_out));
   return HGKS_OK;
 }
 

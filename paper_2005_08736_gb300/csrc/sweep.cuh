@@ -51,6 +51,105 @@ constexpr size_t sweep_smem_bytes() {
                       (TPF - 1) * 10 * TP * TS);
 }
 
+// Geometry of one sweep: normal axis d, transverse axes P (faster in memory)
+// and S, and the first tangential axis t1 = d+1.
+struct SweepAxes {
+  int d, P, S;
+  bool t1P;        // t1 is P (d = x, z) or S (d = y)
+  long long sd;    // stride of the padded state along d
+  int gv[5];       // global variable of each local-frame component
+};
+__device__ __forceinline__ SweepAxes sweep_axes(int d, const GridDev& g) {
+  SweepAxes a;
+  a.d = d;
+  a.P = d == 0 ? 1 : 0;
+  a.S = d == 2 ? 1 : 2;
+  a.t1P = ((d + 1) % 3) == a.P;
+  a.sd = d == 0 ? 1LL : (d == 1 ? (long long)g.p[0] : (long long)g.p[0] * g.p[1]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) a.gv[i] = global_var(d, i);
+  return a;
+}
+
+// Face fields of face layer f at transverse point (Pc, Sc) into ff[k * NH + h]:
+// WENO5 end values of cells f-1 and f, their normal slopes, the compatibility
+// state Q0 and its normal slope (local frame).  Smooth flux: fields Q0, dQ0/dn;
+// full flux: Q_l, Q_r, Q0, dQ_l/dn, dQ_r/dn, dQ0/dn.
+template <class T, int MODE, int FLUX, int NH>
+__device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const GridDev& g,
+                                                 const SweepAxes& ax, const T* __restrict__ wn,
+                                                 const Gas<T>& gas, int f, int Pc, int Sc, int h,
+                                                 T* ff) {
+  int c[3];
+  c[ax.d] = f - 3;
+  c[ax.P] = Pc;
+  c[ax.S] = Sc;
+  const long long cb = pad_index(g, c[0], c[1], c[2]);
+  const long long sd = ax.sd;
+  const T hl = wn[f - 1 + kGhost], hr = wn[f + kGhost];
+  const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
+  T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T* qv = q + ax.gv[i] * g.P + cb;
+    const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd), q3 = __ldg(qv + 3 * sd),
+            q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
+    T Li, Ri, Lr, Rr;
+    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
+    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+    Ql[i] = Ri;
+    Qr[i] = Lr;
+    Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
+    Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
+    D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
+  }
+  T Q0[5];
+  compat_dev(Ql, Qr, gas, Q0);
+  if constexpr (FLUX == FLUX_SMOOTH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      ff[i * NH + h] = Q0[i];
+      ff[(5 + i) * NH + h] = D0[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      ff[i * NH + h] = Ql[i];
+      ff[(5 + i) * NH + h] = Qr[i];
+      ff[(10 + i) * NH + h] = Q0[i];
+      ff[(15 + i) * NH + h] = Dl[i];
+      ff[(20 + i) * NH + h] = Dr[i];
+      ff[(25 + i) * NH + h] = D0[i];
+    }
+  }
+}
+
+// Tangential pass along t1 for one point `at` of the tile (stride st1 in the
+// shared-memory plane): values at both t1 Gauss abscissae of every field and
+// t1-derivatives of the state fields, into tb.
+template <class T, int MODE, int FLUX, int NH>
+__device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1) {
+  constexpr int NV = SweepLayout<FLUX>::NV;
+#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
+  for (int k = 0; k < NV; ++k) {
+    const T* src = ff + k * NH + at;
+    T v[2], dd[2];
+    tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+    tb[(4 * k + 0) * NH + at] = v[0];
+    tb[(4 * k + 1) * NH + at] = v[1];
+    tb[(4 * k + 2) * NH + at] = dd[0];
+    tb[(4 * k + 3) * NH + at] = dd[1];
+  }
+#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
+  for (int k = 0; k < NV; ++k) {
+    const T* src = ff + (NV + k) * NH + at;
+    T v[2];
+    tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
+    tb[(4 * NV + 2 * k + 0) * NH + at] = v[0];
+    tb[(4 * NV + 2 * k + 1) * NH + at] = v[1];
+  }
+}
+
 // Resident CTAs per SM the register budget is sized for: the smooth FP32
 // sweep fits three (shared memory allows three as well), the others one or two.
 template <class T, int FLUX> struct SweepOccupancy { static constexpr int value = 1; };
@@ -72,20 +171,14 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
 
   const int d = a.d;
-  const int P = d == 0 ? 1 : 0;
-  const int S = d == 2 ? 1 : 2;
-  const int t1 = (d + 1) % 3;
-  const bool t1P = (t1 == P);
+  const SweepAxes ax = sweep_axes(d, a.g);
+  const int P = ax.P, S = ax.S;
+  const bool t1P = ax.t1P;
   const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
   const int p0 = blockIdx.x * TP, s0 = blockIdx.y * TS;
   const int f0 = blockIdx.z * a.chunk;
   const int f1 = min(f0 + a.chunk, nd + 1);
-  const long long sd = d == 0 ? 1LL : (d == 1 ? (long long)a.g.p[0] : (long long)a.g.p[0] * a.g.p[1]);
   const int tid = threadIdx.x;
-
-  int gv[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) gv[i] = global_var(d, i);
 
   // Phase-3 role: one face and GPF Gauss points of it.
   const int face = tid % NFACE, sub = tid / NFACE;
@@ -121,47 +214,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
       const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
       T* ff = ffb + l * NFF * NH;
       if (f < f1 && Pc <= nP + 1 && Sc <= nS + 1) {
-        int c[3];
-        c[d] = f - 3;
-        c[P] = Pc;
-        c[S] = Sc;
-        const long long cb = pad_index(a.g, c[0], c[1], c[2]);
-        const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
-        const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
-        T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          const T* qv = a.q + gv[i] * a.g.P + cb;
-          const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd),
-                  q3 = __ldg(qv + 3 * sd), q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
-          T Li, Ri, Lr, Rr;
-          weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
-          weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
-          Ql[i] = Ri;
-          Qr[i] = Lr;
-          Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
-          Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
-          D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
-        }
-        T Q0[5];
-        compat_dev(Ql, Qr, a.gas, Q0);
-        if constexpr (FLUX == FLUX_SMOOTH) {
-#pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            ff[i * NH + h] = Q0[i];
-            ff[(5 + i) * NH + h] = D0[i];
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            ff[i * NH + h] = Ql[i];
-            ff[(5 + i) * NH + h] = Qr[i];
-            ff[(10 + i) * NH + h] = Q0[i];
-            ff[(15 + i) * NH + h] = Dl[i];
-            ff[(20 + i) * NH + h] = Dr[i];
-            ff[(25 + i) * NH + h] = D0[i];
-          }
-        }
+        face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc, Sc, h, ff);
       } else {
 #pragma unroll 1
         for (int k = 0; k < NFF; ++k) ff[k * NH + h] = T(0);
@@ -181,24 +234,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
         const int at = hs2 * HP + hp2;
-#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
-        for (int k = 0; k < NV; ++k) {
-          const T* src = ff + k * NH + at;
-          T v[2], dd[2];
-          tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
-          tb[(4 * k + 0) * NH + at] = v[0];
-          tb[(4 * k + 1) * NH + at] = v[1];
-          tb[(4 * k + 2) * NH + at] = dd[0];
-          tb[(4 * k + 3) * NH + at] = dd[1];
-        }
-#pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
-        for (int k = 0; k < NV; ++k) {
-          const T* src = ff + (NV + k) * NH + at;
-          T v[2];
-          tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
-          tb[(4 * NV + 2 * k + 0) * NH + at] = v[0];
-          tb[(4 * NV + 2 * k + 1) * NH + at] = v[1];
-        }
+        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, at, st1);
       }
     }
     __syncthreads();
@@ -290,8 +326,8 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
       const long long o = fout + (long long)f * fstep;
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        a.fd[gv[i] * FS + o] = T(0.25) * Fs[i];
-        a.fd[(5 + gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
+        a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
+        a.fd[(5 + ax.gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
       }
     }
     __syncthreads();

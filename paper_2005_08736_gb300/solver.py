@@ -146,6 +146,18 @@ class Simulation:
         self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.ctypes.data), 1))
         return out
 
+    def adjoint_step(self, dt: float, adj_in: torch.Tensor, adj_out: torch.Tensor) -> None:
+        """adj_out = (dQ^{n+1}/dQ^n)^T adj_in at the current state Q^n (device FP64 tensors)."""
+        for t in (adj_in, adj_out):
+            assert t.is_cuda and t.dtype == torch.float64 and tuple(t.shape) == self.cfg.shape
+            assert t.is_contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._call(self.lib.hgks_adjoint_step(self.h, float(dt), ctypes.c_void_p(adj_in.data_ptr()),
+                                              ctypes.c_void_p(adj_out.data_ptr())))
+        adj_in.record_stream(self.stream)
+        adj_out.record_stream(self.stream)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
     def profile_step(self, dt: float = 0.0) -> dict:
         """Advance one step with CUDA events per kernel class; device ms per class."""
         ms = (ctypes.c_double * len(_lib.KERNEL_CLASSES))()
@@ -157,3 +169,53 @@ class Simulation:
         self._call(self.lib.hgks_diagnostics(self.h, ctypes.byref(d)))
         return dict(t=d.t, dt=d.dt, mass=d.mass, mom=tuple(d.mom), energy=d.energy, Ek=d.Ek,
                     rho_min=d.rho_min, p_min=d.p_min, step=d.step)
+
+
+class StepWindow(torch.autograd.Function):
+    """Q^0 -> Q^K by K steps of fixed dt, differentiable through the library's
+    adjoint step.  The forward keeps a checkpoint every `every` steps; the
+    backward recomputes each window from its checkpoint and applies the
+    adjoint steps in reverse.  Tensors are device FP64 conservative states
+    [5][nz][ny][nx]."""
+
+    @staticmethod
+    def forward(ctx, q0, sim: "Simulation", nsteps: int, dt: float, every: int):
+        sim.init_conservative(q0.detach())
+        ckpts = {}
+        for n in range(nsteps):
+            if n % every == 0:
+                ckpts[n] = sim.state(device=True).clone()
+            sim.step(1, dt)
+        ctx.sim, ctx.nsteps, ctx.dt, ctx.every, ctx.ckpts = sim, nsteps, dt, every, ckpts
+        return sim.state(device=True)
+
+    @staticmethod
+    def backward(ctx, grad):
+        sim, dt = ctx.sim, ctx.dt
+        lam = grad.detach().contiguous().to(torch.float64)
+        for start in sorted(ctx.ckpts, reverse=True):
+            end = min(start + ctx.every, ctx.nsteps)
+            states = []
+            sim.init_conservative(ctx.ckpts[start])
+            for n in range(start, end):
+                states.append(sim.state(device=True).clone())
+                if n < end - 1:
+                    sim.step(1, dt)
+            for n in range(end - 1, start - 1, -1):
+                sim.init_conservative(states[n - start])
+                out = torch.empty_like(lam)
+                sim.adjoint_step(dt, lam, out)
+                lam = out
+        return lam, None, None, None, None
+
+
+def run_window(q0: torch.Tensor, sim: Simulation, nsteps: int, dt: float, every: int = 10):
+    """Differentiable K-step map (see StepWindow)."""
+    return StepWindow.apply(q0, sim, nsteps, dt, every)
+
+
+def kinetic_energy(q: torch.Tensor, cfg: Config) -> torch.Tensor:
+    """E_k = (1/(rho_ref |Omega|)) sum rho |U|^2 / 2 |Omega_c| on a uniform grid (Sec. 3.1)."""
+    rho = q[0]
+    ke = 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho
+    return ke.mean() / cfg.rho_ref

@@ -1,0 +1,185 @@
+"""The adjoint step against central finite differences (FP64) and the
+autograd window with checkpointing.
+
+J = <r, Q^K> for a seeded r (and the kinetic energy E_k of Sec. 3.1 for the
+autograd window) after K steps of fixed dt from a seeded smooth state; the
+adjoint gradient dJ/dQ^0 is compared with (J(Q^0 + h v) - J(Q^0 - h v))/(2h)
+along seeded directions v, to 1e-6 relative.  Finite differences are taken
+with the forward step of the same library, dt frozen.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2005_08736_gb300 import inputs  # noqa: E402
+from paper_2005_08736_gb300.solver import (Config, Simulation, kinetic_energy,  # noqa: E402
+                                           run_window)
+
+# Modes whose forward map is smooth at the finite-difference scale on resolved
+# data; WENO-Z (|beta0 - beta2|) and the numerical collision time
+# (|p_l - p_r|) have kinks and are checked along localised directions below.
+MODES = [(0, 0), (1, 1), (0, 1), (1, 0)]
+
+
+def setup(n, recon, flux, prec=0, C=0.0, kmax=1, oblique=0.0):
+    # C = 0 by default: the numerical collision time C |p_l - p_r| / (p_l + p_r) dt
+    # has a kink at p_l = p_r, where central differences and the one-sided
+    # derivative of the adjoint disagree.
+    cfg = Config(*n, prec=prec, recon=recon, flux=flux, tau_num_C=C, mu_ref=5e-3, p_ref=1.0,
+                 prandtl=0.7, visc=1, T_ref=1.0, visc_exp=0.76)
+    prim = inputs.random_smooth(n, seed=21, amp=0.15, kmax=kmax)
+    if oblique:
+        # An oblique mode in every variable: no stencil is exactly constant,
+        # where the WENO-Z weights jump under any perturbation.
+        x = [2 * np.pi * (np.arange(m) + 0.5) / m for m in n]
+        z3, y3, x3 = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+        for v in range(5):
+            prim[v] += oblique * (1.0 if v in (0, 4) else 0.3) * np.sin(x3 + 2 * y3 + z3 + v)
+    q0 = torch.from_numpy(np.ascontiguousarray(oracle.conservative(prim, 1.4))).cuda()
+    return cfg, q0
+
+
+def forward(sim, q0, K, dt):
+    sim.init_conservative(q0)
+    sim.step(K, dt)
+    return sim.state(device=True)
+
+
+def adjoint_gradient(sim, q0, K, dt, lamK):
+    states = []
+    sim.init_conservative(q0)
+    for _ in range(K):
+        states.append(sim.state(device=True).clone())
+        sim.step(1, dt)
+    lam = lamK.clone()
+    for n in range(K - 1, -1, -1):
+        sim.init_conservative(states[n])
+        out = torch.empty_like(lam)
+        sim.adjoint_step(dt, lam, out)
+        lam = out
+    return lam
+
+
+@pytest.mark.parametrize("recon,flux", MODES)
+def test_adjoint_matches_central_differences_fp64(recon, flux):
+    n, K, dt = (12, 10, 9), 3, 0.05
+    cfg, q0 = setup(n, recon, flux)
+    sim = Simulation(cfg)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+    grad = adjoint_gradient(sim, q0, K, dt, r)
+    for k in range(3):
+        v = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        v *= q0.abs().amax(dim=(1, 2, 3), keepdim=True)
+        h = 1e-7
+        jp = (r * forward(sim, q0 + h * v, K, dt)).sum().item()
+        jm = (r * forward(sim, q0 - h * v, K, dt)).sum().item()
+        fd = (jp - jm) / (2 * h)
+        ad = (grad * v).sum().item()
+        assert abs(ad - fd) <= 1e-6 * max(abs(fd), 1e-12) + 1e-9, (k, ad, fd)
+
+
+def test_adjoint_matches_differences_with_numerical_collision_time():
+    # The numerical collision time C |p_l - p_r| / (p_l + p_r) dt (Sec. 3) has a
+    # kink at p_l = p_r.  On under-resolved data p_l - p_r is far from zero at
+    # most Gauss points; directions are supported on a random 2x2x2 block and
+    # only those along which the one-sided differences agree (no kink within
+    # +-h) are compared with the adjoint.
+    n, K, dt = (12, 10, 9), 3, 0.05
+    cfg, q0 = setup(n, 0, 1, C=1.0, kmax=3)
+    sim = Simulation(cfg)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+    grad = adjoint_gradient(sim, q0, K, dt, r)
+    j0 = (r * forward(sim, q0, K, dt)).sum().item()
+    rng = np.random.default_rng(1)
+    checked = 0
+    for k in range(10):
+        v = torch.zeros(cfg.shape, dtype=torch.float64, device="cuda")
+        z0, y0, x0 = rng.integers(0, n[2] - 1), rng.integers(0, n[1] - 1), rng.integers(0, n[0] - 1)
+        block = torch.randn((5, 2, 2, 2), dtype=torch.float64, device="cuda", generator=g)
+        v[:, z0:z0 + 2, y0:y0 + 2, x0:x0 + 2] = block * q0.abs().amax(dim=(1, 2, 3)).view(5, 1, 1, 1)
+        h = 1e-7
+        jp = (r * forward(sim, q0 + h * v, K, dt)).sum().item()
+        jm = (r * forward(sim, q0 - h * v, K, dt)).sum().item()
+        fwd, bwd, cen = (jp - j0) / h, (j0 - jm) / h, (jp - jm) / (2 * h)
+        if abs(fwd - bwd) > 1e-6 * abs(cen):
+            continue  # a kink lies within +-h along v
+        checked += 1
+        ad = (grad * v).sum().item()
+        assert abs(ad - cen) <= 1e-6 * abs(cen) + 1e-10, (k, ad, cen)
+    assert checked >= 3, checked
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+def test_wenoz_differences_converge_to_the_adjoint(flux):
+    # WENO-Z weights d_k (1 + |beta0 - beta2| / (beta_k + eps)) vary on very small
+    # scales of the data (kinks of |.|, small beta_k), so central differences
+    # approach the derivative only as h -> 0.  The adjoint must be their limit:
+    # the error falls as h falls and is small at the smallest h.
+    n, K, dt = (12, 10, 9), 2, 0.05
+    cfg, q0 = setup(n, 2, flux, kmax=1, oblique=0.05)
+    sim = Simulation(cfg)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+    grad = adjoint_gradient(sim, q0, K, dt, r)
+    best = 1.0
+    for _ in range(2):
+        v = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        v *= q0.abs().amax(dim=(1, 2, 3), keepdim=True)
+        ad = (grad * v).sum().item()
+        errs = []
+        for h in (1e-6, 1e-8):
+            jp = (r * forward(sim, q0 + h * v, K, dt)).sum().item()
+            jm = (r * forward(sim, q0 - h * v, K, dt)).sum().item()
+            errs.append(abs((jp - jm) / (2 * h) - ad) / abs(ad))
+        assert errs[1] < errs[0] and errs[1] < 1e-3, errs
+        best = min(best, errs[1])
+    assert best < 2e-5, best
+
+
+def test_autograd_window_with_checkpoints_kinetic_energy():
+    n, K, dt = (12, 10, 9), 5, 0.05
+    cfg, q0 = setup(n, 1, 1)
+    sim = Simulation(cfg)
+    x = q0.clone().requires_grad_(True)
+    J = kinetic_energy(run_window(x, sim, K, dt, every=2), cfg)
+    (gq,) = torch.autograd.grad(J, x)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    for _ in range(2):
+        v = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        v *= q0.abs().amax(dim=(1, 2, 3), keepdim=True)
+        h = 1e-7
+        jp = kinetic_energy(forward(sim, q0 + h * v, K, dt), cfg).item()
+        jm = kinetic_energy(forward(sim, q0 - h * v, K, dt), cfg).item()
+        fd = (jp - jm) / (2 * h)
+        ad = (gq * v).sum().item()
+        assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-12, (ad, fd)
+
+
+def test_fp32_adjoint_agrees_with_fp64():
+    n, K, dt = (12, 10, 9), 2, 0.05
+    out = []
+    for prec in (0, 1):
+        cfg, q0 = setup(n, 1, 1, prec)
+        sim = Simulation(cfg)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        out.append(adjoint_gradient(sim, q0, K, dt, r))
+    err = ((out[1] - out[0]).abs().amax() / out[0].abs().amax()).item()
+    print(f"FP32 adjoint vs FP64 adjoint: relative L-inf {err:.3e}")
+    assert err < 1e-3, err
+
+
+def test_adjoint_rejects_walls():
+    from paper_2005_08736_gb300._lib import HGKS_E_UNSUPPORTED, HgksError
+    cfg = Config(8, 8, 8, prec=0, ly=2.0, y0=-1.0, bc_y=1, T_wall=100 / 1.4)
+    sim = Simulation(cfg)
+    z = torch.zeros(cfg.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(HgksError) as e:
+        sim.adjoint_step(0.01, z, torch.empty_like(z))
+    assert e.value.status == HGKS_E_UNSUPPORTED
