@@ -153,6 +153,85 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def extra_workloads(steps: int):
+    """The other measured configurations: isotropic turbulence 256^3 (WENO-Z +
+    full flux, FP32), the stretched wall-bounded channel 128 x 128 x 96 (FP32),
+    the adjoint / forward time ratio at 64^3 (isotropic, kappa0 = 4, WENO-Z +
+    full flux, FP64 and FP32), and an ensemble of 24 isotropic instances of
+    mixed sizes in one graph launch per step against sequential runs."""
+    import torch
+    from paper_2005_08736_gb300 import inputs
+    from paper_2005_08736_gb300.solver import Config, Ensemble, Simulation
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    out = {}
+    # Isotropic turbulence (Sec. 3.4): Ma_t 0.5, Re_lambda 72, mu ~ T^0.76, Pr 0.7.
+    def iso_cfg(n, prec, k0=8.0):
+        c = inputs.isotropic_constants(k0=k0, mach_t=0.5)
+        return Config(n, n, n, prec=prec, recon=2, flux=1, tau_num_C=1.0, prandtl=0.7, visc=1,
+                      mu_ref=c["mu0"], T_ref=c["T0"], visc_exp=0.76, p_ref=c["p0"], rho_ref=1.0)
+    cfg = iso_cfg(256, 1)
+    sim = Simulation(cfg)
+    sim.init_primitive(inputs.isotropic(256, 0))
+    sim.step(3)
+    s_per = timed(lambda: sim.step(steps, sync=False), 1) / steps
+    out["isotropic_256_wenoz_full_fp32"] = {
+        "ms_per_step": 1e3 * s_per, "mcups": cfg.cells / s_per / 1e6,
+        "kernel_ms_per_step": sim.profile_step()}
+    sim.close()
+    # Channel (Sec. 3.3): 128 x 128 x 96, tanh b = 2, walls, f_x = 2.93e-3, Ma 0.1.
+    ccfg = Config(128, 128, 96, lx=2 * 3.141592653589793, ly=2.0, y0=-1.0, lz=3.141592653589793,
+                  y_stretch=1, stretch_b=2.0, bc_y=1, T_wall=100 / 1.4, mu_ref=0.0541 / 180,
+                  force_x=2.93e-3, prec=1, recon=0, flux=0, prandtl=0.72)
+    sim = Simulation(ccfg)
+    sim.init_primitive(inputs.channel(128, 128, 96, 0))
+    sim.step(3)
+    s_per = timed(lambda: sim.step(steps, sync=False), 1) / steps
+    out["channel_128x128x96_fp32"] = {"ms_per_step": 1e3 * s_per,
+                                      "mcups": ccfg.cells / s_per / 1e6}
+    sim.close()
+    # Adjoint / forward time ratio at 64^3.
+    for prec, name in ((0, "fp64"), (1, "fp32")):
+        acfg = iso_cfg(64, prec, k0=4.0)
+        sim = Simulation(acfg)
+        sim.init_primitive(inputs.isotropic(64, 0, k0=4.0))
+        dt = 0.5 * sim.step(1) if False else 2e-3
+        fwd = timed(lambda: sim.step(1, dt, sync=False), 5)
+        lam = torch.randn(acfg.shape, dtype=torch.float64, device="cuda")
+        o = torch.empty_like(lam)
+        adj = timed(lambda: sim.adjoint_step(dt, lam, o), 3)
+        out[f"adjoint_64_wenoz_full_{name}"] = {"forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj,
+                                                "adjoint_over_forward": adj / fwd}
+        sim.close()
+    # Ensemble of 24 isotropic instances, grids {32, 48, 64, 96}^3 by seed, FP32.
+    sims, cells = [], 0
+    for seed in range(24):
+        n = (32, 48, 64, 96)[seed % 4]
+        sim = Simulation(iso_cfg(n, 1))
+        sim.init_primitive(inputs.isotropic(n, seed))
+        sims.append(sim)
+        cells += n ** 3
+    ens = Ensemble(sims)
+    ens.step(2)
+    t_ens = timed(lambda: ens.step(steps, sync=False), 1) / steps
+    t_seq = timed(lambda: [s.step(steps, sync=False) for s in sims], 1) / steps
+    out["ensemble_24_isotropic_mixed"] = {
+        "instances": 24, "cells": cells, "ensemble_ms_per_step": 1e3 * t_ens,
+        "sequential_ms_per_step": 1e3 * t_seq, "speedup": t_seq / t_ens,
+        "ensemble_mcups": cells / t_ens / 1e6}
+    ens.close()
+    for s in sims:
+        s.close()
+    return out
+
+
 def config_dict():
     return {"workload": f"taylor-green-{N_GRID}^3 fp32 linear-WENO5 smooth-GKS S2O4",
             "model": "HGKS", "grid": [N_GRID] * 3, "precision": "fp32", "recon": "linear",
@@ -278,6 +357,7 @@ def run_ours(args, rank: int, world: int):
                 "hbm_frac": DRAM_BYTES_PER_FACE_STAGE1 * faces_per_launch / (flux_ms * 1e-3)
                 / (peaks.get("hbm_gbs", 6802.0) * 1e9)}
     cpu_rate, cpu_s = oracle_sample(2)
+    extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -299,6 +379,7 @@ def run_ours(args, rank: int, world: int):
                 "h2d_bytes_per_step": int(prim.nbytes), "d2h_bytes_per_step": 96},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": sm_clock,
+        "workloads": extras,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -313,6 +394,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=256, help="grid size (profiling cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the isotropic, channel, adjoint and ensemble measurements")
     ap.add_argument("--quick", action="store_true",
                     help="time the step only (no FP64 leg, e2e or CPU baseline); for profiling")
     args = ap.parse_args()

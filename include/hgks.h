@@ -123,6 +123,22 @@ typedef struct {
 /* FP64 reductions of the current state (synchronises). */
 hgks_status hgks_diagnostics(hgks_ctx* ctx, hgks_diag* out);
 
+/* Ensembles (no counterpart in the paper): a batch of independent contexts,
+ * e.g. instances of uneven sizes, advanced together.  hgks_ensemble_create
+ * takes n distinct contexts on the same device, each on its own stream (the
+ * handle borrows them; they must outlive it).  hgks_ensemble_step captures,
+ * on first use (and again when dt changes), ONE CUDA graph in which every
+ * member's S2O4 step is a parallel branch forked from and joined into the
+ * first member's stream, and launches it nsteps times: one graph launch per
+ * step for the whole batch, the members' kernels running concurrently.
+ * dt > 0 fixes every member's step; dt <= 0 takes each member's own CFL step.
+ * With sync != 0 it waits and checks each member as hgks_step does. */
+typedef struct hgks_ensemble hgks_ensemble;
+hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out);
+hgks_status hgks_ensemble_step(hgks_ensemble* ens, int nsteps, double dt, int sync);
+hgks_status hgks_ensemble_destroy(hgks_ensemble* ens);
+const char* hgks_ensemble_last_error(const hgks_ensemble* ens);
+
 /* Adjoint of one S2O4 step (no counterpart in the paper): with the context's
  * state at Q^n (set it with hgks_init_conservative, e.g. from a checkpoint)
  * and dt the forward step's dt (frozen, > 0), write

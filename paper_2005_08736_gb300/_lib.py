@@ -21,7 +21,9 @@ STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONPHYSI
 # Entry points declared in include/hgks.h.
 EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_state",
            "hgks_init_conservative", "hgks_get_state", "hgks_step", "hgks_diagnostics",
-           "hgks_adjoint_step", "hgks_profile_step", "hgks_step_noalloc", "hgks_last_error"]
+           "hgks_adjoint_step", "hgks_profile_step", "hgks_step_noalloc", "hgks_last_error",
+           "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
+           "hgks_ensemble_last_error"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 
 
@@ -89,11 +91,16 @@ def load(path: str | None = None):
         L.hgks_diagnostics.argtypes = [vp, ctypes.POINTER(HgksDiag)]
         L.hgks_profile_step.argtypes = [vp, d, pd, i]
         L.hgks_adjoint_step.argtypes = [vp, d, vp, vp]
+        L.hgks_ensemble_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+        L.hgks_ensemble_step.argtypes = [vp, i, d, i]
+        L.hgks_ensemble_destroy.argtypes = [vp]
+        L.hgks_ensemble_last_error.argtypes = [vp]
+        L.hgks_ensemble_last_error.restype = ctypes.c_char_p
         L.hgks_step_noalloc.argtypes = [pcfg, vp, i, d, vp]
         L.hgks_last_error.argtypes = [vp]
         L.hgks_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name != "hgks_last_error":
+            if name not in ("hgks_last_error", "hgks_ensemble_last_error"):
                 getattr(L, name).restype = i
         _lib = L
         return L

@@ -397,6 +397,117 @@ hgks_status hgks_adjoint_step(hgks_ctx* c, double dt, const double* adj_in, doub
   return HGKS_OK;
 }
 
+struct hgks_ensemble {
+  std::vector<hgks_ctx*> members;
+  cudaStream_t stream = nullptr;  // the first member's stream: fork and join point
+  std::vector<cudaEvent_t> events;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = -1.0;
+  std::string err;
+};
+
+hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out) {
+  if (!ctxs || n <= 0 || !out) return fail(nullptr, HGKS_E_INVAL, "bad ensemble arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(nullptr, HGKS_E_INVAL, "null member");
+    if (ctxs[i]->device != ctxs[0]->device) return fail(nullptr, HGKS_E_INVAL, "members on different devices");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->e.stream == ctxs[i]->e.stream)
+        return fail(nullptr, HGKS_E_INVAL, "members must be distinct contexts on distinct streams");
+  }
+  hgks_ensemble* en = new hgks_ensemble();
+  en->members.assign(ctxs, ctxs + n);
+  en->stream = ctxs[0]->e.stream;
+  en->events.resize(n + 1, nullptr);
+  for (auto& ev : en->events) {
+    const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (auto& x : en->events)
+        if (x) cudaEventDestroy(x);
+      delete en;
+      return cuda_fail(nullptr, e, "cudaEventCreateWithFlags");
+    }
+  }
+  *out = en;
+  return HGKS_OK;
+}
+
+hgks_status hgks_ensemble_destroy(hgks_ensemble* en) {
+  if (!en) return HGKS_OK;
+  cudaStreamSynchronize(en->stream);
+  if (en->graph) cudaGraphExecDestroy(en->graph);
+  for (auto& ev : en->events)
+    if (ev) cudaEventDestroy(ev);
+  delete en;
+  return HGKS_OK;
+}
+
+// One graph holding every member's step as a parallel branch: fork from the
+// first member's stream, each member's kernels on its own stream, join back.
+static hgks_status capture_ensemble(hgks_ensemble* en, double dt_fixed) {
+  if (en->graph) {
+    cudaGraphExecDestroy(en->graph);
+    en->graph = nullptr;
+  }
+  cudaStream_t s0 = en->stream;
+  cudaGraph_t g = nullptr;
+  cudaError_t err = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+  if (err != cudaSuccess) {
+    en->err = std::string("capture: ") + cudaGetErrorString(err);
+    return HGKS_E_CUDA;
+  }
+  err = cudaEventRecord(en->events[0], s0);
+  const int n = (int)en->members.size();
+  for (int i = 0; i < n && err == cudaSuccess; ++i) {
+    hgks::Engine& e = en->members[i]->e;
+    if (e.stream != s0) err = cudaStreamWaitEvent(e.stream, en->events[0], 0);
+    if (err == cudaSuccess) err = enqueue_stage_pair(e, dt_fixed);
+    if (err == cudaSuccess && e.stream != s0) {
+      err = cudaEventRecord(en->events[i + 1], e.stream);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(s0, en->events[i + 1], 0);
+    }
+  }
+  const cudaError_t end = cudaStreamEndCapture(s0, &g);
+  if (err == cudaSuccess) err = end;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&en->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (err != cudaSuccess) {
+    en->err = std::string("ensemble capture: ") + cudaGetErrorString(err);
+    return err == cudaErrorMemoryAllocation ? HGKS_E_NOMEM : HGKS_E_CUDA;
+  }
+  en->graph_dt = dt_fixed;
+  return HGKS_OK;
+}
+
+hgks_status hgks_ensemble_step(hgks_ensemble* en, int nsteps, double dt, int sync) {
+  if (!en || nsteps < 0) return HGKS_E_INVAL;
+  const double dt_fixed = dt > 0.0 ? dt : 0.0;
+  if (nsteps > 0 && (!en->graph || en->graph_dt != dt_fixed)) {
+    const hgks_status s = capture_ensemble(en, dt_fixed);
+    if (s != HGKS_OK) return s;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    const cudaError_t e = cudaGraphLaunch(en->graph, en->stream);
+    if (e != cudaSuccess) {
+      en->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+      return HGKS_E_CUDA;
+    }
+  }
+  if (!sync) return HGKS_OK;
+  // Per-member state check, as in hgks_step.
+  for (hgks_ctx* c : en->members) {
+    const hgks_status s = hgks_step(c, 0, dt, 1, nullptr);
+    if (s != HGKS_OK) {
+      en->err = c->err;
+      return s;
+    }
+  }
+  return HGKS_OK;
+}
+
+const char* hgks_ensemble_last_error(const hgks_ensemble* en) { return en ? en->err.c_str() : ""; }
+
 hgks_status hgks_profile_step(hgks_ctx* c, double dt, double* ms_out, int nclass) {
   if (!c || !ms_out || nclass < hgks::KC_COUNT) return fail(c, HGKS_E_INVAL, "bad argument");
   hgks::Engine& e = c->e;

@@ -97,3 +97,69 @@ def random_smooth(n: tuple[int, int, int], seed: int, amp: float = 0.05,
         scale = base if base != 0.0 else 1.0
         out.append(base + amp * scale * f / 4.0)
     return np.stack(out)
+
+
+def isotropic_constants(k0: float = 8.0, A0: float = 1.3e-4, re_lambda: float = 72.0,
+                        mach_t: float = 0.5, gamma: float = 1.4, rho0: float = 1.0) -> dict:
+    """Initial constants of the isotropic case (Sec. 3.4, Eq. (10) and the
+    Re_lambda / Ma_t definitions): K0, u_rms, tau_to, mu0, c0, T0, p0."""
+    K0 = 3.0 * A0 / 64.0 * math.sqrt(2 * math.pi) * k0 ** 5
+    u_rms = math.sqrt(2.0 * K0 / 3.0)
+    mu0 = (2 * math.pi) ** 0.25 / 4.0 * rho0 * math.sqrt(2 * A0) * k0 ** 1.5 / re_lambda
+    c0 = math.sqrt(3.0) * u_rms / mach_t
+    T0 = c0 * c0 / gamma
+    tau_to = math.sqrt(32.0 / A0) * (2 * math.pi) ** 0.25 * k0 ** -3.5
+    return dict(K0=K0, u_rms=u_rms, mu0=mu0, c0=c0, T0=T0, p0=rho0 * T0, tau_to=tau_to)
+
+
+def isotropic(n: int, seed: int, k0: float = 8.0, A0: float = 1.3e-4, mach_t: float = 0.5,
+              gamma: float = 1.4, rho0: float = 1.0) -> np.ndarray:
+    """Solenoidal random velocity on [0, 2 pi]^3 with spectrum
+    E(k) = A0 k^4 exp(-2 k^2 / k0^2) (Sec. 3.4, Eq. (9)), uniform density and
+    temperature.  Recipe: seeded complex Gaussian Fourier modes (numpy PCG64),
+    projection onto k-orthogonal modes, each integer shell |k| in
+    [m - 1/2, m + 1/2) rescaled to the energy E(m), real part of the inverse
+    FFT, and a final rescale to u_rms = sqrt(2 K0 / 3).  T0 = c0^2 / gamma with
+    c0 = sqrt(3) u_rms / Ma_t; returns primitive (rho, u, v, w, p)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = np.fft.fftfreq(n, 1.0 / n)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    k2 = kx * kx + ky * ky + kz * kz
+    kk = np.sqrt(k2)
+    uh = [rng.normal(size=kk.shape) + 1j * rng.normal(size=kk.shape) for _ in range(3)]
+    safe = np.where(k2 > 0, k2, 1.0)
+    div = (kx * uh[0] + ky * uh[1] + kz * uh[2]) / safe
+    uh = [uh[0] - kx * div, uh[1] - ky * div, uh[2] - kz * div]
+    for c in range(3):
+        uh[c][k2 == 0] = 0.0
+    shell = np.floor(kk + 0.5).astype(int)
+    energy = 0.5 * sum(np.abs(u) ** 2 for u in uh)
+    target = A0 * np.arange(shell.max() + 1) ** 4.0 * np.exp(-2.0 * np.arange(shell.max() + 1) ** 2 / k0 ** 2)
+    have = np.bincount(shell.ravel(), weights=energy.ravel(), minlength=len(target))
+    scale = np.sqrt(np.where(have > 0, target / np.where(have > 0, have, 1.0), 0.0))
+    u = [np.real(np.fft.ifftn(uh[c] * scale[shell])) for c in range(3)]
+    cst = isotropic_constants(k0, A0, 72.0, mach_t, gamma, rho0)
+    rms = math.sqrt(sum(float((x * x).mean()) for x in u) / 3.0)
+    u = [x * (cst["u_rms"] / rms) for x in u]
+    rho = np.full_like(u[0], rho0)
+    p = np.full_like(u[0], cst["p0"])
+    return np.stack([rho, u[0], u[1], u[2], p])
+
+
+def channel(nx: int, ny: int, nz: int, seed: int, mach: float = 0.1, gamma: float = 1.4,
+            b: float = 2.0) -> np.ndarray:
+    """Turbulent-channel start of Sec. 3.3 on [0, 2 pi] x [-1, 1] x [0, pi]:
+    U = 1.5 (1 - y^2) at the centres of the tanh-stretched y cells, with seeded
+    uniform noise of 10 % of the local U on u, v and w; rho = 1 and uniform
+    pressure p0 = c0^2 / gamma with c0 = 1 / Ma (unit bulk velocity)."""
+    yf = channel_faces(ny, b)
+    yc = 0.5 * (yf[1:] + yf[:-1])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    U = 1.5 * (1.0 - yc ** 2)[None, :, None] * np.ones((nz, ny, nx))
+    prim = np.zeros((5, nz, ny, nx))
+    prim[0] = 1.0
+    prim[1] = U * (1.0 + 0.1 * rng.uniform(-1, 1, U.shape))
+    prim[2] = 0.1 * U * rng.uniform(-1, 1, U.shape)
+    prim[3] = 0.1 * U * rng.uniform(-1, 1, U.shape)
+    prim[4] = (1.0 / mach) ** 2 / gamma
+    return prim

@@ -171,6 +171,35 @@ class Simulation:
                     rho_min=d.rho_min, p_min=d.p_min, step=d.step)
 
 
+class Ensemble:
+    """Independent simulations advanced by one CUDA graph launch per step."""
+
+    def __init__(self, sims: list):
+        self.lib = _lib.load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(sims))(*[s.h.value for s in sims])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.hgks_ensemble_create(arr, len(sims), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, nsteps: int = 1, dt: float = 0.0, sync: bool = True) -> None:
+        status = self.lib.hgks_ensemble_step(self.h, int(nsteps), float(dt), int(sync))
+        if status != _lib.HGKS_OK:
+            msg = self.lib.hgks_ensemble_last_error(self.h)
+            raise _lib.HgksError(status, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hgks_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class StepWindow(torch.autograd.Function):
     """Q^0 -> Q^K by K steps of fixed dt, differentiable through the library's
     adjoint step.  The forward keeps a checkpoint every `every` steps; the
