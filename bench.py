@@ -262,7 +262,7 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
 
     prim = inputs.taylor_green(N_GRID)
-    cfg = taylor_green_config(N_GRID, args.precision)
+    cfg = taylor_green_config(N_GRID, args.precision, args.recon, args.flux)
     sim = Simulation(cfg)
     sim.init_primitive(prim)
     stream = sim.stream
@@ -293,6 +293,7 @@ def run_ours(args, rank: int, world: int):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "Mcell-updates/s",
                               "ms_per_step": ms, "grid": N_GRID, "precision": args.precision,
+                              "recon": args.recon, "flux": args.flux,
                               "kernel_ms_per_step": prof, "quick": True}), flush=True)
         return
 
@@ -394,6 +395,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=256, help="grid size (profiling cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--recon", default="linear", choices=["linear", "weno-js", "weno-z"],
+                    help="reconstruction (profiling cases; the headline uses linear)")
+    ap.add_argument("--flux", default="smooth", choices=["smooth", "full"],
+                    help="flux (profiling cases; the headline uses smooth)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the isotropic, channel, adjoint and ensemble measurements")
     ap.add_argument("--quick", action="store_true",

@@ -17,6 +17,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhgks.so")
 SOURCES = ["hgks_api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu"]
+# The FP32 kernels use approximate division and square root (2 ulp) and flush
+# denormals: the WENO weights and the flux need no correctly rounded quotient,
+# and the FP32 results are held to their own tolerance against the FP64 oracle.
+# The FP64 kernels keep IEEE division and square root.
+PER_FILE = {"kernels_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *_flags(extra), *PER_FILE.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -155,6 +155,43 @@ __device__ __forceinline__ void mom_apsi(const Mom<T>& m, const T a[5], T out[5]
              h * (tu[i] + tv[i] + tw[i] + tx[i]);
 }
 
+// Symmetric matrix <u^a v^b w^c psi_i psi_j> (upper triangle, 15 entries in
+// the order 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44).
+template <int A, int B, int C, class T>
+__device__ __forceinline__ void mom_psipsi(const Mom<T>& m, T M[15]) {
+  const T x1 = m.xi1, x2 = m.xi2;
+  const T m0 = mm<A, B, C>(m);
+  const T mu1 = mm<A + 1, B, C>(m), mv1 = mm<A, B + 1, C>(m), mw1 = mm<A, B, C + 1>(m);
+  const T mu2 = mm<A + 2, B, C>(m), mv2 = mm<A, B + 2, C>(m), mw2 = mm<A, B, C + 2>(m);
+  M[0] = m0;
+  M[1] = mu1;
+  M[2] = mv1;
+  M[3] = mw1;
+  M[4] = T(0.5) * (mu2 + mv2 + mw2 + m0 * x1);
+  M[5] = mu2;
+  M[6] = mm<A + 1, B + 1, C>(m);
+  M[7] = mm<A + 1, B, C + 1>(m);
+  M[8] = T(0.5) * (mm<A + 3, B, C>(m) + mm<A + 1, B + 2, C>(m) + mm<A + 1, B, C + 2>(m) + mu1 * x1);
+  M[9] = mv2;
+  M[10] = mm<A, B + 1, C + 1>(m);
+  M[11] = T(0.5) * (mm<A + 2, B + 1, C>(m) + mm<A, B + 3, C>(m) + mm<A, B + 1, C + 2>(m) + mv1 * x1);
+  M[12] = mw2;
+  M[13] = T(0.5) * (mm<A + 2, B, C + 1>(m) + mm<A, B + 2, C + 1>(m) + mm<A, B, C + 3>(m) + mw1 * x1);
+  M[14] = T(0.25) * (mm<A + 4, B, C>(m) + mm<A, B + 4, C>(m) + mm<A, B, C + 4>(m) +
+                     T(2) * (mm<A + 2, B + 2, C>(m) + mm<A + 2, B, C + 2>(m) + mm<A, B + 2, C + 2>(m)) +
+                     T(2) * x1 * (mu2 + mv2 + mw2) + x2 * m0);
+}
+
+// out += M a for the symmetric matrix M of mom_psipsi.
+template <class T>
+__device__ __forceinline__ void sym5_matvec_add(const T M[15], const T a[5], T out[5]) {
+  out[0] += M[0] * a[0] + M[1] * a[1] + M[2] * a[2] + M[3] * a[3] + M[4] * a[4];
+  out[1] += M[1] * a[0] + M[5] * a[1] + M[6] * a[2] + M[7] * a[3] + M[8] * a[4];
+  out[2] += M[2] * a[0] + M[6] * a[1] + M[9] * a[2] + M[10] * a[3] + M[11] * a[4];
+  out[3] += M[3] * a[0] + M[7] * a[1] + M[10] * a[2] + M[12] * a[3] + M[13] * a[4];
+  out[4] += M[4] * a[0] + M[8] * a[1] + M[11] * a[2] + M[13] * a[3] + M[14] * a[4];
+}
+
 // Solution a of <a.psi psi> = b (moment matrix of the Maxwellian, K internal
 // degrees of freedom), in closed form.
 template <class T>
@@ -382,10 +419,25 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
     T a[3][5], A[5];
     slopes_and_A(s, g, st.q, st.dq, a, A);
     moments(s, g, side == 0 ? +1 : -1, mh);
-    T u0[5], ua[5], uA[5];
-    mom_psi<1, 0, 0>(mh, u0);
-    mom_u_adotu(mh, a, ua);
-    mom_apsi<1, 0, 0>(mh, A, uA);
+    // Half-space moments as symmetric matrices: <u psi psi^T>, <u u_d psi psi^T>.
+    // <u psi> is the first column of the first; <u (a.psi) u_d psi> = M_d a.
+    T u0[5], ua[5] = {0, 0, 0, 0, 0}, uA[5] = {0, 0, 0, 0, 0};
+    {
+      T M[15];
+      mom_psipsi<1, 0, 0>(mh, M);
+      u0[0] = M[0];
+      u0[1] = M[1];
+      u0[2] = M[2];
+      u0[3] = M[3];
+      u0[4] = M[4];
+      sym5_matvec_add(M, A, uA);
+      mom_psipsi<2, 0, 0>(mh, M);
+      sym5_matvec_add(M, a[0], ua);
+      mom_psipsi<1, 1, 0>(mh, M);
+      sym5_matvec_add(M, a[1], ua);
+      mom_psipsi<1, 0, 1>(mh, M);
+      sym5_matvec_add(M, a[2], ua);
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       const T v3 = s.rho * u0[i], v4 = s.rho * ua[i], v5 = s.rho * uA[i];
