@@ -265,6 +265,7 @@ def run_ours(args, rank: int, world: int):
     cfg = taylor_green_config(N_GRID, args.precision, args.recon, args.flux)
     sim = Simulation(cfg)
     sim.init_primitive(prim)
+    tune = sim.autotune()  # launch shape of the sweep kernel for this grid
     stream = sim.stream
     for _ in range(args.warmup):
         sim.step(1, sync=False)
@@ -293,7 +294,7 @@ def run_ours(args, rank: int, world: int):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "Mcell-updates/s",
                               "ms_per_step": ms, "grid": N_GRID, "precision": args.precision,
-                              "recon": args.recon, "flux": args.flux,
+                              "recon": args.recon, "flux": args.flux, "autotune": tune,
                               "kernel_ms_per_step": prof, "quick": True}), flush=True)
         return
 
@@ -381,6 +382,7 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": sm_clock,
         "workloads": extras,
+        "autotune": tune,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -152,6 +152,20 @@ const char* hgks_ensemble_last_error(const hgks_ensemble* ens);
  * first call.  Enqueued on the context's stream; does not synchronise. */
 hgks_status hgks_adjoint_step(hgks_ctx* ctx, double dt, const double* adj_in, double* adj_out);
 
+/* Tile autotuner (no counterpart in the paper): time the launch shapes of
+ * the sweep kernel on the context's current state -- the tile variants
+ * available for its configuration (three for linear weights + smooth flux in
+ * FP32, one otherwise) times the number of face layers each CTA marches
+ * through -- with CUDA events on the context's stream, and keep the fastest
+ * for later steps.  The state is unchanged (ghost layers and face-flux
+ * buffers are scratch).  Writes the choice and the time of one stage's three
+ * sweeps (ms) if the pointers are non-NULL.  Synchronises. */
+hgks_status hgks_autotune(hgks_ctx* ctx, int* variant_out, int* chunk_out, double* ms_out);
+
+/* Set the sweep launch shape directly (a cached autotuner result): variant
+ * in [0, number of variants), chunk >= 0 face layers per CTA (0 automatic). */
+hgks_status hgks_set_sweep_shape(hgks_ctx* ctx, int variant, int chunk);
+
 /* Profiling aid (not on the hot path): advance ONE step without the graph,
  * with CUDA events around every kernel launch on the context's stream, and
  * write the summed device time in milliseconds of each kernel class to

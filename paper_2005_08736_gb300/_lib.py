@@ -23,7 +23,7 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_init_conservative", "hgks_get_state", "hgks_step", "hgks_diagnostics",
            "hgks_adjoint_step", "hgks_profile_step", "hgks_step_noalloc", "hgks_last_error",
            "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
-           "hgks_ensemble_last_error"]
+           "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 
 
@@ -91,6 +91,9 @@ def load(path: str | None = None):
         L.hgks_diagnostics.argtypes = [vp, ctypes.POINTER(HgksDiag)]
         L.hgks_profile_step.argtypes = [vp, d, pd, i]
         L.hgks_adjoint_step.argtypes = [vp, d, vp, vp]
+        pi_ = ctypes.POINTER(ctypes.c_int)
+        L.hgks_autotune.argtypes = [vp, pi_, pi_, pd]
+        L.hgks_set_sweep_shape.argtypes = [vp, i, i]
         L.hgks_ensemble_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
         L.hgks_ensemble_step.argtypes = [vp, i, d, i]
         L.hgks_ensemble_destroy.argtypes = [vp]

@@ -39,6 +39,11 @@ struct Engine {
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
+  // Sweep launch choices (set by hgks_autotune): tile variant (0: the default
+  // tile; 1, 2: wider tiles of the linear-weight smooth FP32 sweep) and the
+  // number of face layers each CTA marches through (0: automatic).
+  int sweep_variant = 0;
+  int sweep_chunk = 0;
 };
 
 // Kernel classes timed by hgks_profile_step (order of its output array).
@@ -75,11 +80,15 @@ struct Probe {
 template <class T> cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
+// The stage-1 sweep of direction d on e.q alone (tuning).
+template <class T> cudaError_t enqueue_sweep_only(const Engine& e, int d);
 template <class T> cudaError_t enqueue_diag(const Engine& e);
 template <class T> cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative);
 template <class T> cudaError_t enqueue_to_fp64(const Engine& e, double* dst);
 // Adjoint of one S2O4 step at the state e.q with the step dt already in
 // e.scal[0]: adj_out = (dQ^{n+1}/dQ^n)^T adj_in (FP64 device arrays, [5][N]).
+// Number of tile variants of the sweep kernel for the context's configuration.
+int sweep_variant_count(const Engine& e);
 template <class T> cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in,
                                                     double* adj_out);
 cudaError_t enqueue_reset_scalars(const Engine& e);

@@ -7,6 +7,8 @@
 #include "sweep.cuh"
 #include "adjoint.cuh"
 
+#include <type_traits>
+
 namespace hgks {
 
 inline GridDev grid_of(const Engine& e) {
@@ -65,10 +67,8 @@ template <> struct SweepTile<float, FLUX_FULL> { static constexpr int TP = 16, T
 template <> struct SweepTile<double, FLUX_SMOOTH> { static constexpr int TP = 16, TS = 8, NL = 2; };
 template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NL = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE>
-cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
-  constexpr int TP = SweepTile<T, FLUX>::TP, TS = SweepTile<T, FLUX>::TS;
-  constexpr int NL = SweepTile<T, FLUX>::NL;
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
+cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
   a.q = q;
@@ -84,9 +84,12 @@ cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   const int gx = (g.n[P] + TP - 1) / TP, gy = (g.n[S] + TS - 1) / TS;
   // Chunk the march along d so that the grid holds several waves of CTAs.
   const int layers = g.n[d] + 1;
-  const int want_chunks = (4 * e.sms + gx * gy - 1) / (gx * gy);
-  int chunk = (layers + want_chunks - 1) / want_chunks;
-  if (chunk < 2 * NL) chunk = 2 * NL;
+  int chunk = e.sweep_chunk;
+  if (chunk <= 0) {
+    const int want_chunks = (4 * e.sms + gx * gy - 1) / (gx * gy);
+    chunk = (layers + want_chunks - 1) / want_chunks;
+    if (chunk < 2 * NL) chunk = 2 * NL;
+  }
   chunk = (chunk + NL - 1) / NL * NL;
   a.chunk = chunk;
   const int gz = (layers + chunk - 1) / chunk;
@@ -96,6 +99,18 @@ cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   if (err != cudaSuccess) return err;
   kern<<<dim3(gx, gy, gz), 256, smem, e.stream>>>(a);
   return cudaGetLastError();
+}
+
+// Tile variants: 0 is SweepTile; the linear-weight smooth FP32 sweep also has
+// 32x8 and 16x16 tiles with two layers per face-field pass.
+template <class T, int MODE, int FLUX, int STAGE>
+cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
+  if constexpr (std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH) {
+    if (e.sweep_variant == 1) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2>(e, q, d);
+    if (e.sweep_variant == 2) return launch_sweep_tile<T, MODE, FLUX, STAGE, 16, 16, 2>(e, q, d);
+  }
+  return launch_sweep_tile<T, MODE, FLUX, STAGE, SweepTile<T, FLUX>::TP, SweepTile<T, FLUX>::TS,
+                           SweepTile<T, FLUX>::NL>(e, q, d);
 }
 
 template <class T, int MODE, int FLUX>
@@ -144,6 +159,18 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
     k_update<T, 2><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua);
   if (probe) probe->end(e.stream);
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t enqueue_sweep_only(const Engine& e, int d) {
+  const T* q = static_cast<const T*>(e.q);
+  const int mode = e.cfg.recon, flux = e.cfg.flux;
+#define HGKS_SW(M, F) \
+  if (mode == M && flux == F) return launch_sweep<T, M, F, 1>(e, q, d);
+  HGKS_SW(0, 0) HGKS_SW(1, 0) HGKS_SW(2, 0)
+  HGKS_SW(0, 1) HGKS_SW(1, 1) HGKS_SW(2, 1)
+#undef HGKS_SW
+  return cudaErrorInvalidValue;
 }
 
 template <class T>
@@ -272,6 +299,7 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   template cudaError_t enqueue_ghosts<T>(const Engine&, void*, Probe*);      \
   template cudaError_t enqueue_rhs_and_update<T>(const Engine&, int, Probe*); \
   template cudaError_t enqueue_cfl<T>(const Engine&, const void*);           \
+  template cudaError_t enqueue_sweep_only<T>(const Engine&, int);            \
   template cudaError_t enqueue_diag<T>(const Engine&);                       \
   template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
   template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);           \

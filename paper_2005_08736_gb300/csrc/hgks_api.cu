@@ -1,5 +1,6 @@
 // Host runtime behind include/hgks.h: validation, device buffers, the grid
 // metrics, and the captured CUDA graph of one S2O4 step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -508,6 +509,71 @@ hgks_status hgks_ensemble_step(hgks_ensemble* en, int nsteps, double dt, int syn
 
 const char* hgks_ensemble_last_error(const hgks_ensemble* en) { return en ? en->err.c_str() : ""; }
 
+hgks_status hgks_autotune(hgks_ctx* c, int* variant_out, int* chunk_out, double* ms_out) {
+  if (!c) return fail(c, HGKS_E_INVAL, "null context");
+  hgks::Engine& e = c->e;
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  // The state is not changed: only the stage-1 ghost fill and sweeps run (they
+  // write the ghost layers and the face-flux buffers).
+  HGKS_CHECK(c, f32 ? hgks::enqueue_ghosts<float>(e, e.q) : hgks::enqueue_ghosts<double>(e, e.q));
+  HGKS_CHECK(c, hgks::enqueue_set_dt(e, 1e-3));
+  cudaEvent_t t0, t1;
+  HGKS_CHECK(c, cudaEventCreate(&t0));
+  HGKS_CHECK(c, cudaEventCreate(&t1));
+  const int nmax = std::max(e.n[0], std::max(e.n[1], e.n[2])) + 1;
+  const int chunks[] = {0, 8, 16, 32, 64, 128};
+  float best = 1e30f;
+  int best_v = 0, best_c = 0;
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < hgks::sweep_variant_count(e) && err == cudaSuccess; ++v) {
+    for (int ci = 0; ci < 6 && err == cudaSuccess; ++ci) {
+      if (chunks[ci] > 2 * nmax) continue;
+      e.sweep_variant = v;
+      e.sweep_chunk = chunks[ci];
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {  // rep 0 warms up
+        if (rep == 1) err = cudaEventRecord(t0, e.stream);
+        for (int d = 0; d < 3 && err == cudaSuccess; ++d)
+          err = f32 ? hgks::enqueue_sweep_only<float>(e, d) : hgks::enqueue_sweep_only<double>(e, d);
+      }
+      if (err == cudaSuccess) err = cudaEventRecord(t1, e.stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(t1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        best_v = v;
+        best_c = chunks[ci];
+      }
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  HGKS_CHECK(c, err);
+  e.sweep_variant = best_v;
+  e.sweep_chunk = best_c;
+  if (c->graph) {  // the captured step holds the old launch shapes
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (variant_out) *variant_out = best_v;
+  if (chunk_out) *chunk_out = best_c;
+  if (ms_out) *ms_out = best / 2.0;
+  return HGKS_OK;
+}
+
+hgks_status hgks_set_sweep_shape(hgks_ctx* c, int variant, int chunk) {
+  if (!c) return fail(c, HGKS_E_INVAL, "null context");
+  if (variant < 0 || variant >= hgks::sweep_variant_count(c->e) || chunk < 0)
+    return fail(c, HGKS_E_INVAL, "no such sweep variant");
+  c->e.sweep_variant = variant;
+  c->e.sweep_chunk = chunk;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return HGKS_OK;
+}
+
 hgks_status hgks_profile_step(hgks_ctx* c, double dt, double* ms_out, int nclass) {
   if (!c || !ms_out || nclass < hgks::KC_COUNT) return fail(c, HGKS_E_INVAL, "bad argument");
   hgks::Engine& e = c->e;
@@ -540,6 +606,11 @@ const char* hgks_last_error(const hgks_ctx* c) {
 }  // extern "C"
 
 namespace hgks {
+
+int sweep_variant_count(const Engine& e) {
+  return (e.cfg.prec == HGKS_FP32 && e.cfg.recon == HGKS_RECON_LINEAR &&
+          e.cfg.flux == HGKS_FLUX_SMOOTH) ? 3 : 1;
+}
 
 long long face_flux_elems(const Engine& e, int d) {
   long long s = 1;

@@ -158,6 +158,33 @@ class Simulation:
         adj_out.record_stream(self.stream)
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
+    def autotune(self, cache: str | None = None) -> dict:
+        """Pick the sweep's launch shape for this configuration (tile variant and
+        face layers per CTA) by timing the candidates on the current state; with
+        `cache` (a JSON file) a known configuration reuses its stored choice."""
+        import json
+        import os
+        key = json.dumps({f.name: getattr(self.cfg, f.name) for f in fields(self.cfg)},
+                         sort_keys=True)
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        if key in table:
+            v, c = table[key]["variant"], table[key]["chunk"]
+            self._call(self.lib.hgks_set_sweep_shape(self.h, int(v), int(c)))
+            return dict(table[key], cached=True)
+        v, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._call(self.lib.hgks_autotune(self.h, ctypes.byref(v), ctypes.byref(c), ctypes.byref(ms)))
+        rec = {"variant": v.value, "chunk": c.value, "sweep_ms": ms.value}
+        if cache:
+            table[key] = rec
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1)
+            os.replace(tmp, cache)
+        return dict(rec, cached=False)
+
     def profile_step(self, dt: float = 0.0) -> dict:
         """Advance one step with CUDA events per kernel class; device ms per class."""
         ms = (ctypes.c_double * len(_lib.KERNEL_CLASSES))()
