@@ -35,14 +35,15 @@ N_GRID = 256
 PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.09 s/step
 METRIC = "Mcell-updates/s per S2O4 step"
 LAUNCHES_PER_STEP = 23  # cfl, dt, 2 x (3 ghost + 3 x (face fields + flux) + update), time
-# Executed FP32 operations (fadd + fmul + 2 ffma) per face of the stage-1
-# sweep kernel (FP32, linear WENO5, smooth flux), mean of the three directions,
-# counted by ncu on Taylor-Green 128^3 (profiles/k_sweep_fp32_smooth_taylor_green_128.md);
-# the tiles are the same at 256^3, so the count per face carries over.
-FLOPS_PER_FACE_STAGE1 = 2707.0
-# DRAM bytes (read + write) per face of the same kernel in that capture, mean
-# of the three directions; scaled to a 256^3 launch by its face count.
-DRAM_BYTES_PER_FACE_STAGE1 = (163.8 + 143.9 + 48.8 + 39.8 + 49.0 + 39.0) * 1e6 / 3 / (129 * 128 * 128)
+# Executed FP32 operations (fadd + fmul + 2 ffma) and DRAM bytes (read +
+# write) per face of the stage-1 sweep kernel (FP32, linear WENO5, smooth
+# flux), mean of the three directions, counted by ncu on Taylor-Green 128^3
+# for each tile variant the autotuner can choose
+# (profiles/k_sweep_fp32_smooth_taylor_green_128.md); the tiles are the same
+# at 256^3, so the counts per face carry over.
+SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2576.9, "dram": (132.7 + 40.4 + 40.2) / 3},
+                1: {"tile": "32x8, 2 layers", "flops": 2480.3, "dram": (146.9 + 40.4 + 40.7) / 3},
+                2: {"tile": "16x16, 2 layers", "flops": 2402.2, "dram": (145.9 + 41.6 + 41.9) / 3}}
 
 
 def load_peaks():
@@ -232,6 +233,87 @@ def extra_workloads(steps: int):
     return out
 
 
+def run_history(args):
+    """Taylor-Green 128^3 to t = 10 (Sec. 3.1) in FP32 and FP64 with the same
+    fixed dt: kinetic energy E_k every 10 steps, the dissipation rate
+    eps(E_k) = -dE_k/dt by second-order central differences, and the FP32
+    errors against the FP64 path (itself checked against the oracle)."""
+    import numpy as np
+    from paper_2005_08736_gb300 import inputs
+    from paper_2005_08736_gb300.solver import Simulation, taylor_green_config
+    n, t_end, every = args.grid if args.grid != 256 else 128, args.t_end, 10
+    prim = inputs.taylor_green(n)
+    probe = Simulation(taylor_green_config(n, "fp64"))
+    probe.init_primitive(prim)
+    dt = 0.5 * (2 * np.pi / n) / 11.0  # CFL 0.5 with max(|u| + c) = 11 (Sec. 3.2 table)
+    probe.close()
+    nsteps = int(round(t_end / dt))
+    hist, finals, times = {}, {}, {}
+    for prec in ("fp64", "fp32"):
+        sim = Simulation(taylor_green_config(n, prec))
+        sim.init_primitive(prim)
+        ek = [sim.diagnostics()["Ek"]]
+        t0 = time.perf_counter()
+        for k in range(0, nsteps, every):
+            sim.step(min(every, nsteps - k), dt, sync=False)
+            ek.append(sim.diagnostics()["Ek"])
+        times[prec] = time.perf_counter() - t0
+        hist[prec] = np.array(ek)
+        finals[prec] = sim.state()
+        sim.close()
+    t = np.arange(len(hist["fp64"])) * every * dt
+    eps = {k: -np.gradient(v, t) for k, v in hist.items()}
+    ek_err = np.abs(hist["fp32"] - hist["fp64"]) / hist["fp64"]
+    eps_err = np.abs(eps["fp32"] - eps["fp64"]).max() / np.abs(eps["fp64"]).max()
+    a, b = finals["fp32"], finals["fp64"]
+    rho_err = float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max())
+    out = {"workload": f"taylor-green-{n}^3 to t={t_end}", "steps": nsteps, "dt": dt,
+           "Ek_rel_err_max": float(ek_err.max()), "Ek_rel_err_final": float(ek_err[-1]),
+           "eps_rel_err_max": float(eps_err), "rho_rel_linf_final": rho_err,
+           "Ek_final": float(hist["fp64"][-1]), "eps_peak_fp64": float(eps["fp64"].max()),
+           "t_eps_peak": float(t[int(np.argmax(eps["fp64"]))]),
+           "wall_s": times, "samples_every_steps": every,
+           "Ek_fp64_every_100_steps": [float(x) for x in hist["fp64"][::10]]}
+    print(json.dumps(out), flush=True)
+
+
+def run_errors(args):
+    """FP32 against FP64 (same initial state, same fixed dt) for the isotropic
+    (64^3, kappa0 = 4, Ma_t 0.5, WENO-Z + full flux) and channel (64x64x48,
+    walls, stretched y, body force) workloads: relative L-inf per variable and
+    the kinetic-energy error after `steps` steps."""
+    import numpy as np
+    from paper_2005_08736_gb300 import inputs
+    from paper_2005_08736_gb300.solver import Config, Simulation
+    out = {}
+    c = inputs.isotropic_constants(k0=4.0, mach_t=0.5)
+    cases = {
+        "isotropic_64_wenoz_full": (
+            lambda prec: Config(64, 64, 64, prec=prec, recon=2, flux=1, tau_num_C=1.0, prandtl=0.7,
+                                visc=1, mu_ref=c["mu0"], T_ref=c["T0"], visc_exp=0.76,
+                                p_ref=c["p0"]),
+            inputs.isotropic(64, 0, k0=4.0), 0.5 * (2 * np.pi / 64) / (c["c0"] * 1.5)),
+        "channel_64x64x48_linear_smooth": (
+            lambda prec: Config(64, 64, 48, lx=2 * np.pi, ly=2.0, y0=-1.0, lz=np.pi, y_stretch=1,
+                                stretch_b=2.0, bc_y=1, T_wall=100 / 1.4, mu_ref=0.0541 / 180,
+                                force_x=2.93e-3, prec=prec, recon=0, flux=0),
+            inputs.channel(64, 64, 48, 0), 2e-4),
+    }
+    for name, (mk, prim, dt) in cases.items():
+        res = {}
+        for prec in (0, 1):
+            sim = Simulation(mk(prec))
+            sim.init_primitive(prim)
+            sim.step(args.steps, dt)
+            res[prec] = (sim.state(), sim.diagnostics()["Ek"])
+            sim.close()
+        a, b = res[1][0], res[0][0]
+        out[name] = {"steps": args.steps, "dt": dt,
+                     "rel_linf": [float(np.abs(a[v] - b[v]).max() / np.abs(b[v]).max()) for v in range(5)],
+                     "Ek_rel_err": abs(res[1][1] - res[0][1]) / res[0][1]}
+    print(json.dumps(out), flush=True)
+
+
 def config_dict():
     return {"workload": f"taylor-green-{N_GRID}^3 fp32 linear-WENO5 smooth-GKS S2O4",
             "model": "HGKS", "grid": [N_GRID] * 3, "precision": "fp32", "recon": "linear",
@@ -265,7 +347,12 @@ def run_ours(args, rank: int, world: int):
     cfg = taylor_green_config(N_GRID, args.precision, args.recon, args.flux)
     sim = Simulation(cfg)
     sim.init_primitive(prim)
-    tune = sim.autotune()  # launch shape of the sweep kernel for this grid
+    if args.shape:
+        v, c = (int(x) for x in args.shape.split(","))
+        sim._call(sim.lib.hgks_set_sweep_shape(sim.h, v, c))
+        tune = {"variant": v, "chunk": c, "fixed": True}
+    else:
+        tune = sim.autotune()  # launch shape of the sweep kernel for this grid
     stream = sim.stream
     for _ in range(args.warmup):
         sim.step(1, sync=False)
@@ -348,15 +435,17 @@ def run_ours(args, rank: int, world: int):
     sms, lanes = 152, 128
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = sms * lanes * 2 * clock_mhz * 1e6 / 1e12
-    achieved = FLOPS_PER_FACE_STAGE1 * faces_per_launch / (flux_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_sweep stage 1 (FP32, linear WENO5, smooth flux)",
+    counts = SWEEP_COUNTS[tune["variant"]]
+    achieved = counts["flops"] * faces_per_launch / (flux_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu",
+                "kernel": f"k_sweep stage 1 (FP32, linear WENO5, smooth flux, tile {counts['tile']})",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
-                "traffic": DRAM_BYTES_PER_FACE_STAGE1 * faces_per_launch,
-                "flops_per_launch": FLOPS_PER_FACE_STAGE1 * faces_per_launch,
+                "traffic": counts["dram"] * faces_per_launch,
+                "flops_per_launch": counts["flops"] * faces_per_launch,
                 "peak_source": f"nominal: 152 SMs x 128 FP32 lanes x 2 flops x {clock_mhz:.0f} MHz",
                 "launch_ms": flux_ms, "kernel_ms_per_step": prof,
-                "hbm_frac": DRAM_BYTES_PER_FACE_STAGE1 * faces_per_launch / (flux_ms * 1e-3)
+                "hbm_frac": counts["dram"] * faces_per_launch / (flux_ms * 1e-3)
                 / (peaks.get("hbm_gbs", 6802.0) * 1e9)}
     cpu_rate, cpu_s = oracle_sample(2)
     extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
@@ -401,6 +490,13 @@ def main():
                     help="reconstruction (profiling cases; the headline uses linear)")
     ap.add_argument("--flux", default="smooth", choices=["smooth", "full"],
                     help="flux (profiling cases; the headline uses smooth)")
+    ap.add_argument("--shape", default="",
+                    help="V,C: sweep tile variant and march length (skips the autotuner)")
+    ap.add_argument("--history", action="store_true",
+                    help="Taylor-Green E_k / dissipation history, FP32 against FP64")
+    ap.add_argument("--t-end", type=float, default=10.0)
+    ap.add_argument("--errors", action="store_true",
+                    help="FP32 against FP64 on the isotropic and channel workloads")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the isotropic, channel, adjoint and ensemble measurements")
     ap.add_argument("--quick", action="store_true",
@@ -411,7 +507,11 @@ def main():
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.impl == "reference":
+    if args.history:
+        run_history(args)
+    elif args.errors:
+        run_errors(args)
+    elif args.impl == "reference":
         run_reference(args, rank)
     else:
         run_ours(args, rank, world)
