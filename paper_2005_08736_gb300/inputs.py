@@ -117,7 +117,8 @@ def isotropic(n: int, seed: int, k0: float = 8.0, A0: float = 1.3e-4, mach_t: fl
     """Solenoidal random velocity on [0, 2 pi]^3 with spectrum
     E(k) = A0 k^4 exp(-2 k^2 / k0^2) (Sec. 3.4, Eq. (9)), uniform density and
     temperature.  Recipe: seeded complex Gaussian Fourier modes (numpy PCG64),
-    projection onto k-orthogonal modes, each integer shell |k| in
+    projection onto k-orthogonal modes (mean and Nyquist planes removed), each
+    integer shell |k| in
     [m - 1/2, m + 1/2) rescaled to the energy E(m), real part of the inverse
     FFT, and a final rescale to u_rms = sqrt(2 K0 / 3).  T0 = c0^2 / gamma with
     c0 = sqrt(3) u_rms / Ma_t; returns primitive (rho, u, v, w, p)."""
@@ -130,8 +131,12 @@ def isotropic(n: int, seed: int, k0: float = 8.0, A0: float = 1.3e-4, mach_t: fl
     safe = np.where(k2 > 0, k2, 1.0)
     div = (kx * uh[0] + ky * uh[1] + kz * uh[2]) / safe
     uh = [uh[0] - kx * div, uh[1] - ky * div, uh[2] - kz * div]
+    # Drop the mean and the Nyquist planes (k and -k share an index there, so the
+    # real part of the inverse transform would not stay solenoidal).
+    nyq = (np.abs(kx) == n // 2) | (np.abs(ky) == n // 2) | (np.abs(kz) == n // 2) if n % 2 == 0 \
+        else np.zeros_like(k2, dtype=bool)
     for c in range(3):
-        uh[c][k2 == 0] = 0.0
+        uh[c][(k2 == 0) | nyq] = 0.0
     shell = np.floor(kk + 0.5).astype(int)
     energy = 0.5 * sum(np.abs(u) ** 2 for u in uh)
     target = A0 * np.arange(shell.max() + 1) ** 4.0 * np.exp(-2.0 * np.arange(shell.max() + 1) ** 2 / k0 ** 2)
