@@ -153,10 +153,11 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   ua.force_x = T(e.cfg.force_x);
   ua.rho_r = T(e.cfg.rho_ref);
   if (probe) probe->begin(e.stream, KC_UPDATE);
+  const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
   if (stage == 1)
-    k_update<T, 1><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua);
+    k_update<T, 1><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
   else
-    k_update<T, 2><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua);
+    k_update<T, 2><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
   if (probe) probe->end(e.stream);
   return cudaGetLastError();
 }

@@ -152,17 +152,33 @@ struct UpdateArgs {
 
 // Stage 1: L, dL of Q^n; Q* = Q^n + dt/2 L + dt^2/8 dL; inc = dt L + dt^2/6 dL.
 // Stage 2: dL of Q*; Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), then the body force.
+// One CTA per 32 x 8 cells of an x-y plane.  The x-face fluxes are stored y
+// fastest ([z][x][y]); the CTA stages its 33 x 8 x-faces through shared
+// memory so that both their loads and the per-cell reads are contiguous.
+constexpr int kUpdTX = 32, kUpdTY = 8;
 template <class T, int STAGE>
-__global__ void __launch_bounds__(256) k_update(UpdateArgs<T> a) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= a.g.N) return;
+__global__ void __launch_bounds__(kUpdTX * kUpdTY) k_update(UpdateArgs<T> a) {
+  constexpr int NV = STAGE == 1 ? 10 : 5;  // stage 2 needs dF only
+  constexpr int V0 = STAGE == 1 ? 0 : 5;
+  __shared__ T sfx[NV][kUpdTX + 1][kUpdTY];
   const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-  const int x = int(tid % nx);
-  const long long r = tid / nx;
-  const int y = int(r % ny), z = int(r / ny);
+  const int x0 = blockIdx.x * kUpdTX, y0 = blockIdx.y * kUpdTY, z = blockIdx.z;
+  const int tid = threadIdx.x;
   const long long SX = (long long)(nx + 1) * ny * nz, SY = (long long)nx * (ny + 1) * nz,
                   SZ = (long long)nx * ny * (nz + 1);
-  const long long ix = ((long long)z * ny + y) * (nx + 1) + x;
+  for (int i = tid; i < (kUpdTX + 1) * kUpdTY; i += kUpdTX * kUpdTY) {
+    const int xi = i / kUpdTY, yi = i % kUpdTY;
+    const int x = x0 + xi, y = y0 + yi;
+    const bool ok = x <= nx && y < ny;
+    const long long fi = ((long long)z * (nx + 1) + x) * ny + y;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sfx[v][xi][yi] = ok ? a.fx[(V0 + v) * SX + fi] : T(0);
+  }
+  __syncthreads();
+  const int tx = tid % kUpdTX, ty = tid / kUpdTX;
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= nx || y >= ny) return;
+  const long long cell = ((long long)z * ny + y) * nx + x;
   const long long iy = ((long long)z * (ny + 1) + y) * nx + x;
   const long long iz = ((long long)z * ny + y) * nx + x;
   const long long sy = nx, sz = (long long)nx * ny;
@@ -173,26 +189,26 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs<T> a) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const int o = 5 + v;
-    dL[v] = -((a.fx[o * SX + ix + 1] - a.fx[o * SX + ix]) * ix_w +
+    dL[v] = -((sfx[o - V0][tx + 1][ty] - sfx[o - V0][tx][ty]) * ix_w +
               (a.fy[o * SY + iy + sy] - a.fy[o * SY + iy]) * iy_w +
               (a.fz[o * SZ + iz + sz] - a.fz[o * SZ + iz]) * iz_w);
   }
   if (STAGE == 1) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const T L = -((a.fx[v * SX + ix + 1] - a.fx[v * SX + ix]) * ix_w +
+      const T L = -((sfx[v][tx + 1][ty] - sfx[v][tx][ty]) * ix_w +
                     (a.fy[v * SY + iy + sy] - a.fy[v * SY + iy]) * iy_w +
                     (a.fz[v * SZ + iz + sz] - a.fz[v * SZ + iz]) * iz_w);
       const T qn = a.q[v * a.g.P + pi];
       a.qs[v * a.g.P + pi] = qn + T(0.5) * dt * L + T(0.125) * dt * dt * dL[v];
-      a.inc[v * a.g.N + tid] = dt * L + dt * dt / T(6) * dL[v];
+      a.inc[v * a.g.N + cell] = dt * L + dt * dt / T(6) * dL[v];
     }
   } else {
     T qn[5], dq[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       qn[v] = a.q[v * a.g.P + pi];
-      dq[v] = a.inc[v * a.g.N + tid] + dt * dt / T(3) * dL[v];
+      dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
     }
     if (a.force_x != T(0)) {
       // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
@@ -205,9 +221,9 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs<T> a) {
       // Compensated (Kahan) accumulation of Q^{n+1} = Q^n + dq.
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const T y = dq[v] - a.comp[v * a.g.N + tid];
-        const T t = qn[v] + y;
-        a.comp[v * a.g.N + tid] = (t - qn[v]) - y;
+        const T yv = dq[v] - a.comp[v * a.g.N + cell];
+        const T t = qn[v] + yv;
+        a.comp[v * a.g.N + cell] = (t - qn[v]) - yv;
         a.q[v * a.g.P + pi] = t;
       }
     } else {

@@ -191,15 +191,21 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   const int st2 = t1P ? HP : 1;
   const T dt = T(a.scal[0]);
   const long long FS = (long long)(a.g.n[0] + (d == 0)) * (a.g.n[1] + (d == 1)) * (a.g.n[2] + (d == 2));
-  long long fout = 0;
-  {
+  // Face-flux layout: x fastest for the y and z faces; y fastest ([z][x][y])
+  // for the x faces, so that the tile's threads (running along y) store
+  // contiguously; the update kernel reads them through a shared-memory transpose.
+  long long fout, fstep;
+  if (d == 0) {
+    fout = (long long)cS * (a.g.n[0] + 1) * a.g.n[1] + cP;
+    fstep = a.g.n[1];
+  } else {
     int c[3];
     c[d] = 0;
     c[P] = cP;
     c[S] = cS;
     fout = ((long long)c[2] * (a.g.n[1] + (d == 1)) + c[1]) * (a.g.n[0] + (d == 0)) + c[0];
+    fstep = d == 1 ? (long long)a.g.n[0] : (long long)a.g.n[0] * a.g.n[1];
   }
-  const long long fstep = d == 0 ? 1LL : (d == 1 ? (long long)a.g.n[0] : (long long)a.g.n[0] * a.g.n[1]);
 
   for (int fb = f0; fb < f1; fb += NL) {
     // ---------------- phase 1: face fields of layers fb .. fb+NL-1 ----------------
