@@ -41,9 +41,9 @@ LAUNCHES_PER_STEP = 23  # cfl, dt, 2 x (3 ghost + 3 x (face fields + flux) + upd
 # for each tile variant the autotuner can choose
 # (profiles/k_sweep_fp32_smooth_taylor_green_128.md); the tiles are the same
 # at 256^3, so the counts per face carry over.
-SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2576.9, "dram": (132.7 + 40.4 + 40.2) / 3},
-                1: {"tile": "32x8, 2 layers", "flops": 2480.3, "dram": (146.9 + 40.4 + 40.7) / 3},
-                2: {"tile": "16x16, 2 layers", "flops": 2402.2, "dram": (145.9 + 41.6 + 41.9) / 3}}
+SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2576.9, "dram": 43.2},
+                1: {"tile": "32x8, 2 layers", "flops": 2480.3, "dram": 42.7},
+                2: {"tile": "16x16, 2 layers", "flops": 2402.2, "dram": 43.6}}
 
 
 def load_peaks():
