@@ -123,6 +123,37 @@ typedef struct {
 /* FP64 reductions of the current state (synchronises). */
 hgks_status hgks_diagnostics(hgks_ctx* ctx, hgks_diag* out);
 
+/* Turbulence statistics of the current state (Sec. 3.1 and Sec. 3.4).  <f>
+ * is the volume average over the domain, rho0 = rho_ref, U the velocity,
+ * G_ij = dU_i/dx_j by the sixth-order central difference, theta = tr G,
+ * omega = curl U, S^d the deviatoric part of (G + G^T)/2, mu the local
+ * viscosity mu(T) of the configured law and mu_b = 2N/(3(N+3)) mu its bulk
+ * part (N internal degrees of freedom). */
+typedef struct {
+  double t;          /* time of the state */
+  double Ek;         /* <rho |U|^2/2> / rho0 */
+  double K;          /* <rho |U|^2/2> */
+  double zeta;       /* <rho |omega|^2/2> / rho0 (enstrophy) */
+  double eps1;       /* 2 <mu S^d:S^d> / rho0 */
+  double eps2;       /* <mu_b theta^2> / rho0 */
+  double eps3;       /* -<p theta> / rho0 */
+  double rho_mean, rho_rms;  /* <rho>, sqrt(<(rho - <rho>)^2>) */
+  double u_rms;      /* sqrt(<|U|^2> / 3) */
+  double Su, Fu;     /* means over the axes i with <(d_i U_i)^2> > 0 of
+                        <(d_i U_i)^3>/<(d_i U_i)^2>^1.5 and <(d_i U_i)^4>/<(d_i U_i)^2>^2 */
+  double eps_s;      /* <mu |omega|^2> (solenoidal dissipation) */
+  double eps_d;      /* 4/3 <mu theta^2> (dilatational dissipation) */
+  double p_theta;    /* <p theta> (pressure dilatation) */
+  double theta_rms, omega_rms;  /* sqrt(<theta^2>), sqrt(<|omega|^2>) */
+  double du2[3], du3[3], du4[3];  /* <(d_i U_i)^k>, k = 2, 3, 4 */
+} hgks_turbulence;
+
+/* Fill *out from the current state: one ghost fill, one statistics kernel
+ * and one final reduction on the context's stream, then a synchronise.
+ * Needs a periodic, uniform grid (E_UNSUPPORTED for walls or a stretched y).
+ * Allocates its FP64 partial-sum buffers on the first call. */
+hgks_status hgks_turbulence_stats(hgks_ctx* ctx, hgks_turbulence* out);
+
 /* Ensembles (no counterpart in the paper): a batch of independent contexts,
  * e.g. instances of uneven sizes, advanced together.  hgks_ensemble_create
  * takes n distinct contexts on the same device, each on its own stream (the

@@ -23,7 +23,8 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_init_conservative", "hgks_get_state", "hgks_step", "hgks_diagnostics",
            "hgks_adjoint_step", "hgks_profile_step", "hgks_step_noalloc", "hgks_last_error",
            "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
-           "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape"]
+           "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape",
+           "hgks_turbulence_stats"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 
 
@@ -54,6 +55,13 @@ class HgksDiag(ctypes.Structure):
         ("Ek", ctypes.c_double), ("rho_min", ctypes.c_double), ("p_min", ctypes.c_double),
         ("step", ctypes.c_longlong),
     ]
+
+
+class HgksTurbulence(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "t", "Ek", "K", "zeta", "eps1", "eps2", "eps3", "rho_mean", "rho_rms", "u_rms", "Su", "Fu",
+        "eps_s", "eps_d", "p_theta", "theta_rms", "omega_rms")] + [
+        ("du2", ctypes.c_double * 3), ("du3", ctypes.c_double * 3), ("du4", ctypes.c_double * 3)]
 
 
 _lock = threading.Lock()
@@ -89,6 +97,7 @@ def load(path: str | None = None):
         L.hgks_get_state.argtypes = [vp, vp, i]
         L.hgks_step.argtypes = [vp, i, d, i, pd]
         L.hgks_diagnostics.argtypes = [vp, ctypes.POINTER(HgksDiag)]
+        L.hgks_turbulence_stats.argtypes = [vp, ctypes.POINTER(HgksTurbulence)]
         L.hgks_profile_step.argtypes = [vp, d, pd, i]
         L.hgks_adjoint_step.argtypes = [vp, d, vp, vp]
         pi_ = ctypes.POINTER(ctypes.c_int)

@@ -36,6 +36,8 @@ struct Engine {
   void* adj_mu = nullptr;   // adjoint: cotangent of Q*, 5 * N
   void* adj_wL = nullptr;   // adjoint: cotangents of L and dL/dt, 5 * N each
   void* adj_wdL = nullptr;
+  double* turb_part = nullptr;  // turbulence statistics: per-block partials
+  double* turb_out = nullptr;   // and the final sums (allocated on first use)
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
@@ -44,6 +46,28 @@ struct Engine {
   // number of face layers each CTA marches through (0: automatic).
   int sweep_variant = 0;
   int sweep_chunk = 0;
+};
+
+// Turbulence statistics (turbulence.cuh): raw sums, each the sum over cells
+// of the quantity times the cell volume.
+enum TurbSum {
+  TS_VOL = 0,      // volume
+  TS_KE,           // 1/2 rho |U|^2
+  TS_ENS,          // 1/2 rho |omega|^2
+  TS_MU_SDSD,      // mu S^d : S^d
+  TS_MUB_TH2,      // mu_b theta^2
+  TS_P_TH,         // p theta
+  TS_DRHO,         // rho - rho_ref
+  TS_DRHO2,        // (rho - rho_ref)^2
+  TS_Q2,           // |U|^2
+  TS_MU_W2,        // mu |omega|^2
+  TS_MU_TH2,       // mu theta^2
+  TS_TH2,          // theta^2
+  TS_W2,           // |omega|^2
+  TS_DU2,          // (d_i U_i)^2, i = x, y, z (3 entries)
+  TS_DU3 = TS_DU2 + 3,
+  TS_DU4 = TS_DU3 + 3,
+  kTurbSums = TS_DU4 + 3
 };
 
 // Kernel classes timed by hgks_profile_step (order of its output array).
@@ -78,6 +102,7 @@ struct Probe {
 
 // Kernel sequences, implemented per floating type in kernels_f32.cu / kernels_f64.cu.
 template <class T> cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe = nullptr);
+template <class T> cudaError_t enqueue_turbulence(const Engine& e);
 template <class T> cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
 // The stage-1 sweep of direction d on e.q alone (tuning).

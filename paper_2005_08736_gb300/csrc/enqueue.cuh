@@ -6,6 +6,7 @@
 #include "kernels.cuh"
 #include "sweep.cuh"
 #include "adjoint.cuh"
+#include "turbulence.cuh"
 
 #include <type_traits>
 
@@ -193,6 +194,36 @@ cudaError_t enqueue_diag(const Engine& e) {
   return cudaGetLastError();
 }
 
+// Turbulence statistics: ghost fill of Q^n, per-block FP64 sums, final sum
+// into e.turb_out (kTurbSums doubles).
+template <class T>
+cudaError_t enqueue_turbulence(const Engine& e) {
+  cudaError_t err = enqueue_ghosts<T>(e, e.q, nullptr);
+  if (err != cudaSuccess) return err;
+  const hgks_config& c = e.cfg;
+  TurbArgs a;
+  const double L[3] = {c.lx, c.ly, c.lz};
+  double vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const double h = L[d] / e.n[d];
+    a.inv60h[d] = 1.0 / (60.0 * h);
+    vol *= h;
+  }
+  a.vol = vol;
+  a.rho_r = c.rho_ref;
+  a.E_r = c.p_ref / (c.gamma - 1.0);
+  a.gm1 = c.gamma - 1.0;
+  a.visc_law = c.visc;
+  a.mu_ref = c.mu_ref;
+  a.T_ref_inv = 1.0 / c.T_ref;
+  a.visc_exp = c.visc_exp;
+  const double K = (5.0 - 3.0 * c.gamma) / (c.gamma - 1.0);
+  a.mub_ratio = 2.0 * K / (3.0 * (K + 3.0));
+  k_turb<T><<<e.diag_blocks, 256, 0, e.stream>>>(static_cast<const T*>(e.q), grid_of(e), a, e.turb_part);
+  k_turb_final<<<1, 256, 0, e.stream>>>(e.turb_part, e.diag_blocks, e.turb_out);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative) {
   k_from_prim<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
@@ -302,6 +333,7 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   template cudaError_t enqueue_cfl<T>(const Engine&, const void*);           \
   template cudaError_t enqueue_sweep_only<T>(const Engine&, int);            \
   template cudaError_t enqueue_diag<T>(const Engine&);                       \
+  template cudaError_t enqueue_turbulence<T>(const Engine&);                 \
   template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
   template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);           \
   template cudaError_t enqueue_adjoint_step<T>(const Engine&, const double*, double*);

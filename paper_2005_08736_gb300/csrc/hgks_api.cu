@@ -98,7 +98,7 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 void free_all(hgks::Engine& e) {
   void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
-                  e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL};
+                  e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -374,6 +374,59 @@ hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
   out->Ek = r[5] / (e.cfg.rho_ref * vol);
   out->rho_min = r[6];
   out->p_min = r[7];
+  return HGKS_OK;
+}
+
+hgks_status hgks_turbulence_stats(hgks_ctx* c, hgks_turbulence* out) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  if (e.cfg.bc_y != HGKS_BC_PERIODIC || e.cfg.y_stretch)
+    return fail(c, HGKS_E_UNSUPPORTED, "turbulence statistics need a periodic uniform grid");
+  constexpr int NS = hgks::kTurbSums;
+  if (!e.turb_part) {
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_part, sizeof(double) * NS * e.diag_blocks));
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_out, sizeof(double) * NS));
+  }
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_turbulence<float>(e) : hgks::enqueue_turbulence<double>(e));
+  double r[NS], scal[3];
+  HGKS_CHECK(c, cudaMemcpyAsync(r, e.turb_out, NS * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  using namespace hgks;
+  const double V = r[TS_VOL], rho0 = e.cfg.rho_ref;
+  auto avg = [&](int k) { return r[k] / V; };
+  out->t = scal[1];
+  out->K = avg(TS_KE);
+  out->Ek = out->K / rho0;
+  out->zeta = avg(TS_ENS) / rho0;
+  out->eps1 = 2.0 * avg(TS_MU_SDSD) / rho0;
+  out->eps2 = avg(TS_MUB_TH2) / rho0;
+  out->eps3 = -avg(TS_P_TH) / rho0;
+  const double dm = avg(TS_DRHO);
+  out->rho_mean = rho0 + dm;
+  out->rho_rms = std::sqrt(std::fmax(avg(TS_DRHO2) - dm * dm, 0.0));
+  out->u_rms = std::sqrt(avg(TS_Q2) / 3.0);
+  double su = 0.0, fu = 0.0;
+  int live = 0;
+  for (int i = 0; i < 3; ++i) {
+    const double m2 = avg(TS_DU2 + i), m3 = avg(TS_DU3 + i), m4 = avg(TS_DU4 + i);
+    out->du2[i] = m2;
+    out->du3[i] = m3;
+    out->du4[i] = m4;
+    if (m2 > 0.0) {
+      su += m3 / (m2 * std::sqrt(m2));
+      fu += m4 / (m2 * m2);
+      ++live;
+    }
+  }
+  out->Su = live ? su / live : 0.0;
+  out->Fu = live ? fu / live : 0.0;
+  out->eps_s = avg(TS_MU_W2);
+  out->eps_d = 4.0 / 3.0 * avg(TS_MU_TH2);
+  out->p_theta = avg(TS_P_TH);
+  out->theta_rms = std::sqrt(avg(TS_TH2));
+  out->omega_rms = std::sqrt(avg(TS_W2));
   return HGKS_OK;
 }
 

@@ -197,6 +197,18 @@ class Simulation:
         return dict(t=d.t, dt=d.dt, mass=d.mass, mom=tuple(d.mom), energy=d.energy, Ek=d.Ek,
                     rho_min=d.rho_min, p_min=d.p_min, step=d.step)
 
+    def turbulence(self) -> dict:
+        """Turbulence statistics of the current state (Sec. 3.1, Sec. 3.4):
+        E_k, K, enstrophy zeta, eps1..eps3, rho_rms, u_rms, S_u, F_u, eps_s,
+        eps_d, <p theta> and the per-axis moments du{2,3,4}_{x,y,z}."""
+        d = _lib.HgksTurbulence()
+        self._call(self.lib.hgks_turbulence_stats(self.h, ctypes.byref(d)))
+        out = {k: getattr(d, k) for k, _ in d._fields_ if not k.startswith("du")}
+        for k in ("du2", "du3", "du4"):
+            for i, a in enumerate("xyz"):
+                out[f"{k}_{a}"] = getattr(d, k)[i]
+        return out
+
 
 class Ensemble:
     """Independent simulations advanced by one CUDA graph launch per step."""
