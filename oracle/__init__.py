@@ -59,6 +59,7 @@ class OracleConfig(ctypes.Structure):
         ("recon", ctypes.c_int), ("flux", ctypes.c_int),
         ("tau_num_C", ctypes.c_double),
         ("cfl", ctypes.c_double),
+        ("force_mode", ctypes.c_int), ("mass_flux", ctypes.c_double),
     ]
 
 
@@ -78,6 +79,8 @@ def lib():
             L.oracle_step.argtypes = [vp, i, d]
             L.oracle_time.restype = d
             L.oracle_time.argtypes = [vp]
+            L.oracle_last_force.restype = d
+            L.oracle_last_force.argtypes = [vp]
             L.oracle_cfl_dt.restype = d
             L.oracle_cfl_dt.argtypes = [vp]
             L.oracle_rhs.argtypes = [vp, d, pd, pd]
@@ -138,6 +141,8 @@ class Config:
     flux: int = FLUX_SMOOTH
     tau_num_C: float = 0.0
     cfl: float = 0.5
+    force_mode: int = 0
+    mass_flux: float = 0.0
 
     def c_struct(self) -> OracleConfig:
         return OracleConfig(**{k: getattr(self, k) for k, _ in OracleConfig._fields_})
@@ -177,6 +182,11 @@ class Solver:
 
     def cfl_dt(self) -> float:
         return lib().oracle_cfl_dt(self._h)
+
+    @property
+    def last_force(self) -> float:
+        """Streamwise force f_x of the last step (Sec. 3.3)."""
+        return lib().oracle_last_force(self._h)
 
     def rhs(self, dt: float):
         L = np.empty(self.shape)

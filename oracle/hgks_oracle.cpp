@@ -441,6 +441,8 @@ typedef struct {
   int recon, flux;   // RECON_*, FLUX_*
   double tau_num_C;  // C of the numerical collision time (Sec. 3); 0 disables
   double cfl;
+  int force_mode;    // 0 the constant force_x; 1 the constant-mass-flux force of Sec. 3.3
+  double mass_flux;  // force_mode 1: the volume average of rho U that the force keeps
 } oracle_config;
 
 }  // extern "C"
@@ -556,6 +558,7 @@ struct Solver {
   std::vector<double> q;           // padded conservative state [5][pz][py][px]
   double t = 0.0;
   long step = 0;
+  double last_force = 0.0;         // f_x of the last step
 
   explicit Solver(const oracle_config& cfg) : c(cfg) {
     n[0] = c.nx;
@@ -838,23 +841,44 @@ struct Solver {
             Q(qs, v, i, j, k) = s2o4_stage1(Q(q, v, i, j, k), L0[v * N + ci], dL0[v * N + ci], dt);
           }
     rhs(qs, dt, L1, dL1);
-    for (int k = 0; k < n[2]; ++k)
-      for (int j = 0; j < n[1]; ++j)
-        for (int i = 0; i < n[0]; ++i) {
-          const size_t ci = (size_t(k) * n[1] + j) * n[0] + i;
-          double old[5], nw[5];
-          for (int v = 0; v < 5; ++v) {
-            old[v] = Q(q, v, i, j, k);
-            nw[v] = s2o4_stage2(old[v], L0[v * N + ci], dL0[v * N + ci], dL1[v * N + ci], dt);
+    // Second stage without the force: Q~^{n+1}.
+    std::vector<double> qn = q;
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            const size_t ci = (size_t(k) * n[1] + j) * n[0] + i;
+            Q(q, v, i, j, k) = s2o4_stage2(Q(qn, v, i, j, k), L0[v * N + ci], dL0[v * N + ci],
+                                           dL1[v * N + ci], dt);
           }
-          if (c.force_x != 0.0) {
-            // Sec. 3.3: (rho U)^{n+1} = (rho U)~ + dt/2 (rho^{n+1} + rho^n) f_x,
-            // (rho E)^{n+1} = (rho E)~ + dt/2 ((rho U)^{n+1} + (rho U)^n) f_x.
-            nw[1] += 0.5 * dt * (nw[0] + old[0]) * c.force_x;
-            nw[4] += 0.5 * dt * (nw[1] + old[1]) * c.force_x;
+    // Streamwise force of Sec. 3.3.  force_mode 0: the constant f_x.
+    // force_mode 1: f_x = (int rho U_b - int (rho U)~^{n+1}) /
+    // (dt * 1/2 int (rho^n + rho~^{n+1})), which makes int (rho U)^{n+1} equal
+    // the target; int rho U_b is read as mass_flux times the box volume.
+    double f = c.force_x;
+    if (c.force_mode == 1) {
+      double vol = 0.0, mom = 0.0, half_rho = 0.0;
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            const double dv = w(0, i) * w(1, j) * w(2, k);
+            vol += dv;
+            mom += Q(q, 1, i, j, k) * dv;
+            half_rho += 0.5 * (Q(qn, 0, i, j, k) + Q(q, 0, i, j, k)) * dv;
           }
-          for (int v = 0; v < 5; ++v) Q(q, v, i, j, k) = nw[v];
-        }
+      f = (c.mass_flux * vol - mom) / (dt * half_rho);
+    }
+    last_force = f;
+    if (f != 0.0) {
+      // (rho U)^{n+1} = (rho U)~ + dt/2 (rho^{n+1} + rho^n) f_x,
+      // (rho E)^{n+1} = (rho E)~ + dt/2 ((rho U)^{n+1} + (rho U)^n) f_x.
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            Q(q, 1, i, j, k) += 0.5 * dt * (Q(q, 0, i, j, k) + Q(qn, 0, i, j, k)) * f;
+            Q(q, 4, i, j, k) += 0.5 * dt * (Q(q, 1, i, j, k) + Q(qn, 1, i, j, k)) * f;
+          }
+    }
     t += dt;
     ++step;
     return dt;
@@ -893,6 +917,8 @@ double oracle_step(void* h, int nsteps, double dt) {
   return used;
 }
 double oracle_time(void* h) { return static_cast<Solver*>(h)->t; }
+// Streamwise force f_x applied in the last step.
+double oracle_last_force(void* h) { return static_cast<Solver*>(h)->last_force; }
 double oracle_cfl_dt(void* h) { return static_cast<Solver*>(h)->cfl_dt(); }
 // L(Q) and dL/dt of the current state (interior cells, [5][nz][ny][nx]).
 void oracle_rhs(void* h, double dt, double* L, double* dL) {
