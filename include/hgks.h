@@ -55,6 +55,11 @@ typedef enum { HGKS_RECON_LINEAR = 0, HGKS_RECON_WENO_JS = 1, HGKS_RECON_WENO_Z 
 typedef enum { HGKS_FLUX_SMOOTH = 0, HGKS_FLUX_FULL = 1 } hgks_flux;
 typedef enum { HGKS_VISC_CONST = 0, HGKS_VISC_POWER = 1 } hgks_visc;
 typedef enum { HGKS_FP64 = 0, HGKS_FP32 = 1 } hgks_prec;
+/* Streamwise body force of Sec. 3.3: the constant force_x, or the force that
+ * keeps the volume integral of rho U at mass_flux times the box volume
+ * (f_x = (that target - int (rho U)~^{n+1}) / (dt/2 int (rho^n + rho~^{n+1})),
+ * with ~ the state after the two S2O4 stages). */
+typedef enum { HGKS_FORCE_CONSTANT = 0, HGKS_FORCE_MASS_FLUX = 1 } hgks_force;
 
 typedef struct {
   int nx, ny, nz;                  /* interior cells; >= 6 on every axis */
@@ -72,6 +77,8 @@ typedef struct {
   int prec;                        /* hgks_prec: arithmetic and storage type */
   double rho_ref, p_ref;           /* reference state at rest; the state is stored as its
                                       deviation from it (must be > 0) */
+  int force_mode;                  /* hgks_force (force_x is ignored in mode 1) */
+  double mass_flux;                /* HGKS_FORCE_MASS_FLUX: target volume average of rho U */
 } hgks_config;
 
 typedef struct hgks_ctx hgks_ctx;  /* opaque; owns every device buffer it uses */
@@ -118,6 +125,7 @@ typedef struct {
   double Ek;             /* (1/(rho_ref |Omega|)) sum rho |U|^2/2 |Omega_c| (Sec. 3.1) */
   double rho_min, p_min;
   long long step;
+  double force_x;        /* streamwise force of the last step (Sec. 3.3) */
 } hgks_diag;
 
 /* FP64 reductions of the current state (synchronises). */

@@ -45,6 +45,7 @@ class HgksConfig(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("prec", ctypes.c_int),
         ("rho_ref", ctypes.c_double), ("p_ref", ctypes.c_double),
+        ("force_mode", ctypes.c_int), ("mass_flux", ctypes.c_double),
     ]
 
 
@@ -53,7 +54,7 @@ class HgksDiag(ctypes.Structure):
         ("t", ctypes.c_double), ("dt", ctypes.c_double),
         ("mass", ctypes.c_double), ("mom", ctypes.c_double * 3), ("energy", ctypes.c_double),
         ("Ek", ctypes.c_double), ("rho_min", ctypes.c_double), ("p_min", ctypes.c_double),
-        ("step", ctypes.c_longlong),
+        ("step", ctypes.c_longlong), ("force_x", ctypes.c_double),
     ]
 
 

@@ -151,14 +151,25 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   ua.wz = static_cast<const T*>(e.w[2]);
   ua.scal = e.scal;
   ua.g = grid_of(e);
-  ua.force_x = T(e.cfg.force_x);
+  const bool mass_flux = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX;
+  ua.force_x = mass_flux ? T(0) : T(e.cfg.force_x);
   ua.rho_r = T(e.cfg.rho_ref);
+  ua.stash = mass_flux && stage == 2 ? static_cast<T*>(e.qs) : nullptr;
   if (probe) probe->begin(e.stream, KC_UPDATE);
   const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
   if (stage == 1)
     k_update<T, 1><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
   else
     k_update<T, 2><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
+  if (mass_flux && stage == 2) {
+    // Sec. 3.3: the force that keeps the volume integral of rho U at its target.
+    const GridDev g = grid_of(e);
+    k_massflux_sums<T><<<e.diag_blocks, 256, 0, e.stream>>>(
+        ua.q, ua.stash, ua.comp, g, ua.wx, ua.wy, ua.wz, e.cfg.rho_ref, e.part);
+    k_massflux_force<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, e.cfg.mass_flux, e.scal);
+    k_force_apply<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua.q, ua.stash, ua.comp, g,
+                                                                 e.cfg.rho_ref, e.scal);
+  }
   if (probe) probe->end(e.stream);
   return cudaGetLastError();
 }

@@ -61,6 +61,8 @@ std::string hgks::validate_config(const hgks_config& c) {
   if (c.y_stretch && c.bc_y != HGKS_BC_WALL_ISOTHERMAL) return "the tanh mapping needs wall boundaries";
   if (c.y_stretch && !(c.stretch_b > 0.0)) return "stretch_b must be positive";
   if (!(c.tau_num_C >= 0.0)) return "tau_num_C must be non-negative";
+  if (c.force_mode != HGKS_FORCE_CONSTANT && c.force_mode != HGKS_FORCE_MASS_FLUX)
+    return "unknown force mode";
   return "";
 }
 
@@ -151,6 +153,7 @@ static __global__ void k_reset_scalars(double* scal, unsigned long long* dtmin, 
   scal[0] = 0.0;
   scal[1] = 0.0;
   scal[2] = 0.0;
+  scal[3] = 0.0;
   *dtmin = (unsigned long long)__double_as_longlong(1e300);
   *flag = 0;
 }
@@ -358,9 +361,9 @@ hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
   hgks::Engine& e = c->e;
   const bool f32 = e.cfg.prec == HGKS_FP32;
   HGKS_CHECK(c, f32 ? hgks::enqueue_diag<float>(e) : hgks::enqueue_diag<double>(e));
-  double r[8], scal[3];
+  double r[8], scal[4];
   HGKS_CHECK(c, cudaMemcpyAsync(r, e.diag_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
-  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
   HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
   const double vol = e.cfg.lx * e.cfg.ly * e.cfg.lz;
   out->t = scal[1];
@@ -374,6 +377,7 @@ hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
   out->Ek = r[5] / (e.cfg.rho_ref * vol);
   out->rho_min = r[6];
   out->p_min = r[7];
+  out->force_x = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX ? scal[3] : e.cfg.force_x;
   return HGKS_OK;
 }
 
@@ -436,7 +440,8 @@ hgks_status hgks_adjoint_step(hgks_ctx* c, double dt, const double* adj_in, doub
   hgks::Engine& e = c->e;
   if (e.cfg.bc_y != HGKS_BC_PERIODIC)
     return fail(c, HGKS_E_UNSUPPORTED, "the adjoint supports periodic boundaries only");
-  if (e.cfg.force_x != 0.0) return fail(c, HGKS_E_UNSUPPORTED, "the adjoint has no body force");
+  if (e.cfg.force_x != 0.0 || e.cfg.force_mode != HGKS_FORCE_CONSTANT)
+    return fail(c, HGKS_E_UNSUPPORTED, "the adjoint has no body force");
   const size_t es = elem_size(e.cfg);
   if (!e.adj_acc) {
     HGKS_CHECK(c, cudaMalloc(&e.adj_acc, 5 * e.P * es));

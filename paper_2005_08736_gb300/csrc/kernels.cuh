@@ -148,6 +148,7 @@ struct UpdateArgs {
   GridDev g;
   T force_x;
   T rho_r;
+  T* __restrict__ stash;      // mass-flux force: rho^n, (rho U)^n into planes 0, 1 (or null)
 };
 
 // Stage 1: L, dL of Q^n; Q* = Q^n + dt/2 L + dt^2/8 dL; inc = dt L + dt^2/6 dL.
@@ -209,6 +210,10 @@ __global__ void __launch_bounds__(kUpdTX * kUpdTY) k_update(UpdateArgs<T> a) {
     for (int v = 0; v < 5; ++v) {
       qn[v] = a.q[v * a.g.P + pi];
       dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
+    }
+    if (a.stash) {
+      a.stash[pi] = qn[0];
+      a.stash[a.g.P + pi] = qn[1];
     }
     if (a.force_x != T(0)) {
       // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
@@ -390,6 +395,111 @@ static __global__ void k_diag_final(const double* __restrict__ part, int nblocks
       double v = lane < nw ? sm[k][lane] : (k < 6 ? 0.0 : 1e300);
       v = k < 6 ? warp_sum(v) : warp_min(v);
       if (lane == 0) out[k] = v;
+    }
+  }
+}
+
+// ------------------------------------------------- constant mass flux force ---
+// Sec. 3.3: after the two S2O4 stages (state Q~^{n+1} in q, rho^n and
+// (rho U)^n stashed in planes 0 and 1 of the stash buffer), per-block FP64
+// sums of the cell volume, of (rho U)~ and of (rho^n + rho~)/2, each times
+// the cell volume, into part[3 b + k].  comp (FP32 compensation) may be null.
+template <class T>
+__global__ void __launch_bounds__(256) k_massflux_sums(const T* __restrict__ q, const T* __restrict__ stash,
+                                                       const T* __restrict__ comp,
+                                                       GridDev g, const T* __restrict__ wx,
+                                                       const T* __restrict__ wy, const T* __restrict__ wz,
+                                                       double rho_r, double* __restrict__ part) {
+  double s[3] = {0.0, 0.0, 0.0};
+  const int nx = g.n[0], ny = g.n[1];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = int(c % nx);
+    const long long r = c / nx;
+    const int y = int(r % ny), z = int(r / ny);
+    const long long pi = pad_index(g, x, y, z);
+    const double vol = double(wx[x + kGhost]) * double(wy[y + kGhost]) * double(wz[z + kGhost]);
+    // FP32: the stored value minus its compensation is the accumulated sum.
+    const double c0 = comp ? double(comp[c]) : 0.0, c1 = comp ? double(comp[g.N + c]) : 0.0;
+    s[0] += vol;
+    s[1] += (double(q[g.P + pi]) - c1) * vol;
+    s[2] += (rho_r + 0.5 * (double(q[pi]) - c0 + double(stash[pi]))) * vol;
+  }
+  __shared__ double sm[3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(s[k]);
+    if (lane == 0) sm[k][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v = lane < nw ? sm[k][lane] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) part[blockIdx.x * 3 + k] = v;
+    }
+  }
+}
+
+// f_x = (mass_flux * volume - int (rho U)~) / (dt * int (rho^n + rho~)/2)
+// into scal[3] (one block of 256; deterministic order).
+static __global__ void __launch_bounds__(256) k_massflux_force(const double* __restrict__ part, int nblocks,
+                                                               double mass_flux, double* __restrict__ scal) {
+  __shared__ double sm[3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s[k] += part[b * 3 + k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(s[k]);
+    if (lane == 0) sm[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int k = 0; k < 3; ++k) t[k] += sm[k][w];
+    scal[3] = (mass_flux * t[0] - t[1]) / (scal[0] * t[2]);
+  }
+}
+
+// (rho U)^{n+1} = (rho U)~ + dt/2 (rho~ + rho^n) f_x;
+// (rho E)^{n+1} = (rho E)~ + dt/2 ((rho U)^{n+1} + (rho U)^n) f_x, with the
+// FP32 compensation continued (comp may be null for FP64).
+template <class T>
+__global__ void __launch_bounds__(256) k_force_apply(T* __restrict__ q, const T* __restrict__ stash,
+                                                     T* __restrict__ comp, GridDev g, double rho_r,
+                                                     const double* __restrict__ scal) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const int nx = g.n[0], ny = g.n[1];
+  const int x = int(c % nx);
+  const long long r = c / nx;
+  const int y = int(r % ny), z = int(r / ny);
+  const long long pi = pad_index(g, x, y, z);
+  const T f = T(scal[3]), hdt = T(0.5 * scal[0]);
+  const T rho_t = T(rho_r) + q[pi], rho_n = T(rho_r) + stash[pi];
+  const T m_t = q[g.P + pi], m_n = stash[g.P + pi];
+  const T dm = hdt * (rho_t + rho_n) * f;
+  const T dE = hdt * (m_t + dm + m_n) * f;
+  const T inc[2] = {dm, dE};
+  const int var[2] = {1, 4};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long qi = var[k] * g.P + pi;
+    if (comp) {
+      const long long ci = var[k] * g.N + c;
+      const T yv = inc[k] - comp[ci];
+      const T t = q[qi] + yv;
+      comp[ci] = (t - q[qi]) - yv;
+      q[qi] = t;
+    } else {
+      q[qi] += inc[k];
     }
   }
 }

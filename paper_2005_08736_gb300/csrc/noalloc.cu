@@ -61,6 +61,7 @@ extern "C" hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_in
   if (!cfg || !cons_inout || nsteps < 0) return HGKS_E_INVAL;
   if (!hgks::validate_config(*cfg).empty()) return HGKS_E_INVAL;
   if (cfg->nx > kMaxN || cfg->ny > kMaxN || cfg->nz > kMaxN) return HGKS_E_UNSUPPORTED;
+  if (cfg->force_mode != HGKS_FORCE_CONSTANT) return HGKS_E_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HGKS_E_CUDA;
   unsigned char* base = nullptr;

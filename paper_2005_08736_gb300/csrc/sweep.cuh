@@ -43,12 +43,19 @@ struct SweepLayout {
   static constexpr int NT1 = 4 * NV + 2 * NV;            // t1 pass outputs
 };
 
+// Per-thread slots of the full-flux phase 3 with two threads per face: the
+// three point states (20 values each) of the second t2 abscissa.
+template <int FLUX, int TPF>
+constexpr int sweep_scratch_elems() {
+  return FLUX == FLUX_FULL && TPF == 2 ? 60 * 256 : 0;
+}
+
 template <class T, int FLUX, int TP, int TS, int NL>
 constexpr size_t sweep_smem_bytes() {
   constexpr int NH = (TP + 4) * (TS + 4);
   constexpr int TPF = 256 / (TP * TS);
   return sizeof(T) * ((NL * SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH +
-                      (TPF - 1) * 10 * TP * TS);
+                      (TPF - 1) * 10 * TP * TS + sweep_scratch_elems<FLUX, TPF>());
 }
 
 // Geometry of one sweep: normal axis d, transverse axes P (faster in memory)
@@ -169,6 +176,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
   T* ffb = reinterpret_cast<T*>(smem_raw);  // [NL][NFF][NH]
   T* tb = ffb + NL * NFF * NH;              // [NT1][NH]
   T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
+  T* scr = part + (TPF - 1) * 10 * NFACE;      // [60][256] (full flux, TPF = 2)
 
   const int d = a.d;
   const SweepAxes ax = sweep_axes(d, a.g);
@@ -281,6 +289,57 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
             if (STAGE == 1) Fs[i] += F[i];
             Fs[5 + i] += dF[i];
           }
+        }
+      }
+    } else if constexpr (FLUX == FLUX_FULL && TPF == 2) {
+      // Full flux, two threads per face: thread `sub` takes the t1 abscissa
+      // m1 = sub; one pass along t2 per field gives both t2 abscissae.  The
+      // point states of m2 = 1 wait in the thread's shared-memory slots
+      // (index ((s*4 + c)*5 + i)*256 + tid, c = 0 value, 1..3 derivatives
+      // along n, t1, t2) while the flux at m2 = 0 is evaluated.
+      const int m1 = sub;
+      PointState<T> st[3];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          const int k = 5 * s + i;
+          const T* sv = tb + (4 * k + m1) * NH + at3;
+          const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+          const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+          T v[2], dd[2], vd[2], vs[2];
+          tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
+          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
+          st[s].q[i] = v[0];
+          st[s].dq[0][i] = vs[0];
+          st[s].dq[1][i] = vd[0] * rh1;
+          st[s].dq[2][i] = dd[0] * rh2;
+          scr[((s * 4 + 0) * 5 + i) * 256 + tid] = v[1];
+          scr[((s * 4 + 1) * 5 + i) * 256 + tid] = vs[1];
+          scr[((s * 4 + 2) * 5 + i) * 256 + tid] = vd[1] * rh1;
+          scr[((s * 4 + 3) * 5 + i) * 256 + tid] = dd[1] * rh2;
+        }
+      }
+#pragma unroll 1
+      for (int m2 = 0; m2 < 2; ++m2) {
+        if (m2 == 1) {
+#pragma unroll
+          for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              st[s].q[i] = scr[((s * 4 + 0) * 5 + i) * 256 + tid];
+              st[s].dq[0][i] = scr[((s * 4 + 1) * 5 + i) * 256 + tid];
+              st[s].dq[1][i] = scr[((s * 4 + 2) * 5 + i) * 256 + tid];
+              st[s].dq[2][i] = scr[((s * 4 + 3) * 5 + i) * 256 + tid];
+            }
+        }
+        T F[5], dF[5];
+        flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          if (STAGE == 1) Fs[i] += F[i];
+          Fs[5 + i] += dF[i];
         }
       }
     } else {

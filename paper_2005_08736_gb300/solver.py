@@ -50,6 +50,8 @@ class Config:
     prec: int = 1
     rho_ref: float = 1.0
     p_ref: float = 100.0 / 1.4
+    force_mode: int = 0       # 0 constant force_x; 1 constant mass flux (Sec. 3.3)
+    mass_flux: float = 0.0    # force_mode 1: target volume average of rho U
 
     def c_struct(self) -> _lib.HgksConfig:
         return _lib.HgksConfig(**{f.name: getattr(self, f.name) for f in fields(self)})
@@ -195,7 +197,7 @@ class Simulation:
         d = _lib.HgksDiag()
         self._call(self.lib.hgks_diagnostics(self.h, ctypes.byref(d)))
         return dict(t=d.t, dt=d.dt, mass=d.mass, mom=tuple(d.mom), energy=d.energy, Ek=d.Ek,
-                    rho_min=d.rho_min, p_min=d.p_min, step=d.step)
+                    rho_min=d.rho_min, p_min=d.p_min, step=d.step, force_x=d.force_x)
 
     def turbulence(self) -> dict:
         """Turbulence statistics of the current state (Sec. 3.1, Sec. 3.4):

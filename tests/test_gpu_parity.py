@@ -52,7 +52,8 @@ def oracle_cfg(c: Config) -> oracle.Config:
                          y_stretch=c.y_stretch, stretch_b=c.stretch_b, bc_y=c.bc_y, gamma=c.gamma,
                          prandtl=c.prandtl, visc_law=c.visc, mu_ref=c.mu_ref, T_ref=c.T_ref,
                          visc_exp=c.visc_exp, T_wall=c.T_wall, force_x=c.force_x, recon=c.recon,
-                         flux=c.flux, tau_num_C=c.tau_num_C, cfl=c.cfl)
+                         flux=c.flux, tau_num_C=c.tau_num_C, cfl=c.cfl,
+                         force_mode=c.force_mode, mass_flux=c.mass_flux)
 
 
 def run_both(cfg: Config, prim, steps, dt=0.0):
@@ -116,6 +117,31 @@ def test_channel_with_walls_fp64_matches_oracle():
     gpu, ref, t, to = run_both(cfg, channel_prim(12, 16, 10), 3)
     assert t == pytest.approx(to, rel=1e-13)
     assert rel_linf(gpu, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_channel_constant_mass_flux_matches_oracle(prec, tol):
+    """Sec. 3.3 after transition: the force keeps the volume integral of rho U
+    at its target; the device force of every step matches the oracle's."""
+    n = (12, 16, 10)
+    cfg = channel_cfg(*n, prec=prec)
+    cfg.force_mode, cfg.mass_flux = 1, 1.02
+    prim = channel_prim(*n)
+    sim = Simulation(cfg)
+    sim.init_primitive(prim)
+    o = oracle.Solver(oracle_cfg(cfg))
+    o.set_state(oracle.conservative(prim, cfg.gamma))
+    for _ in range(3):
+        sim.step(1)
+        o.step(1)
+        f_gpu, f_ref = sim.diagnostics()["force_x"], o.last_force
+        assert f_gpu == pytest.approx(f_ref, rel=1e-10 if prec == 0 else 2e-3)
+    gpu = sim.state()
+    d = sim.diagnostics()
+    sim.close()
+    assert rel_linf(gpu, o.state()) <= tol
+    vol = cfg.lx * cfg.ly * cfg.lz
+    assert d["mom"][0] / vol == pytest.approx(1.02, rel=1e-12 if prec == 0 else 1e-6)
 
 
 def test_minimum_grid_and_fixed_dt():
