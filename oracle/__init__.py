@@ -60,6 +60,7 @@ class OracleConfig(ctypes.Structure):
         ("tau_num_C", ctypes.c_double),
         ("cfl", ctypes.c_double),
         ("force_mode", ctypes.c_int), ("mass_flux", ctypes.c_double),
+        ("char_recon", ctypes.c_int),
     ]
 
 
@@ -101,6 +102,9 @@ def lib():
             L.oracle_weno5_left.argtypes = [pd, i]
             L.oracle_tangential.argtypes = [pd, i, pd, pd]
             L.oracle_flux_point.argtypes = [ctypes.POINTER(OracleConfig), pd, d, pd, pd]
+            L.oracle_char_basis.argtypes = [pd, d, pd, pd]
+            L.oracle_normal_end_values.argtypes = [pd, i, i, d, pd]
+            L.oracle_tangential_vec.argtypes = [pd, i, i, pd, d, pd, pd]
             _lib = L
     return _lib
 
@@ -143,6 +147,7 @@ class Config:
     cfl: float = 0.5
     force_mode: int = 0
     mass_flux: float = 0.0
+    char_recon: int = 0
 
     def c_struct(self) -> OracleConfig:
         return OracleConfig(**{k: getattr(self, k) for k, _ in OracleConfig._fields_})
@@ -270,6 +275,28 @@ def flux_point(cfg: Config, st, dt):
     dF = np.empty(5)
     lib().oracle_flux_point(ctypes.byref(c), _p(_f64(st)), float(dt), _p(F), _p(dF))
     return F, dF
+
+
+def char_basis(Qm, gamma):
+    """Right eigenvectors R (columns) of the local-frame Euler Jacobian at Qm and R^{-1}."""
+    R, L = np.empty((5, 5)), np.empty((5, 5))
+    lib().oracle_char_basis(_p(_f64(Qm)), float(gamma), _p(R), _p(L))
+    return R, L
+
+
+def normal_end_values(qc, mode, use_char, gamma=1.4):
+    """WENO5 end values [4][5] of the two cells beside a face from qc[6][5]."""
+    out = np.empty((4, 5))
+    lib().oracle_normal_end_values(_p(_f64(qc)), int(mode), int(use_char), float(gamma), _p(out))
+    return out
+
+
+def tangential_vec(f, mode, use_char, Qm, gamma=1.4):
+    """Values and derivatives [2][5] at the Gauss abscissae from face averages f[5][5]."""
+    val, der = np.empty((2, 5)), np.empty((2, 5))
+    lib().oracle_tangential_vec(_p(_f64(f)), int(mode), int(use_char), _p(_f64(Qm)), float(gamma),
+                                _p(val), _p(der))
+    return val, der
 
 
 def conservative(prim, gamma):

@@ -421,6 +421,114 @@ void tangential(const double f[5], int mode, double val[2], double der[2]) {
 }
 
 // ---------------------------------------------------------------------------
+// Characteristic variables (Sec. 2.1, Remark 1): omega = R^{-1} Q, with R the
+// right eigenvectors of the Jacobian dF/dQ of the Euler flux along the local
+// normal (velocity component 1 of the local frame), taken at a state Qm.
+// Columns of R, for the eigenvalues u - c, u, u, u, u + c:
+//   (1, u - c, v, w, H - u c), (1, u, v, w, |U|^2 / 2), (0, 0, 1, 0, v),
+//   (0, 0, 0, 1, w), (1, u + c, v, w, H + u c);
+// H = (rho E + p)/rho, c^2 = gamma p / rho.  R^{-1} is formed by Gaussian
+// elimination.
+// ---------------------------------------------------------------------------
+struct CharBasis {
+  double R[5][5];
+  double L[5][5];
+};
+
+CharBasis char_basis(const double Qm[5], double gamma) {
+  const double rho = Qm[0], u = Qm[1] / rho, v = Qm[2] / rho, w = Qm[3] / rho;
+  const double q2 = u * u + v * v + w * w;
+  const double p = (gamma - 1.0) * (Qm[4] - 0.5 * rho * q2);
+  const double c = std::sqrt(gamma * p / rho), H = (Qm[4] + p) / rho;
+  const double cols[5][5] = {{1.0, u - c, v, w, H - u * c},
+                             {1.0, u, v, w, 0.5 * q2},
+                             {0.0, 0.0, 1.0, 0.0, v},
+                             {0.0, 0.0, 0.0, 1.0, w},
+                             {1.0, u + c, v, w, H + u * c}};
+  CharBasis B;
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) B.R[i][k] = cols[k][i];
+  for (int k = 0; k < 5; ++k) {  // column k of R^{-1}: R x = e_k
+    double A[25], e[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) A[i * 5 + j] = B.R[i][j];
+    e[k] = 1.0;
+    gauss_solve(5, A, e);
+    for (int i = 0; i < 5; ++i) B.L[i][k] = e[i];
+  }
+  return B;
+}
+
+void mat5(const double M[5][5], const double x[5], double y[5]) {
+  for (int i = 0; i < 5; ++i) {
+    y[i] = 0.0;
+    for (int k = 0; k < 5; ++k) y[i] += M[i][k] * x[k];
+  }
+}
+
+// Tangential reconstruction of a 5-vector field from the five face averages
+// f[s][0..4] (Remark 1), component-wise or, with B, in the characteristic
+// variables of B: project every average, reconstruct each characteristic
+// component, map the values and derivatives back.
+void tangential_vec(const double f[5][5], int mode, const CharBasis* B, double val[2][5],
+                    double der[2][5]) {
+  double g[5][5];
+  for (int s = 0; s < 5; ++s) {
+    if (B) mat5(B->L, f[s], g[s]);
+    else
+      for (int i = 0; i < 5; ++i) g[s][i] = f[s][i];
+  }
+  double cv[2][5], cd[2][5];
+  for (int i = 0; i < 5; ++i) {
+    const double col[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
+    double v2[2], d2[2];
+    tangential(col, mode, v2, d2);
+    for (int m = 0; m < 2; ++m) {
+      cv[m][i] = v2[m];
+      cd[m][i] = d2[m];
+    }
+  }
+  for (int m = 0; m < 2; ++m) {
+    if (B) {
+      mat5(B->R, cv[m], val[m]);
+      mat5(B->R, cd[m], der[m]);
+    } else {
+      for (int i = 0; i < 5; ++i) {
+        val[m][i] = cv[m][i];
+        der[m][i] = cd[m][i];
+      }
+    }
+  }
+}
+
+// Normal WENO5 end values of cells i = f-1 (stencil qc[0..4]) and i+1 = f
+// (qc[1..5]): out[0] = Q at x_{i+1/2} from cell i, out[1] = Q at x_{i-1/2}
+// from cell i, out[2] = Q at x_{i+1/2} from cell i+1, out[3] = Q at x_{i+3/2}
+// from cell i+1; component-wise or in the characteristic variables of B.
+void normal_end_values(const double qc[6][5], int mode, const CharBasis* B, double out[4][5]) {
+  double g[6][5];
+  for (int s = 0; s < 6; ++s) {
+    if (B) mat5(B->L, qc[s], g[s]);
+    else
+      for (int i = 0; i < 5; ++i) g[s][i] = qc[s][i];
+  }
+  double e[4][5];
+  for (int i = 0; i < 5; ++i) {
+    const double sl[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
+    const double sr[5] = {g[1][i], g[2][i], g[3][i], g[4][i], g[5][i]};
+    e[0][i] = weno5_right(sl, mode);
+    e[1][i] = weno5_left(sl, mode);
+    e[2][i] = weno5_left(sr, mode);
+    e[3][i] = weno5_right(sr, mode);
+  }
+  for (int k = 0; k < 4; ++k) {
+    if (B) mat5(B->R, e[k], out[k]);
+    else
+      for (int i = 0; i < 5; ++i) out[k][i] = e[k][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Configuration and the flux at one Gauss point.
 // ---------------------------------------------------------------------------
 }  // namespace
@@ -443,6 +551,7 @@ typedef struct {
   double cfl;
   int force_mode;    // 0 the constant force_x; 1 the constant-mass-flux force of Sec. 3.3
   double mass_flux;  // force_mode 1: the volume average of rho U that the force keeps
+  int char_recon;    // 1: reconstruct characteristic variables (Remark 1); 0: conservative
 } oracle_config;
 
 }  // extern "C"
@@ -679,8 +788,15 @@ struct Solver {
     const int nd = n[d], na = n[t1], nb = n[t2];
     const int ea = na + 4, eb = nb + 4;  // face fields carry 2 tangential ghost rows
     const int mode = c.recon;
-    // Face fields, local frame: 0 Q_l, 1 Q_r, 2 dQ_l/dn, 3 dQ_r/dn, 4 Q0, 5 dQ0/dn.
-    std::vector<double> FF(size_t(nd + 1) * ea * eb * 30);
+    // Face fields, local frame: 0 Q_l, 1 Q_r, 2 dQ_l/dn, 3 dQ_r/dn, 4 Q0,
+    // 5 dQ0/dn, 6 Qm = the mean of the two cell averages beside the face.
+    constexpr int NF = 35;
+    std::vector<double> FF(size_t(nd + 1) * ea * eb * NF);
+    // Reading: with characteristic reconstruction every reconstruction that
+    // serves face point P (the normal one at P, the t1 pass centred at P and
+    // the t2 pass of P's Gauss points) uses the eigenvectors of the Euler
+    // Jacobian along the face normal at Qm of P.
+    const bool chr = c.char_recon != 0;
 #pragma omp parallel for collapse(2) schedule(static)
     for (int f = 0; f <= nd; ++f)
       for (int aa = -2; aa < na + 2; ++aa)
@@ -689,13 +805,14 @@ struct Solver {
           double qc[6][5];
           for (int s = 0; s < 6; ++s) local(a, d, cell(d, f - 3 + s, aa, bb), qc[s]);
           const double hl = w(d, f - 1), hr = w(d, f);
-          double* out = &FF[((size_t(f) * ea + (aa + 2)) * eb + (bb + 2)) * 30];
+          double* out = &FF[((size_t(f) * ea + (aa + 2)) * eb + (bb + 2)) * NF];
+          for (int v = 0; v < 5; ++v) out[30 + v] = 0.5 * (qc[2][v] + qc[3][v]);
+          CharBasis B;
+          if (chr) B = char_basis(&out[30], c.gamma);
+          double e[4][5];
+          normal_end_values(qc, mode, chr ? &B : nullptr, e);
           for (int v = 0; v < 5; ++v) {
-            // Cell i = f-1 uses qc[0..4]; cell i+1 = f uses qc[1..5].
-            const double sl[5] = {qc[0][v], qc[1][v], qc[2][v], qc[3][v], qc[4][v]};
-            const double sr[5] = {qc[1][v], qc[2][v], qc[3][v], qc[4][v], qc[5][v]};
-            const double QRi = weno5_right(sl, mode), QLi = weno5_left(sl, mode);
-            const double QLr = weno5_left(sr, mode), QRr = weno5_right(sr, mode);
+            const double QRi = e[0][v], QLi = e[1][v], QLr = e[2][v], QRr = e[3][v];
             out[0 * 5 + v] = QRi;  // Q_l at the face
             out[1 * 5 + v] = QLr;  // Q_r at the face
             // Reading: normal slopes of the quadratic through both end values
@@ -716,6 +833,9 @@ struct Solver {
             out[4 * 5 + i] = gl.rho * mom(gl, +1, pi) + gr.rho * mom(gr, -1, pi);
           }
         }
+    auto ffield = [&](int f, int aa, int bb, int fld) {
+      return &FF[((size_t(f) * ea + (aa + 2)) * eb + (bb + 2)) * NF + fld * 5];
+    };
     // Tangential reconstruction to the 2x2 Gauss points and the flux there.
     Fd.assign(size_t(nd + 1) * na * nb * 10, 0.0);
 #pragma omp parallel for collapse(2) schedule(static)
@@ -726,33 +846,47 @@ struct Solver {
           // t1 pass over rows bb-2 .. bb+2: value and t1-derivative of every
           // field at the two t1 Gauss abscissae.
           double v1[6][5][5][2], d1[6][5][5][2];  // [field][var][row][m]
-          for (int r = 0; r < 5; ++r)
-            for (int fld = 0; fld < 6; ++fld)
-              for (int v = 0; v < 5; ++v) {
-                double col[5];
-                for (int s = 0; s < 5; ++s)
-                  col[s] = FF[((size_t(f) * ea + (aa + s)) * eb + (bb + r)) * 30 + fld * 5 + v];
-                tangential(col, mode, v1[fld][v][r], d1[fld][v][r]);
-              }
+          for (int r = 0; r < 5; ++r) {
+            CharBasis B;
+            if (chr) B = char_basis(ffield(f, aa, bb - 2 + r, 6), c.gamma);
+            for (int fld = 0; fld < 6; ++fld) {
+              double col[5][5], val[2][5], der[2][5];
+              for (int s = 0; s < 5; ++s)
+                for (int v = 0; v < 5; ++v) col[s][v] = ffield(f, aa - 2 + s, bb - 2 + r, fld)[v];
+              tangential_vec(col, mode, chr ? &B : nullptr, val, der);
+              for (int v = 0; v < 5; ++v)
+                for (int m = 0; m < 2; ++m) {
+                  v1[fld][v][r][m] = val[m][v];
+                  d1[fld][v][r][m] = der[m][v];
+                }
+            }
+          }
+          CharBasis B2;
+          if (chr) B2 = char_basis(ffield(f, aa, bb, 6), c.gamma);
+          const CharBasis* pb = chr ? &B2 : nullptr;
           double Fsum[10] = {0};
           for (int m = 0; m < 2; ++m)
             for (int mm = 0; mm < 2; ++mm) {
               PointData pd;
               const int vf[3] = {0, 1, 4}, sf[3] = {2, 3, 5};
-              for (int s = 0; s < 3; ++s)
+              for (int s = 0; s < 3; ++s) {
+                double col[5][5], val[2][5], der[2][5];
+                for (int r = 0; r < 5; ++r)
+                  for (int v = 0; v < 5; ++v) col[r][v] = v1[vf[s]][v][r][m];
+                tangential_vec(col, mode, pb, val, der);
                 for (int v = 0; v < 5; ++v) {
-                  double col[5], val[2], der[2];
-                  for (int r = 0; r < 5; ++r) col[r] = v1[vf[s]][v][r][m];
-                  tangential(col, mode, val, der);
-                  pd.st[s][0][v] = val[mm];        // value
-                  pd.st[s][3][v] = der[mm] / h2;   // d/dt2
-                  for (int r = 0; r < 5; ++r) col[r] = d1[vf[s]][v][r][m];
-                  tangential(col, mode, val, der);
-                  pd.st[s][2][v] = val[mm] / h1;   // d/dt1
-                  for (int r = 0; r < 5; ++r) col[r] = v1[sf[s]][v][r][m];
-                  tangential(col, mode, val, der);
-                  pd.st[s][1][v] = val[mm];        // d/dn
+                  pd.st[s][0][v] = val[mm][v];       // value
+                  pd.st[s][3][v] = der[mm][v] / h2;  // d/dt2
                 }
+                for (int r = 0; r < 5; ++r)
+                  for (int v = 0; v < 5; ++v) col[r][v] = d1[vf[s]][v][r][m];
+                tangential_vec(col, mode, pb, val, der);
+                for (int v = 0; v < 5; ++v) pd.st[s][2][v] = val[mm][v] / h1;  // d/dt1
+                for (int r = 0; r < 5; ++r)
+                  for (int v = 0; v < 5; ++v) col[r][v] = v1[sf[s]][v][r][m];
+                tangential_vec(col, mode, pb, val, der);
+                for (int v = 0; v < 5; ++v) pd.st[s][1][v] = val[mm][v];  // d/dn
+              }
               double F[5], dF[5];
               flux_point(c, pd, dt, F, dF);
               for (int i = 0; i < 5; ++i) {
@@ -915,6 +1049,44 @@ double oracle_step(void* h, int nsteps, double dt) {
   double used = 0.0;
   for (int n = 0; n < nsteps; ++n) used = s.do_step(dt);
   return used;
+}
+// Characteristic basis at the local-frame state Qm: R and R^{-1}, row-major.
+void oracle_char_basis(const double* Qm, double gamma, double* R, double* L) {
+  const CharBasis B = char_basis(Qm, gamma);
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) {
+      R[i * 5 + k] = B.R[i][k];
+      L[i * 5 + k] = B.L[i][k];
+    }
+}
+// Normal WENO5 end values of the two cells beside a face from six cell
+// averages qc[6][5] (local frame): out[4][5] as normal_end_values; use_char
+// selects the characteristic variables of the mean of qc[2] and qc[3].
+void oracle_normal_end_values(const double* qc, int mode, int use_char, double gamma, double* out) {
+  double q[6][5], e[4][5], qm[5];
+  for (int s = 0; s < 6; ++s)
+    for (int i = 0; i < 5; ++i) q[s][i] = qc[s * 5 + i];
+  for (int i = 0; i < 5; ++i) qm[i] = 0.5 * (q[2][i] + q[3][i]);
+  const CharBasis B = char_basis(qm, gamma);
+  normal_end_values(q, mode, use_char ? &B : nullptr, e);
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 5; ++i) out[k * 5 + i] = e[k][i];
+}
+// Tangential reconstruction of a 5-vector field from five face averages
+// f[5][5]: values and derivatives at the two Gauss abscissae, out[2][5] each;
+// use_char selects the characteristic variables of Qm.
+void oracle_tangential_vec(const double* f, int mode, int use_char, const double* Qm, double gamma,
+                           double* val, double* der) {
+  double F[5][5], v[2][5], d[2][5];
+  for (int s = 0; s < 5; ++s)
+    for (int i = 0; i < 5; ++i) F[s][i] = f[s * 5 + i];
+  const CharBasis B = char_basis(Qm, gamma);
+  tangential_vec(F, mode, use_char ? &B : nullptr, v, d);
+  for (int m = 0; m < 2; ++m)
+    for (int i = 0; i < 5; ++i) {
+      val[m * 5 + i] = v[m][i];
+      der[m * 5 + i] = d[m][i];
+    }
 }
 double oracle_time(void* h) { return static_cast<Solver*>(h)->t; }
 // Streamwise force f_x applied in the last step.
