@@ -79,6 +79,12 @@ typedef struct {
                                       deviation from it (must be > 0) */
   int force_mode;                  /* hgks_force (force_x is ignored in mode 1) */
   double mass_flux;                /* HGKS_FORCE_MASS_FLUX: target volume average of rho U */
+  int recon_vars;                  /* 0 conservative variables; 1 characteristic variables
+                                      (Sec. 2.1, Remark 1) for the WENO modes: each
+                                      reconstruction serving a face point projects onto the
+                                      eigenvectors of the Euler Jacobian along the face normal
+                                      at the mean of the two cells beside it (no effect with
+                                      linear weights) */
 } hgks_config;
 
 typedef struct hgks_ctx hgks_ctx;  /* opaque; owns every device buffer it uses */

@@ -46,6 +46,7 @@ class HgksConfig(ctypes.Structure):
         ("prec", ctypes.c_int),
         ("rho_ref", ctypes.c_double), ("p_ref", ctypes.c_double),
         ("force_mode", ctypes.c_int), ("mass_flux", ctypes.c_double),
+        ("recon_vars", ctypes.c_int),
     ]
 
 

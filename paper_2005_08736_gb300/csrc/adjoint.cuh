@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
       for (int it = tid; it < items; it += NT) {
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
-        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1);
+        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1, a.gas);
       }
     }
     __syncthreads();

@@ -41,6 +41,13 @@ Gas<T> gas_of(const hgks_config& c) {
   return g;
 }
 
+// Kernel MODE of a configuration: the reconstruction, + 2 for WENO in
+// characteristic variables (with linear weights the projection changes
+// nothing, so it is skipped).
+inline int sweep_mode(const hgks_config& c) {
+  return c.recon + (c.recon_vars == 1 && c.recon != HGKS_RECON_LINEAR ? 2 : 0);
+}
+
 inline unsigned blocks_for(long long n, int threads) {
   return unsigned((n + threads - 1) / threads);
 }
@@ -94,7 +101,7 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   chunk = (chunk + NL - 1) / NL * NL;
   a.chunk = chunk;
   const int gz = (layers + chunk - 1) / chunk;
-  constexpr size_t smem = sweep_smem_bytes<T, FLUX, TP, TS, NL>();
+  constexpr size_t smem = sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL>();
   auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -131,11 +138,11 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   T* qin = static_cast<T*>(stage == 1 ? e.q : e.qs);
   cudaError_t err = enqueue_ghosts<T>(e, qin, probe);
   if (err != cudaSuccess) return err;
-  const int mode = e.cfg.recon, flux = e.cfg.flux;
+  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
 #define HGKS_DISPATCH(M, F) \
   if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe);
-  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0)
-  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1)
+  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0) HGKS_DISPATCH(3, 0) HGKS_DISPATCH(4, 0)
+  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1) HGKS_DISPATCH(3, 1) HGKS_DISPATCH(4, 1)
 #undef HGKS_DISPATCH
   if (err != cudaSuccess) return err;
   UpdateArgs<T> ua;
@@ -177,11 +184,11 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
 template <class T>
 cudaError_t enqueue_sweep_only(const Engine& e, int d) {
   const T* q = static_cast<const T*>(e.q);
-  const int mode = e.cfg.recon, flux = e.cfg.flux;
+  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
 #define HGKS_SW(M, F) \
   if (mode == M && flux == F) return launch_sweep<T, M, F, 1>(e, q, d);
-  HGKS_SW(0, 0) HGKS_SW(1, 0) HGKS_SW(2, 0)
-  HGKS_SW(0, 1) HGKS_SW(1, 1) HGKS_SW(2, 1)
+  HGKS_SW(0, 0) HGKS_SW(1, 0) HGKS_SW(2, 0) HGKS_SW(3, 0) HGKS_SW(4, 0)
+  HGKS_SW(0, 1) HGKS_SW(1, 1) HGKS_SW(2, 1) HGKS_SW(3, 1) HGKS_SW(4, 1)
 #undef HGKS_SW
   return cudaErrorInvalidValue;
 }

@@ -63,6 +63,7 @@ std::string hgks::validate_config(const hgks_config& c) {
   if (!(c.tau_num_C >= 0.0)) return "tau_num_C must be non-negative";
   if (c.force_mode != HGKS_FORCE_CONSTANT && c.force_mode != HGKS_FORCE_MASS_FLUX)
     return "unknown force mode";
+  if (c.recon_vars != 0 && c.recon_vars != 1) return "recon_vars must be 0 or 1";
   return "";
 }
 
@@ -442,6 +443,8 @@ hgks_status hgks_adjoint_step(hgks_ctx* c, double dt, const double* adj_in, doub
     return fail(c, HGKS_E_UNSUPPORTED, "the adjoint supports periodic boundaries only");
   if (e.cfg.force_x != 0.0 || e.cfg.force_mode != HGKS_FORCE_CONSTANT)
     return fail(c, HGKS_E_UNSUPPORTED, "the adjoint has no body force");
+  if (e.cfg.recon_vars != 0 && e.cfg.recon != HGKS_RECON_LINEAR)
+    return fail(c, HGKS_E_UNSUPPORTED, "the adjoint reconstructs conservative variables only");
   const size_t es = elem_size(e.cfg);
   if (!e.adj_acc) {
     HGKS_CHECK(c, cudaMalloc(&e.adj_acc, 5 * e.P * es));

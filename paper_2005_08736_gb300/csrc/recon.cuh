@@ -17,13 +17,20 @@ namespace hgks {
 enum Recon { RECON_LINEAR = 0, RECON_WENO_JS = 1, RECON_WENO_Z = 2 };
 enum FluxKind { FLUX_SMOOTH = 0, FLUX_FULL = 1 };
 
+// Kernel template MODE: the Recon value, or Recon + 2 for the WENO modes
+// applied to characteristic variables (charvars.cuh): 3 = WENO-JS, 4 = WENO-Z.
+// The scalar reconstructions below see the underlying Recon.
+template <int MODE> __host__ __device__ constexpr int recon_of() { return MODE >= 3 ? MODE - 2 : MODE; }
+template <int MODE> __host__ __device__ constexpr bool is_char_mode() { return MODE >= 3; }
+
 // Both end values of the centre cell: qL at x_{i-1/2}, qR at x_{i+1/2}.
 // Candidate quadratics on {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2} with optimal
 // weights (1/10, 6/10, 3/10) for the right end; the left end uses the mirrored
 // stencils, whose smoothness indicators are the same three in reverse order.
 // WENO-JS: alpha = d/(1e-6 + beta)^2.  WENO-Z: alpha = d (1 + |beta0 - beta2|/(beta + 1e-20)).
-template <int MODE, class T>
+template <int MODE_, class T>
 __device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, T& qR) {
+  constexpr int MODE = recon_of<MODE_>();
   const T c6 = T(1) / T(6);
   const T pR0 = (T(2) * q0 - T(7) * q1 + T(11) * q2) * c6;
   const T pR1 = (-q1 + T(5) * q2 + T(2) * q3) * c6;
@@ -75,8 +82,9 @@ __device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, 
 //                      B = sqrt3/54 (-f0 + 13 f1 - 24 f2 + 13 f3 - f4).
 // WENO modes: p(s) = a + b s + c s^2 with b = qR - qL, c = 3(qL+qR) - 6 f2,
 // a = f2 - c/12, so p(+-g) = f2 +- b g and p'(+-g) = b +- 2 c g.
-template <int MODE, class T>
+template <int MODE_, class T>
 __device__ __forceinline__ void tangential(T f0, T f1, T f2, T f3, T f4, T v[2], T d[2]) {
+  constexpr int MODE = recon_of<MODE_>();
   const T sq3 = T(1.7320508075688772);
   if (MODE == RECON_LINEAR) {
     const T E = T(719) / T(720) * f2 + (f1 + f3) * (T(1) / T(1080)) - (f0 + f4) * (T(1) / T(4320));

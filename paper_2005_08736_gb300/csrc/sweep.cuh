@@ -18,6 +18,7 @@
 //            summed with weights 1/4 into the face flux, written to HBM.
 #pragma once
 
+#include "charvars.cuh"
 #include "kernels.cuh"
 
 namespace hgks {
@@ -36,10 +37,11 @@ struct SweepArgs {
   Gas<T> gas;
 };
 
-template <int FLUX>
+template <int FLUX, int MODE = 0>
 struct SweepLayout {
   static constexpr int NV = FLUX == FLUX_FULL ? 15 : 5;  // state field components
-  static constexpr int NFF = 2 * NV;                     // + their normal slopes
+  static constexpr int QM = 2 * NV;                      // characteristic modes: Qm
+  static constexpr int NFF = 2 * NV + (is_char_mode<MODE>() ? 5 : 0);  // + normal slopes (+ Qm)
   static constexpr int NT1 = 4 * NV + 2 * NV;            // t1 pass outputs
 };
 
@@ -50,12 +52,81 @@ constexpr int sweep_scratch_elems() {
   return FLUX == FLUX_FULL && TPF == 2 ? 60 * 256 : 0;
 }
 
-template <class T, int FLUX, int TP, int TS, int NL>
+template <class T, int MODE, int FLUX, int TP, int TS, int NL>
 constexpr size_t sweep_smem_bytes() {
   constexpr int NH = (TP + 4) * (TS + 4);
   constexpr int TPF = 256 / (TP * TS);
-  return sizeof(T) * ((NL * SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH +
+  return sizeof(T) * ((NL * SweepLayout<FLUX, MODE>::NFF + SweepLayout<FLUX, MODE>::NT1) * NH +
                       (TPF - 1) * 10 * TP * TS + sweep_scratch_elems<FLUX, TPF>());
+}
+
+// Tangential reconstruction of a 5-vector field (components at src + i*sc,
+// face averages at offsets -2..2 times sr): values v and derivatives d at the
+// two Gauss abscissae, in the characteristic variables of b (the projection
+// of every average, the scalar reconstruction per characteristic component,
+// the map back).
+template <int MODE, class T>
+__device__ __forceinline__ void tangential_char(const T* src, int sc, int sr, const CharBasis<T>& b,
+                                                T v[2][5], T d[2][5]) {
+  T w[5][5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    T qv[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) qv[i] = src[i * sc + (r - 2) * sr];
+    to_char(b, qv, w[r]);
+  }
+  T cv[2][5], cd[2][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    T vv[2], dd[2];
+    tangential<MODE>(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i], vv, dd);
+    cv[0][i] = vv[0];
+    cv[1][i] = vv[1];
+    cd[0][i] = dd[0];
+    cd[1][i] = dd[1];
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    from_char(b, cv[m], v[m]);
+    from_char(b, cd[m], d[m]);
+  }
+}
+
+// t2 pass of the state group s (fields 5s..5s+4 of the t1-pass output) at t1
+// abscissa m1 for the face at at3: value, t2-derivative (per cell length),
+// t1-derivative field and normal-slope field at both t2 abscissae.
+template <class T, int MODE, int NV, int NH>
+__device__ __forceinline__ void t2_group(const T* tb, int s, int m1, int at3, int st2,
+                                         const CharBasis<T>& b, T val[2][5], T dt2[2][5],
+                                         T dt1[2][5], T dn[2][5]) {
+  const T* sv = tb + (4 * (5 * s) + m1) * NH + at3;
+  const T* sdv = tb + (4 * (5 * s) + 2 + m1) * NH + at3;
+  const T* ss = tb + (4 * NV + 2 * (5 * s) + m1) * NH + at3;
+  if constexpr (is_char_mode<MODE>()) {
+    T scratch[2][5];
+    tangential_char<MODE>(sv, 4 * NH, st2, b, val, dt2);
+    tangential_char<MODE>(sdv, 4 * NH, st2, b, dt1, scratch);
+    tangential_char<MODE>(ss, 2 * NH, st2, b, dn, scratch);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const T* a = sv + 4 * i * NH;
+      const T* c = sdv + 4 * i * NH;
+      const T* e = ss + 2 * i * NH;
+      T v[2], dd[2], vd[2], vs[2];
+      tangential<MODE>(a[-2 * st2], a[-st2], a[0], a[st2], a[2 * st2], v, dd);
+      tangential_val<MODE>(c[-2 * st2], c[-st2], c[0], c[st2], c[2 * st2], vd);
+      tangential_val<MODE>(e[-2 * st2], e[-st2], e[0], e[st2], e[2 * st2], vs);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        val[m][i] = v[m];
+        dt2[m][i] = dd[m];
+        dt1[m][i] = vd[m];
+        dn[m][i] = vs[m];
+      }
+    }
+  }
 }
 
 // Geometry of one sweep: normal axis d, transverse axes P (faster in memory)
@@ -96,6 +167,39 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
   const T hl = wn[f - 1 + kGhost], hr = wn[f + kGhost];
   const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
   T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
+  if constexpr (is_char_mode<MODE>()) {
+    // Characteristic variables of Qm, the mean of the two cells beside the face.
+    T qa[6][5], qm[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const T* qv = q + ax.gv[i] * g.P + cb;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qa[k][i] = __ldg(qv + k * sd);
+      qm[i] = T(0.5) * (qa[2][i] + qa[3][i]);
+    }
+    const CharBasis<T> b = char_basis(qm, gas);
+    T w[6][5];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) to_char(b, qa[k], w[k]);
+    T e[4][5];  // Q at x_{i+1/2} and x_{i-1/2} from cell i, at x_{i+1/2} and x_{i+3/2} from cell i+1
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      weno5_pair<MODE>(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i], e[1][i], e[0][i]);
+      weno5_pair<MODE>(w[1][i], w[2][i], w[3][i], w[4][i], w[5][i], e[2][i], e[3][i]);
+    }
+    T E[4][5];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) from_char(b, e[k], E[k]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      Ql[i] = E[0][i];
+      Qr[i] = E[2][i];
+      Dl[i] = (T(4) * E[0][i] + T(2) * E[1][i] - T(6) * qa[2][i]) * rhl;
+      Dr[i] = -(T(4) * E[2][i] + T(2) * E[3][i] - T(6) * qa[3][i]) * rhr;
+      D0[i] = (qa[1][i] - T(15) * qa[2][i] + T(15) * qa[3][i] - qa[4][i]) * r6;
+      ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + h] = qm[i];
+    }
+  } else {
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const T* qv = q + ax.gv[i] * g.P + cb;
@@ -109,6 +213,7 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
     Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
     Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
     D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
+  }
   }
   T Q0[5];
   compat_dev(Ql, Qr, gas, Q0);
@@ -135,8 +240,38 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
 // shared-memory plane): values at both t1 Gauss abscissae of every field and
 // t1-derivatives of the state fields, into tb.
 template <class T, int MODE, int FLUX, int NH>
-__device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1) {
+__device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1, const Gas<T>& gas) {
   constexpr int NV = SweepLayout<FLUX>::NV;
+  if constexpr (is_char_mode<MODE>()) {
+    // Characteristic variables of Qm at the centre point.
+    T qm[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) qm[i] = ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + at];
+    const CharBasis<T> b = char_basis(qm, gas);
+#pragma unroll 1
+    for (int grp = 0; grp < 2 * NV / 5; ++grp) {
+      // groups 0 .. NV/5-1: state fields (values and t1-derivatives);
+      // then their normal slopes (values only)
+      const bool state = grp < NV / 5;
+      const int k0 = 5 * grp;  // first field of the group in ff
+      T v[2][5], d[2][5];
+      tangential_char<MODE>(ff + k0 * NH + at, NH, st1, b, v, d);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        if (state) {
+          const int k = k0 + i;
+          tb[(4 * k + 0) * NH + at] = v[0][i];
+          tb[(4 * k + 1) * NH + at] = v[1][i];
+          tb[(4 * k + 2) * NH + at] = d[0][i];
+          tb[(4 * k + 3) * NH + at] = d[1][i];
+        } else {
+          const int k = k0 - NV + i;
+          tb[(4 * NV + 2 * k + 0) * NH + at] = v[0][i];
+          tb[(4 * NV + 2 * k + 1) * NH + at] = v[1][i];
+        }
+      }
+    }
+  } else {
 #pragma unroll(FLUX == FLUX_SMOOTH ? 5 : 1)
   for (int k = 0; k < NV; ++k) {
     const T* src = ff + k * NH + at;
@@ -155,19 +290,23 @@ __device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1
     tb[(4 * NV + 2 * k + 0) * NH + at] = v[0];
     tb[(4 * NV + 2 * k + 1) * NH + at] = v[1];
   }
+  }
 }
 
 // Resident CTAs per SM the register budget is sized for: the smooth FP32
-// sweep fits three (shared memory allows three as well), the others one or two.
+// sweep fits three (shared memory allows three as well), the others one or two
+// (two at most for the characteristic modes, which need more registers).
 template <class T, int FLUX> struct SweepOccupancy { static constexpr int value = 1; };
 template <> struct SweepOccupancy<float, FLUX_SMOOTH> { static constexpr int value = 3; };
 template <> struct SweepOccupancy<double, FLUX_SMOOTH> { static constexpr int value = 2; };
 
 template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
-__global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T, FLUX>::value > 2
+                                           ? 2 : SweepOccupancy<T, FLUX>::value)
+    k_sweep(SweepArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
   constexpr int NV = SweepLayout<FLUX>::NV;
-  constexpr int NFF = SweepLayout<FLUX>::NFF;
+  constexpr int NFF = SweepLayout<FLUX, MODE>::NFF;
   constexpr int NFACE = TP * TS;
   constexpr int TPF = 256 / NFACE;  // threads per face in phase 3
   constexpr int GPF = 4 / TPF;      // Gauss points per thread
@@ -248,12 +387,20 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
         const int at = hs2 * HP + hp2;
-        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, at, st1);
+        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, at, st1, a.gas);
       }
     }
     __syncthreads();
 
     // ---------------- phase 3: tangential pass along t2 and flux ----------------
+    // Characteristic modes: the basis of Qm at this thread's face.
+    CharBasis<T> cbs{};
+    if constexpr (is_char_mode<MODE>()) {
+      T qm[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) qm[i] = ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + at3];
+      cbs = char_basis(qm, a.gas);
+    }
     T Fs[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) Fs[i] = T(0);
@@ -263,6 +410,19 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
 #pragma unroll 1
       for (int m1 = (TPF == 2 ? sub : 0); m1 < (TPF == 2 ? sub + 1 : 2); ++m1) {
         PointState<T> st[2];
+        if constexpr (is_char_mode<MODE>()) {
+          T val[2][5], d2[2][5], d1[2][5], dn[2][5];
+          t2_group<T, MODE, NV, NH>(tb, 0, m1, at3, st2, cbs, val, d2, d1, dn);
+#pragma unroll
+          for (int m2 = 0; m2 < 2; ++m2)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              st[m2].q[i] = val[m2][i];
+              st[m2].dq[0][i] = dn[m2][i];
+              st[m2].dq[1][i] = d1[m2][i] * rh1;
+              st[m2].dq[2][i] = d2[m2][i] * rh2;
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
           const T* sv = tb + (4 * i + m1) * NH + at3;
@@ -279,6 +439,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
             st[m2].dq[1][i] = vd[m2] * rh1;
             st[m2].dq[2][i] = dd[m2] * rh2;
           }
+        }
         }
 #pragma unroll
         for (int m2 = 0; m2 < 2; ++m2) {
@@ -301,6 +462,21 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
       PointState<T> st[3];
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
+        if constexpr (is_char_mode<MODE>()) {
+          T val[2][5], d2[2][5], d1[2][5], dn[2][5];
+          t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            st[s].q[i] = val[0][i];
+            st[s].dq[0][i] = dn[0][i];
+            st[s].dq[1][i] = d1[0][i] * rh1;
+            st[s].dq[2][i] = d2[0][i] * rh2;
+            scr[((s * 4 + 0) * 5 + i) * 256 + tid] = val[1][i];
+            scr[((s * 4 + 1) * 5 + i) * 256 + tid] = dn[1][i];
+            scr[((s * 4 + 2) * 5 + i) * 256 + tid] = d1[1][i] * rh1;
+            scr[((s * 4 + 3) * 5 + i) * 256 + tid] = d2[1][i] * rh2;
+          }
+        } else {
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
           const int k = 5 * s + i;
@@ -319,6 +495,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
           scr[((s * 4 + 1) * 5 + i) * 256 + tid] = vs[1];
           scr[((s * 4 + 2) * 5 + i) * 256 + tid] = vd[1] * rh1;
           scr[((s * 4 + 3) * 5 + i) * 256 + tid] = dd[1] * rh2;
+        }
         }
       }
 #pragma unroll 1
@@ -349,6 +526,17 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
         PointState<T> st[FLUX == FLUX_FULL ? 3 : 1];
 #pragma unroll
         for (int s = 0; s < (FLUX == FLUX_FULL ? 3 : 1); ++s) {
+          if constexpr (is_char_mode<MODE>()) {
+            T val[2][5], d2[2][5], d1[2][5], dn[2][5];
+            t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              st[s].q[i] = val[m2][i];
+              st[s].dq[0][i] = dn[m2][i];
+              st[s].dq[1][i] = d1[m2][i] * rh1;
+              st[s].dq[2][i] = d2[m2][i] * rh2;
+            }
+          } else {
 #pragma unroll
           for (int i = 0; i < 5; ++i) {
             const int k = 5 * s + i;
@@ -363,6 +551,7 @@ __global__ void __launch_bounds__(256, SweepOccupancy<T, FLUX>::value) k_sweep(S
             st[s].dq[1][i] = v[m2] * rh1;
             tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
             st[s].dq[0][i] = v[m2];
+          }
           }
         }
         T F[5], dF[5];

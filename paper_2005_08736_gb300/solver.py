@@ -52,6 +52,7 @@ class Config:
     p_ref: float = 100.0 / 1.4
     force_mode: int = 0       # 0 constant force_x; 1 constant mass flux (Sec. 3.3)
     mass_flux: float = 0.0    # force_mode 1: target volume average of rho U
+    recon_vars: int = 0       # 1: WENO in characteristic variables (Sec. 2.1, Remark 1)
 
     def c_struct(self) -> _lib.HgksConfig:
         return _lib.HgksConfig(**{f.name: getattr(self, f.name) for f in fields(self)})

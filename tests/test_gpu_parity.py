@@ -53,7 +53,8 @@ def oracle_cfg(c: Config) -> oracle.Config:
                          prandtl=c.prandtl, visc_law=c.visc, mu_ref=c.mu_ref, T_ref=c.T_ref,
                          visc_exp=c.visc_exp, T_wall=c.T_wall, force_x=c.force_x, recon=c.recon,
                          flux=c.flux, tau_num_C=c.tau_num_C, cfl=c.cfl,
-                         force_mode=c.force_mode, mass_flux=c.mass_flux)
+                         force_mode=c.force_mode, mass_flux=c.mass_flux,
+                         char_recon=c.recon_vars)
 
 
 def run_both(cfg: Config, prim, steps, dt=0.0):
@@ -90,6 +91,23 @@ def test_ragged_grid_fp64_matches_oracle(recon, flux):
     gpu, ref, t, to = run_both(cfg, prim, 3)
     assert t == pytest.approx(to, rel=1e-13)
     assert rel_linf(gpu, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("recon,flux", [("weno-js", "smooth"), ("weno-z", "smooth"),
+                                        ("weno-js", "full"), ("weno-z", "full"), ("linear", "full")])
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_characteristic_reconstruction_matches_oracle(recon, flux, prec, tol):
+    """WENO in characteristic variables (Sec. 2.1, Remark 1) on a ragged grid
+    (several tiles and a ragged tail); with linear weights the projection is
+    skipped on the device and the oracle's projected result must agree."""
+    n = (13, 10, 9)
+    cfg = Config(*n, prec=prec, recon=ORACLE_RECON[recon], flux=ORACLE_FLUX[flux], tau_num_C=1.0,
+                 mu_ref=5e-3, p_ref=1.0, prandtl=0.7, visc=1, T_ref=1.0, visc_exp=0.76,
+                 recon_vars=1)
+    prim = inputs.random_smooth(n, seed=8, amp=0.3)
+    gpu, ref, t, to = run_both(cfg, prim, 3)
+    assert t == pytest.approx(to, rel=1e-13 if prec == 0 else 1e-6)
+    assert rel_linf(gpu, ref) <= tol
 
 
 def channel_cfg(nx, ny, nz, prec):
@@ -134,8 +152,10 @@ def test_channel_constant_mass_flux_matches_oracle(prec, tol):
     for _ in range(3):
         sim.step(1)
         o.step(1)
-        f_gpu, f_ref = sim.diagnostics()["force_x"], o.last_force
-        assert f_gpu == pytest.approx(f_ref, rel=1e-10 if prec == 0 else 2e-3)
+        d = sim.diagnostics()
+        # f_x dt is the correction of <rho U> ~ 1 (per unit density), formed
+        # from a difference of O(1) totals: its error is the state tolerance.
+        assert abs(d["force_x"] - o.last_force) * d["dt"] <= 10 * tol * cfg.mass_flux
     gpu = sim.state()
     d = sim.diagnostics()
     sim.close()
