@@ -344,7 +344,8 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
 
     prim = inputs.taylor_green(N_GRID)
-    cfg = taylor_green_config(N_GRID, args.precision, args.recon, args.flux)
+    cfg = taylor_green_config(N_GRID, args.precision, args.recon, args.flux,
+                              recon_vars=1 if args.char else 0)
     sim = Simulation(cfg)
     sim.init_primitive(prim)
     if args.shape:
@@ -381,7 +382,8 @@ def run_ours(args, rank: int, world: int):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "Mcell-updates/s",
                               "ms_per_step": ms, "grid": N_GRID, "precision": args.precision,
-                              "recon": args.recon, "flux": args.flux, "autotune": tune,
+                              "recon": args.recon, "flux": args.flux, "char": args.char,
+                              "autotune": tune,
                               "kernel_ms_per_step": prof, "quick": True}), flush=True)
         return
 
@@ -490,6 +492,8 @@ def main():
                     help="reconstruction (profiling cases; the headline uses linear)")
     ap.add_argument("--flux", default="smooth", choices=["smooth", "full"],
                     help="flux (profiling cases; the headline uses smooth)")
+    ap.add_argument("--char", action="store_true",
+                    help="WENO in characteristic variables (profiling cases)")
     ap.add_argument("--shape", default="",
                     help="V,C: sweep tile variant and march length (skips the autotuner)")
     ap.add_argument("--history", action="store_true",
