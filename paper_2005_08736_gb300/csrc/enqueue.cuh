@@ -75,8 +75,8 @@ template <> struct SweepTile<float, FLUX_FULL> { static constexpr int TP = 16, T
 template <> struct SweepTile<double, FLUX_SMOOTH> { static constexpr int TP = 16, TS = 8, NL = 2; };
 template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NL = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool FUSED = false>
-cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d, const UpdateArgs<T>* ua = nullptr) {
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
+cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
   a.q = q;
@@ -88,7 +88,6 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d, const UpdateAr
   a.g = g;
   a.d = d;
   a.gas = gas_of<T>(e.cfg);
-  if (ua) a.u = *ua;
   const int P = d == 0 ? 1 : 0, S = d == 2 ? 1 : 2;
   const int gx = (g.n[P] + TP - 1) / TP, gy = (g.n[S] + TS - 1) / TS;
   // Chunk the march along d so that the grid holds several waves of CTAs.
@@ -102,8 +101,8 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d, const UpdateAr
   chunk = (chunk + NL - 1) / NL * NL;
   a.chunk = chunk;
   const int gz = (layers + chunk - 1) / chunk;
-  constexpr size_t smem = sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL, STAGE, FUSED>();
-  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL, FUSED>;
+  constexpr size_t smem = sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL>();
+  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<dim3(gx, gy, gz), 256, smem, e.stream>>>(a);
@@ -112,32 +111,22 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d, const UpdateAr
 
 // Tile variants: 0 is SweepTile; the linear-weight smooth FP32 sweep also has
 // 32x8 and 16x16 tiles with two layers per face-field pass.
-// With ua (smooth flux, d = 2) the sweep is the fused z sweep that also
-// applies the S2O4 stage to every cell it closes.
-template <class T, int MODE, int FLUX, int STAGE, bool FUSED = false>
-cudaError_t launch_sweep(const Engine& e, const T* q, int d, const UpdateArgs<T>* ua = nullptr) {
+template <class T, int MODE, int FLUX, int STAGE>
+cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   if constexpr (std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH) {
-    if (e.sweep_variant == 1) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2, FUSED>(e, q, d, ua);
-    if (e.sweep_variant == 2) return launch_sweep_tile<T, MODE, FLUX, STAGE, 16, 16, 2, FUSED>(e, q, d, ua);
+    if (e.sweep_variant == 1) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2>(e, q, d);
+    if (e.sweep_variant == 2) return launch_sweep_tile<T, MODE, FLUX, STAGE, 16, 16, 2>(e, q, d);
   }
   return launch_sweep_tile<T, MODE, FLUX, STAGE, SweepTile<T, FLUX>::TP, SweepTile<T, FLUX>::TS,
-                           SweepTile<T, FLUX>::NL, FUSED>(e, q, d, ua);
+                           SweepTile<T, FLUX>::NL>(e, q, d);
 }
 
-// Sweeps of one stage.  Smooth flux: the z sweep is fused with the update
-// (ua); the full flux keeps the separate update kernel (its sweep has no
-// shared memory to spare and the update is ~1 % of its step).
 template <class T, int MODE, int FLUX>
-cudaError_t launch_all_directions(const Engine& e, const T* q, int stage, Probe* probe,
-                                  const UpdateArgs<T>* ua) {
+cudaError_t launch_all_directions(const Engine& e, const T* q, int stage, Probe* probe) {
   for (int d = 0; d < 3; ++d) {
     if (probe) probe->begin(e.stream, stage == 1 ? KC_FLUX1 : KC_FLUX2);
-    cudaError_t err;
-    if (FLUX == FLUX_SMOOTH && d == 2)
-      err = stage == 1 ? launch_sweep<T, MODE, FLUX, 1, true>(e, q, d, ua)
-                       : launch_sweep<T, MODE, FLUX, 2, true>(e, q, d, ua);
-    else
-      err = stage == 1 ? launch_sweep<T, MODE, FLUX, 1>(e, q, d) : launch_sweep<T, MODE, FLUX, 2>(e, q, d);
+    const cudaError_t err = stage == 1 ? launch_sweep<T, MODE, FLUX, 1>(e, q, d)
+                                       : launch_sweep<T, MODE, FLUX, 2>(e, q, d);
     if (probe) probe->end(e.stream);
     if (err != cudaSuccess) return err;
   }
@@ -148,6 +137,13 @@ template <class T>
 cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   T* qin = static_cast<T*>(stage == 1 ? e.q : e.qs);
   cudaError_t err = enqueue_ghosts<T>(e, qin, probe);
+  if (err != cudaSuccess) return err;
+  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
+#define HGKS_DISPATCH(M, F) \
+  if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe);
+  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0) HGKS_DISPATCH(3, 0) HGKS_DISPATCH(4, 0)
+  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1) HGKS_DISPATCH(3, 1) HGKS_DISPATCH(4, 1)
+#undef HGKS_DISPATCH
   if (err != cudaSuccess) return err;
   UpdateArgs<T> ua;
   ua.q = static_cast<T*>(e.q);
@@ -165,31 +161,20 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   const bool mass_flux = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX;
   ua.force_x = mass_flux ? T(0) : T(e.cfg.force_x);
   ua.rho_r = T(e.cfg.rho_ref);
-  // The fused z sweep writes while other CTAs still read Q*, so the stash
-  // goes to the increment buffer (each cell reads its own increment first).
-  ua.stash = mass_flux && stage == 2;
-  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
-#define HGKS_DISPATCH(M, F) \
-  if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe, &ua);
-  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0) HGKS_DISPATCH(3, 0) HGKS_DISPATCH(4, 0)
-  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1) HGKS_DISPATCH(3, 1) HGKS_DISPATCH(4, 1)
-#undef HGKS_DISPATCH
-  if (err != cudaSuccess) return err;
+  ua.stash = mass_flux && stage == 2 ? static_cast<T*>(e.qs) : nullptr;
   if (probe) probe->begin(e.stream, KC_UPDATE);
-  if (flux == FLUX_FULL) {
-    const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
-    if (stage == 1)
-      k_update<T, 1><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
-    else
-      k_update<T, 2><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
-  }
+  const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
+  if (stage == 1)
+    k_update<T, 1><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
+  else
+    k_update<T, 2><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
   if (mass_flux && stage == 2) {
     // Sec. 3.3: the force that keeps the volume integral of rho U at its target.
     const GridDev g = grid_of(e);
     k_massflux_sums<T><<<e.diag_blocks, 256, 0, e.stream>>>(
-        ua.q, ua.inc, ua.comp, g, ua.wx, ua.wy, ua.wz, e.cfg.rho_ref, e.part);
+        ua.q, ua.stash, ua.comp, g, ua.wx, ua.wy, ua.wz, e.cfg.rho_ref, e.part);
     k_massflux_force<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, e.cfg.mass_flux, e.scal);
-    k_force_apply<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua.q, ua.inc, ua.comp, g,
+    k_force_apply<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua.q, ua.stash, ua.comp, g,
                                                                  e.cfg.rho_ref, e.scal);
   }
   if (probe) probe->end(e.stream);

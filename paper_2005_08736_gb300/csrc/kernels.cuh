@@ -148,57 +148,8 @@ struct UpdateArgs {
   GridDev g;
   T force_x;
   T rho_r;
-  int stash;                  // mass-flux force: rho^n, (rho U)^n into planes 0, 1 of inc
-                              // (after the cell's own increment has been read)
+  T* __restrict__ stash;      // mass-flux force: rho^n, (rho U)^n into planes 0, 1 (or null)
 };
-
-// The S2O4 stage of one cell (padded index pi, interior index cell) from its
-// L (stage 1) and dL: stage 1 writes Q* and the increment; stage 2 forms
-// Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), adds the body force and accumulates
-// with compensation (FP32).
-template <class T, int STAGE>
-__device__ __forceinline__ void update_cell(const UpdateArgs<T>& a, long long pi, long long cell, T dt,
-                                            const T L[5], const T dL[5]) {
-  if (STAGE == 1) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const T qn = a.q[v * a.g.P + pi];
-      a.qs[v * a.g.P + pi] = qn + T(0.5) * dt * L[v] + T(0.125) * dt * dt * dL[v];
-      a.inc[v * a.g.N + cell] = dt * L[v] + dt * dt / T(6) * dL[v];
-    }
-  } else {
-    T qn[5], dq[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      qn[v] = a.q[v * a.g.P + pi];
-      dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
-    }
-    if (a.stash) {  // through the same pointer, after this cell's increment was read
-      a.inc[cell] = qn[0];
-      a.inc[a.g.N + cell] = qn[1];
-    }
-    if (a.force_x != T(0)) {
-      // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
-      // (rho E) += dt/2 ((rho U)^{n+1} + (rho U)^n) f_x; the reference is at rest.
-      const T rho_n = a.rho_r + qn[0];
-      dq[1] += T(0.5) * dt * (T(2) * rho_n + dq[0]) * a.force_x;
-      dq[4] += T(0.5) * dt * (T(2) * qn[1] + dq[1]) * a.force_x;
-    }
-    if (a.comp) {
-      // Compensated (Kahan) accumulation of Q^{n+1} = Q^n + dq.
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T yv = dq[v] - a.comp[v * a.g.N + cell];
-        const T t = qn[v] + yv;
-        a.comp[v * a.g.N + cell] = (t - qn[v]) - yv;
-        a.q[v * a.g.P + pi] = t;
-      }
-    } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) a.q[v * a.g.P + pi] = qn[v] + dq[v];
-    }
-  }
-}
 
 // Stage 1: L, dL of Q^n; Q* = Q^n + dt/2 L + dt^2/8 dL; inc = dt L + dt^2/6 dL.
 // Stage 2: dL of Q*; Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), then the body force.
@@ -243,15 +194,48 @@ __global__ void __launch_bounds__(kUpdTX * kUpdTY) k_update(UpdateArgs<T> a) {
               (a.fy[o * SY + iy + sy] - a.fy[o * SY + iy]) * iy_w +
               (a.fz[o * SZ + iz + sz] - a.fz[o * SZ + iz]) * iz_w);
   }
-  T L[5];
   if (STAGE == 1) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
-      L[v] = -((sfx[v][tx + 1][ty] - sfx[v][tx][ty]) * ix_w +
-               (a.fy[v * SY + iy + sy] - a.fy[v * SY + iy]) * iy_w +
-               (a.fz[v * SZ + iz + sz] - a.fz[v * SZ + iz]) * iz_w);
+    for (int v = 0; v < 5; ++v) {
+      const T L = -((sfx[v][tx + 1][ty] - sfx[v][tx][ty]) * ix_w +
+                    (a.fy[v * SY + iy + sy] - a.fy[v * SY + iy]) * iy_w +
+                    (a.fz[v * SZ + iz + sz] - a.fz[v * SZ + iz]) * iz_w);
+      const T qn = a.q[v * a.g.P + pi];
+      a.qs[v * a.g.P + pi] = qn + T(0.5) * dt * L + T(0.125) * dt * dt * dL[v];
+      a.inc[v * a.g.N + cell] = dt * L + dt * dt / T(6) * dL[v];
+    }
+  } else {
+    T qn[5], dq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qn[v] = a.q[v * a.g.P + pi];
+      dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
+    }
+    if (a.stash) {
+      a.stash[pi] = qn[0];
+      a.stash[a.g.P + pi] = qn[1];
+    }
+    if (a.force_x != T(0)) {
+      // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
+      // (rho E) += dt/2 ((rho U)^{n+1} + (rho U)^n) f_x; the reference is at rest.
+      const T rho_n = a.rho_r + qn[0];
+      dq[1] += T(0.5) * dt * (T(2) * rho_n + dq[0]) * a.force_x;
+      dq[4] += T(0.5) * dt * (T(2) * qn[1] + dq[1]) * a.force_x;
+    }
+    if (a.comp) {
+      // Compensated (Kahan) accumulation of Q^{n+1} = Q^n + dq.
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const T yv = dq[v] - a.comp[v * a.g.N + cell];
+        const T t = qn[v] + yv;
+        a.comp[v * a.g.N + cell] = (t - qn[v]) - yv;
+        a.q[v * a.g.P + pi] = t;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.q[v * a.g.P + pi] = qn[v] + dq[v];
+    }
   }
-  update_cell<T, STAGE>(a, pi, cell, dt, L, dL);
 }
 
 // -------------------------------------------------------------- reductions ---
@@ -417,7 +401,7 @@ static __global__ void k_diag_final(const double* __restrict__ part, int nblocks
 
 // ------------------------------------------------- constant mass flux force ---
 // Sec. 3.3: after the two S2O4 stages (state Q~^{n+1} in q, rho^n and
-// (rho U)^n stashed in planes 0 and 1 of the interior stash buffer), per-block FP64
+// (rho U)^n stashed in planes 0 and 1 of the stash buffer), per-block FP64
 // sums of the cell volume, of (rho U)~ and of (rho^n + rho~)/2, each times
 // the cell volume, into part[3 b + k].  comp (FP32 compensation) may be null.
 template <class T>
@@ -439,7 +423,7 @@ __global__ void __launch_bounds__(256) k_massflux_sums(const T* __restrict__ q, 
     const double c0 = comp ? double(comp[c]) : 0.0, c1 = comp ? double(comp[g.N + c]) : 0.0;
     s[0] += vol;
     s[1] += (double(q[g.P + pi]) - c1) * vol;
-    s[2] += (rho_r + 0.5 * (double(q[pi]) - c0 + double(stash[c]))) * vol;
+    s[2] += (rho_r + 0.5 * (double(q[pi]) - c0 + double(stash[pi]))) * vol;
   }
   __shared__ double sm[3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -499,8 +483,8 @@ __global__ void __launch_bounds__(256) k_force_apply(T* __restrict__ q, const T*
   const int y = int(r % ny), z = int(r / ny);
   const long long pi = pad_index(g, x, y, z);
   const T f = T(scal[3]), hdt = T(0.5 * scal[0]);
-  const T rho_t = T(rho_r) + q[pi], rho_n = T(rho_r) + stash[c];
-  const T m_t = q[g.P + pi], m_n = stash[g.N + c];
+  const T rho_t = T(rho_r) + q[pi], rho_n = T(rho_r) + stash[pi];
+  const T m_t = q[g.P + pi], m_n = stash[g.P + pi];
   const T dm = hdt * (rho_t + rho_n) * f;
   const T dE = hdt * (m_t + dm + m_n) * f;
   const T inc[2] = {dm, dE};

@@ -35,7 +35,6 @@ struct SweepArgs {
   int d;
   int chunk;
   Gas<T> gas;
-  UpdateArgs<T> u;  // the fused z sweep: the S2O4 stage of each cell it closes
 };
 
 template <int FLUX, int MODE = 0>
@@ -49,25 +48,16 @@ struct SweepLayout {
 // Per-thread slots of the full-flux phase 3 with two threads per face: the
 // three point states (20 values each) of the second t2 abscissa.
 template <int FLUX, int TPF>
-__host__ __device__ constexpr int sweep_scratch_elems() {
+constexpr int sweep_scratch_elems() {
   return FLUX == FLUX_FULL && TPF == 2 ? 60 * 256 : 0;
 }
 
-// The fused z sweep stages the x-face fluxes of the cell layer it closes
-// ([NVU][TP+1][TS]) and keeps the previous z-face flux of every face
-// ([NVU][TP*TS]); NVU = 10 values in stage 1 (F, dF), 5 in stage 2 (dF).
-template <int STAGE, int TP, int TS, bool FUSED>
-__host__ __device__ constexpr int sweep_fused_elems() {
-  return FUSED ? (STAGE == 1 ? 10 : 5) * ((TP + 1) * TS + TP * TS) : 0;
-}
-
-template <class T, int MODE, int FLUX, int TP, int TS, int NL, int STAGE = 1, bool FUSED = false>
+template <class T, int MODE, int FLUX, int TP, int TS, int NL>
 constexpr size_t sweep_smem_bytes() {
   constexpr int NH = (TP + 4) * (TS + 4);
   constexpr int TPF = 256 / (TP * TS);
   return sizeof(T) * ((NL * SweepLayout<FLUX, MODE>::NFF + SweepLayout<FLUX, MODE>::NT1) * NH +
-                      (TPF - 1) * 10 * TP * TS + sweep_scratch_elems<FLUX, TPF>() +
-                      sweep_fused_elems<STAGE, TP, TS, FUSED>());
+                      (TPF - 1) * 10 * TP * TS + sweep_scratch_elems<FLUX, TPF>());
 }
 
 // Tangential reconstruction of a 5-vector field (components at src + i*sc,
@@ -310,7 +300,7 @@ template <class T, int FLUX> struct SweepOccupancy { static constexpr int value 
 template <> struct SweepOccupancy<float, FLUX_SMOOTH> { static constexpr int value = 3; };
 template <> struct SweepOccupancy<double, FLUX_SMOOTH> { static constexpr int value = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool FUSED = false>
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
 __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T, FLUX>::value > 2
                                            ? 2 : SweepOccupancy<T, FLUX>::value)
     k_sweep(SweepArgs<T> a) {
@@ -326,11 +316,6 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
   T* tb = ffb + NL * NFF * NH;              // [NT1][NH]
   T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
   T* scr = part + (TPF - 1) * 10 * NFACE;      // [60][256] (full flux, TPF = 2)
-  // Fused z sweep (d = 2 only): staged x-face fluxes of the cell layer and
-  // the previous z-face flux of each face, global variable order.
-  constexpr int NVU = STAGE == 1 ? 10 : 5, VU0 = STAGE == 1 ? 0 : 5;
-  T* fxs = scr + sweep_scratch_elems<FLUX, TPF>();  // [NVU][TP+1][TS]
-  T* fzp = fxs + (FUSED ? NVU * (TP + 1) * TS : 0);  // [NVU][NFACE]
 
   const int d = a.d;
   const SweepAxes ax = sweep_axes(d, a.g);
@@ -339,9 +324,7 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
   const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
   const int p0 = blockIdx.x * TP, s0 = blockIdx.y * TS;
   const int f0 = blockIdx.z * a.chunk;
-  // The fused sweep also computes the first face of the next chunk, so that
-  // it closes every cell of its own chunk.
-  const int f1 = min(f0 + a.chunk + (FUSED ? 1 : 0), nd + 1);
+  const int f1 = min(f0 + a.chunk, nd + 1);
   const int tid = threadIdx.x;
 
   // Phase-3 role: one face and GPF Gauss points of it.
@@ -405,20 +388,6 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
         const int hs2 = t1P ? it / TP : 2 + it / HP;
         const int at = hs2 * HP + hp2;
         t1_pass_item<T, MODE, FLUX, NH>(ff, tb, at, st1, a.gas);
-      }
-      if constexpr (FUSED) {
-        // x-face fluxes of cell layer f-1 ([z][x][y], y fastest) into shared memory.
-        if (f > f0) {
-          const long long SX = (long long)(a.g.n[0] + 1) * a.g.n[1] * a.g.n[2];
-          for (int i = tid; i < (TP + 1) * TS; i += 256) {
-            const int xi = i / TS, yi = i % TS;
-            const int x = p0 + xi, y = s0 + yi;
-            const bool ok = x <= nP && y < nS;
-            const long long fi = ((long long)(f - 1) * (a.g.n[0] + 1) + x) * a.g.n[1] + y;
-#pragma unroll
-            for (int v = 0; v < NVU; ++v) fxs[(v * (TP + 1) + xi) * TS + yi] = ok ? a.u.fx[(VU0 + v) * SX + fi] : T(0);
-          }
-        }
       }
     }
     __syncthreads();
@@ -608,47 +577,11 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
       for (int r = 1; r < TPF; ++r)
 #pragma unroll
         for (int i = 0; i < 10; ++i) Fs[i] += part[((r - 1) * 10 + i) * NFACE + face];
-      if constexpr (FUSED) {
-        // Close cell (x, y, f-1): the divergence of Eq. (4) and the S2O4 stage,
-        // with the same arithmetic as k_update.
-        T Fz[NVU];
+      const long long o = fout + (long long)f * fstep;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          const int gi = global_var(2, i);  // the fused sweep runs along z only
-          if (STAGE == 1) Fz[gi] = T(0.25) * Fs[i];
-          Fz[gi + 5 - VU0] = T(0.25) * Fs[5 + i];
-        }
-        if (f > f0) {
-          const int x = cP, y = cS, z = f - 1;
-          const int nx = a.g.n[0], ny = a.g.n[1];
-          const long long SY = (long long)nx * (ny + 1) * a.g.n[2];
-          const long long iy = ((long long)z * (ny + 1) + y) * nx + x;
-          const T ix_w = T(1) / a.wt1[x + kGhost], iy_w = T(1) / a.wt2[y + kGhost],
-                  iz_w = T(1) / a.wn[z + kGhost];
-          T L[5] = {T(0), T(0), T(0), T(0), T(0)}, dL[5];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const int o = 5 + v, u = o - VU0;
-            dL[v] = -((fxs[(u * (TP + 1) + ip + 1) * TS + is] - fxs[(u * (TP + 1) + ip) * TS + is]) * ix_w +
-                      (a.u.fy[o * SY + iy + nx] - a.u.fy[o * SY + iy]) * iy_w +
-                      (Fz[u] - fzp[u * NFACE + face]) * iz_w);
-            if (STAGE == 1)
-              L[v] = -((fxs[(v * (TP + 1) + ip + 1) * TS + is] - fxs[(v * (TP + 1) + ip) * TS + is]) * ix_w +
-                       (a.u.fy[v * SY + iy + nx] - a.u.fy[v * SY + iy]) * iy_w +
-                       (Fz[v] - fzp[v * NFACE + face]) * iz_w);
-          }
-          const long long cell = ((long long)z * ny + y) * nx + x;
-          update_cell<T, STAGE>(a.u, pad_index(a.g, x, y, z), cell, dt, L, dL);
-        }
-#pragma unroll
-        for (int u = 0; u < NVU; ++u) fzp[u * NFACE + face] = Fz[u];
-      } else {
-        const long long o = fout + (long long)f * fstep;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
-          a.fd[(5 + ax.gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
-        }
+      for (int i = 0; i < 5; ++i) {
+        a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
+        a.fd[(5 + ax.gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
       }
     }
     __syncthreads();
