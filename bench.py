@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 N_GRID = 256
 PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.09 s/step
 METRIC = "Mcell-updates/s per S2O4 step"
-LAUNCHES_PER_STEP = 23  # cfl, dt, 2 x (3 ghost + 3 x (face fields + flux) + update), time
+# cfl, dt, 2 x (3 ghost fills + 3 sweeps + update), time
+LAUNCHES_PER_STEP = 17
 # Executed FP32 operations (fadd + fmul + 2 ffma) and DRAM bytes (read +
 # write) per face of the stage-1 sweep kernel (FP32, linear WENO5, smooth
 # flux), mean of the three directions, counted by ncu on Taylor-Green 128^3
