@@ -293,6 +293,29 @@ __device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1
   }
 }
 
+// One field k of the t1 pass at point `at`: k < NV a state field (values at
+// both t1 abscissae and t1-derivatives), else the normal slope of state
+// field k - NV (values only).
+template <class T, int MODE, int NV, int NH>
+__device__ __forceinline__ void t1_pass_field(const T* ff, T* tb, int at, int st1, int k) {
+  if (k < NV) {
+    const T* src = ff + k * NH + at;
+    T v[2], dd[2];
+    tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+    tb[(4 * k + 0) * NH + at] = v[0];
+    tb[(4 * k + 1) * NH + at] = v[1];
+    tb[(4 * k + 2) * NH + at] = dd[0];
+    tb[(4 * k + 3) * NH + at] = dd[1];
+  } else {
+    const int j = k - NV;
+    const T* src = ff + k * NH + at;
+    T v[2];
+    tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
+    tb[(4 * NV + 2 * j + 0) * NH + at] = v[0];
+    tb[(4 * NV + 2 * j + 1) * NH + at] = v[1];
+  }
+}
+
 // Resident CTAs per SM the register budget is sized for: the smooth FP32
 // sweep fits three (shared memory allows three as well), the others one or two
 // (two at most for the characteristic modes, which need more registers).
@@ -380,14 +403,30 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     const int f = fb + l;
     const T* ff = ffb + l * NFF * NH;
     // ---------------- phase 2: tangential pass along t1 ----------------
-    {
+    // Points of the tile with a halo of 2 along t2.  Conservative variables:
+    // the (field, point) pairs are spread evenly over the CTA; characteristic
+    // variables: one point (all fields) per item.
+    if constexpr (is_char_mode<MODE>()) {
       const int items = t1P ? TP * HS : HP * TS;
       const int st1 = t1P ? 1 : HP;
       for (int it = tid; it < items; it += 256) {
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
-        const int at = hs2 * HP + hp2;
-        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, at, st1, a.gas);
+        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1, a.gas);
+      }
+    } else if (t1P) {
+      constexpr int ITEMS = TP * HS;
+#pragma unroll 1
+      for (int it = tid; it < ITEMS * 2 * NV; it += 256) {
+        const int k = it / ITEMS, pt = it % ITEMS;
+        t1_pass_field<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, k);
+      }
+    } else {
+      constexpr int ITEMS = HP * TS;
+#pragma unroll 1
+      for (int it = tid; it < ITEMS * 2 * NV; it += 256) {
+        const int k = it / ITEMS, pt = it % ITEMS;
+        t1_pass_field<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, k);
       }
     }
     __syncthreads();
