@@ -293,26 +293,33 @@ __device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1
   }
 }
 
-// One field k of the t1 pass at point `at`: k < NV a state field (values at
-// both t1 abscissae and t1-derivatives), else the normal slope of state
-// field k - NV (values only).
+// One group of five fields of the t1 pass at point `at`: group g < NV/5 is
+// state group g (values at both t1 abscissae and t1-derivatives), else the
+// normal slopes of state group g - NV/5 (values only).
 template <class T, int MODE, int NV, int NH>
-__device__ __forceinline__ void t1_pass_field(const T* ff, T* tb, int at, int st1, int k) {
-  if (k < NV) {
-    const T* src = ff + k * NH + at;
-    T v[2], dd[2];
-    tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
-    tb[(4 * k + 0) * NH + at] = v[0];
-    tb[(4 * k + 1) * NH + at] = v[1];
-    tb[(4 * k + 2) * NH + at] = dd[0];
-    tb[(4 * k + 3) * NH + at] = dd[1];
+__device__ __forceinline__ void t1_pass_group(const T* ff, T* tb, int at, int st1, int grp) {
+  if (grp < NV / 5) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int k = 5 * grp + i;
+      const T* src = ff + k * NH + at;
+      T v[2], dd[2];
+      tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+      tb[(4 * k + 0) * NH + at] = v[0];
+      tb[(4 * k + 1) * NH + at] = v[1];
+      tb[(4 * k + 2) * NH + at] = dd[0];
+      tb[(4 * k + 3) * NH + at] = dd[1];
+    }
   } else {
-    const int j = k - NV;
-    const T* src = ff + k * NH + at;
-    T v[2];
-    tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
-    tb[(4 * NV + 2 * j + 0) * NH + at] = v[0];
-    tb[(4 * NV + 2 * j + 1) * NH + at] = v[1];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int j = 5 * (grp - NV / 5) + i;  // state field whose normal slope this is
+      const T* src = ff + (NV + j) * NH + at;
+      T v[2];
+      tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
+      tb[(4 * NV + 2 * j + 0) * NH + at] = v[0];
+      tb[(4 * NV + 2 * j + 1) * NH + at] = v[1];
+    }
   }
 }
 
@@ -404,8 +411,8 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     const T* ff = ffb + l * NFF * NH;
     // ---------------- phase 2: tangential pass along t1 ----------------
     // Points of the tile with a halo of 2 along t2.  Conservative variables:
-    // the (field, point) pairs are spread evenly over the CTA; characteristic
-    // variables: one point (all fields) per item.
+    // the (group of five fields, point) pairs are spread evenly over the CTA;
+    // characteristic variables: one point (all fields) per item.
     if constexpr (is_char_mode<MODE>()) {
       const int items = t1P ? TP * HS : HP * TS;
       const int st1 = t1P ? 1 : HP;
@@ -417,16 +424,16 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     } else if (t1P) {
       constexpr int ITEMS = TP * HS;
 #pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV; it += 256) {
-        const int k = it / ITEMS, pt = it % ITEMS;
-        t1_pass_field<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, k);
+      for (int it = tid; it < ITEMS * 2 * NV / 5; it += 256) {
+        const int grp = it / ITEMS, pt = it % ITEMS;
+        t1_pass_group<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
       }
     } else {
       constexpr int ITEMS = HP * TS;
 #pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV; it += 256) {
-        const int k = it / ITEMS, pt = it % ITEMS;
-        t1_pass_field<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, k);
+      for (int it = tid; it < ITEMS * 2 * NV / 5; it += 256) {
+        const int grp = it / ITEMS, pt = it % ITEMS;
+        t1_pass_group<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
       }
     }
     __syncthreads();
@@ -499,17 +506,20 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
       // along n, t1, t2) while the flux at m2 = 0 is evaluated.
       const int m1 = sub;
       PointState<T> st[3];
-#pragma unroll
+      // One state group per iteration (the loop body once in the code): the
+      // group's m2 = 0 states go to st[s] through constant indices.
+#pragma unroll 1
       for (int s = 0; s < 3; ++s) {
+        PointState<T> g0;
         if constexpr (is_char_mode<MODE>()) {
           T val[2][5], d2[2][5], d1[2][5], dn[2][5];
           t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
 #pragma unroll
           for (int i = 0; i < 5; ++i) {
-            st[s].q[i] = val[0][i];
-            st[s].dq[0][i] = dn[0][i];
-            st[s].dq[1][i] = d1[0][i] * rh1;
-            st[s].dq[2][i] = d2[0][i] * rh2;
+            g0.q[i] = val[0][i];
+            g0.dq[0][i] = dn[0][i];
+            g0.dq[1][i] = d1[0][i] * rh1;
+            g0.dq[2][i] = d2[0][i] * rh2;
             scr[((s * 4 + 0) * 5 + i) * 256 + tid] = val[1][i];
             scr[((s * 4 + 1) * 5 + i) * 256 + tid] = dn[1][i];
             scr[((s * 4 + 2) * 5 + i) * 256 + tid] = d1[1][i] * rh1;
@@ -517,25 +527,28 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
           }
         } else {
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          const int k = 5 * s + i;
-          const T* sv = tb + (4 * k + m1) * NH + at3;
-          const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-          const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-          T v[2], dd[2], vd[2], vs[2];
-          tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
-          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
-          st[s].q[i] = v[0];
-          st[s].dq[0][i] = vs[0];
-          st[s].dq[1][i] = vd[0] * rh1;
-          st[s].dq[2][i] = dd[0] * rh2;
-          scr[((s * 4 + 0) * 5 + i) * 256 + tid] = v[1];
-          scr[((s * 4 + 1) * 5 + i) * 256 + tid] = vs[1];
-          scr[((s * 4 + 2) * 5 + i) * 256 + tid] = vd[1] * rh1;
-          scr[((s * 4 + 3) * 5 + i) * 256 + tid] = dd[1] * rh2;
+          for (int i = 0; i < 5; ++i) {
+            const int k = 5 * s + i;
+            const T* sv = tb + (4 * k + m1) * NH + at3;
+            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+            T v[2], dd[2], vd[2], vs[2];
+            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
+            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
+            g0.q[i] = v[0];
+            g0.dq[0][i] = vs[0];
+            g0.dq[1][i] = vd[0] * rh1;
+            g0.dq[2][i] = dd[0] * rh2;
+            scr[((s * 4 + 0) * 5 + i) * 256 + tid] = v[1];
+            scr[((s * 4 + 1) * 5 + i) * 256 + tid] = vs[1];
+            scr[((s * 4 + 2) * 5 + i) * 256 + tid] = vd[1] * rh1;
+            scr[((s * 4 + 3) * 5 + i) * 256 + tid] = dd[1] * rh2;
+          }
         }
-        }
+        if (s == 0) st[0] = g0;
+        else if (s == 1) st[1] = g0;
+        else st[2] = g0;
       }
 #pragma unroll 1
       for (int m2 = 0; m2 < 2; ++m2) {
