@@ -402,8 +402,11 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
       for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
         const int m1 = g & 1, m2 = g >> 1;
         PointState<T> st[NS], ct[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
+        // Forward t2 pass, one state group per iteration (the body once in
+        // the code); the group's states go to st[s] through constant indices.
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+          PointState<T> g0;
 #pragma unroll
           for (int i = 0; i < 5; ++i) {
             const int k = 5 * s + i;
@@ -412,12 +415,21 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
             const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
             T v[2], dd[2];
             tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-            st[s].q[i] = v[m2];
-            st[s].dq[2][i] = dd[m2] * rh2;
+            g0.q[i] = v[m2];
+            g0.dq[2][i] = dd[m2] * rh2;
             tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
-            st[s].dq[1][i] = v[m2] * rh1;
+            g0.dq[1][i] = v[m2] * rh1;
             tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
-            st[s].dq[0][i] = v[m2];
+            g0.dq[0][i] = v[m2];
+          }
+          if (s == 0) st[0] = g0;
+          else if (NS > 1 && s == 1) st[NS > 1 ? 1 : 0] = g0;
+          else if (NS > 2) st[NS > 2 ? 2 : 0] = g0;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
             ct[s].q[i] = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) ct[s].dq[c][i] = T(0);

@@ -575,36 +575,43 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
 #pragma unroll 1
       for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
         const int m1 = g & 1, m2 = g >> 1;
-        PointState<T> st[FLUX == FLUX_FULL ? 3 : 1];
-#pragma unroll
-        for (int s = 0; s < (FLUX == FLUX_FULL ? 3 : 1); ++s) {
+        constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
+        PointState<T> st[NS];
+        // One state group per iteration (the body once in the code); the
+        // group's states go to st[s] through constant indices.
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+          PointState<T> g0;
           if constexpr (is_char_mode<MODE>()) {
             T val[2][5], d2[2][5], d1[2][5], dn[2][5];
             t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
-              st[s].q[i] = val[m2][i];
-              st[s].dq[0][i] = dn[m2][i];
-              st[s].dq[1][i] = d1[m2][i] * rh1;
-              st[s].dq[2][i] = d2[m2][i] * rh2;
+              g0.q[i] = val[m2][i];
+              g0.dq[0][i] = dn[m2][i];
+              g0.dq[1][i] = d1[m2][i] * rh1;
+              g0.dq[2][i] = d2[m2][i] * rh2;
             }
           } else {
 #pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            const int k = 5 * s + i;
-            const T* sv = tb + (4 * k + m1) * NH + at3;
-            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-            T v[2], dd[2];
-            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-            st[s].q[i] = v[m2];
-            st[s].dq[2][i] = dd[m2] * rh2;
-            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
-            st[s].dq[1][i] = v[m2] * rh1;
-            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
-            st[s].dq[0][i] = v[m2];
+            for (int i = 0; i < 5; ++i) {
+              const int k = 5 * s + i;
+              const T* sv = tb + (4 * k + m1) * NH + at3;
+              const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
+              const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
+              T v[2], dd[2];
+              tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+              g0.q[i] = v[m2];
+              g0.dq[2][i] = dd[m2] * rh2;
+              tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
+              g0.dq[1][i] = v[m2] * rh1;
+              tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
+              g0.dq[0][i] = v[m2];
+            }
           }
-          }
+          if (s == 0) st[0] = g0;
+          else if (NS > 1 && s == 1) st[NS > 1 ? 1 : 0] = g0;
+          else if (NS > 2) st[NS > 2 ? 2 : 0] = g0;
         }
         T F[5], dF[5];
         if constexpr (FLUX == FLUX_SMOOTH) {
