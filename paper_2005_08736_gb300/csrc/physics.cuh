@@ -411,7 +411,7 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
     dT0 = (dp0 - s.theta * st0.dq[0][0]) * s.inv_rho;
   }
   T pl, pr;
-#pragma unroll
+#pragma unroll 1  // one copy of the half-space code for both sides
   for (int side = 0; side < 2; ++side) {
     const PointState<T>& st = side == 0 ? stl : str;
     const Prim<T> s = prim_of(st.q, g);

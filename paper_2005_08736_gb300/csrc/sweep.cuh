@@ -45,6 +45,9 @@ struct SweepLayout {
   static constexpr int NT1 = 4 * NV + 2 * NV;            // t1 pass outputs
 };
 
+// Threads of a sweep CTA: 256, or one per face for tiles of more faces.
+__host__ __device__ constexpr int sweep_threads(int tp, int ts) { return tp * ts > 256 ? tp * ts : 256; }
+
 // Per-thread slots of the full-flux phase 3 with two threads per face: the
 // three point states (20 values each) of the second t2 abscissa.
 template <int FLUX, int TPF>
@@ -55,7 +58,7 @@ constexpr int sweep_scratch_elems() {
 template <class T, int MODE, int FLUX, int TP, int TS, int NL>
 constexpr size_t sweep_smem_bytes() {
   constexpr int NH = (TP + 4) * (TS + 4);
-  constexpr int TPF = 256 / (TP * TS);
+  constexpr int TPF = sweep_threads(TP, TS) / (TP * TS);
   return sizeof(T) * ((NL * SweepLayout<FLUX, MODE>::NFF + SweepLayout<FLUX, MODE>::NT1) * NH +
                       (TPF - 1) * 10 * TP * TS + sweep_scratch_elems<FLUX, TPF>());
 }
@@ -330,17 +333,28 @@ template <class T, int FLUX> struct SweepOccupancy { static constexpr int value 
 template <> struct SweepOccupancy<float, FLUX_SMOOTH> { static constexpr int value = 3; };
 template <> struct SweepOccupancy<double, FLUX_SMOOTH> { static constexpr int value = 2; };
 
+// Resident CTAs per SM for the register budget: SweepOccupancy for 256
+// threads (two at most in the characteristic modes); tiles of 384 threads
+// two, of 512 one.
+template <class T, int MODE, int FLUX, int TP, int TS>
+__host__ __device__ constexpr int sweep_min_blocks() {
+  return sweep_threads(TP, TS) == 512   ? 1
+         : sweep_threads(TP, TS) == 384 ? 2
+         : is_char_mode<MODE>() && SweepOccupancy<T, FLUX>::value > 2 ? 2
+                                                                      : SweepOccupancy<T, FLUX>::value;
+}
+
 template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
-__global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T, FLUX>::value > 2
-                                           ? 2 : SweepOccupancy<T, FLUX>::value)
+__global__ void __launch_bounds__(sweep_threads(TP, TS), (sweep_min_blocks<T, MODE, FLUX, TP, TS>()))
     k_sweep(SweepArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
   constexpr int NV = SweepLayout<FLUX>::NV;
   constexpr int NFF = SweepLayout<FLUX, MODE>::NFF;
   constexpr int NFACE = TP * TS;
-  constexpr int TPF = 256 / NFACE;  // threads per face in phase 3
+  constexpr int NT = sweep_threads(TP, TS);  // threads of the CTA
+  constexpr int TPF = NT / NFACE;  // threads per face in phase 3
   constexpr int GPF = 4 / TPF;      // Gauss points per thread
-  static_assert(TPF * NFACE == 256 && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
+  static_assert(TPF * NFACE == NT && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ffb = reinterpret_cast<T*>(smem_raw);  // [NL][NFF][NH]
   T* tb = ffb + NL * NFF * NH;              // [NT1][NH]
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     // Items (layer, transverse point of the tile plus a halo of 2).  For d = x
     // consecutive threads take consecutive layers, so that the loads along x
     // are coalesced; otherwise consecutive transverse points along P (= x).
-    for (int it = tid; it < NL * NH; it += 256) {
+    for (int it = tid; it < NL * NH; it += NT) {
       const int l = d == 0 ? it % NL : it / NH;
       const int h = d == 0 ? it / NL : it % NH;
       const int f = fb + l;
@@ -416,7 +430,7 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     if constexpr (is_char_mode<MODE>()) {
       const int items = t1P ? TP * HS : HP * TS;
       const int st1 = t1P ? 1 : HP;
-      for (int it = tid; it < items; it += 256) {
+      for (int it = tid; it < items; it += NT) {
         const int hp2 = t1P ? 2 + it % TP : it % HP;
         const int hs2 = t1P ? it / TP : 2 + it / HP;
         t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1, a.gas);
@@ -424,14 +438,14 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
     } else if (t1P) {
       constexpr int ITEMS = TP * HS;
 #pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV / 5; it += 256) {
+      for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
         const int grp = it / ITEMS, pt = it % ITEMS;
         t1_pass_group<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
       }
     } else {
       constexpr int ITEMS = HP * TS;
 #pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV / 5; it += 256) {
+      for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
         const int grp = it / ITEMS, pt = it % ITEMS;
         t1_pass_group<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
       }
@@ -504,6 +518,7 @@ __global__ void __launch_bounds__(256, is_char_mode<MODE>() && SweepOccupancy<T,
       // point states of m2 = 1 wait in the thread's shared-memory slots
       // (index ((s*4 + c)*5 + i)*256 + tid, c = 0 value, 1..3 derivatives
       // along n, t1, t2) while the flux at m2 = 0 is evaluated.
+      static_assert(NT == 256, "the shared-memory slots are laid out for 256 threads");
       const int m1 = sub;
       PointState<T> st[3];
       // One state group per iteration (the loop body once in the code): the
