@@ -239,6 +239,89 @@ __device__ __forceinline__ void flux_full_dq_vjp(const PointState<T>* st, const 
   }
 }
 
+// Value cotangents of the full flux.  With G_k = gF Fq_k + gdF dFq_k the
+// weight of term V_k and phi_tau the sensitivity to tau (fit coefficients
+// and the Prandtl term), each value enters through one part only: q0 the
+// equilibrium part (and tau through mu0/p0), q_l and q_r their half-space
+// part (and tau through p_l, p_r).  One forward-mode pass of that part per
+// value component, instead of a pass of the whole flux.
+template <class T>
+__device__ __forceinline__ void flux_full_value_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
+                                                    const T gF[5], const T gdF[5], PointState<T>* cot) {
+  const Gas<Dual<T>> gd = dual_gas(gas);
+  const T cp = T(0.5) * (gas.K + T(5));
+  FullEq<T> e;
+  flux_full_eq(st[2], gas, e);
+  FullSide<T> hl, hr;
+  flux_full_side(st[0], gas, 0, hl);
+  flux_full_side(st[1], gas, 1, hr);
+  const T tau = collision_time_full(e.mu, e.p, hl.p, hr.p, gas, dt);
+  Dual<T> Fq[6], dFq[6];
+  fit_coefficients(Dual<T>(tau, T(1)), Dual<T>(dt), Fq, dFq);
+  T G[6][5];
+  T phi_tau = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      G[k][i] = gF[i] * Fq[k].v + gdF[i] * dFq[k].v;
+      T Vki = k < 3 ? e.V[k][i] : hl.V[k - 3][i] + hr.V[k - 3][i];
+      if (k == 3 && i == 1) Vki -= gas.p_r;
+      phi_tau += (gF[i] * Fq[k].d + gdF[i] * dFq[k].d) * Vki;
+    }
+  const T wpr = gF[4] * gas.pr_fix * cp;  // F[4] -= pr_fix tau p0 c_p dT0
+  phi_tau -= wpr * e.p * e.dT;
+  const T dtau_dpl = collision_time_full(Dual<T>(e.mu), Dual<T>(e.p), Dual<T>(hl.p, T(1)),
+                                         Dual<T>(hr.p), gd, Dual<T>(dt)).d;
+  const T dtau_dpr = collision_time_full(Dual<T>(e.mu), Dual<T>(e.p), Dual<T>(hl.p),
+                                         Dual<T>(hr.p, T(1)), gd, Dual<T>(dt)).d;
+  // Equilibrium state q0.
+#pragma unroll 1
+  for (int c = 0; c < 5; ++c) {
+    PointState<Dual<T>> x;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      x.q[i] = Dual<T>(st[2].q[i], T(i == c ? 1 : 0));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) x.dq[d][i] = Dual<T>(st[2].dq[d][i], T(0));
+    }
+    FullEq<Dual<T>> de;
+    flux_full_eq(x, gd, de);
+    T sdot = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) sdot += G[k][i] * de.V[k][i].d;
+    const T dtau = (de.mu.d * e.p - e.mu * de.p.d) / (e.p * e.p);
+    sdot += phi_tau * dtau - wpr * tau * (de.p.d * e.dT + e.p * de.dT.d);
+    cot[2].q[c] += sdot;
+  }
+  // Left and right states.
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const T dtau_dp = side == 0 ? dtau_dpl : dtau_dpr;
+#pragma unroll 1
+    for (int c = 0; c < 5; ++c) {
+      PointState<Dual<T>> x;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        x.q[i] = Dual<T>(st[side].q[i], T(i == c ? 1 : 0));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x.dq[d][i] = Dual<T>(st[side].dq[d][i], T(0));
+      }
+      FullSide<Dual<T>> dh;
+      flux_full_side(x, gd, side, dh);
+      T sdot = T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) sdot += G[3 + k][i] * dh.V[k][i].d;
+      sdot += phi_tau * dtau_dp * dh.p.d;
+      cot[side].q[c] += sdot;
+    }
+  }
+}
+
 // Cotangents of the reconstructed Gauss-point states (value and the three
 // derivatives of each of NS states) from the flux cotangents (gF, gdF).
 template <class T, int FLUX>
@@ -246,6 +329,11 @@ __device__ __forceinline__ void flux_vjp(const PointState<T>* st, const Gas<T>& 
                                          bool want_F, const T gF[5], const T gdF[5],
                                          PointState<T>* cot) {
   constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
+  if constexpr (FLUX == FLUX_FULL) {
+    flux_full_value_vjp(st, gas, dt, gF, gdF, cot);
+    flux_full_dq_vjp(st, gas, dt, gF, gdF, cot);
+    return;
+  }
   const Gas<Dual<T>> gd = dual_gas(gas);
   // Values q: one forward-mode (dual-number) pass per component.
 #pragma unroll 1

@@ -110,15 +110,13 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
 }
 
 // Tile variants: 0 is SweepTile; the linear-weight smooth FP32 sweep also has
-// 32x8 and 16x16 tiles with two layers per face-field pass (1, 2) and 32x12
-// and 32x16 tiles of one thread per face with one layer per pass (3, 4).
+// 32x8 and 16x16 tiles with two layers per face-field pass.
 template <class T, int MODE, int FLUX, int STAGE>
 cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   if constexpr (std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH) {
     if (e.sweep_variant == 1) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2>(e, q, d);
     if (e.sweep_variant == 2) return launch_sweep_tile<T, MODE, FLUX, STAGE, 16, 16, 2>(e, q, d);
-    if (e.sweep_variant == 3) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 12, 1>(e, q, d);
-    if (e.sweep_variant == 4) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 16, 1>(e, q, d);
+
   }
   return launch_sweep_tile<T, MODE, FLUX, STAGE, SweepTile<T, FLUX>::TP, SweepTile<T, FLUX>::TS,
                            SweepTile<T, FLUX>::NL>(e, q, d);

@@ -380,6 +380,84 @@ __device__ __forceinline__ void fit_coefficients(T tau, T dt, T Fq[6], T dFq[6])
   dFq[5] = T(4) * r * r * D;
 }
 
+// The full second-order flux (Eq. (5)) in parts, shared by the forward flux
+// and its vector-Jacobian product:
+//   equilibrium part (state 0): V0 = rho0 <u psi> - E(Q_ref) (Euler flux),
+//     V2 = rho0 <u A psi> = J_n Q_t, V1 = rho0 <u (a.u) psi> =
+//     -(viscous flux with mu = p, Pr = 1) - V2; mu0, p0 and the normal
+//     temperature slope dT0 for tau and the Prandtl fix;
+//   half-space part of side l (u > 0, g_l) or r (u < 0, g_r): rho <u psi>,
+//     rho <u (a.psi) u_d psi>, rho <u A psi> over the half space, and p;
+//   tau = mu0/p0 + C |p_l - p_r|/(p_l + p_r) dt (Sec. 3 opening);
+//   the linear fit (Eq. (7)) F = sum_k Fq_k V_k, dF = sum_k dFq_k V_k, and
+//   the Prandtl fix of the heat flux.
+template <class T>
+struct FullEq {
+  T V[3][5];
+  T mu, p, dT;
+};
+template <class T>
+struct FullSide {
+  T V[3][5];
+  T p;
+};
+
+template <class T>
+__device__ __forceinline__ void flux_full_eq(const PointState<T>& st0, const Gas<T>& g, FullEq<T>& o) {
+  const Prim<T> s = prim_of(st0.q, g);
+  const T H = g.h_r + st0.q[4] + s.dp;
+  euler_flux_dev(s, st0.q, g, o.V[0]);
+  T Qt[5], Fv[5];
+  state_time_derivative(s, H, st0.dq, g, Qt);
+  euler_jvp<0>(s, H, Qt, g, o.V[2]);
+  ns_viscous_flux(s, st0.dq, g, s.p, T(1), Fv);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) o.V[1][i] = -Fv[i] - o.V[2][i];
+  o.mu = viscosity(s, g);
+  o.p = s.p;
+  // Normal temperature derivative for the Prandtl fix of the heat flux.
+  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+  const T dp0 = g.gm1 * (st0.dq[0][4] - s.U * st0.dq[0][1] - s.V * st0.dq[0][2] -
+                         s.W * st0.dq[0][3] + T(0.5) * q2 * st0.dq[0][0]);
+  o.dT = (dp0 - s.theta * st0.dq[0][0]) * s.inv_rho;
+}
+
+// side = 0: g_l over u > 0; side = 1: g_r over u < 0.
+template <class T>
+__device__ __forceinline__ void flux_full_side(const PointState<T>& st, const Gas<T>& g, int side,
+                                               FullSide<T>& o) {
+  const Prim<T> s = prim_of(st.q, g);
+  Mom<T> mh;
+  T a[3][5], A[5];
+  slopes_and_A(s, g, st.q, st.dq, a, A);
+  moments(s, g, side == 0 ? +1 : -1, mh);
+  // Half-space moments as symmetric matrices: <u psi psi^T>, <u u_d psi psi^T>.
+  // <u psi> is the first column of the first; <u (a.psi) u_d psi> = M_d a.
+  T ua[5] = {0, 0, 0, 0, 0}, uA[5] = {0, 0, 0, 0, 0};
+  T M[15];
+  mom_psipsi<1, 0, 0>(mh, M);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) o.V[0][i] = s.rho * M[i];
+  sym5_matvec_add(M, A, uA);
+  mom_psipsi<2, 0, 0>(mh, M);
+  sym5_matvec_add(M, a[0], ua);
+  mom_psipsi<1, 1, 0>(mh, M);
+  sym5_matvec_add(M, a[1], ua);
+  mom_psipsi<1, 0, 1>(mh, M);
+  sym5_matvec_add(M, a[2], ua);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    o.V[1][i] = s.rho * ua[i];
+    o.V[2][i] = s.rho * uA[i];
+  }
+  o.p = s.p;
+}
+
+template <class T>
+__device__ __forceinline__ T collision_time_full(T mu0, T p0, T pl, T pr, const Gas<T>& g, T dt) {
+  return mu0 / p0 + g.tau_num_C * tabs((pl - pr) / (pl + pr)) * dt;
+}
+
 // Full second-order flux (Eq. (5)) with the Heaviside factor H(u) on g_l and
 // 1 - H(u) on g_r, integrated over [0, dt] and [0, dt/2] and fitted linearly
 // (Eq. (7)).  Returns F - E(Q_ref) and dF.
@@ -388,73 +466,25 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
                                           const PointState<T>& st0, const Gas<T>& g, T dt,
                                           T F[5], T dF[5]) {
   T V[6][5];
-  T tau, mu0, dT0, p0;
-  {
-    // Equilibrium part: V0 = rho0 <u psi> (Euler flux), V2 = rho0 <u A psi> =
-    // J_n Q_t, V1 = rho0 <u (a.u) psi> = -(viscous flux with mu = p, Pr = 1) - V2.
-    const Prim<T> s = prim_of(st0.q, g);
-    const T H = g.h_r + st0.q[4] + s.dp;
-    euler_flux_dev(s, st0.q, g, V[0]);
-    T Qt[5], Fv[5];
-    state_time_derivative(s, H, st0.dq, g, Qt);
-    euler_jvp<0>(s, H, Qt, g, V[2]);
-    ns_viscous_flux(s, st0.dq, g, s.p, T(1), Fv);
+  FullEq<T> e;
+  flux_full_eq(st0, g, e);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) V[1][i] = -Fv[i] - V[2][i];
-    mu0 = viscosity(s, g);
-    p0 = s.p;
-    tau = mu0 / s.p;
-    // Normal temperature derivative for the Prandtl fix of the heat flux.
-    const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
-    const T dp0 = g.gm1 * (st0.dq[0][4] - s.U * st0.dq[0][1] - s.V * st0.dq[0][2] -
-                           s.W * st0.dq[0][3] + T(0.5) * q2 * st0.dq[0][0]);
-    dT0 = (dp0 - s.theta * st0.dq[0][0]) * s.inv_rho;
-  }
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) V[k][i] = e.V[k][i];
   T pl, pr;
 #pragma unroll 1  // one copy of the half-space code for both sides
   for (int side = 0; side < 2; ++side) {
-    const PointState<T>& st = side == 0 ? stl : str;
-    const Prim<T> s = prim_of(st.q, g);
-    Mom<T> mh;
-    T a[3][5], A[5];
-    slopes_and_A(s, g, st.q, st.dq, a, A);
-    moments(s, g, side == 0 ? +1 : -1, mh);
-    // Half-space moments as symmetric matrices: <u psi psi^T>, <u u_d psi psi^T>.
-    // <u psi> is the first column of the first; <u (a.psi) u_d psi> = M_d a.
-    T u0[5], ua[5] = {0, 0, 0, 0, 0}, uA[5] = {0, 0, 0, 0, 0};
-    {
-      T M[15];
-      mom_psipsi<1, 0, 0>(mh, M);
-      u0[0] = M[0];
-      u0[1] = M[1];
-      u0[2] = M[2];
-      u0[3] = M[3];
-      u0[4] = M[4];
-      sym5_matvec_add(M, A, uA);
-      mom_psipsi<2, 0, 0>(mh, M);
-      sym5_matvec_add(M, a[0], ua);
-      mom_psipsi<1, 1, 0>(mh, M);
-      sym5_matvec_add(M, a[1], ua);
-      mom_psipsi<1, 0, 1>(mh, M);
-      sym5_matvec_add(M, a[2], ua);
-    }
+    FullSide<T> h;
+    flux_full_side(side == 0 ? stl : str, g, side, h);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const T v3 = s.rho * u0[i], v4 = s.rho * ua[i], v5 = s.rho * uA[i];
-      if (side == 0) {
-        V[3][i] = v3;
-        V[4][i] = v4;
-        V[5][i] = v5;
-      } else {
-        V[3][i] += v3;
-        V[4][i] += v4;
-        V[5][i] += v5;
-      }
-    }
-    if (side == 0) pl = s.p; else pr = s.p;
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) V[3 + k][i] = side == 0 ? h.V[k][i] : V[3 + k][i] + h.V[k][i];
+    if (side == 0) pl = h.p; else pr = h.p;
   }
   V[3][1] -= g.p_r;  // the half-space sum minus the reference Euler flux
-  tau += g.tau_num_C * tabs((pl - pr) / (pl + pr)) * dt;
+  const T tau = collision_time_full(e.mu, e.p, pl, pr, g, dt);
   T Fq[6], dFq[6];
   fit_coefficients(tau, dt, Fq, dFq);
 #pragma unroll
@@ -470,7 +500,7 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
   }
   // Prandtl fix: (1/Pr - 1) times the heat flux -tau rho0 <h (a.u + A)> =
   // -tau p0 c_p dT/dn of the equilibrium part (tau includes the numerical term).
-  F[4] -= g.pr_fix * tau * p0 * (T(0.5) * (g.K + T(5))) * dT0;
+  F[4] -= g.pr_fix * tau * e.p * (T(0.5) * (g.K + T(5))) * e.dT;
 }
 
 // Equilibrium state of the compatibility condition, Q0 = int_{u>0} psi g_l +

@@ -15,7 +15,7 @@ from paper_2005_08736_gb300 import inputs  # noqa: E402
 from paper_2005_08736_gb300.solver import Simulation, taylor_green_config  # noqa: E402
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("chunk", [0, 8, 12, 64])
 def test_every_launch_shape_gives_the_same_step(variant, chunk):
     n = (40, 20, 17)
@@ -43,7 +43,7 @@ def test_autotune_keeps_the_state_and_caches_its_choice(tmp_path):
     sim.init_primitive(inputs.taylor_green(32))
     before = sim.state()
     rec = sim.autotune(cache=str(tmp_path / "tune.json"))
-    assert not rec["cached"] and rec["variant"] in (0, 1, 2, 3, 4) and rec["sweep_ms"] > 0
+    assert not rec["cached"] and rec["variant"] in (0, 1, 2) and rec["sweep_ms"] > 0
     assert np.array_equal(sim.state(), before)
     table = json.load(open(tmp_path / "tune.json"))
     assert len(table) == 1
