@@ -14,11 +14,14 @@
 //   R1  per transverse point: the compatibility state, the normal slopes and
 //       the WENO5 pairs transposed, scattered into the cells f-3 .. f+2 with
 //       atomics.
-// The Jacobians of the point-wise nonlinear maps (flux, compatibility state,
-// WENO5 end values and tangential polynomials) are formed by forward-mode dual
-// numbers through the same device functions as the forward sweep, one input
-// direction at a time.  Ghost cells collect cotangents like interior cells;
-// k_fold_ghosts returns them to their periodic images afterwards.
+// The WENO5 end values and the tangential polynomials are transposed in
+// reverse mode (closed-form derivatives of the nonlinear weights); the flux's
+// slope inputs through the transposes of the linear maps that consume them;
+// the flux's values and the compatibility state by forward-mode dual numbers
+// through the same device functions as the forward sweep, one input direction
+// at a time (for the full flux, through the one part each value enters).
+// Ghost cells collect cotangents like interior cells; k_fold_ghosts returns
+// them to their periodic images afterwards.
 #pragma once
 
 #include "dual.cuh"
