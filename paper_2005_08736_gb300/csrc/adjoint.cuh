@@ -152,24 +152,30 @@ __device__ __forceinline__ void tangential_vjp(const T f[5], const T gv[2], cons
   weno5_pair_vjp<MODE>(f, -gb + T(3) * gc, gb + T(3) * gc, cot);
 }
 
-// (cl, cr) += J^T g0 for the compatibility state Q0(Q_l, Q_r).
+// (cl, cr) += J^T g0 for the compatibility state Q0(Q_l, Q_r) =
+// (Q_l + Q_r)/2 + (S(Q_l) - S(Q_r))/2 (compat_dev): the identity part
+// directly, S of each state by one dual-number pass per component.
 template <class T>
 __device__ __forceinline__ void compat_vjp(const T ql[5], const T qr[5], const T g0[5],
                                            const Gas<T>& gas, T cl[5], T cr[5]) {
   const Gas<Dual<T>> gd = dual_gas(gas);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    cl[i] += T(0.5) * g0[i];
+    cr[i] += T(0.5) * g0[i];
+  }
 #pragma unroll 1
   for (int j = 0; j < 10; ++j) {
-    Dual<T> xl[5], xr[5], out[5];
+    const T* q = j < 5 ? ql : qr;
+    const int c = j < 5 ? j : j - 5;
+    Dual<T> x[5], S[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      xl[k] = Dual<T>(ql[k], T(j == k ? 1 : 0));
-      xr[k] = Dual<T>(qr[k], T(j == 5 + k ? 1 : 0));
-    }
-    compat_dev(xl, xr, gd, out);
+    for (int k = 0; k < 5; ++k) x[k] = Dual<T>(q[k], T(k == c ? 1 : 0));
+    sign_moments(x, gd, S);
     T s = T(0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) s += g0[i] * out[i].d;
-    if (j < 5) cl[j] += s; else cr[j - 5] += s;
+    for (int i = 0; i < 5; ++i) s += g0[i] * S[i].d;
+    if (j < 5) cl[c] += T(0.5) * s; else cr[c] -= T(0.5) * s;
   }
 }
 

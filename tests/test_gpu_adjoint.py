@@ -183,3 +183,17 @@ def test_adjoint_rejects_walls():
     with pytest.raises(HgksError) as e:
         sim.adjoint_step(0.01, z, torch.empty_like(z))
     assert e.value.status == HGKS_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("kw", [dict(recon=2, recon_vars=1), dict(force_mode=1, mass_flux=0.0),
+                                dict(force_x=1e-3)])
+def test_adjoint_rejects_what_it_does_not_transpose(kw):
+    """Characteristic variables and the body forces have no adjoint here."""
+    from paper_2005_08736_gb300._lib import HGKS_E_UNSUPPORTED, HgksError
+    cfg = Config(8, 8, 8, prec=0, flux=1, p_ref=1.0, **kw)
+    sim = Simulation(cfg)
+    z = torch.zeros(cfg.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(HgksError) as e:
+        sim.adjoint_step(0.01, z, torch.empty_like(z))
+    sim.close()
+    assert e.value.status == HGKS_E_UNSUPPORTED

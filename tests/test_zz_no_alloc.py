@@ -61,3 +61,14 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     c = cfg.c_struct()
     status = lib.hgks_step_noalloc(ctypes.byref(c), ctypes.c_void_p(dev.data_ptr()), 1, 0.0, None)
     assert status == _lib.HGKS_E_UNSUPPORTED
+
+
+def test_noalloc_rejects_the_mass_flux_force():
+    # the force's FP64 partial sums need a buffer the static scratch does not hold
+    lib = _lib.load()
+    cfg = taylor_green_config(16, "fp64")
+    cfg.force_mode, cfg.mass_flux = 1, 0.0
+    dev = torch.zeros(cfg.shape, dtype=torch.float64, device="cuda")
+    c = cfg.c_struct()
+    status = lib.hgks_step_noalloc(ctypes.byref(c), ctypes.c_void_p(dev.data_ptr()), 1, 0.0, None)
+    assert status == _lib.HGKS_E_UNSUPPORTED
