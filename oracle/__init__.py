@@ -21,27 +21,36 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hgks_oracle.cpp")
+_DEPS = [_SRC, os.path.join(_HERE, "tangent.h")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libhgks_oracle.so")
+_TAN_PATH = os.path.join(_OUT_DIR, "libhgks_oracle_tangent.so")
 _lock = threading.Lock()
 _lib = None
+_tan = None
 
 RECON_LINEAR, RECON_WENO_JS, RECON_WENO_Z = 0, 1, 2
 FLUX_SMOOTH, FLUX_FULL = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (-O2, OpenMP, no FP contraction)."""
-    os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def _compile(path: str, extra, force: bool) -> str:
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= max(os.path.getmtime(f) for f in _DEPS)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
-           "-shared", "-o", tmp, _SRC]
+           "-shared", "-Wl,-Bsymbolic", *extra, "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (-O2, OpenMP, no FP contraction): the plain
+    FP64 build and the dual-number tangent build of the same source."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    _compile(_TAN_PATH, ["-DORACLE_TANGENT"], force)
+    return _compile(_LIB_PATH, [], force)
 
 
 class OracleConfig(ctypes.Structure):
@@ -107,6 +116,27 @@ def lib():
             L.oracle_tangential_vec.argtypes = [pd, i, i, pd, d, pd, pd]
             _lib = L
     return _lib
+
+
+def tangent_lib():
+    """The tangent build: the same solver API plus oracle_set/get_tangent."""
+    global _tan
+    with _lock:
+        if _tan is None:
+            build()
+            L = ctypes.CDLL(_TAN_PATH)
+            d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            pd = ctypes.POINTER(ctypes.c_double)
+            L.oracle_create.restype = vp
+            L.oracle_create.argtypes = [ctypes.POINTER(OracleConfig)]
+            L.oracle_destroy.argtypes = [vp]
+            for name in ("oracle_set_state", "oracle_get_state", "oracle_set_tangent",
+                         "oracle_get_tangent"):
+                getattr(L, name).argtypes = [vp, pd]
+            L.oracle_step.restype = d
+            L.oracle_step.argtypes = [vp, i, d]
+            _tan = L
+    return _tan
 
 
 def _p(a: np.ndarray):
@@ -210,6 +240,46 @@ class Solver:
         out = np.empty((5, c.nz + 6, c.ny + 6, c.nx + 6))
         lib().oracle_padded(self._h, _p(out))
         return out
+
+
+class TangentSolver:
+    """Dual-number tangent run of the oracle: the same step computed with
+    forward-mode dual numbers, so that along with Q^n it carries
+    dQ^n = (dQ^n/dQ^0) dQ^0 for one direction dQ^0.  dt is held fixed (a
+    positive dt is required: the CFL step would make dt depend on the state)."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        self._c = cfg.c_struct()
+        self._h = tangent_lib().oracle_create(ctypes.byref(self._c))
+        self.shape = (5, cfg.nz, cfg.ny, cfg.nx)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            tangent_lib().oracle_destroy(h)
+            self._h = None
+
+    def set_state(self, cons, dcons) -> None:
+        a, da = _f64(cons), _f64(dcons)
+        assert a.shape == self.shape and da.shape == self.shape
+        tangent_lib().oracle_set_state(self._h, _p(a))
+        tangent_lib().oracle_set_tangent(self._h, _p(da))
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.shape)
+        tangent_lib().oracle_get_state(self._h, _p(out))
+        return out
+
+    def tangent(self) -> np.ndarray:
+        out = np.empty(self.shape)
+        tangent_lib().oracle_get_tangent(self._h, _p(out))
+        return out
+
+    def step(self, nsteps: int, dt: float) -> float:
+        if not dt > 0.0:
+            raise ValueError("the tangent run needs a fixed dt > 0")
+        return tangent_lib().oracle_step(self._h, int(nsteps), float(dt))
 
 
 # ---- single pieces -------------------------------------------------------------

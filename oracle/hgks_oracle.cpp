@@ -36,6 +36,27 @@
 #include <cstring>
 #include <vector>
 
+// Scalar type of every quantity that depends on the state.  The plain build
+// computes in double.  The tangent build (-DORACLE_TANGENT) computes in the
+// forward-mode dual numbers of tangent.h: the same code then also carries the
+// derivative along one input direction (a dual-number tangent run), while its
+// value part repeats the double arithmetic of the plain build exactly.
+// Configuration constants, cell widths, the Gauss abscissae and dt stay double
+// (dt is held fixed when differentiating, as in the adjoint).
+#ifdef ORACLE_TANGENT
+#include "tangent.h"
+using real = oracle_dual::Dual;
+using oracle_dual::value;
+#else
+using real = double;
+inline double value(double x) { return x; }
+#endif
+using std::erfc;
+using std::exp;
+using std::fabs;
+using std::pow;
+using std::sqrt;
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -45,13 +66,13 @@ constexpr int G = 3;  // ghost layers on every side
 // Polynomials in the particle velocity (u, v, w) and xi^2.
 // ---------------------------------------------------------------------------
 struct Mono {
-  double c;
+  real c;
   int a, b, w, d;  // c * u^a v^b w^w (xi^2)^d
 };
 struct Poly {
   int n = 0;
   Mono m[24];
-  void add(double c, int a, int b, int w, int d) { m[n++] = Mono{c, a, b, w, d}; }
+  void add(real c, int a, int b, int w, int d) { m[n++] = Mono{c, a, b, w, d}; }
 };
 
 // psi = (1, u, v, w, (u^2 + v^2 + w^2 + xi^2)/2), Sec. 2.1 after Eq. (2).
@@ -79,7 +100,7 @@ Poly vel(int d) {
 }
 
 // a . psi = a1 + a2 u + a3 v + a4 w + a5 (u^2+v^2+w^2+xi^2)/2.
-Poly lin(const double a[5]) {
+Poly lin(const real a[5]) {
   Poly p;
   p.add(a[0], 0, 0, 0, 0);
   p.add(a[1], 1, 0, 0, 0);
@@ -94,7 +115,7 @@ Poly lin(const double a[5]) {
 
 // Peculiar heat-flux density h = c_u (c_u^2 + c_v^2 + c_w^2 + xi^2) / 2 with
 // c = (u - U, v - V, w - W), expanded into monomials.
-Poly heat(double U, double V, double W) {
+Poly heat(real U, real V, real W) {
   Poly p;
   // (u-U)^3 / 2
   p.add(0.5, 3, 0, 0, 0);
@@ -102,9 +123,9 @@ Poly heat(double U, double V, double W) {
   p.add(1.5 * U * U, 1, 0, 0, 0);
   p.add(-0.5 * U * U * U, 0, 0, 0, 0);
   // (u-U)(v-V)^2 / 2 and (u-U)(w-W)^2 / 2
-  const double T[2] = {V, W};
+  const real T[2] = {V, W};
   for (int s = 0; s < 2; ++s) {
-    const double C = T[s];
+    const real C = T[s];
     const int b2 = s == 0 ? 2 : 0, w2 = s == 0 ? 0 : 2;
     const int b1 = s == 0 ? 1 : 0, w1 = s == 0 ? 0 : 1;
     p.add(0.5, 1, b2, w2, 0);
@@ -127,23 +148,23 @@ Poly heat(double U, double V, double W) {
 constexpr int kMaxDeg = 10;
 
 struct Maxwellian {
-  double rho, U, V, W, lam;
-  double uf[kMaxDeg], up[kMaxDeg], un[kMaxDeg];  // <u^n>: full, u>0, u<0
-  double v[kMaxDeg], w[kMaxDeg];                  // <v^n>, <w^n>
-  double xi[4];                                   // <(xi^2)^m>
+  real rho, U, V, W, lam;
+  real uf[kMaxDeg], up[kMaxDeg], un[kMaxDeg];  // <u^n>: full, u>0, u<0
+  real v[kMaxDeg], w[kMaxDeg];                  // <v^n>, <w^n>
+  real xi[4];                                   // <(xi^2)^m>
 };
 
 // One-dimensional Gaussian moments by the recursion
 //   <u^(n+2)> = U <u^(n+1)> + (n+1)/(2 lambda) <u^n>,
 // which holds over the whole line and over each half line (integration by
 // parts; the boundary term at u = 0 vanishes for n >= 0).
-void recur(double* m, double U, double lam) {
+void recur(real* m, real U, real lam) {
   for (int n = 0; n + 2 < kMaxDeg; ++n)
     m[n + 2] = U * m[n + 1] + (n + 1) / (2.0 * lam) * m[n];
 }
 
 void set_moments(Maxwellian& g, double K) {
-  const double lam = g.lam;
+  const real lam = g.lam;
   g.uf[0] = 1.0;
   g.uf[1] = g.U;
   recur(g.uf, g.U, lam);
@@ -155,12 +176,12 @@ void set_moments(Maxwellian& g, double K) {
   recur(g.w, g.W, lam);
   // Half-space moments: <u^0>_{u>0} = erfc(-sqrt(lambda) U)/2,
   // <u^1>_{u>0} = U <u^0>_{u>0} + exp(-lambda U^2) / (2 sqrt(pi lambda)).
-  const double s = std::sqrt(lam);
-  const double e = std::exp(-lam * g.U * g.U) / (2.0 * std::sqrt(kPi * lam));
-  g.up[0] = 0.5 * std::erfc(-s * g.U);
+  const real s = sqrt(lam);
+  const real e = exp(-lam * g.U * g.U) / (2.0 * sqrt(kPi * lam));
+  g.up[0] = 0.5 * erfc(-s * g.U);
   g.up[1] = g.U * g.up[0] + e;
   recur(g.up, g.U, lam);
-  g.un[0] = 0.5 * std::erfc(s * g.U);
+  g.un[0] = 0.5 * erfc(s * g.U);
   g.un[1] = g.U * g.un[0] - e;
   recur(g.un, g.U, lam);
   // Internal degrees of freedom: xi^2 = sum of K squares, each of variance
@@ -170,26 +191,26 @@ void set_moments(Maxwellian& g, double K) {
 }
 
 // Primitive state and moments from a conservative state in the local frame.
-Maxwellian maxwellian(const double Q[5], double gamma) {
+Maxwellian maxwellian(const real Q[5], double gamma) {
   Maxwellian g;
   const double K = (5.0 - 3.0 * gamma) / (gamma - 1.0);  // Sec. 2.1: N = (5-3 gamma)/(gamma-1)
   g.rho = Q[0];
   g.U = Q[1] / Q[0];
   g.V = Q[2] / Q[0];
   g.W = Q[3] / Q[0];
-  const double p = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (g.U * g.U + g.V * g.V + g.W * g.W));
+  const real p = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (g.U * g.U + g.V * g.V + g.W * g.W));
   g.lam = Q[0] / (2.0 * p);
   set_moments(g, K);
   return g;
 }
 
 // <product of the given polynomials>, half = 0 whole space, +1 u > 0, -1 u < 0.
-double mom(const Maxwellian& g, int half, const Poly* const* f, int nf) {
-  const double* um = half == 0 ? g.uf : (half > 0 ? g.up : g.un);
-  double sum = 0.0;
+real mom(const Maxwellian& g, int half, const Poly* const* f, int nf) {
+  const real* um = half == 0 ? g.uf : (half > 0 ? g.up : g.un);
+  real sum = 0.0;
   int idx[4] = {0, 0, 0, 0};
   while (true) {
-    double c = 1.0;
+    real c = 1.0;
     int a = 0, b = 0, w = 0, d = 0;
     for (int k = 0; k < nf; ++k) {
       const Mono& m = f[k]->m[idx[k]];
@@ -206,42 +227,43 @@ double mom(const Maxwellian& g, int half, const Poly* const* f, int nf) {
   }
   return sum;
 }
-double mom(const Maxwellian& g, int half, const Poly& A) {
+real mom(const Maxwellian& g, int half, const Poly& A) {
   const Poly* f[1] = {&A};
   return mom(g, half, f, 1);
 }
-double mom(const Maxwellian& g, int half, const Poly& A, const Poly& B) {
+real mom(const Maxwellian& g, int half, const Poly& A, const Poly& B) {
   const Poly* f[2] = {&A, &B};
   return mom(g, half, f, 2);
 }
-double mom(const Maxwellian& g, int half, const Poly& A, const Poly& B, const Poly& C) {
+real mom(const Maxwellian& g, int half, const Poly& A, const Poly& B, const Poly& C) {
   const Poly* f[3] = {&A, &B, &C};
   return mom(g, half, f, 3);
 }
-double mom(const Maxwellian& g, int half, const Poly& A, const Poly& B, const Poly& C,
+real mom(const Maxwellian& g, int half, const Poly& A, const Poly& B, const Poly& C,
            const Poly& D) {
   const Poly* f[4] = {&A, &B, &C, &D};
   return mom(g, half, f, 4);
 }
 
 // Dense Gaussian elimination with partial pivoting, n <= 8.
-void gauss_solve(int n, double* A, double* b) {
+template <class S>
+void gauss_solve(int n, S* A, S* b) {
   for (int c = 0; c < n; ++c) {
     int piv = c;
     for (int r = c + 1; r < n; ++r)
-      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
     if (piv != c) {
       for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
       std::swap(b[c], b[piv]);
     }
     for (int r = c + 1; r < n; ++r) {
-      const double f = A[r * n + c] / A[c * n + c];
+      const S f = A[r * n + c] / A[c * n + c];
       for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
       b[r] -= f * b[c];
     }
   }
   for (int r = n - 1; r >= 0; --r) {
-    double s = b[r];
+    S s = b[r];
     for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
     b[r] = s / A[r * n + r];
   }
@@ -249,8 +271,8 @@ void gauss_solve(int n, double* A, double* b) {
 
 // Slope coefficients: the a in <a . psi> = dQ / rho, i.e. the solution of
 // M a = b with M_ij = <psi_i psi_j>  (Sec. 2.1, conditions below Eq. (5)).
-void slope_solve(const Maxwellian& g, const double b[5], double a[5]) {
-  double M[25], r[5];
+void slope_solve(const Maxwellian& g, const real b[5], real a[5]) {
+  real M[25], r[5];
   for (int i = 0; i < 5; ++i) {
     const Poly pi = psi(i);
     for (int j = 0; j < 5; ++j) M[i * 5 + j] = mom(g, 0, pi, psi(j));
@@ -263,24 +285,24 @@ void slope_solve(const Maxwellian& g, const double b[5], double a[5]) {
 // Derived kinetic data of one reconstructed state at a Gauss point.
 struct Kin {
   Maxwellian g;
-  double a[3][5];  // spatial slopes along n, t1, t2 (local frame)
-  double A[5];     // time coefficient
+  real a[3][5];  // spatial slopes along n, t1, t2 (local frame)
+  real A[5];     // time coefficient
 };
 
 // Slopes from <a_d> = dQ/dx_d and A from <a_1 u + a_2 v + a_3 w + A> = 0,
 // all moments of the state's own Maxwellian (Sec. 2.1, below Eq. (5)).
-Kin kinetic(const double Q[5], const double dQ[3][5], double gamma) {
+Kin kinetic(const real Q[5], const real dQ[3][5], double gamma) {
   Kin k;
   k.g = maxwellian(Q, gamma);
   for (int d = 0; d < 3; ++d) {
-    double b[5];
+    real b[5];
     for (int i = 0; i < 5; ++i) b[i] = dQ[d][i] / Q[0];
     slope_solve(k.g, b, k.a[d]);
   }
-  double rhs[5];
+  real rhs[5];
   for (int i = 0; i < 5; ++i) {
     const Poly pi = psi(i);
-    double s = 0.0;
+    real s = 0.0;
     for (int d = 0; d < 3; ++d) s += mom(k.g, 0, lin(k.a[d]), vel(d), pi);
     rhs[i] = -s;
   }
@@ -289,19 +311,19 @@ Kin kinetic(const double Q[5], const double dQ[3][5], double gamma) {
 }
 
 // <u psi_i>, <u (a_n.psi u + a_t1.psi v + a_t2.psi w) psi_i>, <u (A.psi) psi_i>.
-double m_u(const Maxwellian& g, int half, int i) { return mom(g, half, vel(0), psi(i)); }
-double m_ua(const Maxwellian& g, int half, const double a[3][5], int i) {
-  double s = 0.0;
+real m_u(const Maxwellian& g, int half, int i) { return mom(g, half, vel(0), psi(i)); }
+real m_ua(const Maxwellian& g, int half, const real a[3][5], int i) {
+  real s = 0.0;
   for (int d = 0; d < 3; ++d) s += mom(g, half, vel(0), lin(a[d]), vel(d), psi(i));
   return s;
 }
-double m_uA(const Maxwellian& g, int half, const double A[5], int i) {
+real m_uA(const Maxwellian& g, int half, const real A[5], int i) {
   return mom(g, half, vel(0), lin(A), psi(i));
 }
 
 // Time integrals over [0, T] of the five coefficients of Eq. (5), e = exp(-T/tau).
-void time_integrals(double T, double tau, double q[6]) {
-  const double e = std::exp(-T / tau);
+void time_integrals(double T, real tau, real q[6]) {
+  const real e = exp(-T / tau);
   q[0] = T - tau * (1.0 - e);                                   // (1 - e^{-t/tau})
   q[1] = 2.0 * tau * tau * (1.0 - e) - tau * T * (1.0 + e);    // (t+tau) e^{-t/tau} - tau
   q[2] = 0.5 * T * T - tau * T + tau * tau * (1.0 - e);        // t - tau + tau e^{-t/tau}
@@ -322,25 +344,25 @@ enum { FLUX_SMOOTH = 0, FLUX_FULL = 1 };
 // (1/10, 6/10, 3/10), and the Jiang-Shu smoothness indicators.
 // Reading: WENO-JS uses eps = 1e-6 and power 2; WENO-Z uses
 // tau5 = |beta0 - beta2|, alpha_k = d_k (1 + tau5 / (beta_k + eps)), eps = 1e-20.
-double weno5_right(const double q[5], int mode) {
-  const double p0 = (2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2]) / 6.0;
-  const double p1 = (-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.0;
-  const double p2 = (2.0 * q[2] + 5.0 * q[3] - q[4]) / 6.0;
-  const double d[3] = {0.1, 0.6, 0.3};
-  double w[3] = {d[0], d[1], d[2]};
+real weno5_right(const real q[5], int mode) {
+  const real p0 = (2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2]) / 6.0;
+  const real p1 = (-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.0;
+  const real p2 = (2.0 * q[2] + 5.0 * q[3] - q[4]) / 6.0;
+  const real d[3] = {0.1, 0.6, 0.3};
+  real w[3] = {d[0], d[1], d[2]};
   if (mode != RECON_LINEAR) {
-    const double s0 = q[0] - 2.0 * q[1] + q[2], t0 = q[0] - 4.0 * q[1] + 3.0 * q[2];
-    const double s1 = q[1] - 2.0 * q[2] + q[3], t1 = q[1] - q[3];
-    const double s2 = q[2] - 2.0 * q[3] + q[4], t2 = 3.0 * q[2] - 4.0 * q[3] + q[4];
-    const double beta[3] = {13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0,
+    const real s0 = q[0] - 2.0 * q[1] + q[2], t0 = q[0] - 4.0 * q[1] + 3.0 * q[2];
+    const real s1 = q[1] - 2.0 * q[2] + q[3], t1 = q[1] - q[3];
+    const real s2 = q[2] - 2.0 * q[3] + q[4], t2 = 3.0 * q[2] - 4.0 * q[3] + q[4];
+    const real beta[3] = {13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0,
                             13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1,
                             13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2};
-    double alpha[3], sum = 0.0;
+    real alpha[3], sum = 0.0;
     for (int k = 0; k < 3; ++k) {
       if (mode == RECON_WENO_JS) {
         alpha[k] = d[k] / ((1e-6 + beta[k]) * (1e-6 + beta[k]));
       } else {
-        const double tau5 = std::fabs(beta[0] - beta[2]);
+        const real tau5 = fabs(beta[0] - beta[2]);
         alpha[k] = d[k] * (1.0 + tau5 / (beta[k] + 1e-20));
       }
       sum += alpha[k];
@@ -350,8 +372,8 @@ double weno5_right(const double q[5], int mode) {
   return w[0] * p0 + w[1] * p1 + w[2] * p2;
 }
 // Value at the left end of the centre cell: the mirrored stencil.
-double weno5_left(const double q[5], int mode) {
-  const double r[5] = {q[4], q[3], q[2], q[1], q[0]};
+real weno5_left(const real q[5], int mode) {
+  const real r[5] = {q[4], q[3], q[2], q[1], q[0]};
   return weno5_right(r, mode);
 }
 
@@ -399,7 +421,7 @@ const QuarticWeights& quartic() {
 // LINEAR: the quartic above.  WENO modes (Remark 1, last paragraph): WENO5
 // values at both ends of cell j plus its average define the quadratic
 // p(s) = a + b s + c s^2 with b = QR - QL, c = 3(QL + QR) - 6 f_j, a = f_j - c/12.
-void tangential(const double f[5], int mode, double val[2], double der[2]) {
+void tangential(const real f[5], int mode, real val[2], real der[2]) {
   if (mode == RECON_LINEAR) {
     const QuarticWeights& W = quartic();
     for (int m = 0; m < 2; ++m) {
@@ -411,10 +433,10 @@ void tangential(const double f[5], int mode, double val[2], double der[2]) {
     }
     return;
   }
-  const double QL = weno5_left(f, mode), QR = weno5_right(f, mode);
-  const double b = QR - QL, c = 3.0 * (QL + QR) - 6.0 * f[2], a = f[2] - c / 12.0;
+  const real QL = weno5_left(f, mode), QR = weno5_right(f, mode);
+  const real b = QR - QL, c = 3.0 * (QL + QR) - 6.0 * f[2], a = f[2] - c / 12.0;
   for (int m = 0; m < 2; ++m) {
-    const double s = kGaussS[m];
+    const real s = kGaussS[m];
     val[m] = a + b * s + c * s * s;
     der[m] = b + 2.0 * c * s;
   }
@@ -431,16 +453,16 @@ void tangential(const double f[5], int mode, double val[2], double der[2]) {
 // elimination.
 // ---------------------------------------------------------------------------
 struct CharBasis {
-  double R[5][5];
-  double L[5][5];
+  real R[5][5];
+  real L[5][5];
 };
 
-CharBasis char_basis(const double Qm[5], double gamma) {
-  const double rho = Qm[0], u = Qm[1] / rho, v = Qm[2] / rho, w = Qm[3] / rho;
-  const double q2 = u * u + v * v + w * w;
-  const double p = (gamma - 1.0) * (Qm[4] - 0.5 * rho * q2);
-  const double c = std::sqrt(gamma * p / rho), H = (Qm[4] + p) / rho;
-  const double cols[5][5] = {{1.0, u - c, v, w, H - u * c},
+CharBasis char_basis(const real Qm[5], double gamma) {
+  const real rho = Qm[0], u = Qm[1] / rho, v = Qm[2] / rho, w = Qm[3] / rho;
+  const real q2 = u * u + v * v + w * w;
+  const real p = (gamma - 1.0) * (Qm[4] - 0.5 * rho * q2);
+  const real c = sqrt(gamma * p / rho), H = (Qm[4] + p) / rho;
+  const real cols[5][5] = {{1.0, u - c, v, w, H - u * c},
                              {1.0, u, v, w, 0.5 * q2},
                              {0.0, 0.0, 1.0, 0.0, v},
                              {0.0, 0.0, 0.0, 1.0, w},
@@ -449,7 +471,7 @@ CharBasis char_basis(const double Qm[5], double gamma) {
   for (int i = 0; i < 5; ++i)
     for (int k = 0; k < 5; ++k) B.R[i][k] = cols[k][i];
   for (int k = 0; k < 5; ++k) {  // column k of R^{-1}: R x = e_k
-    double A[25], e[5] = {0, 0, 0, 0, 0};
+    real A[25], e[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < 5; ++i)
       for (int j = 0; j < 5; ++j) A[i * 5 + j] = B.R[i][j];
     e[k] = 1.0;
@@ -459,7 +481,7 @@ CharBasis char_basis(const double Qm[5], double gamma) {
   return B;
 }
 
-void mat5(const double M[5][5], const double x[5], double y[5]) {
+void mat5(const real M[5][5], const real x[5], real y[5]) {
   for (int i = 0; i < 5; ++i) {
     y[i] = 0.0;
     for (int k = 0; k < 5; ++k) y[i] += M[i][k] * x[k];
@@ -470,18 +492,18 @@ void mat5(const double M[5][5], const double x[5], double y[5]) {
 // f[s][0..4] (Remark 1), component-wise or, with B, in the characteristic
 // variables of B: project every average, reconstruct each characteristic
 // component, map the values and derivatives back.
-void tangential_vec(const double f[5][5], int mode, const CharBasis* B, double val[2][5],
-                    double der[2][5]) {
-  double g[5][5];
+void tangential_vec(const real f[5][5], int mode, const CharBasis* B, real val[2][5],
+                    real der[2][5]) {
+  real g[5][5];
   for (int s = 0; s < 5; ++s) {
     if (B) mat5(B->L, f[s], g[s]);
     else
       for (int i = 0; i < 5; ++i) g[s][i] = f[s][i];
   }
-  double cv[2][5], cd[2][5];
+  real cv[2][5], cd[2][5];
   for (int i = 0; i < 5; ++i) {
-    const double col[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
-    double v2[2], d2[2];
+    const real col[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
+    real v2[2], d2[2];
     tangential(col, mode, v2, d2);
     for (int m = 0; m < 2; ++m) {
       cv[m][i] = v2[m];
@@ -505,17 +527,17 @@ void tangential_vec(const double f[5][5], int mode, const CharBasis* B, double v
 // (qc[1..5]): out[0] = Q at x_{i+1/2} from cell i, out[1] = Q at x_{i-1/2}
 // from cell i, out[2] = Q at x_{i+1/2} from cell i+1, out[3] = Q at x_{i+3/2}
 // from cell i+1; component-wise or in the characteristic variables of B.
-void normal_end_values(const double qc[6][5], int mode, const CharBasis* B, double out[4][5]) {
-  double g[6][5];
+void normal_end_values(const real qc[6][5], int mode, const CharBasis* B, real out[4][5]) {
+  real g[6][5];
   for (int s = 0; s < 6; ++s) {
     if (B) mat5(B->L, qc[s], g[s]);
     else
       for (int i = 0; i < 5; ++i) g[s][i] = qc[s][i];
   }
-  double e[4][5];
+  real e[4][5];
   for (int i = 0; i < 5; ++i) {
-    const double sl[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
-    const double sr[5] = {g[1][i], g[2][i], g[3][i], g[4][i], g[5][i]};
+    const real sl[5] = {g[0][i], g[1][i], g[2][i], g[3][i], g[4][i]};
+    const real sr[5] = {g[1][i], g[2][i], g[3][i], g[4][i], g[5][i]};
     e[0][i] = weno5_right(sl, mode);
     e[1][i] = weno5_left(sl, mode);
     e[2][i] = weno5_left(sr, mode);
@@ -558,30 +580,30 @@ typedef struct {
 
 namespace {
 
-double viscosity(const oracle_config& c, double T) {
+real viscosity(const oracle_config& c, real T) {
   if (c.visc_law == 0) return c.mu_ref;
-  return c.mu_ref * std::pow(T / c.T_ref, c.visc_exp);
+  return c.mu_ref * pow(T / c.T_ref, c.visc_exp);
 }
 
 // Reconstructed data at one Gauss point, local frame (normal velocity first):
 // st[s][0] value, st[s][1..3] derivatives along n, t1, t2, for s = l, r, 0.
 struct PointData {
-  double st[3][4][5];
+  real st[3][4][5];
 };
 
 // Numerical flux density at one Gauss point: F (time-averaged flux of the
 // linear fit, Eq. (7)) and dF (its time derivative), local frame.
-void flux_point(const oracle_config& c, const PointData& pd, double dt, double F[5],
-                double dF[5]) {
-  double dQ[3][5];
+void flux_point(const oracle_config& c, const PointData& pd, double dt, real F[5],
+                real dF[5]) {
+  real dQ[3][5];
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i < 5; ++i) dQ[d][i] = pd.st[2][d + 1][i];
   const Kin k0 = kinetic(pd.st[2][0], dQ, c.gamma);
   const Maxwellian& g0 = k0.g;
   // Collision time (Sec. 3): tau = mu/p with p the interface (g0) pressure;
   // the full flux adds C |p_l - p_r| / (p_l + p_r) dt.
-  const double p0 = g0.rho / (2.0 * g0.lam);
-  double tau = viscosity(c, 1.0 / (2.0 * g0.lam)) / p0;
+  const real p0 = g0.rho / (2.0 * g0.lam);
+  real tau = viscosity(c, 1.0 / (2.0 * g0.lam)) / p0;
 
   if (c.flux == FLUX_SMOOTH) {
     // Simplified smooth flux (Remark 1): f = g0 [1 - tau (abar.u + Abar) + t Abar].
@@ -590,7 +612,7 @@ void flux_point(const oracle_config& c, const PointData& pd, double dt, double F
       dF[i] = g0.rho * m_uA(g0, 0, k0.A, i);
     }
   } else {
-    double dQl[3][5], dQr[3][5];
+    real dQl[3][5], dQr[3][5];
     for (int d = 0; d < 3; ++d)
       for (int i = 0; i < 5; ++i) {
         dQl[d][i] = pd.st[0][d + 1][i];
@@ -598,13 +620,13 @@ void flux_point(const oracle_config& c, const PointData& pd, double dt, double F
       }
     const Kin kl = kinetic(pd.st[0][0], dQl, c.gamma);
     const Kin kr = kinetic(pd.st[1][0], dQr, c.gamma);
-    const double pl = kl.g.rho / (2.0 * kl.g.lam), pr = kr.g.rho / (2.0 * kr.g.lam);
-    tau += c.tau_num_C * std::fabs((pl - pr) / (pl + pr)) * dt;
+    const real pl = kl.g.rho / (2.0 * kl.g.lam), pr = kr.g.rho / (2.0 * kr.g.lam);
+    tau += c.tau_num_C * fabs((pl - pr) / (pl + pr)) * dt;
     // Time-integrated flux W(T) of Eq. (5).  Reading: the Heaviside factor
     // H(u) (u > 0) belongs to g_l and 1 - H(u) to g_r, as in the compatibility
     // condition for Q0 printed below Eq. (5).
     // Moment vectors of the three parts of f, then W(T) for T = dt, dt/2.
-    double m0[3][5], ml[3][5], mr[3][5];
+    real m0[3][5], ml[3][5], mr[3][5];
     for (int i = 0; i < 5; ++i) {
       m0[0][i] = g0.rho * m_u(g0, 0, i);
       m0[1][i] = g0.rho * m_ua(g0, 0, k0.a, i);
@@ -616,10 +638,10 @@ void flux_point(const oracle_config& c, const PointData& pd, double dt, double F
       mr[1][i] = kr.g.rho * m_ua(kr.g, -1, kr.a, i);
       mr[2][i] = kr.g.rho * m_uA(kr.g, -1, kr.A, i);
     }
-    double W[2][5];
+    real W[2][5];
     const double Ts[2] = {dt, 0.5 * dt};
     for (int t = 0; t < 2; ++t) {
-      double q[6];
+      real q[6];
       time_integrals(Ts[t], tau, q);
       for (int i = 0; i < 5; ++i)
         W[t][i] = q[0] * m0[0][i] + q[1] * m0[1][i] + q[2] * m0[2][i] +
@@ -638,7 +660,7 @@ void flux_point(const oracle_config& c, const PointData& pd, double dt, double F
   // frame of g0.  dF is left unchanged.
   if (c.prandtl != 1.0) {
     const Poly h = heat(g0.U, g0.V, g0.W);
-    double q = 0.0;
+    real q = 0.0;
     for (int d = 0; d < 3; ++d) q += mom(g0, 0, h, lin(k0.a[d]), vel(d));
     q += mom(g0, 0, h, lin(k0.A));
     q *= -tau * g0.rho;
@@ -649,10 +671,10 @@ void flux_point(const oracle_config& c, const PointData& pd, double dt, double F
 // Two-stage fourth-order update, Eq. (6):
 //   Q*      = Q^n + dt/2 L(Q^n) + dt^2/8 dL(Q^n)
 //   Q^{n+1} = Q^n + dt L(Q^n) + dt^2/6 (dL(Q^n) + 2 dL(Q*)).
-double s2o4_stage1(double Qn, double L0, double dL0, double dt) {
+real s2o4_stage1(real Qn, real L0, real dL0, double dt) {
   return Qn + 0.5 * dt * L0 + 0.125 * dt * dt * dL0;
 }
-double s2o4_stage2(double Qn, double L0, double dL0, double dL1, double dt) {
+real s2o4_stage2(real Qn, real L0, real dL0, real dL1, double dt) {
   return Qn + dt * L0 + dt * dt / 6.0 * (dL0 + 2.0 * dL1);
 }
 
@@ -664,10 +686,10 @@ struct Solver {
   int n[3];
   int pn[3];                       // padded sizes
   std::vector<double> width[3];    // cell widths, index -G .. n+G-1 (offset G)
-  std::vector<double> q;           // padded conservative state [5][pz][py][px]
+  std::vector<real> q;           // padded conservative state [5][pz][py][px]
   double t = 0.0;
   long step = 0;
-  double last_force = 0.0;         // f_x of the last step
+  real last_force = 0.0;         // f_x of the last step
 
   explicit Solver(const oracle_config& cfg) : c(cfg) {
     n[0] = c.nx;
@@ -701,14 +723,14 @@ struct Solver {
   size_t at(int i, int j, int k) const {
     return (size_t(k + G) * pn[1] + (j + G)) * pn[0] + (i + G);
   }
-  double& Q(std::vector<double>& a, int v, int i, int j, int k) {
+  real& Q(std::vector<real>& a, int v, int i, int j, int k) {
     return a[v * cells_padded() + at(i, j, k)];
   }
   double w(int d, int idx) const { return width[d][idx + G]; }
 
   // Ghost-cell fill, axes in the order x, y, z so that edges and corners take
   // their values from layers that are already filled.
-  void fill_ghosts(std::vector<double>& a) {
+  void fill_ghosts(std::vector<real>& a) {
     // x: periodic
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
@@ -745,15 +767,15 @@ struct Solver {
   // cells): the ghost cell mirrors interior cell jm with velocity negated,
   // equal pressure and temperature T_g = 2 T_wall - T_m (floored at T_wall/2),
   // so that the face average of u and of T equals the wall values.
-  void wall_ghost(std::vector<double>& a, int i, int jm, int jg, int k) {
+  void wall_ghost(std::vector<real>& a, int i, int jm, int jg, int k) {
     const double g1 = c.gamma - 1.0;
-    const double rho = Q(a, 0, i, jm, k);
-    const double u = Q(a, 1, i, jm, k) / rho, v = Q(a, 2, i, jm, k) / rho,
+    const real rho = Q(a, 0, i, jm, k);
+    const real u = Q(a, 1, i, jm, k) / rho, v = Q(a, 2, i, jm, k) / rho,
                  ww = Q(a, 3, i, jm, k) / rho;
-    const double p = g1 * (Q(a, 4, i, jm, k) - 0.5 * rho * (u * u + v * v + ww * ww));
-    double Tg = 2.0 * c.T_wall - p / rho;
+    const real p = g1 * (Q(a, 4, i, jm, k) - 0.5 * rho * (u * u + v * v + ww * ww));
+    real Tg = 2.0 * c.T_wall - p / rho;
     if (Tg < 0.5 * c.T_wall) Tg = 0.5 * c.T_wall;
-    const double rg = p / Tg;
+    const real rg = p / Tg;
     Q(a, 0, i, jg, k) = rg;
     Q(a, 1, i, jg, k) = -rg * u;
     Q(a, 2, i, jg, k) = -rg * v;
@@ -772,7 +794,7 @@ struct Solver {
   }
   // Conservative state of a cell in the local frame of direction d:
   // (rho, rho u_n, rho u_t1, rho u_t2, rho E).
-  void local(const std::vector<double>& a, int d, size_t ci, double out[5]) const {
+  void local(const std::vector<real>& a, int d, size_t ci, real out[5]) const {
     const size_t S = cells_padded();
     out[0] = a[ci];
     out[1] = a[(1 + d) * S + ci];
@@ -783,7 +805,7 @@ struct Solver {
 
   // Fluxes through all faces normal to d: Fd[((f * nt1) + a) * nt2 + b][10],
   // f = 0..n_d (face f lies between cells f-1 and f), F then dF, global frame.
-  void direction_fluxes(const std::vector<double>& a, int d, double dt, std::vector<double>& Fd) {
+  void direction_fluxes(const std::vector<real>& a, int d, double dt, std::vector<real>& Fd) {
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const int nd = n[d], na = n[t1], nb = n[t2];
     const int ea = na + 4, eb = nb + 4;  // face fields carry 2 tangential ghost rows
@@ -791,7 +813,7 @@ struct Solver {
     // Face fields, local frame: 0 Q_l, 1 Q_r, 2 dQ_l/dn, 3 dQ_r/dn, 4 Q0,
     // 5 dQ0/dn, 6 Qm = the mean of the two cell averages beside the face.
     constexpr int NF = 35;
-    std::vector<double> FF(size_t(nd + 1) * ea * eb * NF);
+    std::vector<real> FF(size_t(nd + 1) * ea * eb * NF);
     // Reading: with characteristic reconstruction every reconstruction that
     // serves face point P (the normal one at P, the t1 pass centred at P and
     // the t2 pass of P's Gauss points) uses the eigenvectors of the Euler
@@ -802,17 +824,17 @@ struct Solver {
       for (int aa = -2; aa < na + 2; ++aa)
         for (int bb = -2; bb < nb + 2; ++bb) {
           // Cell averages of cells f-3 .. f+2 along the normal.
-          double qc[6][5];
+          real qc[6][5];
           for (int s = 0; s < 6; ++s) local(a, d, cell(d, f - 3 + s, aa, bb), qc[s]);
           const double hl = w(d, f - 1), hr = w(d, f);
-          double* out = &FF[((size_t(f) * ea + (aa + 2)) * eb + (bb + 2)) * NF];
+          real* out = &FF[((size_t(f) * ea + (aa + 2)) * eb + (bb + 2)) * NF];
           for (int v = 0; v < 5; ++v) out[30 + v] = 0.5 * (qc[2][v] + qc[3][v]);
           CharBasis B;
           if (chr) B = char_basis(&out[30], c.gamma);
-          double e[4][5];
+          real e[4][5];
           normal_end_values(qc, mode, chr ? &B : nullptr, e);
           for (int v = 0; v < 5; ++v) {
-            const double QRi = e[0][v], QLi = e[1][v], QLr = e[2][v], QRr = e[3][v];
+            const real QRi = e[0][v], QLi = e[1][v], QLr = e[2][v], QRr = e[3][v];
             out[0 * 5 + v] = QRi;  // Q_l at the face
             out[1 * 5 + v] = QLr;  // Q_r at the face
             // Reading: normal slopes of the quadratic through both end values
@@ -845,12 +867,12 @@ struct Solver {
           const double h1 = w(t1, aa), h2 = w(t2, bb);
           // t1 pass over rows bb-2 .. bb+2: value and t1-derivative of every
           // field at the two t1 Gauss abscissae.
-          double v1[6][5][5][2], d1[6][5][5][2];  // [field][var][row][m]
+          real v1[6][5][5][2], d1[6][5][5][2];  // [field][var][row][m]
           for (int r = 0; r < 5; ++r) {
             CharBasis B;
             if (chr) B = char_basis(ffield(f, aa, bb - 2 + r, 6), c.gamma);
             for (int fld = 0; fld < 6; ++fld) {
-              double col[5][5], val[2][5], der[2][5];
+              real col[5][5], val[2][5], der[2][5];
               for (int s = 0; s < 5; ++s)
                 for (int v = 0; v < 5; ++v) col[s][v] = ffield(f, aa - 2 + s, bb - 2 + r, fld)[v];
               tangential_vec(col, mode, chr ? &B : nullptr, val, der);
@@ -864,13 +886,13 @@ struct Solver {
           CharBasis B2;
           if (chr) B2 = char_basis(ffield(f, aa, bb, 6), c.gamma);
           const CharBasis* pb = chr ? &B2 : nullptr;
-          double Fsum[10] = {0};
+          real Fsum[10] = {0};
           for (int m = 0; m < 2; ++m)
             for (int mm = 0; mm < 2; ++mm) {
               PointData pd;
               const int vf[3] = {0, 1, 4}, sf[3] = {2, 3, 5};
               for (int s = 0; s < 3; ++s) {
-                double col[5][5], val[2][5], der[2][5];
+                real col[5][5], val[2][5], der[2][5];
                 for (int r = 0; r < 5; ++r)
                   for (int v = 0; v < 5; ++v) col[r][v] = v1[vf[s]][v][r][m];
                 tangential_vec(col, mode, pb, val, der);
@@ -887,7 +909,7 @@ struct Solver {
                 tangential_vec(col, mode, pb, val, der);
                 for (int v = 0; v < 5; ++v) pd.st[s][1][v] = val[mm][v];  // d/dn
               }
-              double F[5], dF[5];
+              real F[5], dF[5];
               flux_point(c, pd, dt, F, dF);
               for (int i = 0; i < 5; ++i) {
                 Fsum[i] += 0.25 * F[i];  // Gauss weights omega_mn = 1/4 of the face
@@ -895,10 +917,10 @@ struct Solver {
               }
             }
           // Back to the global frame.
-          double* out = &Fd[((size_t(f) * na + aa) * nb + bb) * 10];
+          real* out = &Fd[((size_t(f) * na + aa) * nb + bb) * 10];
           for (int s = 0; s < 2; ++s) {
-            const double* L = &Fsum[5 * s];
-            double* o = &out[5 * s];
+            const real* L = &Fsum[5 * s];
+            real* o = &out[5 * s];
             o[0] = L[0];
             o[1 + d] = L[1];
             o[1 + t1] = L[2];
@@ -911,9 +933,9 @@ struct Solver {
   // L(Q) and dL(Q)/dt on interior cells (Eq. (4)): -(1/|Omega|) sum of the
   // six face fluxes; with face area / cell volume = 1 / (cell width along d).
   // Per cell the faces are taken in the order x-, x+, y-, y+, z-, z+.
-  void rhs(std::vector<double>& a, double dt, std::vector<double>& L, std::vector<double>& dL) {
+  void rhs(std::vector<real>& a, double dt, std::vector<real>& L, std::vector<real>& dL) {
     fill_ghosts(a);
-    std::vector<double> Fd[3];
+    std::vector<real> Fd[3];
     for (int d = 0; d < 3; ++d) direction_fluxes(a, d, dt, Fd[d]);
     const size_t N = size_t(n[0]) * n[1] * n[2];
     L.assign(5 * N, 0.0);
@@ -924,12 +946,12 @@ struct Solver {
         for (int i = 0; i < n[0]; ++i) {
           const int x[3] = {i, j, k};
           const size_t ci = (size_t(k) * n[1] + j) * n[0] + i;
-          double acc[10] = {0};
+          real acc[10] = {0};
           for (int d = 0; d < 3; ++d) {
             const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
             const int na = n[t1], nb = n[t2];
-            const double* Fm = &Fd[d][((size_t(x[d]) * na + x[t1]) * nb + x[t2]) * 10];
-            const double* Fp = &Fd[d][((size_t(x[d] + 1) * na + x[t1]) * nb + x[t2]) * 10];
+            const real* Fm = &Fd[d][((size_t(x[d]) * na + x[t1]) * nb + x[t2]) * 10];
+            const real* Fp = &Fd[d][((size_t(x[d] + 1) * na + x[t1]) * nb + x[t2]) * 10];
             const double hd = w(d, x[d]);
             for (int s = 0; s < 10; ++s) acc[s] += -Fm[s] / hd + Fp[s] / hd;
           }
@@ -940,20 +962,20 @@ struct Solver {
         }
   }
 
-  double cfl_dt() {
+  real cfl_dt() {
     const double g1 = c.gamma - 1.0;
-    double best = 1e300;
+    real best = 1e300;
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
         for (int i = 0; i < n[0]; ++i) {
-          const double rho = Q(q, 0, i, j, k);
-          const double u[3] = {Q(q, 1, i, j, k) / rho, Q(q, 2, i, j, k) / rho,
+          const real rho = Q(q, 0, i, j, k);
+          const real u[3] = {Q(q, 1, i, j, k) / rho, Q(q, 2, i, j, k) / rho,
                                Q(q, 3, i, j, k) / rho};
-          const double p = g1 * (Q(q, 4, i, j, k) - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-          const double cs = std::sqrt(c.gamma * p / rho);
+          const real p = g1 * (Q(q, 4, i, j, k) - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+          const real cs = sqrt(c.gamma * p / rho);
           const int x[3] = {i, j, k};
           for (int d = 0; d < 3; ++d) {
-            const double v = w(d, x[d]) / (std::fabs(u[d]) + cs);
+            const real v = w(d, x[d]) / (fabs(u[d]) + cs);
             if (v < best) best = v;
           }
         }
@@ -962,10 +984,10 @@ struct Solver {
 
   // One S2O4 step (Eq. (6)), then the streamwise body force of Sec. 3.3.
   double do_step(double dt) {
-    if (dt <= 0.0) dt = cfl_dt();
+    if (dt <= 0.0) dt = value(cfl_dt());
     const size_t N = size_t(n[0]) * n[1] * n[2];
-    std::vector<double> L0, dL0, L1, dL1;
-    std::vector<double> qs = q;  // Q*
+    std::vector<real> L0, dL0, L1, dL1;
+    std::vector<real> qs = q;  // Q*
     rhs(q, dt, L0, dL0);
     for (int v = 0; v < 5; ++v)
       for (int k = 0; k < n[2]; ++k)
@@ -976,7 +998,7 @@ struct Solver {
           }
     rhs(qs, dt, L1, dL1);
     // Second stage without the force: Q~^{n+1}.
-    std::vector<double> qn = q;
+    std::vector<real> qn = q;
     for (int v = 0; v < 5; ++v)
       for (int k = 0; k < n[2]; ++k)
         for (int j = 0; j < n[1]; ++j)
@@ -989,9 +1011,10 @@ struct Solver {
     // force_mode 1: f_x = (int rho U_b - int (rho U)~^{n+1}) /
     // (dt * 1/2 int (rho^n + rho~^{n+1})), which makes int (rho U)^{n+1} equal
     // the target; int rho U_b is read as mass_flux times the box volume.
-    double f = c.force_x;
+    real f = c.force_x;
     if (c.force_mode == 1) {
-      double vol = 0.0, mom = 0.0, half_rho = 0.0;
+      double vol = 0.0;
+      real mom = 0.0, half_rho = 0.0;
       for (int k = 0; k < n[2]; ++k)
         for (int j = 0; j < n[1]; ++j)
           for (int i = 0; i < n[0]; ++i) {
@@ -1041,7 +1064,7 @@ void oracle_get_state(void* h, double* cons) {
     for (int k = 0; k < s.n[2]; ++k)
       for (int j = 0; j < s.n[1]; ++j)
         for (int i = 0; i < s.n[0]; ++i)
-          cons[((size_t(v) * s.n[2] + k) * s.n[1] + j) * s.n[0] + i] = s.Q(s.q, v, i, j, k);
+          cons[((size_t(v) * s.n[2] + k) * s.n[1] + j) * s.n[0] + i] = value(s.Q(s.q, v, i, j, k));
 }
 // Advance nsteps; dt <= 0 takes the CFL step each time.  Returns the last dt.
 double oracle_step(void* h, int nsteps, double dt) {
@@ -1050,6 +1073,34 @@ double oracle_step(void* h, int nsteps, double dt) {
   for (int n = 0; n < nsteps; ++n) used = s.do_step(dt);
   return used;
 }
+double oracle_time(void* h) { return static_cast<Solver*>(h)->t; }
+// Streamwise force f_x applied in the last step.
+double oracle_last_force(void* h) { return value(static_cast<Solver*>(h)->last_force); }
+double oracle_cfl_dt(void* h) { return value(static_cast<Solver*>(h)->cfl_dt()); }
+
+#ifdef ORACLE_TANGENT
+// Tangent build only: the derivative part of the state.  oracle_set_state
+// sets the values with a zero tangent; oracle_set_tangent then sets the
+// direction dQ^0, and after oracle_step (with a fixed dt > 0)
+// oracle_get_tangent returns dQ^n = (dQ^n/dQ^0) dQ^0, [5][nz][ny][nx].
+void oracle_set_tangent(void* h, const double* dcons) {
+  Solver& s = *static_cast<Solver*>(h);
+  for (int v = 0; v < 5; ++v)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i)
+          s.Q(s.q, v, i, j, k).d = dcons[((size_t(v) * s.n[2] + k) * s.n[1] + j) * s.n[0] + i];
+}
+void oracle_get_tangent(void* h, double* dcons) {
+  Solver& s = *static_cast<Solver*>(h);
+  for (int v = 0; v < 5; ++v)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i)
+          dcons[((size_t(v) * s.n[2] + k) * s.n[1] + j) * s.n[0] + i] =
+              oracle_dual::tangent(s.Q(s.q, v, i, j, k));
+}
+#else
 // Characteristic basis at the local-frame state Qm: R and R^{-1}, row-major.
 void oracle_char_basis(const double* Qm, double gamma, double* R, double* L) {
   const CharBasis B = char_basis(Qm, gamma);
@@ -1088,10 +1139,6 @@ void oracle_tangential_vec(const double* f, int mode, int use_char, const double
       der[m * 5 + i] = d[m][i];
     }
 }
-double oracle_time(void* h) { return static_cast<Solver*>(h)->t; }
-// Streamwise force f_x applied in the last step.
-double oracle_last_force(void* h) { return static_cast<Solver*>(h)->last_force; }
-double oracle_cfl_dt(void* h) { return static_cast<Solver*>(h)->cfl_dt(); }
 // L(Q) and dL/dt of the current state (interior cells, [5][nz][ny][nx]).
 void oracle_rhs(void* h, double dt, double* L, double* dL) {
   Solver& s = *static_cast<Solver*>(h);
@@ -1177,5 +1224,7 @@ void oracle_flux_point(const oracle_config* cfg, const double* st, double dt, do
   std::memcpy(pd.st, st, sizeof(pd.st));
   flux_point(*cfg, pd, dt, F, dF);
 }
+
+#endif  // ORACLE_TANGENT
 
 }  // extern "C"
