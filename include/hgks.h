@@ -241,6 +241,16 @@ hgks_status hgks_profile_step(hgks_ctx* ctx, double dt, double* ms_out, int ncla
 hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_inout, int nsteps, double dt,
                               void* stream);
 
+/* Measured arithmetic peaks of the current device (no counterpart in the
+ * paper; the denominators of the kernels' ALU rooflines): tflops_out[0] FP32
+ * FMA throughput, [1] the same with packed FP32 pairs (one instruction, two
+ * FMAs on a float2), [2] FP64 FMA throughput, in TFLOP/s (an FMA counts as
+ * two flops).  Each is the best of two timed launches of independent FMA
+ * chains over 8 CTAs of 256 threads per SM, after one warm-up launch, on
+ * `stream` (a cudaStream_t; NULL the legacy default stream); about 0.1 s in
+ * all.  Allocates and frees a small output buffer; synchronises. */
+hgks_status hgks_measure_fp_peaks(void* stream, double* tflops_out);
+
 /* Message of the last failed call on ctx ("" if none); valid until the next
  * call on ctx.  ctx may be NULL for errors of hgks_create. */
 const char* hgks_last_error(const hgks_ctx* ctx);

@@ -290,3 +290,13 @@ def kinetic_energy(q: torch.Tensor, cfg: Config) -> torch.Tensor:
     rho = q[0]
     ke = 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho
     return ke.mean() / cfg.rho_ref
+
+
+def measure_fp_peaks(stream: torch.cuda.Stream | None = None) -> dict:
+    """Measured FMA throughput of the current GPU in TFLOP/s: FP32, packed
+    FP32 pairs and FP64 (hgks_measure_fp_peaks)."""
+    lib = _lib.load()
+    out = (ctypes.c_double * 3)()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _lib.check(lib.hgks_measure_fp_peaks(ctypes.c_void_p(s.cuda_stream), out))
+    return {"fp32": out[0], "fp32x2": out[1], "fp64": out[2]}

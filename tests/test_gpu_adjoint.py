@@ -142,6 +142,35 @@ def test_wenoz_differences_converge_to_the_adjoint(flux):
     assert best < 2e-5, best
 
 
+@pytest.mark.parametrize("recon,flux,C", [(0, 0, 0.0), (1, 1, 0.0), (2, 1, 1.0), (2, 0, 0.0)])
+def test_adjoint_matches_the_oracle_tangent_run(recon, flux, C):
+    # <lambda^0, v> from the CUDA adjoint against <r, dQ^K> of the oracle's
+    # dual-number tangent run along v: both are exact derivatives (same
+    # conventions, d|x|/dx = sign(x)), so they agree to round-off even where
+    # WENO-Z and the numerical collision time make central differences fail.
+    n, K, dt = (12, 10, 9), 3, 0.05
+    cfg, q0 = setup(n, recon, flux, C=C, kmax=1, oblique=0.05)
+    sim = Simulation(cfg)
+    g = torch.Generator(device="cuda").manual_seed(13)
+    r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+    grad = adjoint_gradient(sim, q0, K, dt, r)
+    sim.close()
+    ocfg = oracle.Config(*n, recon=recon, flux=flux, tau_num_C=C, prandtl=cfg.prandtl,
+                         visc_law=cfg.visc, mu_ref=cfg.mu_ref, T_ref=cfg.T_ref,
+                         visc_exp=cfg.visc_exp)
+    q0h, rh = q0.cpu().numpy(), r.cpu().numpy()
+    for k in range(2):
+        v = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        v *= q0.abs().amax(dim=(1, 2, 3), keepdim=True)
+        t = oracle.TangentSolver(ocfg)
+        t.set_state(q0h, v.cpu().numpy())
+        t.step(K, dt)
+        tan = float((rh * t.tangent()).sum())
+        ad = (grad * v).sum().item()
+        print(f"adjoint {ad:.15e} oracle tangent {tan:.15e} rel {abs(ad - tan) / abs(tan):.2e}")
+        assert abs(ad - tan) <= 1e-11 * abs(tan), (k, ad, tan)
+
+
 def test_autograd_window_with_checkpoints_kinetic_energy():
     n, K, dt = (12, 10, 9), 5, 0.05
     cfg, q0 = setup(n, 1, 1)
