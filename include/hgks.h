@@ -199,7 +199,7 @@ hgks_status hgks_adjoint_step(hgks_ctx* ctx, double dt, const double* adj_in, do
 
 /* Tile autotuner (no counterpart in the paper): time the launch shapes of
  * the sweep kernel on the context's current state -- the tile variants
- * available for its configuration (three for linear weights + smooth flux in
+ * available for its configuration (four for linear weights + smooth flux in
  * FP32, one otherwise) times the number of face layers each CTA marches
  * through -- with CUDA events on the context's stream, and keep the fastest
  * for later steps.  The state is unchanged (ghost layers and face-flux

@@ -75,7 +75,7 @@ template <> struct SweepTile<float, FLUX_FULL> { static constexpr int TP = 16, T
 template <> struct SweepTile<double, FLUX_SMOOTH> { static constexpr int TP = 16, TS = 8, NL = 2; };
 template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NL = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK = false>
 cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
@@ -102,7 +102,7 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   a.chunk = chunk;
   const int gz = (layers + chunk - 1) / chunk;
   constexpr size_t smem = sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL>();
-  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL>;
+  auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL, PK>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<dim3(gx, gy, gz), sweep_threads(TP, TS), smem, e.stream>>>(a);
@@ -110,12 +110,14 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
 }
 
 // Tile variants: 0 is SweepTile; the linear-weight smooth FP32 sweep also has
-// 32x8 and 16x16 tiles with two layers per face-field pass.
+// 32x8 and 16x16 tiles with two layers per face-field pass (1, 2) and the
+// 32x8 tile with the packed FP32-pair last phase (3).
 template <class T, int MODE, int FLUX, int STAGE>
 cudaError_t launch_sweep(const Engine& e, const T* q, int d) {
   if constexpr (std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH) {
     if (e.sweep_variant == 1) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2>(e, q, d);
     if (e.sweep_variant == 2) return launch_sweep_tile<T, MODE, FLUX, STAGE, 16, 16, 2>(e, q, d);
+    if (e.sweep_variant == 3) return launch_sweep_tile<T, MODE, FLUX, STAGE, 32, 8, 2, true>(e, q, d);
 
   }
   return launch_sweep_tile<T, MODE, FLUX, STAGE, SweepTile<T, FLUX>::TP, SweepTile<T, FLUX>::TS,

@@ -670,7 +670,7 @@ namespace hgks {
 
 int sweep_variant_count(const Engine& e) {
   return (e.cfg.prec == HGKS_FP32 && e.cfg.recon == HGKS_RECON_LINEAR &&
-          e.cfg.flux == HGKS_FLUX_SMOOTH) ? 3 : 1;
+          e.cfg.flux == HGKS_FLUX_SMOOTH) ? 4 : 1;
 }
 
 long long face_flux_elems(const Engine& e, int d) {

@@ -1,0 +1,158 @@
+// Packed FP32 pairs for the sweep's last phase: one instruction applies an
+// add, multiply or fused multiply-add to both halves of a float2
+// (__fadd2_rn / __fmul2_rn / __ffma2_rn, sm_100 and later).  The sweep kernel
+// is bound by instruction issue, not by the FMA pipe, so evaluating two Gauss
+// points in the halves of one float2 halves the issue slots of their
+// arithmetic.
+//
+// Here the two halves are the two t1 Gauss abscissae of one face; the
+// shared-memory layout of the t1 pass keeps them adjacent, so one 64-bit load
+// fetches both.  The formulas are those of recon.cuh (linear tangential
+// reconstruction) and physics.cuh (smooth flux), evaluated pairwise; only the
+// rounding of the fused operations can differ from the scalar code.
+#pragma once
+
+#include "physics.cuh"
+
+namespace hgks {
+
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.f / a.x, 1.f / a.y); }
+
+// Linear-weight tangential reconstruction (the quartic through five face
+// averages) of two columns at once: values v[m] and derivatives d[m] (per
+// unit cell length) at the Gauss abscissae s_m = -+1/(2 sqrt 3):
+//   P(+-g) = E +- O,  P'(+-g) = A +- B  with
+//   E = 719/720 f2 + (f1+f3)/1080 - (f0+f4)/4320,
+//   O = sqrt3 (7/432 (f0-f4) + 25/216 (f3-f1)),
+//   A = (f0-f4)/12 + 2(f3-f1)/3,  B = sqrt3/54 (13 (f1+f3) - 24 f2 - (f0+f4)).
+__device__ __forceinline__ void tangential_linear_x2(float2 f0, float2 f1, float2 f2, float2 f3,
+                                                     float2 f4, float2 v[2], float2 d[2]) {
+  const float sq3 = 1.7320508075688772f;
+  const float2 s13 = add2(f1, f3), s04 = add2(f0, f4);
+  const float2 d04 = sub2(f0, f4), d31 = sub2(f3, f1);
+  const float2 E = fma2(f2, bc2(719.f / 720.f), fma2(s13, bc2(1.f / 1080.f), mul2(s04, bc2(-1.f / 4320.f))));
+  const float2 O = fma2(d04, bc2(sq3 * 7.f / 432.f), mul2(d31, bc2(sq3 * 25.f / 216.f)));
+  const float2 A = fma2(d04, bc2(1.f / 12.f), mul2(d31, bc2(2.f / 3.f)));
+  const float k = sq3 / 54.f;
+  const float2 B = fma2(s13, bc2(13.f * k), fma2(f2, bc2(-24.f * k), mul2(s04, bc2(-k))));
+  v[0] = sub2(E, O);
+  v[1] = add2(E, O);
+  d[0] = sub2(A, B);
+  d[1] = add2(A, B);
+}
+
+__device__ __forceinline__ void tangential_linear_val_x2(float2 f0, float2 f1, float2 f2, float2 f3,
+                                                         float2 f4, float2 v[2]) {
+  const float sq3 = 1.7320508075688772f;
+  const float2 s13 = add2(f1, f3), s04 = add2(f0, f4);
+  const float2 d04 = sub2(f0, f4), d31 = sub2(f3, f1);
+  const float2 E = fma2(f2, bc2(719.f / 720.f), fma2(s13, bc2(1.f / 1080.f), mul2(s04, bc2(-1.f / 4320.f))));
+  const float2 O = fma2(d04, bc2(sq3 * 7.f / 432.f), mul2(d31, bc2(sq3 * 25.f / 216.f)));
+  v[0] = sub2(E, O);
+  v[1] = add2(E, O);
+}
+
+// Two point states (deviation value and derivatives along n, t1, t2, local
+// frame), one per half.
+struct PointStateX2 {
+  float2 q[5];
+  float2 dq[3][5];
+};
+
+// Velocity gradient and pressure derivative of the state along one axis:
+// du[k] = d u_k, dp = d p for the conservative derivative dQ (the pieces the
+// Euler Jacobian-vector product and the viscous flux share).
+struct DirDeriv {
+  float2 du[3], dp;
+};
+
+// Smooth BGK flux at two points (physics.cuh, flux_smooth): F - E(Q_ref)
+// (want_F) and -dF are accumulated into Fs[0..4] and Fs[5..9] summed over the
+// halves: Fs[i] += F_i(.x) + F_i(.y), Fs[5+i] += dF_i(.x) + dF_i(.y).
+// dF = J_n(Q0) Q_t with Q_t = -sum_d J_d(Q0) dQ0/dx_d; F = Euler flux + the
+// BGK Navier-Stokes viscous flux with the heat flux scaled by 1/Pr.
+template <bool WANT_F>
+__device__ __forceinline__ void flux_smooth_x2(const PointStateX2& st, const Gas<float>& g, float Fs[10]) {
+  // Primitive state (prim_of).
+  const float2 rho = add2(bc2(g.rho_r), st.q[0]);
+  const float2 inv = rcp2(rho);
+  const float2 U[3] = {mul2(st.q[1], inv), mul2(st.q[2], inv), mul2(st.q[3], inv)};
+  const float2 nU[3] = {mul2(U[0], bc2(-1.f)), mul2(U[1], bc2(-1.f)), mul2(U[2], bc2(-1.f))};
+  const float2 ke2 = fma2(st.q[1], U[0], fma2(st.q[2], U[1], mul2(st.q[3], U[2])));  // |m|^2/rho
+  const float2 dp = mul2(bc2(g.gm1), fma2(ke2, bc2(-0.5f), st.q[4]));
+  const float2 H = add2(add2(bc2(g.h_r), st.q[4]), dp);
+  const float2 hq2 = mul2(bc2(0.5f), fma2(U[0], U[0], fma2(U[1], U[1], mul2(U[2], U[2]))));
+  const float2 m[3] = {mul2(rho, U[0]), mul2(rho, U[1]), mul2(rho, U[2])};
+
+  auto deriv = [&](const float2 dQ[5]) {
+    DirDeriv r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.du[k] = mul2(fma2(nU[k], dQ[0], dQ[1 + k]), inv);
+    float2 t = fma2(nU[0], dQ[1], dQ[4]);
+    t = fma2(nU[1], dQ[2], t);
+    t = fma2(nU[2], dQ[3], t);
+    t = fma2(hq2, dQ[0], t);
+    r.dp = mul2(bc2(g.gm1), t);
+    return r;
+  };
+  // J_J(Q) dQ (euler_jvp) from the shared pieces.
+  auto jvp = [&](int J, const float2 dQ[5], const DirDeriv& r, float2 out[5]) {
+    out[0] = dQ[1 + J];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[1 + i] = fma2(dQ[1 + J], U[i], mul2(m[J], r.du[i]));
+    out[1 + J] = add2(out[1 + J], r.dp);
+    out[4] = fma2(r.du[J], H, mul2(U[J], add2(dQ[4], r.dp)));
+  };
+
+  const DirDeriv r0 = deriv(st.dq[0]), r1 = deriv(st.dq[1]), r2 = deriv(st.dq[2]);
+  // S = sum_d J_d dQ/dx_d = -Q_t.
+  float2 S[5], j[5];
+  jvp(0, st.dq[0], r0, S);
+  jvp(1, st.dq[1], r1, j);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) S[i] = add2(S[i], j[i]);
+  jvp(2, st.dq[2], r2, j);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) S[i] = add2(S[i], j[i]);
+  // dF = J_n Q_t = -J_n S.
+  const DirDeriv rs = deriv(S);
+  float2 dF[5];
+  jvp(0, S, rs, dF);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Fs[5 + i] -= dF[i].x + dF[i].y;
+  if constexpr (WANT_F) {
+    // Viscosity mu(T) of the gas law at T = p/rho.
+    float2 mu = bc2(g.mu_ref);
+    if (g.visc_law == 1) {
+      const float2 th = mul2(add2(bc2(g.p_r), dp), inv);
+      mu = make_float2(g.mu_ref * tpow(th.x * g.T_ref_inv, g.visc_exp),
+                       g.mu_ref * tpow(th.y * g.T_ref_inv, g.visc_exp));
+    }
+    // Viscous stress row of the normal direction and the heat flux
+    // (ns_viscous_flux) from the gradients of the three directions.
+    const float2 theta = mul2(add2(bc2(g.p_r), dp), inv);
+    const float2 divU = add2(add2(r0.du[0], r1.du[1]), r2.du[2]);
+    const float2 dT0 = mul2(fma2(theta, mul2(st.dq[0][0], bc2(-1.f)), r0.dp), inv);
+    const float2 s00 = mul2(mu, fma2(divU, bc2(-2.f / (g.K + 3.f)), mul2(bc2(2.f), r0.du[0])));
+    const float2 s01 = mul2(mu, add2(r0.du[1], r1.du[0]));
+    const float2 s02 = mul2(mu, add2(r0.du[2], r2.du[0]));
+    const float hc = -(g.pr_fix + 1.f) * 0.5f * (g.K + 5.f);
+    float2 F[5];
+    F[0] = m[0];
+    F[1] = sub2(fma2(m[0], U[0], dp), s00);
+    F[2] = sub2(mul2(m[0], U[1]), s01);
+    F[3] = sub2(mul2(m[0], U[2]), s02);
+    const float2 work = fma2(s00, U[0], fma2(s01, U[1], mul2(s02, U[2])));
+    F[4] = fma2(mul2(mu, bc2(hc)), dT0, sub2(mul2(U[0], H), work));
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Fs[i] += F[i].x + F[i].y;
+  }
+}
+
+}  // namespace hgks

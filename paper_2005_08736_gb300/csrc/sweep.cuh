@@ -20,6 +20,9 @@
 
 #include "charvars.cuh"
 #include "kernels.cuh"
+#include "packed.cuh"
+
+#include <type_traits>
 
 namespace hgks {
 
@@ -326,6 +329,35 @@ __device__ __forceinline__ void t1_pass_group(const T* ff, T* tb, int at, int st
   }
 }
 
+// t1_pass_group with the packed layout of the last phase (FP32, linear
+// weights): the outputs at the two t1 abscissae are stored side by side as a
+// float2 -- state field k: pair plane 2k (values), 2k+1 (t1-derivatives);
+// normal slope of state field j: pair plane 2 NV + j (values).
+template <int MODE, int NV, int NH>
+__device__ __forceinline__ void t1_pass_group_x2(const float* ff, float* tb, int at, int st1, int grp) {
+  float2* tb2 = reinterpret_cast<float2*>(tb);
+  if (grp < NV / 5) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int k = 5 * grp + i;
+      const float* src = ff + k * NH + at;
+      float v[2], dd[2];
+      tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+      tb2[(2 * k) * NH + at] = make_float2(v[0], v[1]);
+      tb2[(2 * k + 1) * NH + at] = make_float2(dd[0], dd[1]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int j = 5 * (grp - NV / 5) + i;
+      const float* src = ff + (NV + j) * NH + at;
+      float v[2];
+      tangential_val<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v);
+      tb2[(2 * NV + j) * NH + at] = make_float2(v[0], v[1]);
+    }
+  }
+}
+
 // Resident CTAs per SM the register budget is sized for: the smooth FP32
 // sweep fits three (shared memory allows three as well), the others one or two
 // (two at most for the characteristic modes, which need more registers).
@@ -344,8 +376,12 @@ __host__ __device__ constexpr int sweep_min_blocks() {
                                                                       : SweepOccupancy<T, FLUX>::value;
 }
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL>
-__global__ void __launch_bounds__(sweep_threads(TP, TS), (sweep_min_blocks<T, MODE, FLUX, TP, TS>()))
+// PK (FP32, linear weights, smooth flux, one thread per face): the last
+// phase evaluates the two t1 abscissae of a face as the halves of packed FP32
+// pairs (packed.cuh); shared memory allows two CTAs per SM for this tile, so
+// the register budget is sized for two.
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK = false>
+__global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blocks<T, MODE, FLUX, TP, TS>()))
     k_sweep(SweepArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
   constexpr int NV = SweepLayout<FLUX>::NV;
@@ -440,14 +476,16 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (sweep_min_blocks<T, MO
 #pragma unroll 1
       for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
         const int grp = it / ITEMS, pt = it % ITEMS;
-        t1_pass_group<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
+        if constexpr (PK) t1_pass_group_x2<MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
+        else t1_pass_group<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
       }
     } else {
       constexpr int ITEMS = HP * TS;
 #pragma unroll 1
       for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
         const int grp = it / ITEMS, pt = it % ITEMS;
-        t1_pass_group<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
+        if constexpr (PK) t1_pass_group_x2<MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
+        else t1_pass_group<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
       }
     }
     __syncthreads();
@@ -464,7 +502,34 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (sweep_min_blocks<T, MO
     T Fs[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) Fs[i] = T(0);
-    if constexpr (FLUX == FLUX_SMOOTH && TPF <= 2) {
+    if constexpr (PK) {
+      // Both t1 abscissae at once, as the halves of packed pairs: one pass
+      // along t2 per field gives both t2 abscissae; the flux at (., m2) is
+      // evaluated for the two t1 abscissae together.
+      static_assert(std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH &&
+                        TPF == 1, "packed phase 3: FP32, linear weights, smooth flux, one thread per face");
+      const float2* tb2 = reinterpret_cast<const float2*>(tb);
+      PointStateX2 st[2];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const float2* sv = tb2 + (2 * i) * NH + at3;
+        const float2* sdv = tb2 + (2 * i + 1) * NH + at3;
+        const float2* ss = tb2 + (2 * NV + i) * NH + at3;
+        float2 v[2], dd[2], vd[2], vs[2];
+        tangential_linear_x2(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
+        tangential_linear_val_x2(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
+        tangential_linear_val_x2(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
+#pragma unroll
+        for (int m2 = 0; m2 < 2; ++m2) {
+          st[m2].q[i] = v[m2];
+          st[m2].dq[0][i] = vs[m2];
+          st[m2].dq[1][i] = mul2(vd[m2], bc2(rh1));
+          st[m2].dq[2][i] = mul2(dd[m2], bc2(rh2));
+        }
+      }
+      flux_smooth_x2<STAGE == 1>(st[0], a.gas, Fs);
+      flux_smooth_x2<STAGE == 1>(st[1], a.gas, Fs);
+    } else if constexpr (FLUX == FLUX_SMOOTH && TPF <= 2) {
       // One pass along t2 gives both t2 abscissae: each thread takes one (or
       // both) t1 abscissae m1 and evaluates the flux at (m1, 0) and (m1, 1).
 #pragma unroll 1

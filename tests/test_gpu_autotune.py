@@ -1,6 +1,7 @@
 """The tile autotuner: every sweep launch shape gives the same step (bitwise
 for the march length; to FP32 rounding for the tile variants, whose threads
-sum the four Gauss points of a face in another order), and the tuner's choice
+sum the four Gauss points of a face in another order, or evaluate two of them
+as the halves of packed FP32 pairs), and the tuner's choice
 is cached per configuration."""
 import json
 
@@ -15,7 +16,7 @@ from paper_2005_08736_gb300 import inputs  # noqa: E402
 from paper_2005_08736_gb300.solver import Simulation, taylor_green_config  # noqa: E402
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("chunk", [0, 8, 12, 64])
 def test_every_launch_shape_gives_the_same_step(variant, chunk):
     n = (40, 20, 17)
@@ -43,7 +44,7 @@ def test_autotune_keeps_the_state_and_caches_its_choice(tmp_path):
     sim.init_primitive(inputs.taylor_green(32))
     before = sim.state()
     rec = sim.autotune(cache=str(tmp_path / "tune.json"))
-    assert not rec["cached"] and rec["variant"] in (0, 1, 2) and rec["sweep_ms"] > 0
+    assert not rec["cached"] and rec["variant"] in (0, 1, 2, 3) and rec["sweep_ms"] > 0
     assert np.array_equal(sim.state(), before)
     table = json.load(open(tmp_path / "tune.json"))
     assert len(table) == 1
