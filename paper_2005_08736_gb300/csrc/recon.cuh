@@ -31,6 +31,14 @@ template <int MODE> __host__ __device__ constexpr bool is_char_mode() { return M
 template <int MODE_, class T>
 __device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, T& qR) {
   constexpr int MODE = recon_of<MODE_>();
+  if (MODE == RECON_LINEAR) {
+    // The optimal-weight combination of the three candidates is the
+    // fifth-degree reconstruction (2, -13, 47, 27, -3)/60 of the five averages.
+    const T c60 = T(1) / T(60);
+    qR = (T(2) * q0 - T(13) * q1 + T(47) * q2 + T(27) * q3 - T(3) * q4) * c60;
+    qL = (T(2) * q4 - T(13) * q3 + T(47) * q2 + T(27) * q1 - T(3) * q0) * c60;
+    return;
+  }
   const T c6 = T(1) / T(6);
   const T pR0 = (T(2) * q0 - T(7) * q1 + T(11) * q2) * c6;
   const T pR1 = (-q1 + T(5) * q2 + T(2) * q3) * c6;
@@ -38,11 +46,6 @@ __device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, 
   const T pL0 = (T(2) * q4 - T(7) * q3 + T(11) * q2) * c6;
   const T pL1 = (-q3 + T(5) * q2 + T(2) * q1) * c6;
   const T pL2 = (T(2) * q2 + T(5) * q1 - q0) * c6;
-  if (MODE == RECON_LINEAR) {
-    qR = T(0.1) * pR0 + T(0.6) * pR1 + T(0.3) * pR2;
-    qL = T(0.1) * pL0 + T(0.6) * pL1 + T(0.3) * pL2;
-    return;
-  }
   const T s0 = q0 - T(2) * q1 + q2, t0 = q0 - T(4) * q1 + T(3) * q2;
   const T s1 = q1 - T(2) * q2 + q3, t1 = q1 - q3;
   const T s2 = q2 - T(2) * q3 + q4, t2 = T(3) * q2 - T(4) * q3 + q4;

@@ -155,6 +155,96 @@ __device__ __forceinline__ SweepAxes sweep_axes(int d, const GridDev& g) {
   return a;
 }
 
+// Face fields (conservative-variable reconstruction) of one face point from
+// the six cells f-3..f+2 along the normal, qa[i][k] = variable i of cell
+// f-3+k (local frame), and the widths hl, hr of cells f-1 and f: the WENO5
+// end values, the normal slopes, the compatibility state Q0 and its normal
+// slope, into ff[k * NH + h].
+template <class T, int MODE, int FLUX, int NH>
+__device__ __forceinline__ void face_fields_cells(const T qa[5][6], T hl, T hr, const Gas<T>& gas,
+                                                  int h, T* ff) {
+  const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
+  T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T q0 = qa[i][0], q1 = qa[i][1], q2 = qa[i][2], q3 = qa[i][3], q4 = qa[i][4], q5 = qa[i][5];
+    T Li, Ri, Lr, Rr;
+    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
+    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+    Ql[i] = Ri;
+    Qr[i] = Lr;
+    Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
+    Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
+    D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
+  }
+  T Q0[5];
+  compat_dev(Ql, Qr, gas, Q0);
+  if constexpr (FLUX == FLUX_SMOOTH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      ff[i * NH + h] = Q0[i];
+      ff[(5 + i) * NH + h] = D0[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      ff[i * NH + h] = Ql[i];
+      ff[(5 + i) * NH + h] = Qr[i];
+      ff[(10 + i) * NH + h] = Q0[i];
+      ff[(15 + i) * NH + h] = Dl[i];
+      ff[(20 + i) * NH + h] = Dr[i];
+      ff[(25 + i) * NH + h] = D0[i];
+    }
+  }
+}
+
+// Face fields of the x sweep (conservative variables) for the layers
+// fb .. fb+nl-1 at transverse point (Pc, Sc): one thread reads the nl+5 cells
+// fb-3 .. fb+nl+1 along x of each variable, contiguous in memory, as pairs
+// (two-element vector loads; the caller guarantees an even padded row length,
+// so that with fb even every pair is aligned), and forms the fields of each
+// layer l into ffb + l * NFF * NH.
+template <class T, int MODE, int FLUX, int NH, int NL, int NFF>
+__device__ __forceinline__ void face_fields_x_item(const T* __restrict__ q, const GridDev& g,
+                                                   const SweepAxes& ax, const T* __restrict__ wn,
+                                                   const Gas<T>& gas, int fb, int nl, int Pc, int Sc,
+                                                   int h, T* ffb) {
+  using V2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+  constexpr int NC = NL + 5;  // cells of NL layers
+  const long long cb = pad_index(g, fb - 3, ax.P == 1 ? Pc : Sc, ax.P == 1 ? Sc : Pc);
+  T cells[5][NC + 1];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T* qv = q + ax.gv[i] * g.P + cb;
+#pragma unroll
+    for (int j = 0; j < (NC + 1) / 2; ++j) {
+      if (2 * j + 1 < nl + 5) {
+        const V2 v = __ldg(reinterpret_cast<const V2*>(qv + 2 * j));
+        cells[i][2 * j] = v.x;
+        cells[i][2 * j + 1] = v.y;
+      } else if (2 * j < nl + 5) {
+        cells[i][2 * j] = __ldg(qv + 2 * j);
+        cells[i][2 * j + 1] = T(0);
+      } else {
+        cells[i][2 * j] = cells[i][2 * j + 1] = T(0);
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    if (l < nl) {
+      T qa[5][6];
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qa[i][k] = cells[i][l + k];
+      const int f = fb + l;
+      face_fields_cells<T, MODE, FLUX, NH>(qa, wn[f - 1 + kGhost], wn[f + kGhost], gas, h,
+                                           ffb + l * NFF * NH);
+    }
+  }
+}
+
 // Face fields of face layer f at transverse point (Pc, Sc) into ff[k * NH + h]:
 // WENO5 end values of cells f-1 and f, their normal slopes, the compatibility
 // state Q0 and its normal slope (local frame).  Smooth flux: fields Q0, dQ0/dn;
@@ -206,20 +296,15 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
       ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + h] = qm[i];
     }
   } else {
+    T qa[5][6];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const T* qv = q + ax.gv[i] * g.P + cb;
-    const T q0 = __ldg(qv), q1 = __ldg(qv + sd), q2 = __ldg(qv + 2 * sd), q3 = __ldg(qv + 3 * sd),
-            q4 = __ldg(qv + 4 * sd), q5 = __ldg(qv + 5 * sd);
-    T Li, Ri, Lr, Rr;
-    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
-    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
-    Ql[i] = Ri;
-    Qr[i] = Lr;
-    Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
-    Dr[i] = -(T(4) * Lr + T(2) * Rr - T(6) * q3) * rhr;
-    D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
-  }
+    for (int i = 0; i < 5; ++i) {
+      const T* qv = q + ax.gv[i] * g.P + cb;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qa[i][k] = __ldg(qv + k * sd);
+    }
+    face_fields_cells<T, MODE, FLUX, NH>(qa, hl, hr, gas, h, ff);
+    return;
   }
   T Q0[5];
   compat_dev(Ql, Qr, gas, Q0);
@@ -439,6 +524,28 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
     // Items (layer, transverse point of the tile plus a halo of 2).  For d = x
     // consecutive threads take consecutive layers, so that the loads along x
     // are coalesced; otherwise consecutive transverse points along P (= x).
+    if (NL == 2 && !is_char_mode<MODE>() && d == 0 && (a.g.p[0] & 1) == 0) {
+      // x sweep: one item per transverse point for both layers (pair loads
+      // along x; fb is even because chunks and NL are).  Tiles with more
+      // layers per pass keep the per-layer items below (register budget).
+      const int nl = min(NL, f1 - fb);
+      for (int h = tid; h < NH; h += NT) {
+        const int hp = h % HP, hs = h / HP;
+        const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+        if (Pc <= nP + 1 && Sc <= nS + 1) {
+          face_fields_x_item<T, MODE, FLUX, NH, NL, NFF>(a.q, a.g, ax, a.wn, a.gas, fb, nl, Pc, Sc, h, ffb);
+        } else {
+#pragma unroll 1
+          for (int l = 0; l < NL; ++l)
+#pragma unroll 1
+            for (int k = 0; k < NFF; ++k) ffb[(l * NFF + k) * NH + h] = T(0);
+        }
+#pragma unroll 1
+        for (int l = nl; l < NL; ++l)
+#pragma unroll 1
+          for (int k = 0; k < NFF; ++k) ffb[(l * NFF + k) * NH + h] = T(0);
+      }
+    } else
     for (int it = tid; it < NL * NH; it += NT) {
       const int l = d == 0 ? it % NL : it / NH;
       const int h = d == 0 ? it / NL : it % NH;
