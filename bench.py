@@ -36,18 +36,24 @@ PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.0
 METRIC = "Mcell-updates/s per S2O4 step"
 # cfl, dt, 2 x (3 ghost fills + 3 sweeps + update), time
 LAUNCHES_PER_STEP = 17
-# Executed FP32 operations (fadd + fmul + 2 ffma) and DRAM bytes (read +
-# write) per face of the stage-1 sweep kernel (FP32, linear WENO5, smooth
-# flux), mean of the three directions, counted by ncu on Taylor-Green 128^3
-# for each tile variant the autotuner can choose
-# (profiles/k_sweep_fp32_smooth_taylor_green_128.md); the tiles are the same
-# at 256^3, so the counts per face carry over.
-SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2575.5, "dram": 43.4},
-                1: {"tile": "32x8, 2 layers", "flops": 2477.8, "dram": 42.6},
-                2: {"tile": "16x16, 2 layers", "flops": 2399.7, "dram": 43.7},
-                # the packed variant performs the operations of variant 1 (same
-                # tile and passes), two Gauss points per instruction
-                3: {"tile": "32x8, 2 layers, packed FP32 pairs", "flops": 2477.8, "dram": 42.6}}
+# Algorithmic FP32 work of the stage-1 sweep per face (linear WENO5, smooth
+# flux): the flops of the three phases without the halo recomputation of the
+# tile -- face fields 373 per point, t1 pass 189 per point, t2 pass and flux
+# 1428 per face -- solved from the executed FP32 operations (fadd + fmul +
+# 2 ffma) that ncu counted on Taylor-Green 128^3 for the three scalar tile
+# variants, whose halo factors differ
+# (profiles/k_sweep_fp32_smooth_taylor_green_128.md).  The same per face for
+# every tile variant and grid.
+ALG_FLOPS_PER_FACE = 1990.0
+# Per tile variant: executed FP32 flops per face (mean of the three
+# directions; the packed variant performs the operations of variant 1) and
+# DRAM bytes (read + write) per face, from the ncu capture of the current
+# kernels at 128^3 (the tiles are the same at 256^3, so the counts per face
+# carry over).
+SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2391.8, "dram": 43.3},
+                1: {"tile": "32x8, 2 layers", "flops": 2313.7, "dram": 42.4},
+                2: {"tile": "16x16, 2 layers", "flops": 2247.7, "dram": 43.4},
+                3: {"tile": "32x8, 2 layers, packed FP32 pairs", "flops": 2313.7, "dram": 42.4}}
 
 
 def load_peaks():
@@ -444,21 +450,25 @@ def run_ours(args, rank: int, world: int):
     fp_peaks = measure_fp_peaks()  # FMA throughput of this GPU, outside the timed region
     peak_tflops = fp_peaks["fp32"]
     counts = SWEEP_COUNTS[tune["variant"]]
-    achieved = counts["flops"] * faces_per_launch / (flux_ms * 1e-3) / 1e12
+    achieved = ALG_FLOPS_PER_FACE * faces_per_launch / (flux_ms * 1e-3) / 1e12
+    traffic = counts["dram"] * faces_per_launch if counts["dram"] else None
     roofline = {"bound": "alu",
                 "kernel": f"k_sweep stage 1 (FP32, linear WENO5, smooth flux, tile {counts['tile']})",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
-                "traffic": counts["dram"] * faces_per_launch,
-                "flops_per_launch": counts["flops"] * faces_per_launch,
+                "traffic": traffic,
+                "flops_per_launch": ALG_FLOPS_PER_FACE * faces_per_launch,
+                "flops_note": "algorithmic: per-face flops of the kernel's formulas without the "
+                              "tile's halo recomputation",
+                "executed_flops_per_launch": counts["flops"] * faces_per_launch,
                 "peak_source": "measured: FP32 FMA throughput of this GPU (hgks_measure_fp_peaks)",
                 "nominal_peak": nominal_tflops,
                 "nominal_source": f"152 SMs x 128 FP32 lanes x 2 flops x {clock_mhz:.0f} MHz",
                 "frac_of_nominal": achieved / nominal_tflops,
                 "measured_fma_tflops": fp_peaks,
                 "launch_ms": flux_ms, "kernel_ms_per_step": prof,
-                "hbm_frac": counts["dram"] * faces_per_launch / (flux_ms * 1e-3)
-                / (peaks.get("hbm_gbs", 6802.0) * 1e9)}
+                "hbm_frac": (traffic / (flux_ms * 1e-3) / (peaks.get("hbm_gbs", 6802.0) * 1e9)
+                             if traffic else None)}
     cpu_rate, cpu_s = oracle_sample(2)
     extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
     line = {
