@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 N_GRID = 256
 PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.09 s/step
 METRIC = "Mcell-updates/s per S2O4 step"
-# cfl, dt, 2 x (3 ghost fills + 3 sweeps + update), time
-LAUNCHES_PER_STEP = 17
+# cfl, dt, 2 x (3 ghost fills + transposed copy + 3 sweeps + update), time
+LAUNCHES_PER_STEP = 19
 # Algorithmic FP32 work of the stage-1 sweep per face (linear WENO5, smooth
 # flux): the flops of the three phases without the halo recomputation of the
 # tile -- face fields 373 per point, t1 pass 189 per point, t2 pass and flux

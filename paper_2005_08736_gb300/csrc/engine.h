@@ -22,6 +22,8 @@ struct Engine {
   long long N = 0;  // interior cells
   void* q = nullptr;     // padded state Q^n (deviation), 5 * P
   void* qs = nullptr;    // padded state Q*, 5 * P
+  void* qx = nullptr;    // padded state with x slowest, [5][x][z][y], read by the x sweep
+                         // (null: the x sweep reads q with pair loads along x)
   void* inc = nullptr;   // stage-1 increment, 5 * N
   void* comp = nullptr;  // FP32 compensation, 5 * N (null for FP64)
   void* fd[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction, 10 * faces

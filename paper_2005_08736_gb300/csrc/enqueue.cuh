@@ -79,7 +79,14 @@ template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool P
 cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
-  a.q = q;
+  // The x sweep reads the copy of the state with x slowest, made here.
+  const bool xt = d == 0 && e.qx != nullptr;
+  if (xt) {
+    const dim3 tgrid((g.p[0] + 31) / 32, (g.p[1] + 31) / 32, g.p[2]);
+    k_transpose_x<T><<<tgrid, 256, 0, e.stream>>>(q, static_cast<T*>(e.qx), g);
+  }
+  a.q = xt ? static_cast<const T*>(e.qx) : q;
+  a.xt = xt ? 1 : 0;
   a.fd = static_cast<T*>(e.fd[d]);
   a.wn = static_cast<const T*>(e.w[d]);
   a.wt1 = static_cast<const T*>(e.w[(d + 1) % 3]);

@@ -99,7 +99,7 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 }
 
 void free_all(hgks::Engine& e) {
-  void* ptrs[] = {e.q, e.qs, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
+  void* ptrs[] = {e.q, e.qs, e.qx, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
                   e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out};
   for (void* p : ptrs)
@@ -239,6 +239,7 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   cudaError_t err = cudaSuccess;
   if (err == cudaSuccess) err = alloc(&e.q, 5 * e.P * es);
   if (err == cudaSuccess) err = alloc(&e.qs, 5 * e.P * es);
+  if (err == cudaSuccess) err = alloc(&e.qx, 5 * e.P * es);
   if (err == cudaSuccess) err = alloc(&e.inc, 5 * e.N * es);
   if (err == cudaSuccess && cfg->prec == HGKS_FP32) err = alloc(&e.comp, 5 * e.N * es);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.fd[d], hgks::face_flux_elems(e, d) * es);

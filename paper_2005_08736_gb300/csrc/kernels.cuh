@@ -123,6 +123,38 @@ __global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
   for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
 }
 
+// Copy of the padded state with x slowest, qx[v][x][z][y] = q[v][z][y][x]
+// (padded coordinates, ghosts included), so that the x sweep reads its cells
+// like the y and z sweeps read q: consecutive threads along y, the normal
+// axis strided.  One CTA per 32 x 32 tile of an x-y plane, all five
+// variables through shared memory (the 20 loads of a thread are in flight
+// together); grid (ceil(p0/32), ceil(p1/32), p2), 256 threads.
+template <class T>
+__global__ void __launch_bounds__(256) k_transpose_x(const T* __restrict__ q, T* __restrict__ qx,
+                                                     GridDev g) {
+  __shared__ T tile[5][32][33];
+  const int p0 = g.p[0], p1 = g.p[1], p2 = g.p[2];
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+  const T* src = q + (long long)z * p1 * p0;
+  T* dst = qx + (long long)z * p1;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int j = ty; j < 32; j += 8) {
+      const int x = x0 + tx, y = y0 + j;
+      if (x < p0 && y < p1) tile[v][j][tx] = __ldg(src + v * g.P + (long long)y * p0 + x);
+    }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int j = ty; j < 32; j += 8) {
+      const int x = x0 + j, y = y0 + tx;
+      if (x < p0 && y < p1) dst[v * g.P + (long long)x * p2 * p1 + y] = tile[v][tx][j];
+    }
+}
+
 // Global conservative-variable index of local-frame component i for sweep
 // direction d (local frame: normal momentum first, then t1, t2).
 __host__ __device__ __forceinline__ int global_var(int d, int i) {

@@ -37,6 +37,7 @@ struct SweepArgs {
   GridDev g;
   int d;
   int chunk;
+  int xt;  // d = x and q is the copy with x slowest ([5][x][z][y], k_transpose_x)
   Gas<T> gas;
 };
 
@@ -142,14 +143,22 @@ struct SweepAxes {
   bool t1P;        // t1 is P (d = x, z) or S (d = y)
   long long sd;    // stride of the padded state along d
   int gv[5];       // global variable of each local-frame component
+  bool xt;         // the state is the copy with x slowest (x sweep)
+  // Padded index of cell (x, y, z) in the state the sweep reads.
+  __device__ __forceinline__ long long index(const GridDev& g, int x, int y, int z) const {
+    return xt ? ((long long)(x + kGhost) * g.p[2] + (z + kGhost)) * g.p[1] + (y + kGhost)
+              : pad_index(g, x, y, z);
+  }
 };
-__device__ __forceinline__ SweepAxes sweep_axes(int d, const GridDev& g) {
+__device__ __forceinline__ SweepAxes sweep_axes(int d, const GridDev& g, bool xt = false) {
   SweepAxes a;
   a.d = d;
   a.P = d == 0 ? 1 : 0;
   a.S = d == 2 ? 1 : 2;
   a.t1P = ((d + 1) % 3) == a.P;
-  a.sd = d == 0 ? 1LL : (d == 1 ? (long long)g.p[0] : (long long)g.p[0] * g.p[1]);
+  a.xt = xt && d == 0;
+  a.sd = a.xt ? (long long)g.p[1] * g.p[2]
+              : (d == 0 ? 1LL : (d == 1 ? (long long)g.p[0] : (long long)g.p[0] * g.p[1]));
 #pragma unroll
   for (int i = 0; i < 5; ++i) a.gv[i] = global_var(d, i);
   return a;
@@ -258,7 +267,7 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
   c[ax.d] = f - 3;
   c[ax.P] = Pc;
   c[ax.S] = Sc;
-  const long long cb = pad_index(g, c[0], c[1], c[2]);
+  const long long cb = ax.index(g, c[0], c[1], c[2]);
   const long long sd = ax.sd;
   const T hl = wn[f - 1 + kGhost], hr = wn[f + kGhost];
   const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
   T* scr = part + (TPF - 1) * 10 * NFACE;      // [60][256] (full flux, TPF = 2)
 
   const int d = a.d;
-  const SweepAxes ax = sweep_axes(d, a.g);
+  const SweepAxes ax = sweep_axes(d, a.g, a.xt != 0);
   const int P = ax.P, S = ax.S;
   const bool t1P = ax.t1P;
   const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
@@ -524,7 +533,7 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
     // Items (layer, transverse point of the tile plus a halo of 2).  For d = x
     // consecutive threads take consecutive layers, so that the loads along x
     // are coalesced; otherwise consecutive transverse points along P (= x).
-    if (NL == 2 && !is_char_mode<MODE>() && d == 0 && (a.g.p[0] & 1) == 0) {
+    if (NL == 2 && !is_char_mode<MODE>() && d == 0 && !ax.xt && (a.g.p[0] & 1) == 0) {
       // x sweep: one item per transverse point for both layers (pair loads
       // along x; fb is even because chunks and NL are).  Tiles with more
       // layers per pass keep the per-layer items below (register budget).
@@ -547,8 +556,11 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
       }
     } else
     for (int it = tid; it < NL * NH; it += NT) {
-      const int l = d == 0 ? it % NL : it / NH;
-      const int h = d == 0 ? it / NL : it % NH;
+      // Consecutive threads: consecutive layers for the x sweep reading q
+      // (cells along x are contiguous), else consecutive points along P.
+      const bool by_layer = d == 0 && !ax.xt;
+      const int l = by_layer ? it % NL : it / NH;
+      const int h = by_layer ? it / NL : it % NH;
       const int f = fb + l;
       const int hp = h % HP, hs = h / HP;
       const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
@@ -826,7 +838,8 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
       const long long o = fout + (long long)f * fstep;
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
+        // The second stage needs dF only (Eq. (6)); its F planes are not written.
+        if (STAGE == 1) a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
         a.fd[(5 + ax.gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
       }
     }
