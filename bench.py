@@ -46,14 +46,15 @@ LAUNCHES_PER_STEP = 19
 # every tile variant and grid.
 ALG_FLOPS_PER_FACE = 1990.0
 # Per tile variant: executed FP32 flops per face (mean of the three
-# directions; the packed variant performs the operations of variant 1) and
-# DRAM bytes (read + write) per face, from the ncu capture of the current
-# kernels at 128^3 (the tiles are the same at 256^3, so the counts per face
-# carry over).
-SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2391.8, "dram": 43.3},
-                1: {"tile": "32x8, 2 layers", "flops": 2313.7, "dram": 42.4},
-                2: {"tile": "16x16, 2 layers", "flops": 2247.7, "dram": 43.4},
-                3: {"tile": "32x8, 2 layers, packed FP32 pairs", "flops": 2313.7, "dram": 42.4}}
+# directions, ncu at 128^3; the packed variant performs the operations of
+# variant 1) and DRAM bytes (read + write) per face of the stage-1 sweep from
+# a one-pass ncu capture at 256^3 (None where not captured for the current
+# kernel; at 128^3 the L2 holds part of the writes, so smaller grids
+# undercount).
+SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2391.8, "dram": None},
+                1: {"tile": "32x8, 2 layers", "flops": 2313.7, "dram": None},
+                2: {"tile": "16x16, 2 layers", "flops": 2247.7, "dram": None},
+                3: {"tile": "32x8, 2 layers, packed FP32 pairs", "flops": 2313.7, "dram": 58.3}}
 
 
 def load_peaks():
