@@ -21,13 +21,15 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hgks_oracle.cpp")
-_DEPS = [_SRC, os.path.join(_HERE, "tangent.h")]
+_DEPS = [_SRC, os.path.join(_HERE, "tangent.h"), os.path.join(_HERE, "counted.h")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libhgks_oracle.so")
 _TAN_PATH = os.path.join(_OUT_DIR, "libhgks_oracle_tangent.so")
+_CNT_PATH = os.path.join(_OUT_DIR, "libhgks_oracle_count.so")
 _lock = threading.Lock()
 _lib = None
 _tan = None
+_cnt = None
 
 RECON_LINEAR, RECON_WENO_JS, RECON_WENO_Z = 0, 1, 2
 FLUX_SMOOTH, FLUX_FULL = 0, 1
@@ -38,7 +40,8 @@ def _compile(path: str, extra, force: bool) -> str:
             and os.path.getmtime(path) >= max(os.path.getmtime(f) for f in _DEPS)):
         return path
     tmp = path + f".tmp{os.getpid()}"
-    cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+    omp = [] if "-DORACLE_COUNT" in extra else ["-fopenmp"]  # the tallies need one thread
+    cmd = ["g++", "-std=c++17", "-O2", *omp, "-ffp-contract=off", "-fPIC",
            "-shared", "-Wl,-Bsymbolic", *extra, "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, path)
@@ -47,9 +50,11 @@ def _compile(path: str, extra, force: bool) -> str:
 
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (-O2, OpenMP, no FP contraction): the plain
-    FP64 build and the dual-number tangent build of the same source."""
+    FP64 build, the dual-number tangent build and the operation-counting build
+    (one thread) of the same source."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     _compile(_TAN_PATH, ["-DORACLE_TANGENT"], force)
+    _compile(_CNT_PATH, ["-DORACLE_COUNT"], force)
     return _compile(_LIB_PATH, [], force)
 
 
@@ -240,6 +245,52 @@ class Solver:
         out = np.empty((5, c.nz + 6, c.ny + 6, c.nx + 6))
         lib().oracle_padded(self._h, _p(out))
         return out
+
+
+def count_lib():
+    """The counting build: the solver API plus oracle_count_get / _reset."""
+    global _cnt
+    with _lock:
+        if _cnt is None:
+            build()
+            L = ctypes.CDLL(_CNT_PATH)
+            d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            pd = ctypes.POINTER(ctypes.c_double)
+            L.oracle_create.restype = vp
+            L.oracle_create.argtypes = [ctypes.POINTER(OracleConfig)]
+            L.oracle_destroy.argtypes = [vp]
+            L.oracle_set_state.argtypes = [vp, pd]
+            L.oracle_get_state.argtypes = [vp, pd]
+            L.oracle_step.restype = d
+            L.oracle_step.argtypes = [vp, i, d]
+            L.oracle_count_get.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+            L.oracle_count_reset.argtypes = []
+            _cnt = L
+    return _cnt
+
+
+COUNT_KEYS = ("add", "mul", "div", "sqrt", "exp", "erfc", "pow")
+
+
+def count_step(cfg: Config, cons, nsteps: int = 1, dt: float = 0.0):
+    """Run the counting build for nsteps from the conservative state cons:
+    returns (final state, tallies of the oracle's operations over the run,
+    a dict over COUNT_KEYS).  Single-threaded."""
+    L = count_lib()
+    c = cfg.c_struct()
+    h = L.oracle_create(ctypes.byref(c))
+    try:
+        a = _f64(cons)
+        L.oracle_set_state(h, _p(a))
+        L.oracle_count_reset()
+        L.oracle_step(h, int(nsteps), float(dt))
+        out = (ctypes.c_ulonglong * 7)()
+        L.oracle_count_get(out)
+        state = np.empty((5, cfg.nz, cfg.ny, cfg.nx))
+        L.oracle_get_state(h, _p(state))
+    finally:
+        L.oracle_destroy(h)
+    return state, dict(zip(COUNT_KEYS, (int(x) for x in out)))
 
 
 class TangentSolver:

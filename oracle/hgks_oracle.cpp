@@ -40,13 +40,19 @@
 // computes in double.  The tangent build (-DORACLE_TANGENT) computes in the
 // forward-mode dual numbers of tangent.h: the same code then also carries the
 // derivative along one input direction (a dual-number tangent run), while its
-// value part repeats the double arithmetic of the plain build exactly.
+// value part repeats the double arithmetic of the plain build exactly.  The
+// counting build (-DORACLE_COUNT) computes in the tallying doubles of
+// counted.h: the same values, plus the number of operations performed.
 // Configuration constants, cell widths, the Gauss abscissae and dt stay double
 // (dt is held fixed when differentiating, as in the adjoint).
-#ifdef ORACLE_TANGENT
+#if defined(ORACLE_TANGENT)
 #include "tangent.h"
 using real = oracle_dual::Dual;
 using oracle_dual::value;
+#elif defined(ORACLE_COUNT)
+#include "counted.h"
+using real = oracle_count::Counted;
+using oracle_count::value;
 #else
 using real = double;
 inline double value(double x) { return x; }
@@ -1078,6 +1084,17 @@ double oracle_time(void* h) { return static_cast<Solver*>(h)->t; }
 double oracle_last_force(void* h) { return value(static_cast<Solver*>(h)->last_force); }
 double oracle_cfl_dt(void* h) { return value(static_cast<Solver*>(h)->cfl_dt()); }
 
+#ifdef ORACLE_COUNT
+// Counting build only: the tallies since the last reset, out[7] = additions
+// and subtractions, multiplications, divisions, sqrt, exp, erfc, pow calls.
+void oracle_count_get(unsigned long long* out) {
+  const oracle_count::Tally& t = oracle_count::g_tally;
+  const unsigned long long v[7] = {t.add, t.mul, t.div, t.sqrt, t.exp, t.erfc, t.pow};
+  for (int i = 0; i < 7; ++i) out[i] = v[i];
+}
+void oracle_count_reset() { oracle_count::g_tally = oracle_count::Tally{}; }
+#endif
+
 #ifdef ORACLE_TANGENT
 // Tangent build only: the derivative part of the state.  oracle_set_state
 // sets the values with a zero tangent; oracle_set_tangent then sets the
@@ -1100,7 +1117,9 @@ void oracle_get_tangent(void* h, double* dcons) {
           dcons[((size_t(v) * s.n[2] + k) * s.n[1] + j) * s.n[0] + i] =
               oracle_dual::tangent(s.Q(s.q, v, i, j, k));
 }
-#else
+#endif  // ORACLE_TANGENT
+
+#if !defined(ORACLE_TANGENT) && !defined(ORACLE_COUNT)
 // Characteristic basis at the local-frame state Qm: R and R^{-1}, row-major.
 void oracle_char_basis(const double* Qm, double gamma, double* R, double* L) {
   const CharBasis B = char_basis(Qm, gamma);
@@ -1225,6 +1244,6 @@ void oracle_flux_point(const oracle_config* cfg, const double* st, double dt, do
   flux_point(*cfg, pd, dt, F, dF);
 }
 
-#endif  // ORACLE_TANGENT
+#endif  // the plain build
 
 }  // extern "C"
