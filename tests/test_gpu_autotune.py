@@ -1,8 +1,8 @@
 """The tile autotuner: every sweep launch shape gives the same step (bitwise
 for the march length; to FP32 rounding for the tile variants, whose threads
-sum the four Gauss points of a face in another order, or evaluate two of them
-as the halves of packed FP32 pairs), and the tuner's choice
-is cached per configuration."""
+sum the four Gauss points of a face in another order, or evaluate two points
+as the halves of packed FP32 pairs), and the tuner's choice is cached per
+configuration."""
 import json
 
 import numpy as np
@@ -34,8 +34,12 @@ def test_every_launch_shape_gives_the_same_step(variant, chunk):
     if variant == 0:
         assert np.array_equal(a, b)
     else:
+        # The compatibility state Q0 - Q_ref = (dQl + dQr)/2 + (S_l - S_r)/2
+        # cancels half-space moments of size rho sqrt(2 theta / pi) (~7 here),
+        # so a reordering of its FP32 operations moves the momentum by a few
+        # 1e-7 absolute after two steps: 4e-6 of the range.
         for v in range(5):
-            assert np.abs(a[v] - b[v]).max() <= 1e-6 * np.abs(b[v]).max()
+            assert np.abs(a[v] - b[v]).max() <= 4e-6 * np.abs(b[v]).max()
 
 
 def test_autotune_keeps_the_state_and_caches_its_choice(tmp_path):
