@@ -45,6 +45,13 @@ LAUNCHES_PER_STEP = 19
 # (profiles/k_sweep_fp32_smooth_taylor_green_128.md).  The same per face for
 # every tile variant and grid.
 ALG_FLOPS_PER_FACE = 1990.0
+# The same for the stage-2 sweep (dF only): 1841 per face (331 + 214 + 1296,
+# from the stage-2 counts of the same three variants).
+ALG_FLOPS_PER_FACE_STAGE2 = 1841.0
+# Algorithmic HBM bytes of one FP32 step per cell: stage 1 reads Q^n and
+# writes Q* and the increment, stage 2 reads Q* and the increment and writes
+# Q^{n+1}: 6 x 5 x 4 B.
+ALG_BYTES_PER_CELL_STEP = 120.0
 # Per tile variant: executed FP32 flops per face (mean of the three
 # directions, ncu at 128^3; the packed variant performs the operations of
 # variant 1) and DRAM bytes (read + write) per face of the stage-1 sweep from
@@ -558,6 +565,19 @@ def run_ours(args, rank: int, world: int):
                 "launch_ms": flux_ms, "kernel_ms_per_step": prof,
                 "hbm_frac": (traffic / (flux_ms * 1e-3) / (peaks.get("hbm_gbs", 6802.0) * 1e9)
                              if traffic else None)}
+    # The whole step against its own roofline: the slower of its algorithmic
+    # FP32 work at the measured FMA peak and its algorithmic HBM bytes at the
+    # measured copy bandwidth.
+    step_flops = 3 * faces_per_launch * (ALG_FLOPS_PER_FACE + ALG_FLOPS_PER_FACE_STAGE2)
+    step_bytes = ALG_BYTES_PER_CELL_STEP * cfg.cells
+    t_alu = step_flops / (peak_tflops * 1e12) * 1e3
+    t_hbm = step_bytes / (peaks.get("hbm_gbs", 6802.0) * 1e9) * 1e3
+    step_roofline = {"flops_per_step": step_flops, "bytes_per_step": step_bytes,
+                     "alu_bound_ms": t_alu, "hbm_bound_ms": t_hbm,
+                     "bound": "alu" if t_alu >= t_hbm else "hbm",
+                     "frac": max(t_alu, t_hbm) / ms,
+                     "note": "algorithmic flops of the six sweeps (halo excluded) at the measured "
+                             "FP32 FMA peak vs 120 B per cell-step at the measured HBM copy rate"}
     cpu_rate, cpu_s = oracle_sample(2)
     extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
     line = {
@@ -573,6 +593,7 @@ def run_ours(args, rank: int, world: int):
                        "Ek_rel_diff": abs(ek32 - ek64) / ek64},
         "t_reached": t_reached,
         "roofline": roofline,
+        "step_roofline": step_roofline,
         "cpu_baseline": {"value": cpu_rate, "unit": "Mcell-updates/s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": f"FP64 CPU oracle, 2 steps of Taylor-Green 32^3 "
