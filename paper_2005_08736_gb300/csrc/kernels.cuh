@@ -297,25 +297,41 @@ __global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
   int bad = 0;
   const int nx = g.n[0], ny = g.n[1];
   const T tr = T(rho_r), tp = T(p_r), tg = T(gamma), tg1 = T(gamma - 1.0);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int x = int(c % nx);
-    const long long r = c / nx;
-    const int y = int(r % ny), z = int(r / ny);
-    const long long pi = pad_index(g, x, y, z);
-    const T rho = tr + q[pi];
-    const T mx = q[g.P + pi], my = q[2 * g.P + pi], mz = q[3 * g.P + pi];
+  // Rows (y, z) of the interior, four per block and pass, x over the threads
+  // (coalesced, no 64-bit division per cell); the loads of the four rows are
+  // issued before any of them is used.
+  const int rows = ny * g.n[2];
+  auto cell = [&](T rho, T mx, T my, T mz, T E, int x, int y, int z) {
     const T inv = T(1) / rho;
     const T ke = T(0.5) * (mx * mx + my * my + mz * mz) * inv;
-    const T p = tp + tg1 * (q[4 * g.P + pi] - ke);
-    if (!(rho > T(0)) || !(p > T(0))) {
-      bad = 1;
-      continue;
+    const T p = tp + tg1 * (E - ke);
+    const bool ok = rho > T(0) && p > T(0);  // false for NaN too
+    bad |= !ok;
+    const T cs = tsqrt(ok ? tg * p * inv : T(1));
+    T b = fmin(wx[x + kGhost] / (tabs(mx * inv) + cs), wy[y + kGhost] / (tabs(my * inv) + cs));
+    b = fmin(b, wz[z + kGhost] / (tabs(mz * inv) + cs));
+    if (ok) best = fmin(best, b);
+  };
+  for (int row0 = 4 * blockIdx.x; row0 < rows; row0 += 4 * gridDim.x) {
+    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
+      const int x = x0 + threadIdx.x;
+      T v[4][5];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int row = row0 + k;
+        if (row < rows && x < nx) {
+          const long long pi = pad_index(g, x, row % ny, row / ny);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) v[k][c] = q[c * g.P + pi];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int row = row0 + k;
+        if (row < rows && x < nx)
+          cell(tr + v[k][0], v[k][1], v[k][2], v[k][3], v[k][4], x, row % ny, row / ny);
+      }
     }
-    const T cs = tsqrt(tg * p * inv);
-    best = fmin(best, wx[x + kGhost] / (tabs(mx * inv) + cs));
-    best = fmin(best, wy[y + kGhost] / (tabs(my * inv) + cs));
-    best = fmin(best, wz[z + kGhost] / (tabs(mz * inv) + cs));
   }
   double bd = warp_min(double(best));
   __shared__ double sm[32];
@@ -358,11 +374,13 @@ __global__ void __launch_bounds__(256) k_diag(const T* __restrict__ q, GridDev g
   double rmin = 1e300, pmin = 1e300;
   const int nx = g.n[0], ny = g.n[1];
   const double E_r = p_r / (gamma - 1.0);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int x = int(c % nx);
-    const long long r = c / nx;
-    const int y = int(r % ny), z = int(r / ny);
+  // Rows (y, z) of the interior spread over the blocks, x over the threads
+  // (coalesced, no 64-bit division per cell).
+  const int rows = ny * g.n[2];
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+#pragma unroll 2
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    const int y = row % ny, z = row / ny;
     const long long pi = pad_index(g, x, y, z);
     const double vol = double(wx[x + kGhost]) * double(wy[y + kGhost]) * double(wz[z + kGhost]);
     const double rho = rho_r + double(q[pi]);
@@ -444,12 +462,15 @@ __global__ void __launch_bounds__(256) k_massflux_sums(const T* __restrict__ q, 
                                                        double rho_r, double* __restrict__ part) {
   double s[3] = {0.0, 0.0, 0.0};
   const int nx = g.n[0], ny = g.n[1];
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int x = int(c % nx);
-    const long long r = c / nx;
-    const int y = int(r % ny), z = int(r / ny);
+  // Rows (y, z) of the interior spread over the blocks, x over the threads
+  // (coalesced, no 64-bit division per cell).
+  const int rows = ny * g.n[2];
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+#pragma unroll 2
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    const int y = row % ny, z = row / ny;
     const long long pi = pad_index(g, x, y, z);
+    const long long c = ((long long)z * ny + y) * nx + x;  // interior index
     const double vol = double(wx[x + kGhost]) * double(wy[y + kGhost]) * double(wz[z + kGhost]);
     // FP32: the stored value minus its compensation is the accumulated sum.
     const double c0 = comp ? double(comp[c]) : 0.0, c1 = comp ? double(comp[g.N + c]) : 0.0;
