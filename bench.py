@@ -240,10 +240,15 @@ def extra_workloads(steps: int):
     ens = Ensemble(sims)
     ens.step(2)
     t_ens = timed(lambda: ens.step(steps, sync=False), 1) / steps
-    t_seq = timed(lambda: [s.step(steps, sync=False) for s in sims], 1) / steps
+    # Sequential runs: each member advanced alone, one after another.
+    t_seq = timed(lambda: [s.step(steps, sync=True) for s in sims], 1) / steps
+    # Each member's own graph launched on its own stream without waiting (the
+    # streams may overlap on the device).
+    t_str = timed(lambda: [s.step(steps, sync=False) for s in sims], 1) / steps
     out["ensemble_24_isotropic_mixed"] = {
         "instances": 24, "cells": cells, "ensemble_ms_per_step": 1e3 * t_ens,
         "sequential_ms_per_step": 1e3 * t_seq, "speedup": t_seq / t_ens,
+        "member_streams_ms_per_step": 1e3 * t_str, "speedup_vs_member_streams": t_str / t_ens,
         "ensemble_mcups": cells / t_ens / 1e6}
     ens.close()
     for s in sims:
@@ -613,7 +618,7 @@ def run_ours(args, rank: int, world: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=256, help="grid size (profiling cases)")
