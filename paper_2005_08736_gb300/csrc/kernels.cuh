@@ -188,9 +188,11 @@ struct UpdateArgs {
 // One CTA per 32 x 8 cells of an x-y plane.  The x-face fluxes are stored y
 // fastest ([z][x][y]); the CTA stages its 33 x 8 x-faces through shared
 // memory so that both their loads and the per-cell reads are contiguous.
+// The kernel waits on memory; in FP32 its registers are held to 32 so that
+// eight CTAs (all 64 warps) fit an SM.
 constexpr int kUpdTX = 32, kUpdTY = 8;
 template <class T, int STAGE>
-__global__ void __launch_bounds__(kUpdTX * kUpdTY) k_update(UpdateArgs<T> a) {
+__global__ void __launch_bounds__(kUpdTX * kUpdTY, sizeof(T) == 4 ? 8 : 1) k_update(UpdateArgs<T> a) {
   constexpr int NV = STAGE == 1 ? 10 : 5;  // stage 2 needs dF only
   constexpr int V0 = STAGE == 1 ? 0 : 5;
   __shared__ T sfx[NV][kUpdTX + 1][kUpdTY];
