@@ -270,10 +270,19 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
   const long long cb = ax.index(g, c[0], c[1], c[2]);
   const long long sd = ax.sd;
   const T hl = wn[f - 1 + kGhost], hr = wn[f + kGhost];
-  const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
-  T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
-  if constexpr (is_char_mode<MODE>()) {
+  if constexpr (!is_char_mode<MODE>()) {
+    T qa[5][6];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const T* qv = q + ax.gv[i] * g.P + cb;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qa[i][k] = __ldg(qv + k * sd);
+    }
+    face_fields_cells<T, MODE, FLUX, NH>(qa, hl, hr, gas, h, ff);
+  } else {
     // Characteristic variables of Qm, the mean of the two cells beside the face.
+    const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
+    T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
     T qa[6][5], qm[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -304,34 +313,24 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
       D0[i] = (qa[1][i] - T(15) * qa[2][i] + T(15) * qa[3][i] - qa[4][i]) * r6;
       ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + h] = qm[i];
     }
-  } else {
-    T qa[5][6];
+    T Q0[5];
+    compat_dev(Ql, Qr, gas, Q0);
+    if constexpr (FLUX == FLUX_SMOOTH) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const T* qv = q + ax.gv[i] * g.P + cb;
+      for (int i = 0; i < 5; ++i) {
+        ff[i * NH + h] = Q0[i];
+        ff[(5 + i) * NH + h] = D0[i];
+      }
+    } else {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) qa[i][k] = __ldg(qv + k * sd);
-    }
-    face_fields_cells<T, MODE, FLUX, NH>(qa, hl, hr, gas, h, ff);
-    return;
-  }
-  T Q0[5];
-  compat_dev(Ql, Qr, gas, Q0);
-  if constexpr (FLUX == FLUX_SMOOTH) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      ff[i * NH + h] = Q0[i];
-      ff[(5 + i) * NH + h] = D0[i];
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      ff[i * NH + h] = Ql[i];
-      ff[(5 + i) * NH + h] = Qr[i];
-      ff[(10 + i) * NH + h] = Q0[i];
-      ff[(15 + i) * NH + h] = Dl[i];
-      ff[(20 + i) * NH + h] = Dr[i];
-      ff[(25 + i) * NH + h] = D0[i];
+      for (int i = 0; i < 5; ++i) {
+        ff[i * NH + h] = Ql[i];
+        ff[(5 + i) * NH + h] = Qr[i];
+        ff[(10 + i) * NH + h] = Q0[i];
+        ff[(15 + i) * NH + h] = Dl[i];
+        ff[(20 + i) * NH + h] = Dr[i];
+        ff[(25 + i) * NH + h] = D0[i];
+      }
     }
   }
 }
@@ -556,52 +555,52 @@ __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blo
       }
     } else if (PK && !(d == 0 && !ax.xt)) {
       if constexpr (PK) {
-      // Packed variant: one item per pair of adjacent points along P (the
-      // state is contiguous along P, so both points' cells are neighbours);
-      // pairs that reach past the grid's halo take the per-point path.
-      static_assert(HP % 2 == 0, "point pairs must not straddle a row");
-      constexpr int NH2 = NH / 2;
-      for (int it = tid; it < NL * NH2; it += NT) {
-        const int l = it / NH2, h = 2 * (it % NH2);
-        const int f = fb + l;
-        const int hp = h % HP, hs = h / HP;
-        const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
-        T* ff = ffb + l * NFF * NH;
-        const bool ok0 = f < f1 && Pc <= nP + 1 && Sc <= nS + 1;
-        const bool ok1 = ok0 && Pc + 1 <= nP + 1;
-        if (ok1) {
-          // Cell f-3 along d at (Pc, Sc): P = y, S = z for d = x; P = x otherwise.
-          const int cx = d == 0 ? f - 3 : Pc;
-          const int cy = d == 0 ? Pc : (d == 1 ? f - 3 : Sc);
-          const int cz = d == 2 ? f - 3 : Sc;
-          const long long cb = ax.index(a.g, cx, cy, cz);
-          float2 qk[5][6];
+        // Packed variant: one item per pair of adjacent points along P (the
+        // state is contiguous along P, so both points' cells are neighbours);
+        // pairs that reach past the grid's halo take the per-point path.
+        static_assert(HP % 2 == 0, "point pairs must not straddle a row");
+        constexpr int NH2 = NH / 2;
+        for (int it = tid; it < NL * NH2; it += NT) {
+          const int l = it / NH2, h = 2 * (it % NH2);
+          const int f = fb + l;
+          const int hp = h % HP, hs = h / HP;
+          const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+          T* ff = ffb + l * NFF * NH;
+          const bool ok0 = f < f1 && Pc <= nP + 1 && Sc <= nS + 1;
+          const bool ok1 = ok0 && Pc + 1 <= nP + 1;
+          if (ok1) {
+            // Cell f-3 along d at (Pc, Sc): P = y, S = z for d = x; P = x otherwise.
+            const int cx = d == 0 ? f - 3 : Pc;
+            const int cy = d == 0 ? Pc : (d == 1 ? f - 3 : Sc);
+            const int cz = d == 2 ? f - 3 : Sc;
+            const long long cb = ax.index(a.g, cx, cy, cz);
+            float2 qk[5][6];
 #pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            const T* qv = a.q + ax.gv[i] * a.g.P + cb;
+            for (int i = 0; i < 5; ++i) {
+              const T* qv = a.q + ax.gv[i] * a.g.P + cb;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) qk[i][k] = make_float2(__ldg(qv + k * ax.sd), __ldg(qv + k * ax.sd + 1));
-          }
-          float2 Q0[5], D0[5];
-          face_fields_smooth_linear_x2(qk, a.wn[f - 1 + kGhost], a.wn[f + kGhost], a.gas, Q0, D0);
+              for (int k = 0; k < 6; ++k) qk[i][k] = make_float2(__ldg(qv + k * ax.sd), __ldg(qv + k * ax.sd + 1));
+            }
+            float2 Q0[5], D0[5];
+            face_fields_smooth_linear_x2(qk, a.wn[f - 1 + kGhost], a.wn[f + kGhost], a.gas, Q0, D0);
 #pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            *reinterpret_cast<float2*>(ff + i * NH + h) = Q0[i];
-            *reinterpret_cast<float2*>(ff + (5 + i) * NH + h) = D0[i];
-          }
-        } else {
+            for (int i = 0; i < 5; ++i) {
+              *reinterpret_cast<float2*>(ff + i * NH + h) = Q0[i];
+              *reinterpret_cast<float2*>(ff + (5 + i) * NH + h) = D0[i];
+            }
+          } else {
 #pragma unroll 1
-          for (int e2 = 0; e2 < 2; ++e2) {
-            const bool ok = e2 == 0 ? ok0 : (f < f1 && Pc + 1 <= nP + 1 && Sc <= nS + 1);
-            if (ok) {
-              face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc + e2, Sc, h + e2, ff);
-            } else {
+            for (int e2 = 0; e2 < 2; ++e2) {
+              const bool ok = e2 == 0 ? ok0 : (f < f1 && Pc + 1 <= nP + 1 && Sc <= nS + 1);
+              if (ok) {
+                face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc + e2, Sc, h + e2, ff);
+              } else {
 #pragma unroll 1
-              for (int k = 0; k < NFF; ++k) ff[k * NH + h + e2] = T(0);
+                for (int k = 0; k < NFF; ++k) ff[k * NH + h + e2] = T(0);
+              }
             }
           }
         }
-      }
       }
     } else
     for (int it = tid; it < NL * NH; it += NT) {
