@@ -199,11 +199,12 @@ def extra_workloads(steps: int):
     cfg = iso_cfg(256, 1)
     sim = Simulation(cfg)
     sim.init_primitive(inputs.isotropic(256, 0))
+    iso_tune = sim.autotune()
     sim.step(3)
     s_per = timed(lambda: sim.step(steps, sync=False), 1) / steps
     out["isotropic_256_wenoz_full_fp32"] = {
         "ms_per_step": 1e3 * s_per, "mcups": cfg.cells / s_per / 1e6,
-        "kernel_ms_per_step": sim.profile_step()}
+        "kernel_ms_per_step": sim.profile_step(), "autotune": iso_tune}
     sim.close()
     # Channel (Sec. 3.3): 128 x 128 x 96, tanh b = 2, walls, f_x = 2.93e-3, Ma 0.1.
     ccfg = Config(128, 128, 96, lx=2 * 3.141592653589793, ly=2.0, y0=-1.0, lz=3.141592653589793,
@@ -211,10 +212,11 @@ def extra_workloads(steps: int):
                   force_x=2.93e-3, prec=1, recon=0, flux=0, prandtl=0.72)
     sim = Simulation(ccfg)
     sim.init_primitive(inputs.channel(128, 128, 96, 0))
+    ch_tune = sim.autotune()
     sim.step(3)
     s_per = timed(lambda: sim.step(steps, sync=False), 1) / steps
     out["channel_128x128x96_fp32"] = {"ms_per_step": 1e3 * s_per,
-                                      "mcups": ccfg.cells / s_per / 1e6}
+                                      "mcups": ccfg.cells / s_per / 1e6, "autotune": ch_tune}
     sim.close()
     # Adjoint / forward time ratio at 64^3.
     for prec, name in ((0, "fp64"), (1, "fp32")):

@@ -164,6 +164,28 @@ def test_channel_constant_mass_flux_matches_oracle(prec, tol):
     assert d["mom"][0] / vol == pytest.approx(1.02, rel=1e-12 if prec == 0 else 1e-6)
 
 
+@pytest.mark.parametrize("variant", [1, 3])
+def test_channel_fp32_tile_variants_match_oracle(variant):
+    """The wider and the packed sweep tiles with walls, the stretched y grid and
+    the body force (FP32, ragged 40 x 24 x 18 grid: several tiles and a ragged
+    tail in every direction)."""
+    n = (40, 24, 18)
+    cfg = channel_cfg(*n, prec=1)
+    prim = channel_prim(*n)
+    sim = Simulation(cfg)
+    sim._call(sim.lib.hgks_set_sweep_shape(sim.h, variant, 0))
+    sim.init_primitive(prim)
+    sim.step(3)
+    gpu = sim.state()
+    sim.close()
+    o = oracle.Solver(oracle_cfg(cfg))
+    o.set_state(oracle.conservative(prim, cfg.gamma))
+    o.step(3)
+    err = rel_linf(gpu, o.state())
+    print(f"channel FP32 variant {variant}: relative L-inf error against the oracle {err:.3e}")
+    assert err <= FP32_TOL, err
+
+
 def test_minimum_grid_and_fixed_dt():
     cfg = taylor_green_config(6, "fp64", "weno-z", "full")
     gpu, ref, t, to = run_both(cfg, inputs.taylor_green(6), 2, dt=0.01)
