@@ -435,6 +435,22 @@ def config_dict():
             "l2": "inputs larger than L2: the FP32 state alone is 335 MB per step"}
 
 
+def job_rate(seconds_local: float, cells_per_rank: int, dist=None, device: str = "cpu"):
+    """Whole-job rate of independent replicas, one per rank: the slowest
+    rank's time per step (max over ranks) and the cells all ranks advanced per
+    second, in Mcell-updates/s.  `dist` is torch.distributed with an
+    initialised process group (None for one process); `device` holds the
+    reduction tensor ("cuda" for NCCL, "cpu" for gloo)."""
+    world, t = 1, seconds_local
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        x = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, world * cells_per_rank / t / 1e6
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_2005_08736_gb300 import build as cuda_build
@@ -480,12 +496,8 @@ def run_ours(args, rank: int, world: int):
         stop.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = start.elapsed_time(stop) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cfg.cells / (ms * 1e-3) / 1e6
+    s_step, value = job_rate(start.elapsed_time(stop) / args.steps * 1e-3, cfg.cells, dist, "cuda")
+    ms = 1e3 * s_step
     t_reached = sim.step(0)  # sync + non-physical check
 
     # Kernel classes of one step (CUDA events around each launch).
@@ -536,7 +548,7 @@ def run_ours(args, rank: int, world: int):
     e2e_s = (time.perf_counter() - t0) / args.steps
     barrier()
     sim.close()
-    e2e_value = world * cfg.cells / e2e_s / 1e6
+    e2e_s, e2e_value = job_rate(e2e_s, cfg.cells, dist, "cuda")
 
     if rank != 0:
         if dist is not None:
