@@ -140,6 +140,17 @@ def oracle_sample(steps: int, n: int = 32):
     return n ** 3 * steps / el / 1e6, el
 
 
+def oracle_sample_one_core(n: int = 32):
+    """oracle_sample(1, n) in a child process restricted to one OpenMP thread;
+    (Mcell-upd/s, seconds)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = f"import bench, json; print(json.dumps(bench.oracle_sample(1, {n})))"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=600, check=True)
+    rate, secs = json.loads(out.stdout.strip().splitlines()[-1])
+    return rate, secs
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -598,6 +609,7 @@ def run_ours(args, rank: int, world: int):
                      "note": "algorithmic flops of the six sweeps (halo excluded) at the measured "
                              "FP32 FMA peak vs 120 B per cell-step at the measured HBM copy rate"}
     cpu_rate, cpu_s = oracle_sample(2)
+    cpu1_rate, cpu1_s = oracle_sample_one_core()
     extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
@@ -616,7 +628,9 @@ def run_ours(args, rank: int, world: int):
         "cpu_baseline": {"value": cpu_rate, "unit": "Mcell-updates/s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": f"FP64 CPU oracle, 2 steps of Taylor-Green 32^3 "
-                                   f"({cpu_s:.1f} s), same physics and scheme"},
+                                   f"({cpu_s:.1f} s), same physics and scheme",
+                         "one_core": {"value": cpu1_rate, "cores": 1,
+                                      "sample": f"1 step of Taylor-Green 32^3 ({cpu1_s:.1f} s)"}},
         "e2e": {"value": e2e_value, "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": int(prim.nbytes), "d2h_bytes_per_step": 96},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
