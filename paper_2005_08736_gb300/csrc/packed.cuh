@@ -7,7 +7,7 @@
 // In the last phase the two halves are the two t1 Gauss abscissae of one
 // face; the shared-memory layout of the t1 pass keeps them adjacent, so one
 // 64-bit load fetches both.  In the face-field phase they are two adjacent
-// points of a face layer.  The formulas are those of recon.cuh (linear tangential
+// points of a face layer (compat.cuh).  The formulas are those of recon.cuh (linear tangential
 // reconstruction) and physics.cuh (smooth flux), evaluated pairwise; only the
 // rounding of the fused operations can differ from the scalar code.
 #pragma once
@@ -153,72 +153,6 @@ __device__ __forceinline__ void flux_smooth_x2(const PointStateX2& st, const Gas
 #pragma unroll
     for (int i = 0; i < 5; ++i) Fs[i] += F[i].x + F[i].y;
   }
-}
-
-// Half-space sign moments of the compatibility state (physics.cuh,
-// sign_moments) for two states at once:
-// S = rho (D0, D1, V D0, W D0, (D2 + D0 (V^2 + W^2 + (K+2) theta))/2) with
-// D0 = erf(sqrt(lam) U), D1 = U D0 + exp(-lam U^2) sqrt(2 theta / pi),
-// D2 = U D1 + theta D0.  erf, exp and the square roots per half.
-__device__ __forceinline__ void sign_moments_x2(const float2 dq[5], const Gas<float>& g, float2 S[5]) {
-  const float2 rho = add2(bc2(g.rho_r), dq[0]);
-  const float2 inv = rcp2(rho);
-  const float2 U = mul2(dq[1], inv), V = mul2(dq[2], inv), W = mul2(dq[3], inv);
-  const float2 ke2 = fma2(dq[1], U, fma2(dq[2], V, mul2(dq[3], W)));
-  const float2 dp = mul2(bc2(g.gm1), fma2(ke2, bc2(-0.5f), dq[4]));
-  const float2 theta = mul2(add2(bc2(g.p_r), dp), inv);
-  const float2 lam = mul2(bc2(0.5f), rcp2(theta));
-  const float2 sl = make_float2(sqrtf(lam.x), sqrtf(lam.y));
-  const float2 x = mul2(sl, U);
-  const float2 D0 = make_float2(erff(x.x), erff(x.y));
-  const float2 tt = add2(theta, theta);
-  const float2 ex = make_float2(expf(-x.x * x.x) * sqrtf(tt.x), expf(-x.y * x.y) * sqrtf(tt.y));
-  const float2 D1 = fma2(U, D0, mul2(ex, bc2(0.5641895835477563f)));
-  const float2 D2 = fma2(U, D1, mul2(theta, D0));
-  S[0] = mul2(rho, D0);
-  S[1] = mul2(rho, D1);
-  const float2 rD0 = S[0];
-  S[2] = mul2(rD0, V);
-  S[3] = mul2(rD0, W);
-  const float2 vw = fma2(V, V, fma2(W, W, mul2(bc2(g.K + 2.f), theta)));
-  S[4] = mul2(mul2(bc2(0.5f), rho), fma2(D0, vw, D2));
-}
-
-// Face fields of the smooth flux (Q0 and its normal slope) at two adjacent
-// points of a face layer: qk[i][k] = variable i of cell f-3+k at both points
-// (conservative variables, linear weights; face_fields_cells in sweep.cuh).
-__device__ __forceinline__ void face_fields_smooth_linear_x2(const float2 qk[5][6], float hl, float hr,
-                                                             const Gas<float>& g, float2 Q0[5],
-                                                             float2 D0[5]) {
-  const float r6 = 1.f / (6.f * (hl + hr));
-  const float c60 = 1.f / 60.f;
-  float2 Ql[5], Qr[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float2* q = qk[i];
-    // WENO5 end values with the optimal weights: (2, -13, 47, 27, -3)/60.
-    float2 t = mul2(bc2(2.f), q[0]);
-    t = fma2(bc2(-13.f), q[1], t);
-    t = fma2(bc2(47.f), q[2], t);
-    t = fma2(bc2(27.f), q[3], t);
-    t = fma2(bc2(-3.f), q[4], t);
-    Ql[i] = mul2(t, bc2(c60));
-    float2 u = mul2(bc2(2.f), q[5]);
-    u = fma2(bc2(-13.f), q[4], u);
-    u = fma2(bc2(47.f), q[3], u);
-    u = fma2(bc2(27.f), q[2], u);
-    u = fma2(bc2(-3.f), q[1], u);
-    Qr[i] = mul2(u, bc2(c60));
-    float2 w = sub2(q[1], mul2(bc2(15.f), q[2]));
-    w = fma2(bc2(15.f), q[3], w);
-    D0[i] = mul2(sub2(w, q[4]), bc2(r6));
-  }
-  float2 Sl[5], Sr[5];
-  sign_moments_x2(Ql, g, Sl);
-  sign_moments_x2(Qr, g, Sr);
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-    Q0[i] = fma2(bc2(0.5f), add2(Ql[i], Qr[i]), mul2(bc2(0.5f), sub2(Sl[i], Sr[i])));
 }
 
 }  // namespace hgks

@@ -19,6 +19,7 @@
 #pragma once
 
 #include "charvars.cuh"
+#include "compat.cuh"
 #include "kernels.cuh"
 #include "packed.cuh"
 
@@ -187,7 +188,7 @@ __device__ __forceinline__ void face_fields_cells(const T qa[5][6], T hl, T hr, 
     D0[i] = (q1 - T(15) * q2 + T(15) * q3 - q4) * r6;
   }
   T Q0[5];
-  compat_dev(Ql, Qr, gas, Q0);
+  compat_state(Ql, Qr, gas, Q0);
   if constexpr (FLUX == FLUX_SMOOTH) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -314,7 +315,7 @@ __device__ __forceinline__ void face_fields_item(const T* __restrict__ q, const 
       ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + h] = qm[i];
     }
     T Q0[5];
-    compat_dev(Ql, Qr, gas, Q0);
+    compat_state(Ql, Qr, gas, Q0);
     if constexpr (FLUX == FLUX_SMOOTH) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
