@@ -43,7 +43,8 @@ LAUNCHES_PER_STEP = 19
 # 2 ffma) that ncu counted on Taylor-Green 128^3 for the three scalar tile
 # variants, whose halo factors differ
 # (profiles/k_sweep_fp32_smooth_taylor_green_128.md).  The same per face for
-# every tile variant and grid.
+# every tile variant and grid; counted with the direct form of the
+# compatibility state (its FP32 midpoint-rule form adds work not counted).
 ALG_FLOPS_PER_FACE = 1990.0
 # The same for the stage-2 sweep (dF only): 1841 per face (331 + 214 + 1296,
 # from the stage-2 counts of the same three variants).
