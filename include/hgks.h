@@ -168,6 +168,31 @@ typedef struct {
  * Allocates its FP64 partial-sum buffers on the first call. */
 hgks_status hgks_turbulence_stats(hgks_ctx* ctx, hgks_turbulence* out);
 
+/* Mean-flow statistics of the wall-bounded channel (Sec. 3.3), from the
+ * current state, instantaneous (time averaging is the caller's): plane
+ * averages over x and z of each y row, and from them
+ *   tau_w = mu(T_wall) d<U>/dn at each wall (the paper's tau_wall =
+ *     dU/dy|wall with the viscosity its dimensions need), d<U>/dn from the
+ *     quadratic with <U> = 0 at the wall whose averages over the two
+ *     wall-adjacent cells equal theirs;
+ *   u_tau = sqrt(tau_w / rho_w), Re_tau = rho_w u_tau H / mu_w with H = ly/2
+ *     and rho_w the mean of the two wall-adjacent rows' <rho>;
+ *   U_b = (1/ly) int <U> dy, rho_b likewise, U_c = <U> at the mid-plane (the
+ *     cubic through the averages of the four cells nearest to it),
+ *     nu = mu_w / rho_b, Re_c = U_c H / nu, Re_b = U_b 2H / nu,
+ *     C_f = tau_w / (rho_b U_b^2 / 2).
+ * profiles (HOST, may be NULL): [8][ny] plane means of rho, rho U, U, V, W,
+ * U V, U U and T = p / rho per y row.  Needs bc_y = HGKS_BC_WALL_ISOTHERMAL
+ * (else E_UNSUPPORTED).  Allocates a small device buffer on the first call;
+ * synchronises. */
+typedef struct {
+  double t;                       /* time of the state */
+  double tau_w, tau_w_lower, tau_w_upper;
+  double rho_w, mu_w, u_tau, Re_tau;
+  double U_b, U_c, rho_b, Re_b, Re_c, C_f;
+} hgks_channel;
+hgks_status hgks_channel_stats(hgks_ctx* ctx, double* profiles, hgks_channel* out);
+
 /* Ensembles (no counterpart in the paper): a batch of independent contexts,
  * e.g. instances of uneven sizes, advanced together.  hgks_ensemble_create
  * takes n distinct contexts on the same device, each on its own stream (the

@@ -24,7 +24,7 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_adjoint_step", "hgks_profile_step", "hgks_step_noalloc", "hgks_last_error",
            "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
            "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape",
-           "hgks_turbulence_stats", "hgks_measure_fp_peaks"]
+           "hgks_turbulence_stats", "hgks_measure_fp_peaks", "hgks_channel_stats"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 
 
@@ -64,6 +64,12 @@ class HgksTurbulence(ctypes.Structure):
         "t", "Ek", "K", "zeta", "eps1", "eps2", "eps3", "rho_mean", "rho_rms", "u_rms", "Su", "Fu",
         "eps_s", "eps_d", "p_theta", "theta_rms", "omega_rms")] + [
         ("du2", ctypes.c_double * 3), ("du3", ctypes.c_double * 3), ("du4", ctypes.c_double * 3)]
+
+
+class HgksChannel(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "t", "tau_w", "tau_w_lower", "tau_w_upper", "rho_w", "mu_w", "u_tau", "Re_tau",
+        "U_b", "U_c", "rho_b", "Re_b", "Re_c", "C_f")]
 
 
 _lock = threading.Lock()
@@ -112,6 +118,7 @@ def load(path: str | None = None):
         L.hgks_ensemble_last_error.restype = ctypes.c_char_p
         L.hgks_step_noalloc.argtypes = [pcfg, vp, i, d, vp]
         L.hgks_measure_fp_peaks.argtypes = [vp, pd]
+        L.hgks_channel_stats.argtypes = [vp, pd, ctypes.POINTER(HgksChannel)]
         L.hgks_last_error.argtypes = [vp]
         L.hgks_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:

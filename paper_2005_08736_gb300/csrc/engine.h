@@ -40,6 +40,7 @@ struct Engine {
   void* adj_wdL = nullptr;
   double* turb_part = nullptr;  // turbulence statistics: per-block partials
   double* turb_out = nullptr;   // and the final sums (allocated on first use)
+  double* chan_out = nullptr;   // channel statistics: kChanSums sums per y row (first use)
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
@@ -71,6 +72,10 @@ enum TurbSum {
   TS_DU4 = TS_DU3 + 3,
   kTurbSums = TS_DU4 + 3
 };
+
+// Channel statistics (turbulence.cuh, k_channel_rows): plane sums per y row
+// of rho, rho U, U, V, W, U V, U U, T.
+constexpr int kChanSums = 8;
 
 // Kernel classes timed by hgks_profile_step (order of its output array).
 enum KernelClass {
@@ -105,6 +110,7 @@ struct Probe {
 // Kernel sequences, implemented per floating type in kernels_f32.cu / kernels_f64.cu.
 template <class T> cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_turbulence(const Engine& e);
+template <class T> cudaError_t enqueue_channel_rows(const Engine& e);
 template <class T> cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
 // The stage-1 sweep of direction d on e.q alone (tuning).

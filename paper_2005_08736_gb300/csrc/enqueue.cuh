@@ -252,6 +252,15 @@ cudaError_t enqueue_turbulence(const Engine& e) {
   return cudaGetLastError();
 }
 
+// Channel plane averages: kChanSums FP64 sums per y row into e.chan_out.
+template <class T>
+cudaError_t enqueue_channel_rows(const Engine& e) {
+  const hgks_config& c = e.cfg;
+  k_channel_rows<T><<<e.n[1], 256, 0, e.stream>>>(static_cast<const T*>(e.q), grid_of(e), c.rho_ref,
+                                                  c.p_ref, c.gamma - 1.0, e.chan_out);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative) {
   k_from_prim<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
@@ -362,6 +371,7 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   template cudaError_t enqueue_sweep_only<T>(const Engine&, int);            \
   template cudaError_t enqueue_diag<T>(const Engine&);                       \
   template cudaError_t enqueue_turbulence<T>(const Engine&);                 \
+  template cudaError_t enqueue_channel_rows<T>(const Engine&);               \
   template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
   template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);           \
   template cudaError_t enqueue_adjoint_step<T>(const Engine&, const double*, double*);

@@ -101,7 +101,8 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 void free_all(hgks::Engine& e) {
   void* ptrs[] = {e.q, e.qs, e.qx, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
-                  e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out};
+                  e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out,
+                  e.chan_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -380,6 +381,121 @@ hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
   out->rho_min = r[6];
   out->p_min = r[7];
   out->force_x = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX ? scal[3] : e.cfg.force_x;
+  return HGKS_OK;
+}
+
+// Linear solve of a small dense system by Gaussian elimination with partial
+// pivoting (n <= 4): the cell-average fits of the channel statistics.
+static void solve_small(int n, double* A, double* b) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+    for (int k = 0; k < n; ++k) std::swap(A[col * n + k], A[piv * n + k]);
+    std::swap(b[col], b[piv]);
+    for (int r = col + 1; r < n; ++r) {
+      const double f = A[r * n + col] / A[col * n + col];
+      for (int k = col; k < n; ++k) A[r * n + k] -= f * A[col * n + k];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double t = b[r];
+    for (int k = r + 1; k < n; ++k) t -= A[r * n + k] * b[k];
+    b[r] = t / A[r * n + r];
+  }
+}
+
+// Mean over [a, b] of s^p.
+static double mean_pow(double a, double b, int p) {
+  return (std::pow(b, p + 1) - std::pow(a, p + 1)) / ((p + 1) * (b - a));
+}
+
+// d<U>/ds at a wall (s = distance from it) from the averages U1, U2 of the
+// first two cells, [0, w1] and [w1, w1 + w2]: the quadratic a s + b s^2 with
+// U = 0 at the wall whose cell averages are U1 and U2; returns a.
+static double wall_gradient(double w1, double w2, double U1, double U2) {
+  double A[4] = {mean_pow(0, w1, 1), mean_pow(0, w1, 2), mean_pow(w1, w1 + w2, 1), mean_pow(w1, w1 + w2, 2)};
+  double r[2] = {U1, U2};
+  solve_small(2, A, r);
+  return r[0];
+}
+
+hgks_status hgks_channel_stats(hgks_ctx* c, double* profiles, hgks_channel* out) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  const hgks_config& cf = e.cfg;
+  if (cf.bc_y != HGKS_BC_WALL_ISOTHERMAL)
+    return fail(c, HGKS_E_UNSUPPORTED, "channel statistics need the isothermal walls in y");
+  const int ny = e.n[1], NS = hgks::kChanSums;
+  if (!e.chan_out) HGKS_CHECK(c, cudaMalloc((void**)&e.chan_out, sizeof(double) * NS * ny));
+  const bool f32 = cf.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_channel_rows<float>(e) : hgks::enqueue_channel_rows<double>(e));
+  std::vector<double> m(size_t(NS) * ny);
+  double scal[3];
+  HGKS_CHECK(c, cudaMemcpyAsync(m.data(), e.chan_out, m.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  const double cells = double(e.n[0]) * e.n[2];
+  for (double& v : m) v /= cells;  // plane means
+  if (profiles) std::memcpy(profiles, m.data(), m.size() * sizeof(double));
+  const std::vector<double> w = widths(cf, 1);  // includes 3 ghosts per side
+  auto wy = [&](int j) { return w[j + 3]; };
+  const double* rho = &m[0];
+  const double* U = &m[2 * ny];
+  // Wall shear stress (Sec. 3.3): tau_w = mu(T_wall) d<U>/dn at each wall.
+  const double a_lo = wall_gradient(wy(0), wy(1), U[0], U[1]);
+  const double a_hi = wall_gradient(wy(ny - 1), wy(ny - 2), U[ny - 1], U[ny - 2]);
+  const double mu_w = cf.visc == HGKS_VISC_POWER ? cf.mu_ref * std::pow(cf.T_wall / cf.T_ref, cf.visc_exp)
+                                                 : cf.mu_ref;
+  out->t = scal[1];
+  out->tau_w_lower = mu_w * a_lo;
+  out->tau_w_upper = mu_w * a_hi;
+  out->tau_w = 0.5 * (out->tau_w_lower + out->tau_w_upper);
+  out->mu_w = mu_w;
+  out->rho_w = 0.5 * (rho[0] + rho[ny - 1]);
+  out->u_tau = std::sqrt(std::fmax(out->tau_w, 0.0) / out->rho_w);
+  const double H = 0.5 * cf.ly;
+  out->Re_tau = out->rho_w * out->u_tau * H / mu_w;
+  // Bulk means over the height.
+  double ub = 0.0, rb = 0.0;
+  for (int j = 0; j < ny; ++j) {
+    ub += U[j] * wy(j);
+    rb += rho[j] * wy(j);
+  }
+  out->U_b = ub / cf.ly;
+  out->rho_b = rb / cf.ly;
+  // Centreline <U>: the cubic whose averages over the four cells nearest the
+  // mid-plane equal theirs, at the mid-plane.
+  std::vector<double> yf(ny + 1);
+  yf[0] = cf.y0;
+  for (int j = 0; j < ny; ++j) yf[j + 1] = yf[j] + wy(j);
+  const double yc = cf.y0 + H;
+  int j0 = 0;
+  double best = 1e300;
+  for (int j = 0; j + 3 < ny; ++j) {  // the window of four cells centred best on yc
+    const double d = std::fabs(0.5 * (yf[j] + yf[j + 4]) - yc);
+    if (d < best) {
+      best = d;
+      j0 = j;
+    }
+  }
+  if (ny >= 4) {
+    double A[16], r[4];
+    for (int k = 0; k < 4; ++k) {
+      for (int pw = 0; pw < 4; ++pw) A[k * 4 + pw] = mean_pow(yf[j0 + k] - yc, yf[j0 + k + 1] - yc, pw);
+      r[k] = U[j0 + k];
+    }
+    solve_small(4, A, r);
+    out->U_c = r[0];
+  } else {
+    out->U_c = U[ny / 2];
+  }
+  const double nu = mu_w / out->rho_b;
+  out->Re_c = out->U_c * H / nu;
+  out->Re_b = out->U_b * 2.0 * H / nu;
+  out->C_f = out->tau_w / (0.5 * out->rho_b * out->U_b * out->U_b);
   return HGKS_OK;
 }
 

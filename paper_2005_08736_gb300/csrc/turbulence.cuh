@@ -147,4 +147,52 @@ static __global__ void __launch_bounds__(256) k_turb_final(const double* __restr
   }
 }
 
+// Plane averages of a wall-bounded channel (Sec. 3.3): one block per y row,
+// FP64 sums over the x-z plane of rho, rho U, U, V, W, U V, U U and
+// T = p / rho (interior cells; x and z are uniform and periodic, so the
+// plane mean is the plain mean).  out[k * ny + y] = sum k of row y.
+template <class T>
+__global__ void __launch_bounds__(256) k_channel_rows(const T* __restrict__ q, GridDev g, double rho_r,
+                                                      double p_r, double gm1, double* __restrict__ out) {
+  const int y = blockIdx.x;
+  const int nx = g.n[0], nz = g.n[2];
+  double s[kChanSums];
+#pragma unroll
+  for (int k = 0; k < kChanSums; ++k) s[k] = 0.0;
+  for (int c = threadIdx.x; c < nx * nz; c += blockDim.x) {
+    const long long pi = pad_index(g, c % nx, y, c / nx);
+    const double rho = rho_r + double(q[pi]);
+    const double mx = double(q[g.P + pi]), my = double(q[2 * g.P + pi]), mz = double(q[3 * g.P + pi]);
+    const double inv = 1.0 / rho;
+    const double U = mx * inv, V = my * inv, W = mz * inv;
+    // p - p_r = (gamma - 1)(dE - |m|^2 / (2 rho)); the reference is at rest.
+    const double p = p_r + gm1 * (double(q[4 * g.P + pi]) - 0.5 * (mx * U + my * V + mz * W));
+    s[0] += rho;
+    s[1] += mx;
+    s[2] += U;
+    s[3] += V;
+    s[4] += W;
+    s[5] += U * V;
+    s[6] += U * U;
+    s[7] += p * inv;
+  }
+  __shared__ double sm[kChanSums][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kChanSums; ++k) {
+    const double t = warp_sum(s[k]);
+    if (lane == 0) sm[k][wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kChanSums; ++k) {
+      double t = lane < nw ? sm[k][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) out[k * g.n[1] + y] = t;
+    }
+  }
+}
+
 }  // namespace hgks

@@ -212,6 +212,36 @@ class Simulation:
                 out[f"{k}_{a}"] = getattr(d, k)[i]
         return out
 
+    def channel_stats(self) -> dict:
+        """Mean-flow statistics of the wall-bounded channel (Sec. 3.3,
+        hgks_channel_stats): tau_w, u_tau, Re_tau, U_b, U_c, Re_b, Re_c, C_f and
+        the plane-mean profiles per y row, with y+ (distance to the nearer wall
+        in wall units) and U+ = <U>/u_tau, <u'v'>+ = (<UV> - <U><V>)/u_tau^2."""
+        out = _lib.HgksChannel()
+        ny = self.cfg.ny
+        prof = np.empty((8, ny))
+        self._call(self.lib.hgks_channel_stats(
+            self.h, prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out)))
+        res = {k: getattr(out, k) for k, _ in _lib.HgksChannel._fields_}
+        names = ("rho", "rhoU", "U", "V", "W", "UV", "UU", "T")
+        res["profiles"] = dict(zip(names, prof))
+        faces = self.cfg.y0 + np.concatenate([[0.0], np.cumsum(self._y_widths())])
+        yc = 0.5 * (faces[1:] + faces[:-1])
+        dist = np.minimum(yc - self.cfg.y0, self.cfg.y0 + self.cfg.ly - yc)
+        ut = res["u_tau"]
+        res["y"] = yc
+        res["y_plus"] = res["rho_w"] * ut * dist / res["mu_w"]
+        res["U_plus"] = prof[2] / ut
+        res["uv_plus"] = (prof[5] - prof[2] * prof[3]) / (ut * ut)
+        return res
+
+    def _y_widths(self) -> np.ndarray:
+        c = self.cfg
+        if not c.y_stretch:
+            return np.full(c.ny, c.ly / c.ny)
+        from . import inputs
+        return np.diff(inputs.channel_faces(c.ny, c.stretch_b))
+
 
 class Ensemble:
     """Independent simulations advanced by one CUDA graph launch per step."""

@@ -50,8 +50,9 @@ def test_struct_layouts_match_the_header():
 #include <stddef.h>
 #include "hgks.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(hgks_config), offsetof(hgks_config, prec),
-         offsetof(hgks_config, p_ref), sizeof(hgks_diag), offsetof(hgks_diag, step));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hgks_config), offsetof(hgks_config, prec),
+         offsetof(hgks_config, p_ref), sizeof(hgks_diag), offsetof(hgks_diag, step),
+         sizeof(hgks_turbulence), sizeof(hgks_channel), offsetof(hgks_channel, C_f));
   return 0;
 }
 '''
@@ -64,7 +65,8 @@ int main(void) {
                                                check=True).stdout.split()]
     assert vals == [ctypes.sizeof(_lib.HgksConfig), _lib.HgksConfig.prec.offset,
                     _lib.HgksConfig.p_ref.offset, ctypes.sizeof(_lib.HgksDiag),
-                    _lib.HgksDiag.step.offset]
+                    _lib.HgksDiag.step.offset, ctypes.sizeof(_lib.HgksTurbulence),
+                    ctypes.sizeof(_lib.HgksChannel), _lib.HgksChannel.C_f.offset]
 
 
 @pytest.mark.parametrize("field,value", [("nx", 5), ("gamma", 1.0), ("prandtl", 0.0), ("cfl", -1.0),
