@@ -322,6 +322,24 @@ def kinetic_energy(q: torch.Tensor, cfg: Config) -> torch.Tensor:
     return ke.mean() / cfg.rho_ref
 
 
+def total_stress_residual(stats: dict) -> tuple[np.ndarray, np.ndarray]:
+    """The stationarity check of the channel (Sec. 3.3): in a statistically
+    steady channel the total stress is linear,
+        dU+/dY+ - <u'v'>+ = 1 - Y+/Re_tau,
+    so the residual dU+/dY+ - <u'v'>+ - (1 - Y+/Re_tau) vanishes.  Evaluated
+    on the lower half of the channel from the statistics of
+    Simulation.channel_stats (dU/dy by second-order differences of the row
+    means on the stretched grid).  Returns (Y+, residual)."""
+    y, U = stats["y"], stats["profiles"]["U"]
+    lower = y < y[0] + 0.5 * (y[-1] - y[0]) + 1e-12
+    ut, mu, rho = stats["u_tau"], stats["mu_w"], stats["rho_w"]
+    dudy = np.gradient(U, y)
+    dUp_dYp = mu * dudy / (rho * ut * ut)
+    yp = stats["y_plus"]
+    res = dUp_dYp - stats["uv_plus"] - (1.0 - yp / stats["Re_tau"])
+    return yp[lower], res[lower]
+
+
 def measure_fp_peaks(stream: torch.cuda.Stream | None = None) -> dict:
     """Measured FMA throughput of the current GPU in TFLOP/s: FP32, packed
     FP32 pairs and FP64 (hgks_measure_fp_peaks)."""
