@@ -117,6 +117,12 @@ hgks_status hgks_init_conservative(hgks_ctx* ctx, const double* cons, int is_hos
  * is_host != 0. */
 hgks_status hgks_get_state(hgks_ctx* ctx, double* cons_out, int is_host);
 
+/* Set the simulated time and the step counter (both reset to 0 by
+ * hgks_init_state / hgks_init_conservative): with hgks_get_state and
+ * hgks_init_conservative this checkpoints and resumes a run.  step >= 0
+ * (else E_INVAL).  Enqueued on the context's stream. */
+hgks_status hgks_set_time(hgks_ctx* ctx, double t, long long step);
+
 /* Advance nsteps S2O4 steps (Eq. (6)).  dt > 0 fixes the step; dt <= 0 takes
  * the CFL step each time (computed on the device).  One step is captured as
  * a CUDA graph on first use and replayed.  With sync != 0 the call waits,

@@ -160,6 +160,12 @@ static __global__ void k_reset_scalars(double* scal, unsigned long long* dtmin, 
   *flag = 0;
 }
 
+static __global__ void k_set_time(double* scal, double t, double step) {
+  if (threadIdx.x != 0) return;
+  scal[1] = t;
+  scal[2] = step;
+}
+
 cudaError_t enqueue_reset_scalars(const Engine& e) {
   k_reset_scalars<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.flag);
   return cudaGetLastError();
@@ -315,6 +321,13 @@ hgks_status hgks_init_state(hgks_ctx* c, const double* prim, int is_host) {
 }
 hgks_status hgks_init_conservative(hgks_ctx* c, const double* cons, int is_host) {
   return init_common(c, cons, is_host, 1);
+}
+
+hgks_status hgks_set_time(hgks_ctx* c, double t, long long step) {
+  if (!c || step < 0) return fail(c, HGKS_E_INVAL, "null context or negative step");
+  hgks::k_set_time<<<1, 32, 0, c->e.stream>>>(c->e.scal, t, double(step));
+  HGKS_CHECK(c, cudaGetLastError());
+  return HGKS_OK;
 }
 
 hgks_status hgks_get_state(hgks_ctx* c, double* out, int is_host) {

@@ -149,6 +149,23 @@ class Simulation:
         self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.ctypes.data), 1))
         return out
 
+    def save_checkpoint(self, path: str) -> None:
+        """Write the state (FP64 conservative), the time and the step counter
+        to an .npz file."""
+        d = self.diagnostics()
+        np.savez(path, state=self.state(), t=d["t"], step=d["step"],
+                 shape=np.array(self.cfg.shape))
+
+    def load_checkpoint(self, path: str) -> None:
+        """Resume from save_checkpoint's file (same grid): the state, the
+        time and the step counter.  In FP32 the accumulation's compensation
+        restarts at zero."""
+        ck = np.load(path)
+        if tuple(ck["shape"]) != tuple(self.cfg.shape):
+            raise ValueError(f"checkpoint grid {tuple(ck['shape'])} != {self.cfg.shape}")
+        self.init_conservative(ck["state"])
+        self._call(self.lib.hgks_set_time(self.h, float(ck["t"]), int(ck["step"])))
+
     def adjoint_step(self, dt: float, adj_in: torch.Tensor, adj_out: torch.Tensor) -> None:
         """adj_out = (dQ^{n+1}/dQ^n)^T adj_in at the current state Q^n (device FP64 tensors)."""
         for t in (adj_in, adj_out):
