@@ -42,7 +42,7 @@ LAUNCHES_PER_STEP = 19
 # 1428 per face -- solved from the executed FP32 operations (fadd + fmul +
 # 2 ffma) that ncu counted on Taylor-Green 128^3 for the three scalar tile
 # variants, whose halo factors differ
-# (profiles/k_sweep_fp32_smooth_taylor_green_128.md).  The same per face for
+# (the ncu summary of the sweep kernel at 128^3).  The same per face for
 # every tile variant and grid; counted with the direct form of the
 # compatibility state (its FP32 midpoint-rule form adds work not counted).
 ALG_FLOPS_PER_FACE = 1990.0

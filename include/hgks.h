@@ -47,7 +47,7 @@ typedef enum {
   HGKS_E_CUDA = 3,         /* a CUDA call failed */
   HGKS_E_NONPHYSICAL = 4,  /* rho <= 0, p <= 0 or NaN in the state after a step */
   HGKS_E_TIMEOUT = 5,      /* reserved: a bounded device wait expired */
-  HGKS_E_UNSUPPORTED = 6   /* a valid request this build does not implement */
+  HGKS_E_UNSUPPORTED = 6   /* a valid request the library does not implement */
 } hgks_status;
 
 typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_WALL_ISOTHERMAL = 1 } hgks_bc;

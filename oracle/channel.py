@@ -4,7 +4,7 @@ numpy from a conservative state.
 TEST INFRASTRUCTURE ONLY: only tests/ may import this module; it shares no
 code with the CUDA path.
 
-Definitions (Sec. 3.3; the readings are listed in the design doc):
+Definitions (Sec. 3.3, with the readings where the paper is silent or garbled):
   plane means over x and z of each y row;
   tau_w = mu(T_wall) d<U>/dn at each wall (the paper writes tau_wall =
   dU/dy|wall; the viscosity makes it a stress), d<U>/dn from the quadratic

@@ -21,7 +21,7 @@
 //   Sec. 3.3               tanh channel mapping, isothermal no-slip walls,
 //                          streamwise body force
 // Points the paper leaves open are marked "Reading:"; the same readings are
-// listed in the design doc.  Moments are evaluated generically: every needed
+// followed by the CUDA path.  Moments are evaluated generically: every needed
 // velocity-space integral is written as a product of polynomials in
 // (u, v, w, xi^2) and integrated monomial by monomial against the
 // Maxwellian, which factorises over u, v, w and xi.  Linear solves use plain
