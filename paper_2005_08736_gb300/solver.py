@@ -76,6 +76,37 @@ def taylor_green_config(n: int, prec: str = "fp32", recon: str = "linear", flux:
     return c
 
 
+def isotropic_config(n: int, prec: str = "fp32", mach_t: float = 0.5, k0: float = 8.0,
+                     recon: str = "weno-z", flux: str = "full", **kw) -> Config:
+    """Decaying isotropic turbulence of Sec. 3.4 on [0, 2 pi]^3: Re_lambda 72,
+    mu = mu0 (T/T0)^0.76, Pr 0.7, gamma 1.4, WENO-Z with the full flux and the
+    numerical collision time; the initial constants (mu0, T0 = p0) from the
+    spectrum E(k) = A0 k^4 exp(-2 k^2/k0^2) and Ma_t.  Start it with
+    inputs.isotropic(n, seed, k0=k0, mach_t=mach_t)."""
+    from . import inputs
+    ic = inputs.isotropic_constants(k0=k0, mach_t=mach_t)
+    c = Config(n, n, n, prec=PREC[prec], recon=RECON[recon], flux=FLUX[flux],
+               tau_num_C=1.0 if flux == "full" else 0.0, prandtl=0.7, visc=1, mu_ref=ic["mu0"],
+               T_ref=ic["T0"], visc_exp=0.76, p_ref=ic["p0"], rho_ref=1.0)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def channel_config(nx: int = 128, ny: int = 128, nz: int = 96, prec: str = "fp32", **kw) -> Config:
+    """Turbulent channel of Sec. 3.3 at Re_tau 180: box 2 pi x 2 x pi, tanh
+    stretching in y (b = 2), isothermal no-slip walls at y = -1, 1 with
+    T_wall = c0^2/gamma (c0 = 10, bulk Ma 0.1), mu = 0.0541/180, constant
+    streamwise force f_x = 2.93e-3, linear weights with the smooth flux.
+    Start it with inputs.channel(nx, ny, nz, seed)."""
+    c = Config(nx, ny, nz, lx=2 * math.pi, ly=2.0, y0=-1.0, lz=math.pi, y_stretch=1, stretch_b=2.0,
+               bc_y=1, T_wall=100 / 1.4, mu_ref=0.0541 / 180, force_x=2.93e-3, prec=PREC[prec],
+               recon=0, flux=0, prandtl=0.72)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
 class Simulation:
     """One HGKS context on the current CUDA device."""
 

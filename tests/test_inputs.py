@@ -73,3 +73,18 @@ def test_taylor_green_initial_kinetic_energy_and_divergence():
     ek = 0.5 * (prim[0] * (prim[1] ** 2 + prim[2] ** 2 + prim[3] ** 2)).mean()
     assert ek == pytest.approx(0.125, rel=1e-12)   # <sin^2 cos^2 cos^2> terms, Sec. 3.1
     assert prim[4].min() > 0 and np.allclose(prim[0], 1.0)
+
+
+def test_config_presets_carry_the_papers_constants():
+    import math
+    from paper_2005_08736_gb300.solver import channel_config, isotropic_config
+    ch = channel_config()
+    assert (ch.nx, ch.ny, ch.nz) == (128, 128, 96)
+    assert ch.mu_ref == pytest.approx(0.0541 / 180) and ch.force_x == pytest.approx(2.93e-3)
+    assert ch.bc_y == 1 and ch.y_stretch == 1 and ch.ly == 2.0 and ch.lx == pytest.approx(2 * math.pi)
+    assert ch.T_wall == pytest.approx(100 / 1.4)  # c0 = 10 with U_b = 1 (Ma 0.1)
+    iso = isotropic_config(64, k0=4.0)
+    c = inputs.isotropic_constants(k0=4.0, mach_t=0.5)
+    assert iso.mu_ref == pytest.approx(c["mu0"]) and iso.p_ref == pytest.approx(c["p0"])
+    assert iso.visc == 1 and iso.visc_exp == 0.76 and iso.prandtl == 0.7
+    assert iso.recon == 2 and iso.flux == 1 and iso.tau_num_C == 1.0
