@@ -2,7 +2,8 @@
 
 * Free-stream preservation and exact discrete conservation on periodic grids.
 * Convergence order of the semi-discrete operator L and of dL/dt on an
-  advected density wave, an exact Euler solution.
+  advected density wave, an exact Euler solution, and of whole runs of the
+  scheme on it against the exact solution.
 * Mirror symmetry of a channel with isothermal walls and the wall ghost cells.
 * The printed time steps of the Taylor-Green runs (Sec. 3.2 table) and the
   printed channel grid spacings (Sec. 3.3 table), from tests/golden/.
@@ -100,6 +101,37 @@ def test_wenoz_full_operator_orders():
     assert orders([e[0] for e in al])[-1] > 4.6, al
     ob = [wave_error(n, 2, 1, aligned=False) for n in (8, 16, 32)]
     assert orders([e[0] for e in ob])[-1] > 2.7, ob
+
+
+def advected_wave_error(n, recon, flux, T=0.5, cfl=0.4):
+    """Max error after a run to time T of the aligned density wave
+    rho = 1 + amp sin(x - U t), u = U, p = 1 (an exact Euler solution),
+    against its exact cell averages; dt = cfl h, rounded down to divide T."""
+    U, amp, gamma = 1.0, 0.2, 1.4
+    h = 2 * math.pi / n
+    x = inputs.centres(n, 2 * math.pi)
+    sx = math.sin(h / 2) / (h / 2)
+
+    def cons(t):
+        r = np.broadcast_to(1 + amp * sx * np.sin(x - U * t), (4, 4, n))
+        return np.stack([r, U * r, 0 * r, 0 * r, 1 / (gamma - 1) + 0.5 * U * U * r])
+
+    sv = oracle.Solver(oracle.Config(n, 4, 4, ly=4 * h, lz=4 * h, recon=recon, flux=flux,
+                                     mu_ref=0.0, tau_num_C=0.0, prandtl=1.0))
+    sv.set_state(cons(0.0))
+    k = math.ceil(T / (cfl * h))
+    sv.step(k, T / k)
+    return np.abs(sv.state() - cons(T)).max()
+
+
+@pytest.mark.parametrize("recon,flux", MODES)
+def test_advected_wave_run_converges_at_fifth_order(recon, flux):
+    # The whole scheme, S2O4 steps included, against the exact solution at
+    # a fixed CFL number.  The two-stage update is fourth order in time for
+    # the PDE, and its time error here is far below the fifth-order spatial
+    # error (measured orders 4.92 and 4.99 from 16 to 32 cells).
+    errs = [advected_wave_error(n, recon, flux) for n in (8, 16, 32)]
+    assert orders(errs)[-1] > 4.7, errs
 
 
 def channel_state(nx, ny, nz, seed):
