@@ -128,17 +128,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_sample(steps: int, n: int = 32):
-    """The FP64 oracle on a bounded sample: TG n^3, `steps` steps; (Mcell-upd/s, seconds)."""
+def oracle_sample(steps: int = 1, n: int = 32, seconds: float = 0.0):
+    """The FP64 oracle on a bounded sample of the workload: Taylor-Green n^3
+    from its initial state, `steps` steps, or whole steps until `seconds` have
+    elapsed (at least one); (Mcell-upd/s, seconds, steps)."""
     import oracle
     from paper_2005_08736_gb300 import inputs
     s = oracle.Solver(oracle.Config(n, n, n, recon=0, flux=0, prandtl=0.72, mu_ref=1 / 1600,
                                     cfl=0.5))
     s.set_state(oracle.conservative(inputs.taylor_green(n), 1.4))
+    done, el = 0, 0.0
     t0 = time.perf_counter()
-    s.step(steps)
-    el = time.perf_counter() - t0
-    return n ** 3 * steps / el / 1e6, el
+    while done < steps or el < seconds:
+        s.step(1)
+        done += 1
+        el = time.perf_counter() - t0
+    return n ** 3 * done / el / 1e6, el, done
+
+
+def oracle_threads() -> int:
+    import oracle
+    return oracle.threads()
 
 
 def oracle_sample_one_core(n: int = 32):
@@ -148,8 +158,13 @@ def oracle_sample_one_core(n: int = 32):
     code = f"import bench, json; print(json.dumps(bench.oracle_sample(1, {n})))"
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
                          text=True, timeout=600, check=True)
-    rate, secs = json.loads(out.stdout.strip().splitlines()[-1])
+    rate, secs, _ = json.loads(out.stdout.strip().splitlines()[-1])
     return rate, secs
+
+
+# The reference arm's whole run (warm-up and timed steps) is held to about
+# this many seconds by shrinking each step's sample grid.
+REFERENCE_RUN_SECONDS = 150.0
 
 
 def run_reference(args, rank: int):
@@ -157,17 +172,22 @@ def run_reference(args, rank: int):
         return
     import oracle
     oracle.build()
+    # One step of the 32^3 sample loads the library and gives the time per
+    # step; a smaller grid is taken if K + W such steps would exceed the bound.
     n = 32
-    oracle_sample(1, n)  # load and warm the library
+    _, t_step, _ = oracle_sample(1, n)
+    while n > 16 and (args.steps + args.warmup) * t_step > REFERENCE_RUN_SECONDS:
+        t_step *= ((n - 8) / n) ** 3
+        n -= 8
     for _ in range(args.warmup):
-        pass  # the oracle has no warm state beyond the library load
+        oracle_sample(1, n)
     rates, times = [], []
     for _ in range(args.steps):
-        r, el = oracle_sample(1, n)
+        r, el, _ = oracle_sample(1, n)
         rates.append(r)
         times.append(el)
     value = n ** 3 * args.steps / sum(times) / 1e6
-    cores = os.cpu_count()
+    cores = oracle_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mcell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -609,7 +629,8 @@ def run_ours(args, rank: int, world: int):
                      "frac": max(t_alu, t_hbm) / ms,
                      "note": "algorithmic flops of the six sweeps (halo excluded) at the measured "
                              "FP32 FMA peak vs 120 B per cell-step at the measured HBM copy rate"}
-    cpu_rate, cpu_s = oracle_sample(2)
+    cpu_rate, cpu_s, cpu_steps = oracle_sample(1, 32, seconds=10.0)
+    cpu_cores = oracle_threads()
     cpu1_rate, cpu1_s = oracle_sample_one_core()
     extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
     line = {
@@ -626,9 +647,9 @@ def run_ours(args, rank: int, world: int):
         "t_reached": t_reached,
         "roofline": roofline,
         "step_roofline": step_roofline,
-        "cpu_baseline": {"value": cpu_rate, "unit": "Mcell-updates/s", "cores": os.cpu_count(),
+        "cpu_baseline": {"value": cpu_rate, "unit": "Mcell-updates/s", "cores": cpu_cores,
                          "kind": "oracle",
-                         "sample": f"FP64 CPU oracle, 2 steps of Taylor-Green 32^3 "
+                         "sample": f"FP64 CPU oracle, {cpu_steps} steps of Taylor-Green 32^3 "
                                    f"({cpu_s:.1f} s), same physics and scheme",
                          "one_core": {"value": cpu1_rate, "cores": 1,
                                       "sample": f"1 step of Taylor-Green 32^3 ({cpu1_s:.1f} s)"}},

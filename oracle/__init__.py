@@ -96,6 +96,8 @@ def lib():
             L.oracle_time.argtypes = [vp]
             L.oracle_last_force.restype = d
             L.oracle_last_force.argtypes = [vp]
+            L.oracle_threads.restype = i
+            L.oracle_threads.argtypes = []
             L.oracle_cfl_dt.restype = d
             L.oracle_cfl_dt.argtypes = [vp]
             L.oracle_rhs.argtypes = [vp, d, pd, pd]
@@ -270,6 +272,12 @@ def count_lib():
 
 
 COUNT_KEYS = ("add", "mul", "div", "sqrt", "exp", "erfc", "pow")
+
+
+def threads() -> int:
+    """Threads the plain oracle's parallel loops use (OMP_NUM_THREADS, else
+    the cores OpenMP sees)."""
+    return int(lib().oracle_threads())
 
 
 def count_step(cfg: Config, cons, nsteps: int = 1, dt: float = 0.0):

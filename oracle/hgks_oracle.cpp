@@ -35,6 +35,9 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 // Scalar type of every quantity that depends on the state.  The plain build
 // computes in double.  The tangent build (-DORACLE_TANGENT) computes in the
@@ -1051,6 +1054,15 @@ struct Solver {
 }  // namespace
 
 extern "C" {
+
+// Threads the oracle's parallel loops use (OpenMP's maximum; 1 without OpenMP).
+int oracle_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void* oracle_create(const oracle_config* cfg) { return new Solver(*cfg); }
 void oracle_destroy(void* h) { delete static_cast<Solver*>(h); }
