@@ -48,6 +48,12 @@ def _compile(path: str, extra, force: bool) -> str:
     return path
 
 
+def _built(path: str, extra) -> str:
+    """Compile one variant if its library is missing or older than the source."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    return _compile(path, extra, False)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (-O2, OpenMP, no FP contraction): the plain
     FP64 build, the dual-number tangent build and the operation-counting build
@@ -82,7 +88,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(_built(_LIB_PATH, []))
             d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             pd = ctypes.POINTER(ctypes.c_double)
             L.oracle_create.restype = vp
@@ -130,8 +136,7 @@ def tangent_lib():
     global _tan
     with _lock:
         if _tan is None:
-            build()
-            L = ctypes.CDLL(_TAN_PATH)
+            L = ctypes.CDLL(_built(_TAN_PATH, ["-DORACLE_TANGENT"]))
             d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             pd = ctypes.POINTER(ctypes.c_double)
             L.oracle_create.restype = vp
@@ -254,8 +259,7 @@ def count_lib():
     global _cnt
     with _lock:
         if _cnt is None:
-            build()
-            L = ctypes.CDLL(_CNT_PATH)
+            L = ctypes.CDLL(_built(_CNT_PATH, ["-DORACLE_COUNT"]))
             d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             pd = ctypes.POINTER(ctypes.c_double)
             L.oracle_create.restype = vp

@@ -144,6 +144,22 @@ def test_smooth_flux_shear_stress():
     assert F[4] == pytest.approx(-MU * s * V, rel=1e-9)
 
 
+@pytest.mark.parametrize("flux", [0, 1])
+def test_shear_stress_follows_the_power_law_viscosity(flux):
+    # Sec. 3.4: mu = mu_ref (T / T_ref)^0.76; the stress of a uniform shear at
+    # a temperature T = 2.5 T_ref carries that viscosity (both fluxes).
+    rho, V, T_ref, s = 1.0, 0.3, 0.8, 0.8
+    p = 2.5 * T_ref * rho
+    Q = cons(rho, 0.0, V, 0.0, p)
+    dQ = np.array([0.0, 0.0, rho * s, 0.0, rho * V * s])
+    c = oracle.Config(8, 8, 8, flux=flux, prandtl=0.7, mu_ref=MU, visc_law=1, T_ref=T_ref,
+                      visc_exp=0.76)
+    F, _ = oracle.flux_point(c, point_with_x_gradient(Q, dQ), 1e-4)
+    mu = MU * 2.5 ** 0.76
+    assert F[2] == pytest.approx(-mu * s, rel=1e-8)
+    assert F[4] == pytest.approx(-mu * s * V, rel=1e-8)
+
+
 @pytest.mark.parametrize("prandtl", [1.0, 0.72, 0.7])
 def test_smooth_flux_heat_flux(prandtl):
     p, T, s = 2.0, 1.6, 0.5                      # T(x) with dT/dx = s, p uniform

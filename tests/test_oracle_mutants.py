@@ -1,0 +1,124 @@
+"""Planted mistakes in the oracle are caught by its pins (CPU only).
+
+Each case copies oracle/ into a temporary directory, plants one plausible
+mistake in the copy's C++ source - a swapped index, slot or width, a wrong
+coefficient, sign or stencil - and runs, against the copy, the pins that
+must catch it: at least one has to fail.  The unmodified copy passes the
+same pins.  The repository's own oracle is never modified.  A planted
+pattern that no longer occurs in the source fails the test, so the list
+follows the source.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+ANISO = "tests/test_oracle_scheme.py::test_operator_converges_on_an_anisotropic_box"
+OBLIQUE = "tests/test_oracle_scheme.py::test_linear_smooth_operator_is_fifth_order_on_oblique_wave"
+ASSEMBLY = "tests/test_oracle_assembly.py"
+REFLECT = "tests/test_oracle_symmetry.py::test_step_commutes_with_a_reflection"
+BRUTE = "tests/test_oracle_flux.py::test_full_flux_matches_brute_force_phase_space_quadrature"
+POWER = "tests/test_oracle_flux.py::test_shear_stress_follows_the_power_law_viscosity"
+S2O4 = "tests/test_oracle_pieces.py::test_s2o4_on_linear_ode_is_the_fourth_order_taylor_polynomial"
+WENOZ = "tests/test_oracle_pieces.py::test_weno_z_is_linear_where_the_outer_indicators_agree"
+WENOQ = "tests/test_oracle_pieces.py::test_weno5_exact_on_quadratics"
+MOMENTS = "tests/test_oracle_pieces.py::test_moments_match_quadrature"
+QUARTIC = "tests/test_oracle_pieces.py::test_tangential_quartic_exact"
+WALL = "tests/test_oracle_scheme.py::test_wall_ghost_cells"
+
+# (name, text in hgks_oracle.cpp, planted replacement, pins)
+MUTANTS = [
+    ("t2 derivative divided by the t1 width",
+     "pd.st[s][3][v] = der[mm][v] / h2;", "pd.st[s][3][v] = der[mm][v] / h1;", [ANISO]),
+    ("t2 derivative at the t1 Gauss index",
+     "pd.st[s][3][v] = der[mm][v] / h2;", "pd.st[s][3][v] = der[m][v] / h2;", [OBLIQUE]),
+    ("tangential flux components swapped on output",
+     "o[1 + t1] = L[2];\n            o[1 + t2] = L[3];",
+     "o[1 + t1] = L[3];\n            o[1 + t2] = L[2];", [ANISO]),
+    ("tangential momenta swapped on input",
+     "out[2] = a[(1 + (d + 1) % 3) * S + ci];\n    out[3] = a[(1 + (d + 2) % 3) * S + ci];",
+     "out[2] = a[(1 + (d + 2) % 3) * S + ci];\n    out[3] = a[(1 + (d + 1) % 3) * S + ci];", [ANISO]),
+    ("Gauss weight of dF",
+     "Fsum[5 + i] += 0.25 * dF[i];", "Fsum[5 + i] += 0.3 * dF[i];", [OBLIQUE]),
+    ("sign of the outer taps of the equilibrium slope",
+     "(qc[1][v] - 15.0 * qc[2][v] + 15.0 * qc[3][v] - qc[4][v])",
+     "(-qc[1][v] - 15.0 * qc[2][v] + 15.0 * qc[3][v] + qc[4][v])", [OBLIQUE]),
+    ("equilibrium slope over the left width only",
+     "/ (6.0 * (hl + hr));", "/ (12.0 * hl);", [ASSEMBLY]),
+    ("left normal slope over the right width",
+     "out[2 * 5 + v] = (4.0 * QRi + 2.0 * QLi - 6.0 * qc[2][v]) / hl;",
+     "out[2 * 5 + v] = (4.0 * QRi + 2.0 * QLi - 6.0 * qc[2][v]) / hr;", [ASSEMBLY]),
+    ("normal slopes of the left and right states exchanged",
+     "sf[3] = {2, 3, 5}", "sf[3] = {3, 2, 5}", [ASSEMBLY]),
+    ("Heaviside factor on the wrong state",
+     "out[4 * 5 + i] = gl.rho * mom(gl, +1, pi) + gr.rho * mom(gr, -1, pi);",
+     "out[4 * 5 + i] = gl.rho * mom(gl, -1, pi) + gr.rho * mom(gr, +1, pi);", [ASSEMBLY]),
+    ("characteristic basis at the left cell instead of the mean",
+     "out[30 + v] = 0.5 * (qc[2][v] + qc[3][v]);", "out[30 + v] = qc[2][v];", [REFLECT]),
+    ("numerical collision time halved",
+     "tau += c.tau_num_C * fabs((pl - pr) / (pl + pr)) * dt;",
+     "tau += c.tau_num_C * fabs((pl - pr) / (pl + pr)) * dt * 0.5;", [BRUTE]),
+    ("viscosity law inverted",
+     "pow(T / c.T_ref, c.visc_exp)", "pow(c.T_ref / T, c.visc_exp)", [POWER]),
+    ("S2O4 first-stage coefficient",
+     "0.125 * dt * dt * dL0", "0.1 * dt * dt * dL0", [S2O4]),
+    ("S2O4 second-stage weights exchanged",
+     "dt * dt / 6.0 * (dL0 + 2.0 * dL1)", "dt * dt / 6.0 * (2.0 * dL0 + dL1)", [S2O4]),
+    ("WENO-Z indicator from the wrong pair",
+     "fabs(beta[0] - beta[2])", "fabs(beta[0] - beta[1])", [WENOZ]),
+    ("WENO5 middle candidate coefficient",
+     "(-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.0", "(-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.5", [WENOQ]),
+    ("Gaussian moment recursion index",
+     "(n + 1) / (2.0 * lam) * m[n]", "(n + 2) / (2.0 * lam) * m[n]", [MOMENTS]),
+    ("quartic cell averages",
+     "(std::pow(hi, p + 1) - std::pow(lo, p + 1)) / (p + 1)",
+     "(std::pow(hi, p + 1) - std::pow(lo, p + 1)) / (p + 2)", [QUARTIC]),
+    ("wall ghost temperature",
+     "real Tg = 2.0 * c.T_wall - p / rho;", "real Tg = 1.5 * c.T_wall - 0.5 * p / rho;", [WALL]),
+]
+
+
+def copy_oracle(dst):
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    return os.path.join(dst, "oracle", "hgks_oracle.cpp")
+
+
+def run_pins(workdir, pins):
+    """pytest of the pins with the oracle package of workdir first on the path."""
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([workdir, ROOT]), OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+           *[os.path.join(ROOT, p) for p in pins]]
+    return subprocess.run(cmd, cwd=workdir, env=env, capture_output=True, text=True, timeout=900)
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "hgks_oracle.cpp")).read()
+    missing = [name for name, old, _, _ in MUTANTS if src.count(old) != 1]
+    assert not missing, f"planted patterns not found once in the source: {missing}"
+
+    control = str(tmp_path / "control")
+    copy_oracle(control)
+    pins = sorted({p for *_, ps in MUTANTS for p in ps})
+    r = run_pins(control, pins)
+    assert r.returncode == 0, r.stdout[-3000:]
+
+    def one(k):
+        name, old, new, ps = MUTANTS[k]
+        work = str(tmp_path / f"m{k}")
+        path = copy_oracle(work)
+        with open(path, "w") as fh:
+            fh.write(src.replace(old, new, 1))
+        r = run_pins(work, ps)
+        # A failed pin (exit 1), not a collection or build error (other codes).
+        return name, r.returncode, r.stdout[-1500:]
+
+    with ThreadPoolExecutor(max_workers=6) as ex:
+        results = list(ex.map(one, range(len(MUTANTS))))
+    survivors = [name for name, rc, _ in results if rc == 0]
+    broken = [(name, rc, out) for name, rc, out in results if rc not in (0, 1)]
+    assert not broken, broken
+    assert not survivors, f"planted mistakes no pin caught: {survivors}"

@@ -186,6 +186,18 @@ def test_weno5_nonlinear_weights_converge_to_linear(mode, order):
     assert rates.min() > order, (errs, rates)
 
 
+def test_weno_z_is_linear_where_the_outer_indicators_agree():
+    # Data symmetric about the centre cell give beta_0 = beta_2, so the
+    # WENO-Z indicator |beta_0 - beta_2| vanishes and its weights are the
+    # linear ones; WENO-JS weights still follow beta_k and differ.
+    for q in ([0.3, 1.1, -0.4, 1.1, 0.3], [2.0, 0.5, 1.0, 0.5, 2.0]):
+        q = np.array(q)
+        for side in (oracle.weno5_right, oracle.weno5_left):
+            lin = side(q, 0)
+            assert side(q, 2) == pytest.approx(lin, rel=1e-14, abs=1e-14)
+            assert abs(side(q, 1) - lin) > 1e-3
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_weno5_non_oscillatory_at_a_step(mode):
     q = np.array([0.0, 0.0, 0.0, 1.0, 1.0])
