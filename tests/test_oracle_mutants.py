@@ -28,6 +28,13 @@ WENOQ = "tests/test_oracle_pieces.py::test_weno5_exact_on_quadratics"
 MOMENTS = "tests/test_oracle_pieces.py::test_moments_match_quadrature"
 QUARTIC = "tests/test_oracle_pieces.py::test_tangential_quartic_exact"
 WALL = "tests/test_oracle_scheme.py::test_wall_ghost_cells"
+WENODEF = "tests/test_oracle_pieces.py::test_weno5_matches_its_definition_on_random_data"
+HEAT = "tests/test_oracle_flux.py::test_smooth_flux_heat_flux"
+TIMEINT = "tests/test_oracle_pieces.py::test_time_integrals_match_numerical_integration"
+TANGQ = "tests/test_oracle_pieces.py::test_tangential_weno_quadratic_exact"
+GRID = "tests/test_oracle_scheme.py::test_channel_grid_matches_printed_table"
+TGDT = "tests/test_oracle_scheme.py::test_taylor_green_time_steps_match_printed_table"
+MASSFLUX = "tests/test_oracle_force.py::test_mass_flux_force_holds_the_target"
 
 # (name, text in hgks_oracle.cpp, planted replacement, pins)
 MUTANTS = [
@@ -78,6 +85,27 @@ MUTANTS = [
      "(std::pow(hi, p + 1) - std::pow(lo, p + 1)) / (p + 2)", [QUARTIC]),
     ("wall ghost temperature",
      "real Tg = 2.0 * c.T_wall - p / rho;", "real Tg = 1.5 * c.T_wall - 0.5 * p / rho;", [WALL]),
+    ("smoothness indicator coefficient",
+     "13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1", "13.0 / 12.0 * s1 * s1 + 0.5 * t1 * t1", [WENODEF]),
+    ("flux fit of F",
+     "F[i] = (4.0 * W[1][i] - W[0][i]) / dt;", "F[i] = (3.0 * W[1][i] - W[0][i]) / dt;", [BRUTE]),
+    ("flux fit of dF",
+     "dF[i] = 4.0 * (W[0][i] - 2.0 * W[1][i]) / (dt * dt);",
+     "dF[i] = 2.0 * (W[0][i] - 2.0 * W[1][i]) / (dt * dt);", [BRUTE]),
+    ("Prandtl correction",
+     "F[4] += (1.0 / c.prandtl - 1.0) * q;", "F[4] += (c.prandtl - 1.0) * q;", [HEAT]),
+    ("time integral of -(tau + t) e^{-t/tau}",
+     "q[4] = tau * (T * e - 2.0 * tau * (1.0 - e));", "q[4] = tau * (T * e - tau * (1.0 - e));",
+     [TIMEINT]),
+    ("tangential quadratic constant term",
+     "a = f[2] - c / 12.0;", "a = f[2] - c / 6.0;", [TANGQ]),
+    ("tanh mapping offset",
+     "(eta / (1.5 * kPi) - 1.0)", "(eta / (1.5 * kPi) - 0.9)", [GRID]),
+    ("CFL sound speed",
+     "w(d, x[d]) / (fabs(u[d]) + cs)", "w(d, x[d]) / (fabs(u[d]) + 0.9 * cs)", [TGDT]),
+    ("mass-flux force",
+     "f = (c.mass_flux * vol - mom) / (dt * half_rho);",
+     "f = 0.5 * (c.mass_flux * vol - mom) / (dt * half_rho);", [MASSFLUX]),
 ]
 
 

@@ -186,6 +186,48 @@ def test_weno5_nonlinear_weights_converge_to_linear(mode, order):
     assert rates.min() > order, (errs, rates)
 
 
+def weno5_right_by_definition(q, mode):
+    """The WENO5 value at the right end of the centre cell built from the
+    definitions (Jiang & Shu; Borges et al. for WENO-Z), cell units: each
+    candidate is the quadratic whose averages over its three cells are the
+    data (a 3x3 solve), its indicator is the integral over the centre cell of
+    p'^2 + p''^2 (Gauss-Legendre quadrature, exact here), and the weights are
+    d_k / (eps + beta_k)^2 (WENO-JS, eps 1e-6) or d_k (1 + |beta_0 - beta_2| /
+    (beta_k + eps)) (WENO-Z, eps 1e-20), normalised."""
+    xg, wg = np.polynomial.legendre.leggauss(4)
+    xg, wg = 0.5 * xg, 0.5 * wg                  # the centre cell [-1/2, 1/2]
+    d = np.array([0.1, 0.6, 0.3])
+    vals, beta = [], []
+    for k in range(3):                           # stencils {i-2..i}, {i-1..i+1}, {i..i+2}
+        cells = np.arange(3) + k - 2
+        # average of s^m over [c - 1/2, c + 1/2]
+        A = np.array([[((c + 0.5) ** (m + 1) - (c - 0.5) ** (m + 1)) / (m + 1) for m in range(3)]
+                      for c in cells])
+        a = np.linalg.solve(A, q[k:k + 3])
+        vals.append(a[0] + a[1] * 0.5 + a[2] * 0.25)
+        d1 = a[1] + 2 * a[2] * xg
+        beta.append(float(np.sum(wg * (d1 ** 2 + (2 * a[2]) ** 2))))
+    beta = np.array(beta)
+    if mode == 1:
+        alpha = d / (1e-6 + beta) ** 2
+    else:
+        alpha = d * (1 + abs(beta[0] - beta[2]) / (beta + 1e-20))
+    return float(np.dot(alpha / alpha.sum(), vals))
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_weno5_matches_its_definition_on_random_data(mode):
+    rng = np.random.default_rng(5)
+    for scale in (1.0, 0.05, 3e-3):              # rough to nearly smooth data
+        for _ in range(40):
+            q = 1.0 + scale * rng.normal(size=5)
+            ref = weno5_right_by_definition(q, mode)
+            assert oracle.weno5_right(q, mode) == pytest.approx(ref, rel=1e-12, abs=1e-13)
+            # the left end value is the mirror image
+            refl = weno5_right_by_definition(q[::-1].copy(), mode)
+            assert oracle.weno5_left(q, mode) == pytest.approx(refl, rel=1e-12, abs=1e-13)
+
+
 def test_weno_z_is_linear_where_the_outer_indicators_agree():
     # Data symmetric about the centre cell give beta_0 = beta_2, so the
     # WENO-Z indicator |beta_0 - beta_2| vanishes and its weights are the
