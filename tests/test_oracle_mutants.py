@@ -1,8 +1,8 @@
 """Planted mistakes in the oracle are caught by its pins (CPU only).
 
 Each case copies oracle/ into a temporary directory, plants one plausible
-mistake in the copy's C++ source - a swapped index, slot or width, a wrong
-coefficient, sign or stencil - and runs, against the copy, the pins that
+mistake in the copy's source - the C++ scheme or the numpy statistics: a
+swapped index, slot or width, a wrong coefficient, sign or stencil - and runs, against the copy, the pins that
 must catch it: at least one has to fail.  The unmodified copy passes the
 same pins.  The repository's own oracle is never modified.  A planted
 pattern that no longer occurs in the source fails the test, so the list
@@ -109,6 +109,50 @@ MUTANTS = [
 ]
 
 
+TG = "tests/test_oracle_turbulence.py::test_taylor_green_closed_forms"
+ENSTROPHY = "tests/test_oracle_turbulence.py::test_enstrophy_sixth_order_convergence"
+COMPRESSION = "tests/test_oracle_turbulence.py::test_compression_wave"
+TWOMODES = "tests/test_oracle_turbulence.py::test_skewness_and_flatness_of_two_modes"
+POWERNP = "tests/test_oracle_turbulence.py::test_power_law_viscosity_scales_with_temperature"
+POISEUILLE = "tests/test_oracle_channel.py::test_poiseuille_statistics_in_closed_form"
+POTENTIAL = "tests/test_oracle_turbulence.py::test_potential_flow_closed_forms"
+
+# The numpy statistics: (file, name, text, planted replacement, pins)
+STAT_MUTANTS = [
+    ("turbulence.py", "sixth-order difference coefficient",
+     "(45.0 * s(1) - 9.0 * s(2) + s(3))", "(45.0 * s(1) - 8.0 * s(2) + s(3))", [ENSTROPHY]),
+    ("turbulence.py", "vorticity component from the wrong gradient",
+     "G[2][1] - G[1][2]", "G[2][1] - G[1][1]", [POTENTIAL]),
+    ("turbulence.py", "deviatoric part of the strain rate",
+     "(theta / 3.0 if i == j else 0.0)", "(theta / 2.0 if i == j else 0.0)", [COMPRESSION]),
+    ("turbulence.py", "bulk viscosity",
+     "2.0 * N / (3.0 * (N + 3.0)) * mu", "2.0 * N / (3.0 * (N + 2.0)) * mu", [COMPRESSION]),
+    ("turbulence.py", "sign of the pressure-dilatation dissipation",
+     'out["eps3"] = -avg(p * theta) / rho0', 'out["eps3"] = avg(p * theta) / rho0', [COMPRESSION]),
+    ("turbulence.py", "dilatational dissipation factor",
+     'out["eps_d"] = 4.0 / 3.0 * avg', 'out["eps_d"] = avg', [COMPRESSION]),
+    ("turbulence.py", "skewness normalisation",
+     "m3[i] / m2[i] ** 1.5", "m3[i] / m2[i] ** 2", [TWOMODES]),
+    ("turbulence.py", "viscosity law",
+     "mu_ref * (T / T_ref) ** exp", "mu_ref * (T_ref / T) ** exp", [POWERNP]),
+    ("channel.py", "upper-wall slope from swapped rows",
+     "hi = _wall_slope(dy[-1], dy[-2], Um[-1], Um[-2])",
+     "hi = _wall_slope(dy[-1], dy[-2], Um[-2], Um[-1])", [POISEUILLE]),
+    ("channel.py", "bulk Reynolds number length",
+     'out["Re_b"] = out["U_b"] * 2.0 * H / nu', 'out["Re_b"] = out["U_b"] * H / nu', [POISEUILLE]),
+    ("channel.py", "skin-friction dynamic pressure",
+     "(0.5 * out[\"rho_b\"] * out[\"U_b\"] ** 2)", "(out[\"rho_b\"] * out[\"U_b\"] ** 2)",
+     [POISEUILLE]),
+    ("channel.py", "centreline cubic about the wrong point",
+     "faces[j0 + k] - yc, faces[j0 + k + 1] - yc", "faces[j0 + k] - yc, faces[j0 + k + 1] - yc + 0.01",
+     [POISEUILLE]),
+]
+
+
+def all_mutants():
+    return [("hgks_oracle.cpp", *m) for m in MUTANTS] + STAT_MUTANTS
+
+
 def copy_oracle(dst):
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
@@ -124,28 +168,29 @@ def run_pins(workdir, pins):
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
-    src = open(os.path.join(ROOT, "oracle", "hgks_oracle.cpp")).read()
-    missing = [name for name, old, _, _ in MUTANTS if src.count(old) != 1]
+    mutants = all_mutants()
+    src = {f: open(os.path.join(ROOT, "oracle", f)).read() for f, *_ in mutants}
+    missing = [name for f, name, old, _, _ in mutants if src[f].count(old) != 1]
     assert not missing, f"planted patterns not found once in the source: {missing}"
 
     control = str(tmp_path / "control")
     copy_oracle(control)
-    pins = sorted({p for *_, ps in MUTANTS for p in ps})
+    pins = sorted({p for *_, ps in mutants for p in ps})
     r = run_pins(control, pins)
     assert r.returncode == 0, r.stdout[-3000:]
 
     def one(k):
-        name, old, new, ps = MUTANTS[k]
+        f, name, old, new, ps = mutants[k]
         work = str(tmp_path / f"m{k}")
-        path = copy_oracle(work)
-        with open(path, "w") as fh:
-            fh.write(src.replace(old, new, 1))
+        copy_oracle(work)
+        with open(os.path.join(work, "oracle", f), "w") as fh:
+            fh.write(src[f].replace(old, new, 1))
         r = run_pins(work, ps)
         # A failed pin (exit 1), not a collection or build error (other codes).
         return name, r.returncode, r.stdout[-1500:]
 
     with ThreadPoolExecutor(max_workers=6) as ex:
-        results = list(ex.map(one, range(len(MUTANTS))))
+        results = list(ex.map(one, range(len(mutants))))
     survivors = [name for name, rc, _ in results if rc == 0]
     broken = [(name, rc, out) for name, rc, out in results if rc not in (0, 1)]
     assert not broken, broken

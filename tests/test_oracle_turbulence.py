@@ -111,6 +111,27 @@ def test_skewness_and_flatness_of_two_modes():
     assert s["Fu"] == pytest.approx(m4 / m2 ** 2, rel=1e-12)
 
 
+def test_potential_flow_closed_forms():
+    # U = grad phi, phi = sin x sin y sin z (uniform rho, p): the difference
+    # operators of different axes commute, so omega = 0 to rounding, and
+    # theta = -3 g phi, <theta^2> = 9 g^2 / 8.
+    n, mu = 16, 0.01
+    x = inputs.centres(n, 2 * math.pi)
+    z3, y3, x3 = np.meshgrid(x, x, x, indexing="ij")
+    prim = np.zeros((5, n, n, n))
+    prim[0] = 1.0
+    prim[1] = np.cos(x3) * np.sin(y3) * np.sin(z3)
+    prim[2] = np.sin(x3) * np.cos(y3) * np.sin(z3)
+    prim[3] = np.sin(x3) * np.sin(y3) * np.cos(z3)
+    prim[4] = 3.0
+    s = statistics(conservative(prim, GAMMA), gamma=GAMMA, mu_ref=mu)
+    g = symbol(1, 2 * math.pi / n)
+    assert s["zeta"] < 1e-28 and s["eps_s"] < 1e-30
+    assert s["theta_rms"] == pytest.approx(3 * g / math.sqrt(8), rel=1e-12)
+    assert s["eps_d"] == pytest.approx(1.5 * mu * g * g, rel=1e-12)
+    assert s["eps1"] == pytest.approx(1.5 * mu * g * g, rel=1e-12)
+
+
 def test_summation_by_parts_identity():
     # On a periodic grid the central-difference operators are skew-adjoint and
     # commute, so 2 <S^d:S^d> = <|omega|^2> + 4/3 <theta^2> exactly:
