@@ -26,7 +26,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_2005_08736_gb300 import inputs  # noqa: E402
-from paper_2005_08736_gb300._lib import HGKS_E_NONPHYSICAL, HgksError  # noqa: E402
+from paper_2005_08736_gb300._lib import HGKS_E_INVAL, HGKS_E_NONPHYSICAL, HgksError  # noqa: E402
 from paper_2005_08736_gb300.solver import Config, Simulation, taylor_green_config  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -292,6 +292,21 @@ def test_graph_replay_equals_single_steps():
     for _ in range(4):
         b.step(1)
     assert np.array_equal(a.state(), b.state())
+
+
+def test_zero_steps_leave_state_and_time_unchanged():
+    # The empty call: no step runs, the state check still runs; a negative
+    # count is rejected before any device work.
+    for prec in ("fp64", "fp32"):
+        sim = Simulation(taylor_green_config(8, prec))
+        sim.init_primitive(inputs.taylor_green(8))
+        q0 = sim.state()
+        assert sim.step(0) == 0.0
+        assert np.array_equal(sim.state(), q0)
+        with pytest.raises(HgksError) as e:
+            sim.step(-1)
+        assert e.value.status == HGKS_E_INVAL
+        sim.close()
 
 
 def test_nonphysical_state_is_reported():
