@@ -45,8 +45,9 @@ struct Engine {
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
   // Sweep launch choices (set by hgks_autotune): tile variant (0: the default
-  // tile; 1, 2: wider tiles of the linear-weight smooth FP32 sweep) and the
-  // number of face layers each CTA marches through (0: automatic).
+  // tile; 1, 2: wider tiles of the linear-weight smooth FP32 sweep; 3: the
+  // 32x8 tile in packed FP32 pairs) and the number of face layers each CTA
+  // marches through (0: automatic).
   int sweep_variant = 0;
   int sweep_chunk = 0;
 };
