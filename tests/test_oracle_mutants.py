@@ -35,6 +35,11 @@ TANGQ = "tests/test_oracle_pieces.py::test_tangential_weno_quadratic_exact"
 GRID = "tests/test_oracle_scheme.py::test_channel_grid_matches_printed_table"
 TGDT = "tests/test_oracle_scheme.py::test_taylor_green_time_steps_match_printed_table"
 MASSFLUX = "tests/test_oracle_force.py::test_mass_flux_force_holds_the_target"
+ADVECTED = "tests/test_oracle_scheme.py::test_advected_wave_run_converges_at_fifth_order"
+FORCE = "tests/test_oracle_force.py::test_constant_force_on_uniform_state_is_exact"
+FORCEFORM = ("tests/test_oracle_force.py::"
+             "test_mass_flux_force_equals_the_closed_form_and_the_constant_force_step")
+WRAP = "tests/test_oracle_scheme.py::test_periodic_ghost_cells_wrap_including_corners"
 
 # (name, text in hgks_oracle.cpp, planted replacement, pins)
 MUTANTS = [
@@ -106,6 +111,21 @@ MUTANTS = [
     ("mass-flux force",
      "f = (c.mass_flux * vol - mom) / (dt * half_rho);",
      "f = 0.5 * (c.mass_flux * vol - mom) / (dt * half_rho);", [MASSFLUX]),
+    ("second stage with the first stage's dL",
+     "dL1[v * N + ci], dt);", "dL0[v * N + ci], dt);", [ADVECTED]),
+    ("first stage over half the step",
+     "L0[v * N + ci], dL0[v * N + ci], dt);\n          }\n    rhs(qs",
+     "L0[v * N + ci], dL0[v * N + ci], 0.5 * dt);\n          }\n    rhs(qs", [ADVECTED]),
+    ("wall-normal velocity not reversed in the ghost",
+     "Q(a, 2, i, jg, k) = -rg * v;", "Q(a, 2, i, jg, k) = rg * v;", [WALL]),
+    ("force work from the old momentum only",
+     "(Q(q, 1, i, j, k) + Q(qn, 1, i, j, k)) * f", "2.0 * Q(qn, 1, i, j, k) * f", [FORCE]),
+    ("mass-flux force over the old density only",
+     "half_rho += 0.5 * (Q(qn, 0, i, j, k) + Q(q, 0, i, j, k)) * dv;",
+     "half_rho += Q(qn, 0, i, j, k) * dv;", [FORCEFORM]),
+    ("periodic ghost from the wrong layer",
+     "Q(a, v, i, j, n[2] - 1 + m) = Q(a, v, i, j, m - 1);",
+     "Q(a, v, i, j, n[2] - 1 + m) = Q(a, v, i, j, m);", [WRAP]),
 ]
 
 
