@@ -40,6 +40,9 @@ FORCE = "tests/test_oracle_force.py::test_constant_force_on_uniform_state_is_exa
 FORCEFORM = ("tests/test_oracle_force.py::"
              "test_mass_flux_force_equals_the_closed_form_and_the_constant_force_step")
 WRAP = "tests/test_oracle_scheme.py::test_periodic_ghost_cells_wrap_including_corners"
+CHARBASIS = "tests/test_oracle_char.py::test_basis_diagonalises_the_euler_jacobian"
+CHARTANG = "tests/test_oracle_char.py::test_tangential_reconstruction_separates_superposed_fields"
+CHARNORM = "tests/test_oracle_char.py::test_two_superposed_fields_are_reconstructed_separately"
 
 # (name, text in hgks_oracle.cpp, planted replacement, pins)
 MUTANTS = [
@@ -126,6 +129,18 @@ MUTANTS = [
     ("periodic ghost from the wrong layer",
      "Q(a, v, i, j, n[2] - 1 + m) = Q(a, v, i, j, m - 1);",
      "Q(a, v, i, j, n[2] - 1 + m) = Q(a, v, i, j, m);", [WRAP]),
+    ("eigenvector of u - c",
+     "{1.0, u - c, v, w, H - u * c}", "{1.0, u - c, v, w, H - v * c}", [CHARBASIS]),
+    ("characteristic derivatives mapped back with R^-1",
+     "mat5(B->R, cd[m], der[m]);", "mat5(B->L, cd[m], der[m]);", [CHARTANG]),
+    ("opposite end value of the left cell",
+     "e[1][i] = weno5_left(sl, mode);", "e[1][i] = weno5_right(sl, mode);", [CHARNORM, ASSEMBLY]),
+    ("sign of the time-coefficient condition",
+     "rhs[i] = -s;", "rhs[i] = s;", [BRUTE]),
+    ("slope condition without the density",
+     "b[i] = dQ[d][i] / Q[0];", "b[i] = dQ[d][i];", [BRUTE]),
+    ("derivative of the tangential quadratic",
+     "der[m] = b + 2.0 * c * s;", "der[m] = b + c * s;", [TANGQ]),
 ]
 
 
