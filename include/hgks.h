@@ -64,7 +64,7 @@ typedef enum { HGKS_FORCE_CONSTANT = 0, HGKS_FORCE_MASS_FLUX = 1 } hgks_force;
 typedef struct {
   int nx, ny, nz;                  /* interior cells; >= 6 on every axis */
   double x0, lx, y0, ly, z0, lz;   /* origin and extent of the box */
-  int y_stretch;                   /* 0 uniform y; 1 tanh mapping of Sec. 3.3 (ly = 2) */
+  int y_stretch;                   /* 0 uniform y; 1 tanh mapping of Sec. 3.3 (ly = 2, else E_INVAL) */
   double stretch_b;                /* b_g of the mapping */
   int bc_y;                        /* hgks_bc for both y ends; x and z are periodic */
   double gamma, prandtl;           /* gamma > 1; Pr > 0 */

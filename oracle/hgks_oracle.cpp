@@ -708,7 +708,8 @@ struct Solver {
     const double L[3] = {c.lx, c.ly, c.lz};
     for (int d = 0; d < 3; ++d) width[d].assign(pn[d], L[d] / n[d]);
     if (c.y_stretch) {
-      // Sec. 3.3: y = tanh(b_g (eta/(1.5 pi) - 1)) / tanh(b_g), eta uniform in [0, 3 pi].
+      // Sec. 3.3: y = tanh(b_g (eta/(1.5 pi) - 1)) / tanh(b_g), eta uniform in [0, 3 pi]:
+      // the channel of height 2 (ly = 2 whenever y_stretch is set).
       std::vector<double> yf(c.ny + 1);
       for (int j = 0; j <= c.ny; ++j) {
         const double eta = 3.0 * kPi * j / c.ny;

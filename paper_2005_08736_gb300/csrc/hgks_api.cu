@@ -60,6 +60,8 @@ std::string hgks::validate_config(const hgks_config& c) {
   if (c.bc_y == HGKS_BC_WALL_ISOTHERMAL && !(c.T_wall > 0.0)) return "wall temperature must be positive";
   if (c.y_stretch && c.bc_y != HGKS_BC_WALL_ISOTHERMAL) return "the tanh mapping needs wall boundaries";
   if (c.y_stretch && !(c.stretch_b > 0.0)) return "stretch_b must be positive";
+  if (c.y_stretch && std::fabs(c.ly - 2.0) > 1e-12)
+    return "the tanh mapping spans the channel height ly = 2";
   if (!(c.tau_num_C >= 0.0)) return "tau_num_C must be non-negative";
   if (c.force_mode != HGKS_FORCE_CONSTANT && c.force_mode != HGKS_FORCE_MASS_FLUX)
     return "unknown force mode";

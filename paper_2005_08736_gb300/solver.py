@@ -288,7 +288,8 @@ class Simulation:
         if not c.y_stretch:
             return np.full(c.ny, c.ly / c.ny)
         from . import inputs
-        return np.diff(inputs.channel_faces(c.ny, c.stretch_b))
+        # the mapping's faces span [-1, 1]; the channel spans ly
+        return np.diff(inputs.channel_faces(c.ny, c.stretch_b)) * (0.5 * c.ly)
 
 
 class Ensemble:

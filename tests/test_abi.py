@@ -73,9 +73,18 @@ int main(void) {
                                          ("recon", 7), ("flux", 2), ("prec", 3), ("p_ref", 0.0),
                                          ("bc_y", 4), ("y_stretch", 1)])
 def test_invalid_configurations_are_rejected_before_any_device_work(lib, field, value):
+    reject(lib, {field: value})
+
+
+def test_the_tanh_mapping_needs_the_channel_height_two(lib):
+    reject(lib, {"bc_y": 1, "y_stretch": 1, "ly": 3.0, "y0": -1.5})
+
+
+def reject(lib, fields):
     cfg = _lib.HgksConfig()
     assert lib.hgks_default_config(ctypes.byref(cfg), 16) == _lib.HGKS_OK
-    setattr(cfg, field, value)
+    for field, value in fields.items():
+        setattr(cfg, field, value)
     h = ctypes.c_void_p()
     assert lib.hgks_create(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.HGKS_E_INVAL
     assert not h.value

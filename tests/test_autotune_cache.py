@@ -50,3 +50,18 @@ def test_choices_are_cached_per_configuration(tmp_path):
     assert len(table) == 2
     # without a cache file every call times the candidates
     assert not a.autotune()["cached"] and lib.timed == 3
+
+
+@pytest.mark.parametrize("ly,stretch", [(2.0, 1), (3.0, 0)])
+def test_y_widths_of_the_statistics_match_the_grid(ly, stretch):
+    # The row positions Simulation.channel_stats reports come from the same
+    # cell widths as the grid: compared with the oracle's widths (the tanh
+    # mapping spans the channel height 2; the library rejects another ly).
+    import oracle
+    from paper_2005_08736_gb300.solver import Config
+    cfg = Config(8, 12, 8, ly=ly, y0=-0.5 * ly, y_stretch=stretch, stretch_b=2.0, bc_y=1)
+    got = stand_in(cfg, StandInLib())._y_widths()
+    o = oracle.Solver(oracle.Config(8, 12, 8, ly=ly, y0=-0.5 * ly, y_stretch=stretch,
+                                    stretch_b=2.0, bc_y=1))
+    assert got == pytest.approx(o.widths(1), rel=1e-13)
+    assert got.sum() == pytest.approx(ly, rel=1e-14)
