@@ -152,8 +152,22 @@ POWERNP = "tests/test_oracle_turbulence.py::test_power_law_viscosity_scales_with
 POISEUILLE = "tests/test_oracle_channel.py::test_poiseuille_statistics_in_closed_form"
 POTENTIAL = "tests/test_oracle_turbulence.py::test_potential_flow_closed_forms"
 
-# The numpy statistics: (file, name, text, planted replacement, pins)
+TANFD = "tests/test_oracle_tangent.py::test_tangent_equals_central_differences_where_smooth"
+
+# The dual numbers of the tangent build and the numpy statistics:
+# (file, name, text, planted replacement, pins)
 STAT_MUTANTS = [
+    ("tangent.h", "derivative of sqrt",
+     "return {s, x.d / (2.0 * s)};", "return {s, x.d / s};", [TANFD]),
+    ("tangent.h", "sign of the derivative of erfc",
+     "-two_over_sqrt_pi * std::exp", "two_over_sqrt_pi * std::exp", [TANFD]),
+    ("tangent.h", "product rule with a dropped term",
+     "return {a.v * b.v, a.d * b.v + a.v * b.d};", "return {a.v * b.v, a.d * b.v};", [TANFD]),
+    ("tangent.h", "quotient rule sign",
+     "return {q, (a.d - q * b.d) / b.v};", "return {q, (a.d + q * b.d) / b.v};", [TANFD]),
+    ("tangent.h", "power rule without the exponent",
+     "return {p, e * std::pow(x.v, e - 1.0) * x.d};", "return {p, std::pow(x.v, e - 1.0) * x.d};",
+     [TANFD]),
     ("turbulence.py", "sixth-order difference coefficient",
      "(45.0 * s(1) - 9.0 * s(2) + s(3))", "(45.0 * s(1) - 8.0 * s(2) + s(3))", [ENSTROPHY]),
     ("turbulence.py", "vorticity component from the wrong gradient",
