@@ -98,3 +98,41 @@ def test_default_config_is_the_taylor_green_setting(lib):
     assert cfg.mu_ref == pytest.approx(1 / 1600)
     assert cfg.p_ref == pytest.approx(100 / 1.4)
     assert lib.hgks_default_config(ctypes.byref(cfg), 5) == _lib.HGKS_E_INVAL
+
+
+def test_null_arguments_are_rejected_before_any_device_work(lib):
+    # The error behaviour the header states: a null context or output is
+    # E_INVAL (destroying nothing is OK); no call reaches the device.
+    E = _lib.HGKS_E_INVAL
+    d = ctypes.c_double()
+    i = ctypes.c_int()
+    buf = (ctypes.c_double * 8)()
+    cfg = _lib.HgksConfig()
+    assert lib.hgks_default_config(ctypes.byref(cfg), 16) == _lib.HGKS_OK
+    calls = [
+        lib.hgks_default_config(None, 16),
+        lib.hgks_create(ctypes.byref(cfg), None, None),
+        lib.hgks_init_state(None, buf, 1),
+        lib.hgks_init_conservative(None, buf, 1),
+        lib.hgks_get_state(None, buf, 1),
+        lib.hgks_step(None, 1, 0.0, 1, ctypes.byref(d)),
+        lib.hgks_set_time(None, 0.0, 0),
+        lib.hgks_diagnostics(None, ctypes.byref(_lib.HgksDiag())),
+        lib.hgks_turbulence_stats(None, ctypes.byref(_lib.HgksTurbulence())),
+        lib.hgks_channel_stats(None, buf, ctypes.byref(_lib.HgksChannel())),
+        lib.hgks_adjoint_step(None, 0.1, buf, buf),
+        lib.hgks_autotune(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(d)),
+        lib.hgks_set_sweep_shape(None, 0, 0),
+        lib.hgks_profile_step(None, 0.0, buf, 8),
+        lib.hgks_ensemble_create(None, 1, None),
+        lib.hgks_ensemble_step(None, 1, 0.0, 1),
+        lib.hgks_step_noalloc(None, buf, 1, 0.0, None),
+        lib.hgks_step_noalloc(ctypes.byref(cfg), None, 1, 0.0, None),
+        lib.hgks_step_noalloc(ctypes.byref(cfg), buf, -1, 0.0, None),
+        lib.hgks_measure_fp_peaks(None, None),
+    ]
+    assert calls == [E] * len(calls)
+    assert lib.hgks_destroy(None) == _lib.HGKS_OK
+    assert lib.hgks_ensemble_destroy(None) == _lib.HGKS_OK
+    assert lib.hgks_last_error(None)
+    assert lib.hgks_ensemble_last_error(None) == b""
