@@ -259,8 +259,9 @@ hgks_status hgks_profile_step(hgks_ctx* ctx, double dt, double* ms_out, int ncla
  * may).  No counterpart in the paper: it is the step of hgks_step with its
  * working buffers in one scratch array of fixed size (about 15 MiB) that is
  * part of the library image; every GPU that loads the library holds it until
- * the process exits.  Limits: at most 32 cells on every axis (larger grids
- * return E_UNSUPPORTED); cfg must be valid (else E_INVAL).  dt > 0 fixes the
+ * the process exits.  Limits: at most 32 cells on every axis and the
+ * constant body force only (larger grids and force_mode 1 return
+ * E_UNSUPPORTED); cfg must be valid (else E_INVAL).  dt > 0 fixes the
  * step, dt <= 0 takes the CFL step.  Work is enqueued on `stream` (a
  * cudaStream_t; NULL is the legacy default stream) and the call returns
  * without waiting; no non-physical-state check is made.  The first call on a

@@ -136,3 +136,18 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert lib.hgks_ensemble_destroy(None) == _lib.HGKS_OK
     assert lib.hgks_last_error(None)
     assert lib.hgks_ensemble_last_error(None) == b""
+
+
+def test_allocation_free_step_limits_are_checked_on_the_host(lib):
+    # hgks_step_noalloc: an invalid configuration is E_INVAL, a grid above its
+    # fixed capacity or the constant-mass-flux force is E_UNSUPPORTED, all
+    # before any device call.
+    buf = (ctypes.c_double * 8)()
+    for fields, status in (({"gamma": 1.0}, _lib.HGKS_E_INVAL),
+                           ({"nx": 33}, _lib.HGKS_E_UNSUPPORTED),
+                           ({"force_mode": 1}, _lib.HGKS_E_UNSUPPORTED)):
+        cfg = _lib.HgksConfig()
+        assert lib.hgks_default_config(ctypes.byref(cfg), 16) == _lib.HGKS_OK
+        for k, v in fields.items():
+            setattr(cfg, k, v)
+        assert lib.hgks_step_noalloc(ctypes.byref(cfg), buf, 1, 0.0, None) == status
