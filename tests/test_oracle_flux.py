@@ -7,7 +7,7 @@
 * Equal left, right and equilibrium states reduce the full flux to the
   simplified smooth flux (Sec. 2.1, Remark 1).
 * Navier-Stokes limits of the smooth flux: shear stress mu du/dy, heat flux
-  kappa dT/dx with kappa = mu c_p / Pr, and normal stress
+  kappa dT/dx with kappa = mu c_p / Pr (at rest and in a moving gas), and normal stress
   (4/3 mu + mu_b) du/dx with mu_b = 2N/(3(N+3)) mu (Sec. 3.1).
 """
 import math
@@ -144,6 +144,25 @@ def test_smooth_flux_shear_stress():
     assert F[4] == pytest.approx(-MU * s * V, rel=1e-9)
 
 
+@pytest.mark.parametrize("prandtl", [1.0, 0.72])
+def test_heat_flux_in_a_moving_gas(prandtl):
+    # Galilean invariance: a temperature gradient at uniform pressure carried
+    # by a uniform velocity (U, V, W) has no viscous stress, so the energy
+    # flux is the Euler one plus -mu c_p / Pr dT/dx, with the Prandtl
+    # correction measured in the frame of the gas.
+    p, T, s = 2.0, 1.6, 0.5                      # T(x) with dT/dx = s, p uniform
+    U, V, W = 0.7, -0.4, 0.3
+    rho = p / T
+    Q = cons(rho, U, V, W, p)
+    drho = -rho * s / T
+    dQ = np.array([drho, U * drho, V * drho, W * drho, 0.5 * (U * U + V * V + W * W) * drho])
+    F, _ = oracle.flux_point(cfg(0, prandtl, MU), point_with_x_gradient(Q, dQ), 1e-3)
+    cp = (K + 5) / 2.0
+    E = euler_flux(Q)
+    assert F[:4] == pytest.approx(E[:4], rel=1e-12, abs=1e-12)
+    assert F[4] == pytest.approx(E[4] - MU * cp / prandtl * s, rel=1e-10)
+
+
 @pytest.mark.parametrize("flux", [0, 1])
 def test_shear_stress_follows_the_power_law_viscosity(flux):
     # Sec. 3.4: mu = mu_ref (T / T_ref)^0.76; the stress of a uniform shear at
@@ -179,3 +198,23 @@ def test_smooth_flux_normal_stress_and_bulk_viscosity():
     F, _ = oracle.flux_point(cfg(0, 0.72, MU), point_with_x_gradient(Q, dQ), 1e-3)
     mu_b = 2 * K / (3 * (K + 3)) * MU
     assert F[1] == pytest.approx(p - (4.0 / 3.0 * MU + mu_b) * s, rel=1e-12)
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+def test_normal_stress_work_in_a_moving_gas(flux):
+    # u = U + s x with V, W uniform, rho and p uniform: the stress is the
+    # normal one, (4/3 mu + mu_b) s, it does work U (4/3 mu + mu_b) s on the
+    # energy flux, and no heat flows (T uniform), so the Prandtl correction,
+    # taken in the frame of the gas, adds nothing (Pr = 0.72 here).
+    rho, p, s = 1.0, 5.0, 0.7
+    U, V, W = 0.6, -0.5, 0.25
+    Q = cons(rho, U, V, W, p)
+    dQ = np.array([0.0, rho * s, 0.0, 0.0, rho * U * s])
+    F, _ = oracle.flux_point(cfg(flux, 0.72, MU), point_with_x_gradient(Q, dQ), 1e-4)
+    sxx = (4.0 / 3.0 * MU + 2 * K / (3 * (K + 3)) * MU) * s
+    E = euler_flux(Q)
+    assert F[0] == pytest.approx(E[0], rel=1e-12)
+    assert F[1] == pytest.approx(E[1] - sxx, rel=1e-10)
+    assert F[2] == pytest.approx(E[2], rel=1e-10)
+    assert F[3] == pytest.approx(E[3], rel=1e-10)
+    assert F[4] == pytest.approx(E[4] - U * sxx, rel=1e-10)

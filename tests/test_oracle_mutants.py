@@ -43,6 +43,8 @@ WRAP = "tests/test_oracle_scheme.py::test_periodic_ghost_cells_wrap_including_co
 CHARBASIS = "tests/test_oracle_char.py::test_basis_diagonalises_the_euler_jacobian"
 CHARTANG = "tests/test_oracle_char.py::test_tangential_reconstruction_separates_superposed_fields"
 CHARNORM = "tests/test_oracle_char.py::test_two_superposed_fields_are_reconstructed_separately"
+MOVINGSTRESS = "tests/test_oracle_flux.py::test_normal_stress_work_in_a_moving_gas"
+XIMOM = "tests/test_oracle_pieces.py::test_internal_moments_match_radial_quadrature"
 
 # (name, text in hgks_oracle.cpp, planted replacement, pins)
 MUTANTS = [
@@ -141,6 +143,21 @@ MUTANTS = [
      "b[i] = dQ[d][i] / Q[0];", "b[i] = dQ[d][i];", [BRUTE]),
     ("derivative of the tangential quadratic",
      "der[m] = b + 2.0 * c * s;", "der[m] = b + c * s;", [TANGQ]),
+    ("heat polynomial of the Prandtl correction (xi^2 term)",
+     "p.add(-0.5 * U, 0, 0, 0, 1);", "p.add(0.5 * U, 0, 0, 0, 1);", [MOVINGSTRESS]),
+    ("sign of the exponential term of the u < 0 half-space moment",
+     "g.un[1] = g.U * g.un[0] - e;", "g.un[1] = g.U * g.un[0] + e;", [MOMENTS]),
+    ("moments of the internal degrees of freedom",
+     "g.xi[m - 1] * (K + 2.0 * (m - 1)) / (2.0 * lam)", "g.xi[m - 1] * (K + 2.0 * m) / (2.0 * lam)",
+     [XIMOM]),
+    ("lambda of the Maxwellian",
+     "g.lam = Q[0] / (2.0 * p);", "g.lam = Q[0] / p;", [BRUTE]),
+    ("internal degrees of freedom",
+     "const double K = (5.0 - 3.0 * gamma) / (gamma - 1.0);",
+     "const double K = (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0;", [BRUTE]),
+    ("time integral of (t + tau) e^{-t/tau} - tau",
+     "q[1] = 2.0 * tau * tau * (1.0 - e) - tau * T * (1.0 + e);",
+     "q[1] = 2.0 * tau * tau * (1.0 - e) - tau * T * (1.0 - e);", [TIMEINT]),
 ]
 
 
