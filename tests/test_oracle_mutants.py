@@ -158,6 +158,20 @@ MUTANTS = [
     ("time integral of (t + tau) e^{-t/tau} - tau",
      "q[1] = 2.0 * tau * tau * (1.0 - e) - tau * T * (1.0 + e);",
      "q[1] = 2.0 * tau * tau * (1.0 - e) - tau * T * (1.0 - e);", [TIMEINT]),
+    ("Gauss abscissae",
+     "const double kGaussS[2] = {-0.5 / std::sqrt(3.0), 0.5 / std::sqrt(3.0)};",
+     "const double kGaussS[2] = {-0.3, 0.3};", [QUARTIC]),
+    ("periodic x ghost one cell off",
+     "Q(a, v, -m, j, k) = Q(a, v, n[0] - m, j, k);", "Q(a, v, -m, j, k) = Q(a, v, n[0] - m - 1, j, k);",
+     [WRAP]),
+    ("periodic y ghosts all from one row",
+     "Q(a, v, i, -m, k) = Q(a, v, i, n[1] - m, k);", "Q(a, v, i, -m, k) = Q(a, v, i, n[1] - 1, k);",
+     [WRAP]),
+    ("internal-energy factor of a moment product",
+     "c * um[a] * g.v[b] * g.w[w] * g.xi[d]", "c * um[a] * g.v[b] * g.w[w] * g.xi[d > 0 ? d - 1 : 0]",
+     [BRUTE]),
+    ("w factor of a moment product taken from v",
+     "c * um[a] * g.v[b] * g.w[w] * g.xi[d]", "c * um[a] * g.v[b] * g.v[w] * g.xi[d]", [BRUTE]),
 ]
 
 
