@@ -188,6 +188,12 @@ TANFD = "tests/test_oracle_tangent.py::test_tangent_equals_central_differences_w
 # The dual numbers of the tangent build and the numpy statistics:
 # (file, name, text, planted replacement, pins)
 STAT_MUTANTS = [
+    ("__init__.py", "energy of the primitive-to-conservative map",
+     "p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)",
+     "p / gamma + 0.5 * rho * (u * u + v * v + w * w)", [CHARBASIS, COMPRESSION]),
+    ("__init__.py", "momenta of the primitive-to-conservative map exchanged",
+     "return np.stack([rho, rho * u, rho * v, rho * w,", "return np.stack([rho, rho * u, rho * w, rho * v,",
+     [POTENTIAL]),
     ("tangent.h", "derivative of sqrt",
      "return {s, x.d / (2.0 * s)};", "return {s, x.d / s};", [TANFD]),
     ("tangent.h", "sign of the derivative of erfc",
