@@ -182,6 +182,7 @@ TWOMODES = "tests/test_oracle_turbulence.py::test_skewness_and_flatness_of_two_m
 POWERNP = "tests/test_oracle_turbulence.py::test_power_law_viscosity_scales_with_temperature"
 POISEUILLE = "tests/test_oracle_channel.py::test_poiseuille_statistics_in_closed_form"
 POTENTIAL = "tests/test_oracle_turbulence.py::test_potential_flow_closed_forms"
+DENSITY = "tests/test_oracle_channel.py::test_wall_and_bulk_densities_with_a_density_profile"
 
 TANFD = "tests/test_oracle_tangent.py::test_tangent_equals_central_differences_where_smooth"
 
@@ -229,6 +230,10 @@ STAT_MUTANTS = [
     ("channel.py", "skin-friction dynamic pressure",
      "(0.5 * out[\"rho_b\"] * out[\"U_b\"] ** 2)", "(out[\"rho_b\"] * out[\"U_b\"] ** 2)",
      [POISEUILLE]),
+    ("channel.py", "wall density from the lower wall only",
+     'out["rho_w"] = 0.5 * (rm[0] + rm[-1])', 'out["rho_w"] = rm[0]', [DENSITY]),
+    ("channel.py", "bulk density without the cell heights",
+     'out["rho_b"] = (rm * dy).sum() / ly', 'out["rho_b"] = rm.mean()', [DENSITY]),
     ("channel.py", "centreline cubic about the wrong point",
      "faces[j0 + k] - yc, faces[j0 + k + 1] - yc", "faces[j0 + k] - yc, faces[j0 + k + 1] - yc + 0.01",
      [POISEUILLE]),
