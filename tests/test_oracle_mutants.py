@@ -183,6 +183,7 @@ POWERNP = "tests/test_oracle_turbulence.py::test_power_law_viscosity_scales_with
 POISEUILLE = "tests/test_oracle_channel.py::test_poiseuille_statistics_in_closed_form"
 POTENTIAL = "tests/test_oracle_turbulence.py::test_potential_flow_closed_forms"
 DENSITY = "tests/test_oracle_channel.py::test_wall_and_bulk_densities_with_a_density_profile"
+RHO0 = "tests/test_oracle_turbulence.py::test_reference_density_divides_the_normalised_quantities"
 
 TANFD = "tests/test_oracle_tangent.py::test_tangent_equals_central_differences_where_smooth"
 
@@ -218,6 +219,10 @@ STAT_MUTANTS = [
      'out["eps3"] = -avg(p * theta) / rho0', 'out["eps3"] = avg(p * theta) / rho0', [COMPRESSION]),
     ("turbulence.py", "dilatational dissipation factor",
      'out["eps_d"] = 4.0 / 3.0 * avg', 'out["eps_d"] = avg', [COMPRESSION]),
+    ("turbulence.py", "eps2 not normalised by the reference density",
+     'out["eps2"] = avg(mu_b * theta ** 2) / rho0', 'out["eps2"] = avg(mu_b * theta ** 2)', [RHO0]),
+    ("turbulence.py", "enstrophy not normalised by the reference density",
+     'out["zeta"] = avg(0.5 * rho * w2) / rho0', 'out["zeta"] = avg(0.5 * rho * w2)', [RHO0]),
     ("turbulence.py", "skewness normalisation",
      "m3[i] / m2[i] ** 1.5", "m3[i] / m2[i] ** 2", [TWOMODES]),
     ("turbulence.py", "viscosity law",

@@ -154,3 +154,20 @@ def test_power_law_viscosity_scales_with_temperature():
     for k in ("eps1", "eps2", "eps_s", "eps_d"):
         assert b[k] == pytest.approx(f * a[k], rel=1e-12)
     assert b["eps3"] == pytest.approx(a["eps3"], rel=1e-12)
+
+
+def test_reference_density_divides_the_normalised_quantities():
+    # Sec. 3.1 / 3.4: E_k, zeta and eps1..eps3 are normalised by rho0; K,
+    # eps_s, eps_d and <p theta> are not.  A compressed Taylor-Green field
+    # (so that theta != 0) evaluated with rho0 = 1 and rho0 = 2.
+    n = 12
+    prim = inputs.taylor_green(n)
+    x = inputs.centres(n, 2 * math.pi)
+    prim[1] += 0.2 * np.sin(x)[None, None, :]
+    cons = conservative(prim, GAMMA)
+    a = statistics(cons, gamma=GAMMA, rho0=1.0, mu_ref=0.01)
+    b = statistics(cons, gamma=GAMMA, rho0=2.0, mu_ref=0.01)
+    for k in ("Ek", "zeta", "eps1", "eps2", "eps3"):
+        assert abs(a[k]) > 0 and b[k] == pytest.approx(a[k] / 2, rel=1e-14), k
+    for k in ("K", "eps_s", "eps_d", "p_theta"):
+        assert abs(a[k]) > 0 and b[k] == pytest.approx(a[k], rel=1e-14), k
