@@ -283,6 +283,23 @@ hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_inout, int ns
  * all.  Allocates and frees a small output buffer; synchronises. */
 hgks_status hgks_measure_fp_peaks(void* stream, double* tflops_out);
 
+/* Algorithmic operation count of one face of the sweep kernel (no
+ * counterpart in the paper; the numerator of the sweep's ALU roofline).  The
+ * closed forms the kernel evaluates -- WENO5 end values, normal slopes and
+ * the compatibility state of Sec. 2.1 and Remark 1 at one face point, the
+ * tangential pass along t1 at one point, and the tangential pass along t2
+ * with the flux of Eq. (5) (smooth or full) at the four Gauss points of one
+ * face -- are run on the HOST with a counting number type, once each, i.e.
+ * without the recomputation of a tile's halo.  Stage 1 or 2 (stage 2 needs
+ * dF only, Eq. (6)).  out (host, 21 doubles): for each part p = 0 (face
+ * fields, per point), 1 (t1 pass, per point), 2 (t2 pass and flux, per face)
+ * the counts out[7p + 0..6] of additions (and subtractions), multiplications,
+ * divisions, square roots, exponentials, error functions and powers.  An FMA
+ * counts as one addition and one multiplication; operations on per-run
+ * constants only are not counted.  Conservative-variable reconstruction only
+ * (E_UNSUPPORTED for recon_vars = 1 with WENO).  No device work. */
+hgks_status hgks_count_flops(const hgks_config* cfg, int stage, double* out);
+
 /* Message of the last failed call on ctx ("" if none); valid until the next
  * call on ctx.  ctx may be NULL for errors of hgks_create. */
 const char* hgks_last_error(const hgks_ctx* ctx);

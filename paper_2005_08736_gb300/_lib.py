@@ -25,7 +25,7 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
            "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape",
            "hgks_turbulence_stats", "hgks_measure_fp_peaks", "hgks_channel_stats",
-           "hgks_set_time"]
+           "hgks_set_time", "hgks_count_flops"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 
 
@@ -121,6 +121,7 @@ def load(path: str | None = None):
         L.hgks_measure_fp_peaks.argtypes = [vp, pd]
         L.hgks_channel_stats.argtypes = [vp, pd, ctypes.POINTER(HgksChannel)]
         L.hgks_set_time.argtypes = [vp, d, ctypes.c_longlong]
+        L.hgks_count_flops.argtypes = [pcfg, i, pd]
         L.hgks_last_error.argtypes = [vp]
         L.hgks_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:

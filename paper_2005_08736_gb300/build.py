@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhgks.so")
-SOURCES = ["hgks_api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "peaks.cu"]
+SOURCES = ["hgks_api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "peaks.cu", "flopcount.cu"]
 # The FP32 kernels use approximate division and square root (2 ulp) and flush
 # denormals: the WENO weights and the flux need no correctly rounded quotient,
 # and the FP32 results are held to their own tolerance against the FP64 oracle.

@@ -30,7 +30,7 @@ struct CharBasis {
 
 // Basis at the state Q_ref + dqm.
 template <class T>
-__device__ __forceinline__ CharBasis<T> char_basis(const T dqm[5], const Gas<T>& g) {
+HGKS_HD CharBasis<T> char_basis(const T dqm[5], const Gas<T>& g) {
   const Prim<T> s = prim_of(dqm, g);
   CharBasis<T> b;
   b.u = s.U;
@@ -48,7 +48,7 @@ __device__ __forceinline__ CharBasis<T> char_basis(const T dqm[5], const Gas<T>&
 
 // omega = R^{-1} q
 template <class T>
-__device__ __forceinline__ void to_char(const CharBasis<T>& b, const T q[5], T o[5]) {
+HGKS_HD void to_char(const CharBasis<T>& b, const T q[5], T o[5]) {
   const T k = b.b1 * (b.u * q[1] + b.v * q[2] + b.w * q[3] - q[4]);  // b1 (U.m - E)
   const T a = b.b2 * q[0] - k;                                        // b2 q0 - k
   const T s = (b.u * q[0] - q[1]) * b.ic;                             // (u q0 - q1)/c
@@ -61,7 +61,7 @@ __device__ __forceinline__ void to_char(const CharBasis<T>& b, const T q[5], T o
 
 // q = R omega
 template <class T>
-__device__ __forceinline__ void from_char(const CharBasis<T>& b, const T o[5], T q[5]) {
+HGKS_HD void from_char(const CharBasis<T>& b, const T o[5], T q[5]) {
   const T m = o[0] + o[1] + o[4];
   const T d = (o[4] - o[0]) * b.c;
   q[0] = m;

@@ -38,7 +38,7 @@ __device__ __forceinline__ bool compat_small_jump(const float dm[5], const float
 }
 
 template <class T>
-__device__ __forceinline__ void compat_state(const T dql[5], const T dqr[5], const Gas<T>& g, T dq0[5]) {
+HGKS_HD void compat_state(const T dql[5], const T dqr[5], const Gas<T>& g, T dq0[5]) {
   if constexpr (std::is_same<T, float>::value) {
     float dm[5], dd[5];
 #pragma unroll

@@ -13,6 +13,12 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+// The arithmetic below is compiled for the device and, where host code
+// instantiates it (the operation tally of flopcount.cu), for the host.
+#ifndef HGKS_HD
+#define HGKS_HD __host__ __device__ __forceinline__
+#endif
+
 namespace hgks {
 
 // Problem constants passed by value to every kernel.
@@ -28,22 +34,22 @@ struct Gas {
   T h_r;            // rho_r E_r + p_r = gamma/(gamma-1) p_r
 };
 
-template <class T> __device__ __forceinline__ T tsqrt(T x);
-template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
-template <class T> __device__ __forceinline__ T texp(T x);
-template <> __device__ __forceinline__ float texp<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
-template <class T> __device__ __forceinline__ T texpm1(T x);
-template <> __device__ __forceinline__ float texpm1<float>(float x) { return expm1f(x); }
-template <> __device__ __forceinline__ double texpm1<double>(double x) { return expm1(x); }
-template <class T> __device__ __forceinline__ T terf(T x);
-template <> __device__ __forceinline__ float terf<float>(float x) { return erff(x); }
-template <> __device__ __forceinline__ double terf<double>(double x) { return erf(x); }
-template <class T> __device__ __forceinline__ T tpow(T x, T y);
-template <> __device__ __forceinline__ float tpow<float>(float x, float y) { return powf(x, y); }
-template <> __device__ __forceinline__ double tpow<double>(double x, double y) { return pow(x, y); }
-template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+template <class T> HGKS_HD T tsqrt(T x);
+template <> HGKS_HD float tsqrt<float>(float x) { return sqrtf(x); }
+template <> HGKS_HD double tsqrt<double>(double x) { return sqrt(x); }
+template <class T> HGKS_HD T texp(T x);
+template <> HGKS_HD float texp<float>(float x) { return expf(x); }
+template <> HGKS_HD double texp<double>(double x) { return exp(x); }
+template <class T> HGKS_HD T texpm1(T x);
+template <> HGKS_HD float texpm1<float>(float x) { return expm1f(x); }
+template <> HGKS_HD double texpm1<double>(double x) { return expm1(x); }
+template <class T> HGKS_HD T terf(T x);
+template <> HGKS_HD float terf<float>(float x) { return erff(x); }
+template <> HGKS_HD double terf<double>(double x) { return erf(x); }
+template <class T> HGKS_HD T tpow(T x, T y);
+template <> HGKS_HD float tpow<float>(float x, float y) { return powf(x, y); }
+template <> HGKS_HD double tpow<double>(double x, double y) { return pow(x, y); }
+template <class T> HGKS_HD T tabs(T x) { return x < T(0) ? -x : x; }
 
 template <class T>
 struct Prim {
@@ -55,7 +61,7 @@ struct Prim {
 
 // Primitive variables of the state Q_ref + dq (local frame).
 template <class T>
-__device__ __forceinline__ Prim<T> prim_of(const T dq[5], const Gas<T>& g) {
+HGKS_HD Prim<T> prim_of(const T dq[5], const Gas<T>& g) {
   Prim<T> s;
   s.rho = g.rho_r + dq[0];
   const T inv = T(1) / s.rho;
@@ -80,7 +86,7 @@ struct Mom {
 };
 
 template <class T>
-__device__ __forceinline__ void gauss_recursion(T* m, T U, T theta) {
+HGKS_HD void gauss_recursion(T* m, T U, T theta) {
   // <c^(n+2)> = U <c^(n+1)> + (n+1) theta <c^n>, on the line and on half lines.
 #pragma unroll
   for (int n = 0; n < 5; ++n) m[n + 2] = U * m[n + 1] + T(n + 1) * theta * m[n];
@@ -88,7 +94,7 @@ __device__ __forceinline__ void gauss_recursion(T* m, T U, T theta) {
 
 // half: 0 whole line, +1 u > 0, -1 u < 0.
 template <class T>
-__device__ __forceinline__ void moments(const Prim<T>& s, const Gas<T>& g, int half, Mom<T>& m) {
+HGKS_HD void moments(const Prim<T>& s, const Gas<T>& g, int half, Mom<T>& m) {
   if (half == 0) {
     m.u[0] = T(1);
     m.u[1] = s.U;
@@ -113,13 +119,13 @@ __device__ __forceinline__ void moments(const Prim<T>& s, const Gas<T>& g, int h
 
 // <u^a v^b w^c>
 template <int A, int B, int C, class T>
-__device__ __forceinline__ T mm(const Mom<T>& m) {
+HGKS_HD T mm(const Mom<T>& m) {
   return m.u[A] * m.v[B] * m.w[C];
 }
 
 // <u^a v^b w^c psi>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2)
 template <int A, int B, int C, class T>
-__device__ __forceinline__ void mom_psi(const Mom<T>& m, T out[5]) {
+HGKS_HD void mom_psi(const Mom<T>& m, T out[5]) {
   const T m0 = mm<A, B, C>(m);
   out[0] = m0;
   out[1] = mm<A + 1, B, C>(m);
@@ -130,7 +136,7 @@ __device__ __forceinline__ void mom_psi(const Mom<T>& m, T out[5]) {
 
 // <(a.psi) u^a v^b w^c psi>, a.psi = a0 + a1 u + a2 v + a3 w + a4 (u^2+v^2+w^2+xi^2)/2.
 template <int A, int B, int C, class T>
-__device__ __forceinline__ void mom_apsi(const Mom<T>& m, const T a[5], T out[5]) {
+HGKS_HD void mom_apsi(const Mom<T>& m, const T a[5], T out[5]) {
   T t0[5], t1[5], t2[5], t3[5], tu[5], tv[5], tw[5];
   mom_psi<A, B, C>(m, t0);
   mom_psi<A + 1, B, C>(m, t1);
@@ -158,7 +164,7 @@ __device__ __forceinline__ void mom_apsi(const Mom<T>& m, const T a[5], T out[5]
 // Symmetric matrix <u^a v^b w^c psi_i psi_j> (upper triangle, 15 entries in
 // the order 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44).
 template <int A, int B, int C, class T>
-__device__ __forceinline__ void mom_psipsi(const Mom<T>& m, T M[15]) {
+HGKS_HD void mom_psipsi(const Mom<T>& m, T M[15]) {
   const T x1 = m.xi1, x2 = m.xi2;
   const T m0 = mm<A, B, C>(m);
   const T mu1 = mm<A + 1, B, C>(m), mv1 = mm<A, B + 1, C>(m), mw1 = mm<A, B, C + 1>(m);
@@ -184,7 +190,7 @@ __device__ __forceinline__ void mom_psipsi(const Mom<T>& m, T M[15]) {
 
 // out += M a for the symmetric matrix M of mom_psipsi.
 template <class T>
-__device__ __forceinline__ void sym5_matvec_add(const T M[15], const T a[5], T out[5]) {
+HGKS_HD void sym5_matvec_add(const T M[15], const T a[5], T out[5]) {
   out[0] += M[0] * a[0] + M[1] * a[1] + M[2] * a[2] + M[3] * a[3] + M[4] * a[4];
   out[1] += M[1] * a[0] + M[5] * a[1] + M[6] * a[2] + M[7] * a[3] + M[8] * a[4];
   out[2] += M[2] * a[0] + M[6] * a[1] + M[9] * a[2] + M[10] * a[3] + M[11] * a[4];
@@ -195,7 +201,7 @@ __device__ __forceinline__ void sym5_matvec_add(const T M[15], const T a[5], T o
 // Solution a of <a.psi psi> = b (moment matrix of the Maxwellian, K internal
 // degrees of freedom), in closed form.
 template <class T>
-__device__ __forceinline__ void slope_solve(const Prim<T>& s, const Gas<T>& g, const T b[5],
+HGKS_HD void slope_solve(const Prim<T>& s, const Gas<T>& g, const T b[5],
                                             T a[5]) {
   const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
   const T k3t = (g.K + T(3)) * s.theta;
@@ -210,7 +216,7 @@ __device__ __forceinline__ void slope_solve(const Prim<T>& s, const Gas<T>& g, c
 
 // <u (a_n.psi u + a_t1.psi v + a_t2.psi w) psi>
 template <class T>
-__device__ __forceinline__ void mom_u_adotu(const Mom<T>& m, const T a[3][5], T out[5]) {
+HGKS_HD void mom_u_adotu(const Mom<T>& m, const T a[3][5], T out[5]) {
   T r0[5], r1[5], r2[5];
   mom_apsi<2, 0, 0>(m, a[0], r0);
   mom_apsi<1, 1, 0>(m, a[1], r1);
@@ -222,7 +228,7 @@ __device__ __forceinline__ void mom_u_adotu(const Mom<T>& m, const T a[3][5], T 
 // rho <u psi> - E(Q_ref): the Euler flux of the state minus that of the
 // reference state (0, p_r, 0, 0, 0), formed from deviations.
 template <class T>
-__device__ __forceinline__ void euler_flux_dev(const Prim<T>& s, const T dq[5], const Gas<T>& g,
+HGKS_HD void euler_flux_dev(const Prim<T>& s, const T dq[5], const Gas<T>& g,
                                                T out[5]) {
   const T m = s.rho * s.U;
   out[0] = m;
@@ -243,7 +249,7 @@ struct PointState {
 // Directional derivative of the Euler flux along local axis J at the state s
 // (H = rho E + p) in the direction dQ: J_J(Q) dQ.
 template <int J, class T>
-__device__ __forceinline__ void euler_jvp(const Prim<T>& s, T H, const T dQ[5], const Gas<T>& g,
+HGKS_HD void euler_jvp(const Prim<T>& s, T H, const T dQ[5], const Gas<T>& g,
                                           T out[5]) {
   const T inv = s.inv_rho;
   const T U[3] = {s.U, s.V, s.W};
@@ -264,7 +270,7 @@ __device__ __forceinline__ void euler_jvp(const Prim<T>& s, T H, const T dQ[5], 
 // each moment of (a.psi) g is the derivative of the Maxwellian's moment along
 // the parameter change that a encodes.
 template <class T>
-__device__ __forceinline__ void state_time_derivative(const Prim<T>& s, T H, const T dq[3][5],
+HGKS_HD void state_time_derivative(const Prim<T>& s, T H, const T dq[3][5],
                                                       const Gas<T>& g, T Qt[5]) {
   T j0[5], j1[5], j2[5];
   euler_jvp<0>(s, H, dq[0], g, j0);
@@ -278,7 +284,7 @@ __device__ __forceinline__ void state_time_derivative(const Prim<T>& s, T H, con
 // time coefficient A from <(a_n u + a_t1 v + a_t2 w + A) psi> = 0 (Sec. 2.1),
 // i.e. <A psi> = Q_t / rho.
 template <class T>
-__device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Gas<T>& g, const T q[5],
+HGKS_HD void slopes_and_A(const Prim<T>& s, const Gas<T>& g, const T q[5],
                                              const T dq[3][5], T a[3][5], T A[5]) {
   const T inv = s.inv_rho;
 #pragma unroll
@@ -302,7 +308,7 @@ __device__ __forceinline__ void slopes_and_A(const Prim<T>& s, const Gas<T>& g, 
 // with c_p = (K+5)/2; `heat_scale` multiplies the heat flux (1/Pr for the
 // Prandtl fix).
 template <class T>
-__device__ __forceinline__ void ns_viscous_flux(const Prim<T>& s, const T dq[3][5], const Gas<T>& g,
+HGKS_HD void ns_viscous_flux(const Prim<T>& s, const T dq[3][5], const Gas<T>& g,
                                                 T mu, T heat_scale, T Fv[5]) {
   const T inv = s.inv_rho;
   const T U[3] = {s.U, s.V, s.W};
@@ -328,7 +334,7 @@ __device__ __forceinline__ void ns_viscous_flux(const Prim<T>& s, const T dq[3][
 }
 
 template <class T>
-__device__ __forceinline__ T viscosity(const Prim<T>& s, const Gas<T>& g) {
+HGKS_HD T viscosity(const Prim<T>& s, const Gas<T>& g) {
   if (g.visc_law == 1) return g.mu_ref * tpow(s.theta * g.T_ref_inv, g.visc_exp);
   return g.mu_ref;
 }
@@ -341,7 +347,7 @@ __device__ __forceinline__ T viscosity(const Prim<T>& s, const Gas<T>& g) {
 // scales the heat flux by 1/Pr.  Returns F - E(Q_ref) and dF; want_F = false
 // skips F (second S2O4 stage).
 template <class T>
-__device__ __forceinline__ void flux_smooth(const PointState<T>& st0, const Gas<T>& g, bool want_F,
+HGKS_HD void flux_smooth(const PointState<T>& st0, const Gas<T>& g, bool want_F,
                                             T F[5], T dF[5]) {
   const Prim<T> s = prim_of(st0.q, g);
   const T H = g.h_r + st0.q[4] + s.dp;
@@ -360,7 +366,7 @@ __device__ __forceinline__ void flux_smooth(const PointState<T>& st0, const Gas<
 // time-integrated terms of Eq. (5), in closed form with y = 1 - exp(-dt/(2 tau)),
 // r = tau/dt: term k contributes Fq[k] V_k to F and dFq[k] V_k to dF.
 template <class T>
-__device__ __forceinline__ void fit_coefficients(T tau, T dt, T Fq[6], T dFq[6]) {
+HGKS_HD void fit_coefficients(T tau, T dt, T Fq[6], T dFq[6]) {
   const T y = -texpm1(-dt / (T(2) * tau));
   const T eh = T(1) - y;
   const T r = tau / dt;
@@ -403,7 +409,7 @@ struct FullSide {
 };
 
 template <class T>
-__device__ __forceinline__ void flux_full_eq(const PointState<T>& st0, const Gas<T>& g, FullEq<T>& o) {
+HGKS_HD void flux_full_eq(const PointState<T>& st0, const Gas<T>& g, FullEq<T>& o) {
   const Prim<T> s = prim_of(st0.q, g);
   const T H = g.h_r + st0.q[4] + s.dp;
   euler_flux_dev(s, st0.q, g, o.V[0]);
@@ -424,7 +430,7 @@ __device__ __forceinline__ void flux_full_eq(const PointState<T>& st0, const Gas
 
 // side = 0: g_l over u > 0; side = 1: g_r over u < 0.
 template <class T>
-__device__ __forceinline__ void flux_full_side(const PointState<T>& st, const Gas<T>& g, int side,
+HGKS_HD void flux_full_side(const PointState<T>& st, const Gas<T>& g, int side,
                                                FullSide<T>& o) {
   const Prim<T> s = prim_of(st.q, g);
   Mom<T> mh;
@@ -454,7 +460,7 @@ __device__ __forceinline__ void flux_full_side(const PointState<T>& st, const Ga
 }
 
 template <class T>
-__device__ __forceinline__ T collision_time_full(T mu0, T p0, T pl, T pr, const Gas<T>& g, T dt) {
+HGKS_HD T collision_time_full(T mu0, T p0, T pl, T pr, const Gas<T>& g, T dt) {
   return mu0 / p0 + g.tau_num_C * tabs((pl - pr) / (pl + pr)) * dt;
 }
 
@@ -462,7 +468,7 @@ __device__ __forceinline__ T collision_time_full(T mu0, T p0, T pl, T pr, const 
 // 1 - H(u) on g_r, integrated over [0, dt] and [0, dt/2] and fitted linearly
 // (Eq. (7)).  Returns F - E(Q_ref) and dF.
 template <class T>
-__device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointState<T>& str,
+HGKS_HD void flux_full(const PointState<T>& stl, const PointState<T>& str,
                                           const PointState<T>& st0, const Gas<T>& g, T dt,
                                           T F[5], T dF[5]) {
   T V[6][5];
@@ -508,7 +514,7 @@ __device__ __forceinline__ void flux_full(const PointState<T>& stl, const PointS
 // with S = int sign(u) psi g = rho (D0, D1, V D0, W D0, (D2 + D0 (V^2+W^2+(K+2) theta))/2),
 // D0 = erf(sqrt(lam) U), D1 = U D0 + exp(-lam U^2)/sqrt(pi lam), D2 = U D1 + theta D0.
 template <class T>
-__device__ __forceinline__ void sign_moments(const T dq[5], const Gas<T>& g, T S[5]) {
+HGKS_HD void sign_moments(const T dq[5], const Gas<T>& g, T S[5]) {
   const Prim<T> s = prim_of(dq, g);
   const T sl = tsqrt(s.lam);
   const T x = sl * s.U;
@@ -523,7 +529,7 @@ __device__ __forceinline__ void sign_moments(const T dq[5], const Gas<T>& g, T S
 }
 
 template <class T>
-__device__ __forceinline__ void compat_dev(const T dql[5], const T dqr[5], const Gas<T>& g,
+HGKS_HD void compat_dev(const T dql[5], const T dqr[5], const Gas<T>& g,
                                            T dq0[5]) {
   T Sl[5], Sr[5];
   sign_moments(dql, g, Sl);

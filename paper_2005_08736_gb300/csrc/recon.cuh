@@ -29,7 +29,7 @@ template <int MODE> __host__ __device__ constexpr bool is_char_mode() { return M
 // stencils, whose smoothness indicators are the same three in reverse order.
 // WENO-JS: alpha = d/(1e-6 + beta)^2.  WENO-Z: alpha = d (1 + |beta0 - beta2|/(beta + 1e-20)).
 template <int MODE_, class T>
-__device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, T& qR) {
+HGKS_HD void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, T& qR) {
   constexpr int MODE = recon_of<MODE_>();
   if (MODE == RECON_LINEAR) {
     // The optimal-weight combination of the three candidates is the
@@ -86,7 +86,7 @@ __device__ __forceinline__ void weno5_pair(T q0, T q1, T q2, T q3, T q4, T& qL, 
 // WENO modes: p(s) = a + b s + c s^2 with b = qR - qL, c = 3(qL+qR) - 6 f2,
 // a = f2 - c/12, so p(+-g) = f2 +- b g and p'(+-g) = b +- 2 c g.
 template <int MODE_, class T>
-__device__ __forceinline__ void tangential(T f0, T f1, T f2, T f3, T f4, T v[2], T d[2]) {
+HGKS_HD void tangential(T f0, T f1, T f2, T f3, T f4, T v[2], T d[2]) {
   constexpr int MODE = recon_of<MODE_>();
   const T sq3 = T(1.7320508075688772);
   if (MODE == RECON_LINEAR) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void tangential(T f0, T f1, T f2, T f3, T f4, T v[2],
 
 // Values only (for fields whose tangential derivative is not needed).
 template <int MODE, class T>
-__device__ __forceinline__ void tangential_val(T f0, T f1, T f2, T f3, T f4, T v[2]) {
+HGKS_HD void tangential_val(T f0, T f1, T f2, T f3, T f4, T v[2]) {
   T d[2];
   tangential<MODE>(f0, f1, f2, f3, f4, v, d);
 }

@@ -171,7 +171,7 @@ __device__ __forceinline__ SweepAxes sweep_axes(int d, const GridDev& g, bool xt
 // end values, the normal slopes, the compatibility state Q0 and its normal
 // slope, into ff[k * NH + h].
 template <class T, int MODE, int FLUX, int NH>
-__device__ __forceinline__ void face_fields_cells(const T qa[5][6], T hl, T hr, const Gas<T>& gas,
+HGKS_HD void face_fields_cells(const T qa[5][6], T hl, T hr, const Gas<T>& gas,
                                                   int h, T* ff) {
   const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
   T Ql[5], Qr[5], Dl[5], Dr[5], D0[5];
@@ -397,7 +397,7 @@ __device__ __forceinline__ void t1_pass_item(const T* ff, T* tb, int at, int st1
 // state group g (values at both t1 abscissae and t1-derivatives), else the
 // normal slopes of state group g - NV/5 (values only).
 template <class T, int MODE, int NV, int NH>
-__device__ __forceinline__ void t1_pass_group(const T* ff, T* tb, int at, int st1, int grp) {
+HGKS_HD void t1_pass_group(const T* ff, T* tb, int at, int st1, int grp) {
   if (grp < NV / 5) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {

@@ -168,3 +168,45 @@ def channel(nx: int, ny: int, nz: int, seed: int, mach: float = 0.1, gamma: floa
     prim[3] = 0.1 * U * rng.uniform(-1, 1, U.shape)
     prim[4] = (1.0 / mach) ** 2 / gamma
     return prim
+
+
+def slab(n: tuple[int, int, int], seed: int, axis: int = 0, rho: tuple[float, float] = (1.0, 0.5),
+         p: tuple[float, float] = (1.0, 0.4), u_amp: float = 0.1) -> np.ndarray:
+    """Piecewise-constant density and pressure with jumps: state 1 (rho[1],
+    p[1]) between the planes at a quarter and three quarters of `axis`, state
+    0 outside (two periodic contact/pressure jumps, the data on which WENO5's
+    nonlinear weights move far from the linear ones), plus a seeded smooth
+    velocity (random_smooth's modes, relative amplitude u_amp of unit speed).
+    Shape (nx, ny, nz); [0, 2 pi]^3."""
+    base = random_smooth(n, seed, amp=u_amp, rho0=1.0, p0=1.0)
+    nx, ny, nz = n
+    m = (nx, ny, nz)[axis]
+    inner = (np.arange(m) >= m // 4) & (np.arange(m) < (3 * m) // 4)
+    shape = [1, 1, 1]
+    shape[2 - axis] = m
+    mask = np.broadcast_to(inner.reshape(shape), (nz, ny, nx))
+    out = base.copy()
+    out[0] = np.where(mask, rho[1], rho[0])
+    out[4] = np.where(mask, p[1], p[0])
+    return out
+
+
+def shear_layer(n: tuple[int, int, int], seed: int, U0: float = 1.0, delta: float = 0.05,
+                mach: float = 0.3, amp: float = 0.05, gamma: float = 1.4) -> np.ndarray:
+    """Periodic double shear layer on [0, 2 pi]^3: u = U0 tanh((y - pi/2)/delta)
+    for y < pi and U0 tanh((3 pi/2 - y)/delta) above (layers thinner than a
+    cell at these grids), v and w seeded smooth perturbations of relative
+    amplitude `amp` (random_smooth's modes), rho = 1, uniform p = 1/(gamma
+    Ma^2) with Ma = mach for U0 = 1.  Shape (nx, ny, nz)."""
+    nx, ny, nz = n
+    pert = random_smooth(n, seed, amp=amp, rho0=1.0, p0=1.0)
+    y = centres(ny, 2 * math.pi)
+    u = np.where(y < math.pi, U0 * np.tanh((y - 0.5 * math.pi) / delta),
+                 U0 * np.tanh((1.5 * math.pi - y) / delta))
+    out = np.empty((5, nz, ny, nx))
+    out[0] = 1.0
+    out[1] = u[None, :, None]
+    out[2] = pert[2] * U0
+    out[3] = pert[3] * U0
+    out[4] = 1.0 / (gamma * mach * mach)
+    return out

@@ -168,8 +168,15 @@ class Simulation:
         self._call(self.lib.hgks_step(self.h, int(nsteps), float(dt), int(sync), ctypes.byref(t)))
         return t.value if sync else None
 
-    def state(self, device: bool = False):
-        """Conservative state, FP64 [5][nz][ny][nx] (numpy, or a CUDA tensor)."""
+    def state(self, device: bool = False, out=None):
+        """Conservative state, FP64 [5][nz][ny][nx] (numpy, or a CUDA tensor).
+        `out`: a host (e.g. pinned) FP64 CPU tensor of that shape to fill
+        instead (returned)."""
+        if out is not None:
+            assert (isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
+                    and tuple(out.shape) == self.cfg.shape and out.is_contiguous())
+            self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
         if device:
             out = torch.empty(self.cfg.shape, dtype=torch.float64, device=self.device)
             self._call(self.lib.hgks_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 0))
