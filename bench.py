@@ -36,33 +36,46 @@ PAPER_MCUPS_256 = 2.0 ** 24 / 9.09 / 1e6  # Sec. 3.2 table: 256^3, 64 cores, 9.0
 METRIC = "Mcell-updates/s per S2O4 step"
 # cfl, dt, 2 x (3 ghost fills + transposed copy + 3 sweeps + update), time
 LAUNCHES_PER_STEP = 19
-# Algorithmic FP32 work of the stage-1 sweep per face (linear WENO5, smooth
-# flux): the flops of the three phases without the halo recomputation of the
-# tile -- face fields 373 per point, t1 pass 189 per point, t2 pass and flux
-# 1428 per face -- solved from the executed FP32 operations (fadd + fmul +
-# 2 ffma) that ncu counted on Taylor-Green 128^3 for the three scalar tile
-# variants, whose halo factors differ
-# (the ncu summary of the sweep kernel at 128^3).  The same per face for
-# every tile variant and grid; counted with the direct form of the
-# compatibility state (its FP32 midpoint-rule form adds work not counted).
-ALG_FLOPS_PER_FACE = 1990.0
-# The same for the stage-2 sweep (dF only): 1841 per face (331 + 214 + 1296,
-# from the stage-2 counts of the same three variants).
-ALG_FLOPS_PER_FACE_STAGE2 = 1841.0
+# Algorithmic work of the sweep kernel per face comes from hgks_count_flops:
+# the kernel's closed forms run on the host with a counting number type, for
+# one face point's face fields, one point's t1 pass and one face's t2 pass and
+# flux -- i.e. without the tile's halo recomputation -- with common
+# subexpressions counted once and dead results not counted (additions,
+# multiplications and divisions; square roots, exponentials and error
+# functions are listed beside it, not counted as flops).
 # Algorithmic HBM bytes of one FP32 step per cell: stage 1 reads Q^n and
 # writes Q* and the increment, stage 2 reads Q* and the increment and writes
 # Q^{n+1}: 6 x 5 x 4 B.
 ALG_BYTES_PER_CELL_STEP = 120.0
-# Per tile variant: executed FP32 flops per face (mean of the three
-# directions, ncu at 128^3; the packed variant performs the operations of
-# variant 1) and DRAM bytes (read + write) per face of the stage-1 sweep from
-# a one-pass ncu capture at 256^3 (None where not captured for the current
-# kernel; at 128^3 the L2 holds part of the writes, so smaller grids
-# undercount).
+# Per tile variant: EXECUTED FP32 flops per face (fadd + fmul + 2 ffma, mean
+# of the three directions, ncu at 128^3, halo recomputation and the
+# polynomial evaluation of erf/exp included; the packed variant performs the
+# operations of variant 1) and DRAM bytes (read + write) per face of the
+# stage-1 sweep from a one-pass ncu capture at 256^3 (None where not captured
+# for the current kernel; at 128^3 the L2 holds part of the writes, so
+# smaller grids undercount).  Reported beside the algorithmic count.
 SWEEP_COUNTS = {0: {"tile": "16x8, 4 layers", "flops": 2391.8, "dram": None},
                 1: {"tile": "32x8, 2 layers", "flops": 2313.7, "dram": None},
                 2: {"tile": "16x16, 2 layers", "flops": 2247.7, "dram": None},
                 3: {"tile": "32x8, 2 layers, packed FP32 pairs", "flops": 2313.7, "dram": 58.3}}
+
+
+def alg_flops_per_face(cfg, stage: int = 1) -> dict:
+    """Algorithmic operations of one face of the sweep kernel for `cfg`
+    (hgks_count_flops): flops = additions + multiplications + divisions of the
+    face fields (one point), the t1 pass (one point) and the t2 pass and flux
+    (one face); the transcendental calls listed beside them."""
+    import ctypes
+    from paper_2005_08736_gb300 import _lib
+    lib = _lib.load()
+    out = (ctypes.c_double * 21)()
+    c = cfg.c_struct()
+    _lib.check(lib.hgks_count_flops(ctypes.byref(c), int(stage), out))
+    names = ("add", "mul", "div", "sqrt", "exp", "erf", "pow")
+    parts = [dict(zip(names, out[7 * k:7 * k + 7])) for k in range(3)]
+    fl = [p["add"] + p["mul"] + p["div"] for p in parts]
+    return {"flops": sum(fl), "face_fields": fl[0], "t1_pass": fl[1], "t2_flux": fl[2],
+            "transcendentals": {k: sum(p[k] for p in parts) for k in ("sqrt", "exp", "erf", "pow")}}
 
 
 def load_peaks():
@@ -206,7 +219,7 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
-def extra_workloads(steps: int):
+def extra_workloads(steps: int, peak_tflops: float | None = None):
     """The other measured configurations: isotropic turbulence 256^3 (WENO-Z +
     full flux, FP32), the stretched wall-bounded channel 128 x 128 x 96 (FP32),
     the adjoint / forward time ratio at 64^3 (isotropic, kappa0 = 4, WENO-Z +
@@ -236,9 +249,21 @@ def extra_workloads(steps: int):
     iso_tune = sim.autotune()
     sim.step(3)
     s_per = timed(lambda: sim.step(steps, sync=False), 1) / steps
+    prof = sim.profile_step()
+    # ALU roofline of its stage-1 sweep: algorithmic flops per face (the
+    # kernel's formulas, hgks_count_flops) x faces per launch / launch time.
+    alg = alg_flops_per_face(cfg, 1)
+    faces = (cfg.nx + 1) * cfg.ny * cfg.nz
+    launch_ms = prof["flux_stage1"] / 3.0
+    achieved = alg["flops"] * faces / (launch_ms * 1e-3) / 1e12
     out["isotropic_256_wenoz_full_fp32"] = {
         "ms_per_step": 1e3 * s_per, "mcups": cfg.cells / s_per / 1e6,
-        "kernel_ms_per_step": sim.profile_step(), "autotune": iso_tune}
+        "kernel_ms_per_step": prof, "autotune": iso_tune,
+        "roofline": {"bound": "alu", "kernel": "k_sweep stage 1 (FP32, WENO-Z, full flux)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops if peak_tflops else None,
+                     "alg_flops_per_face": alg, "launch_ms": launch_ms,
+                     "peak_source": "measured FP32 FMA throughput of this GPU"}}
     sim.close()
     # Channel (Sec. 3.3): 128 x 128 x 96, tanh b = 2, walls, f_x = 2.93e-3, Ma 0.1.
     ccfg = Config(128, 128, 96, lx=2 * 3.141592653589793, ly=2.0, y0=-1.0, lz=3.141592653589793,
@@ -418,7 +443,7 @@ def run_gradcheck(args):
         x = u0.clone().requires_grad_(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        J = kinetic_energy(run_window(cons(x), sim, K, dt, every), sim.cfg)
+        J = kinetic_energy(run_window(cons(x), sim, K, dt, every), sim)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         (g,) = torch.autograd.grad(J, x)
@@ -437,7 +462,7 @@ def run_gradcheck(args):
     def J_of(u):
         fsim.init_conservative(cons(u))
         fsim.step(K, dt)
-        return kinetic_energy(fsim.state(device=True), fsim.cfg).item()
+        return kinetic_energy(fsim.state(device=True), fsim).item()
 
     h0 = 1e-6 * u0.norm().item()
     rows = []
@@ -619,17 +644,22 @@ def run_ours(args, rank: int, world: int):
     fp_peaks = measure_fp_peaks()  # FMA throughput of this GPU, outside the timed region
     peak_tflops = fp_peaks["fp32"]
     counts = SWEEP_COUNTS[tune["variant"]]
-    achieved = ALG_FLOPS_PER_FACE * faces_per_launch / (flux_ms * 1e-3) / 1e12
+    alg1, alg2 = alg_flops_per_face(cfg, 1), alg_flops_per_face(cfg, 2)
+    achieved = alg1["flops"] * faces_per_launch / (flux_ms * 1e-3) / 1e12
     traffic = counts["dram"] * faces_per_launch if counts["dram"] else None
     roofline = {"bound": "alu",
                 "kernel": f"k_sweep stage 1 (FP32, linear WENO5, smooth flux, tile {counts['tile']})",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": traffic,
-                "flops_per_launch": ALG_FLOPS_PER_FACE * faces_per_launch,
-                "flops_note": "algorithmic: per-face flops of the kernel's formulas without the "
-                              "tile's halo recomputation",
+                "flops_per_launch": alg1["flops"] * faces_per_launch,
+                "alg_flops_per_face": alg1,
+                "flops_note": "algorithmic (hgks_count_flops): the kernel's closed forms tallied on "
+                              "the host per face, no halo recomputation, common subexpressions "
+                              "once, dead results not counted, erf/exp/sqrt not counted",
                 "executed_flops_per_launch": counts["flops"] * faces_per_launch,
+                "executed_note": "ncu fadd + fmul + 2 ffma per face at 128^3 (halo recomputation and "
+                                 "the polynomial work of erf/exp included)",
                 "peak_source": "measured: FP32 FMA throughput of this GPU (hgks_measure_fp_peaks)",
                 "nominal_peak": nominal_tflops,
                 "nominal_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {clock_mhz:.0f} MHz",
@@ -641,7 +671,7 @@ def run_ours(args, rank: int, world: int):
     # The whole step against its own roofline: the slower of its algorithmic
     # FP32 work at the measured FMA peak and its algorithmic HBM bytes at the
     # measured copy bandwidth.
-    step_flops = 3 * faces_per_launch * (ALG_FLOPS_PER_FACE + ALG_FLOPS_PER_FACE_STAGE2)
+    step_flops = 3 * faces_per_launch * (alg1["flops"] + alg2["flops"])
     step_bytes = ALG_BYTES_PER_CELL_STEP * cfg.cells
     t_alu = step_flops / (peak_tflops * 1e12) * 1e3
     t_hbm = step_bytes / (peaks.get("hbm_gbs", 6802.0) * 1e9) * 1e3
@@ -654,7 +684,7 @@ def run_ours(args, rank: int, world: int):
     cpu_rate, cpu_s, cpu_steps = oracle_sample(1, 32, seconds=10.0)
     cpu_cores = oracle_threads()
     cpu1_rate, cpu1_s = oracle_sample_one_core()
-    extras = extra_workloads(min(args.steps, 10)) if not args.no_extras else None
+    extras = extra_workloads(min(args.steps, 10), peak_tflops) if not args.no_extras else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -126,9 +126,17 @@ hgks_status hgks_set_time(hgks_ctx* ctx, double t, long long step);
 /* Advance nsteps S2O4 steps (Eq. (6)).  dt > 0 fixes the step; dt <= 0 takes
  * the CFL step each time (computed on the device).  One step is captured as
  * a CUDA graph on first use and replayed.  With sync != 0 the call waits,
- * checks the state (E_NONPHYSICAL if rho <= 0, p <= 0 or NaN somewhere; the
- * state is then that of the failed step) and writes the time reached to
- * *t_out (may be NULL).  With sync == 0 it returns after enqueuing. */
+ * checks the state and writes the time reached to *t_out (may be NULL).
+ * With sync == 0 it returns after enqueuing.
+ * Non-physical states (rho <= 0, p <= 0 or NaN in some cell): each step
+ * checks its input state on the device first; once one is non-physical,
+ * that step and every later one write nothing (no host round trip per
+ * step).  The next synchronising call (this one with sync != 0, or a later
+ * hgks_step(ctx, 0, dt, 1, ...)) then returns E_NONPHYSICAL with the state,
+ * time and step count left at the last good step -- the step before the
+ * first non-physical state (or the state the caller set, if that was
+ * non-physical) -- and clears the flag, so that stepping may resume (e.g.
+ * with a smaller fixed dt). */
 hgks_status hgks_step(hgks_ctx* ctx, int nsteps, double dt, int sync, double* t_out);
 
 typedef struct {
@@ -187,10 +195,21 @@ hgks_status hgks_turbulence_stats(hgks_ctx* ctx, hgks_turbulence* out);
  *     cubic through the averages of the four cells nearest to it),
  *     nu = mu_w / rho_b, Re_c = U_c H / nu, Re_b = U_b 2H / nu,
  *     C_f = tau_w / (rho_b U_b^2 / 2).
- * profiles (HOST, may be NULL): [8][ny] plane means of rho, rho U, U, V, W,
- * U V, U U and T = p / rho per y row.  Needs bc_y = HGKS_BC_WALL_ISOTHERMAL
- * (else E_UNSUPPORTED).  Allocates a small device buffer on the first call;
- * synchronises. */
+ * profiles (HOST, may be NULL): [14][ny], per y row j: rows 0-7 the plane
+ * means of rho, rho U, U, V, W, U V, U U and T = p / rho; then
+ *   8  y_j, the cell centre;
+ *   9  y+ = rho_w u_tau d_j / mu_w, d_j the distance to the nearer wall;
+ *   10 U+ = <U> / u_tau;
+ *   11 <u'v'>+ = (<U V> - <U><V>) / u_tau^2;
+ *   12 dU+/dY+ = mu_w d<U>/dy / (rho_w u_tau^2), d<U>/dy by the second-order
+ *      difference of the row means on the non-uniform centres (one-sided in
+ *      the first and last rows);
+ *   13 the total-stress residual of the statistically stationary channel,
+ *      dU+/dY+ - <u'v'>+ - (1 - Y+/Re_tau) (Sec. 3.3: the total stress is
+ *      linear in y; Y+ = y+ here).
+ * Needs bc_y = HGKS_BC_WALL_ISOTHERMAL (else E_UNSUPPORTED).  Allocates a
+ * small device buffer on the first call; synchronises.  The host part is
+ * hgks_channel_compose. */
 typedef struct {
   double t;                       /* time of the state */
   double tau_w, tau_w_lower, tau_w_upper;
@@ -198,6 +217,32 @@ typedef struct {
   double U_b, U_c, rho_b, Re_b, Re_c, C_f;
 } hgks_channel;
 hgks_status hgks_channel_stats(hgks_ctx* ctx, double* profiles, hgks_channel* out);
+
+/* The host part of hgks_channel_stats: from the plane means `means` (HOST,
+ * [8][ny], rows as rows 0-7 of the profiles above) of a channel configured by
+ * cfg, the statistics *out (t = 0) and, if profiles is not NULL, the
+ * [14][ny] profiles.  No device work; E_INVAL for a bad cfg, E_UNSUPPORTED
+ * without walls in y. */
+hgks_status hgks_channel_compose(const hgks_config* cfg, const double* means, double* profiles,
+                                 hgks_channel* out);
+
+/* Cell widths of axis 0, 1 or 2 (x, y, z) of the grid cfg describes: the
+ * uniform extent / n, or the tanh mapping of Sec. 3.3 in y
+ * (y_j = y0 + ly/2 (1 + tanh(b (eta_j / (1.5 pi) - 1)) / tanh b),
+ * eta_j = 3 pi j / ny).  out (HOST): n doubles.  No device work. */
+hgks_status hgks_cell_widths(const hgks_config* cfg, int axis, double* out);
+
+/* Kinetic energy functional of Sec. 3.1 of an FP64 conservative array cons
+ * (DEVICE, [5][nz][ny][nx], e.g. a state read with hgks_get_state):
+ *   *ek_out = (1 / (rho_ref |Omega|)) sum_c |rho U|^2 / (2 rho) |Omega_c|,
+ * an FP64 sum over the cells with the context's cell volumes, in a fixed
+ * order (deterministic).  If grad (DEVICE, same layout, may not alias cons)
+ * is not NULL it receives dE_k/dQ per cell: -|U|^2/2, U, V, W, 0 times
+ * |Omega_c| / (rho_ref |Omega|) -- the seed of an adjoint (hgks_adjoint_step)
+ * for a final kinetic-energy functional.  Enqueued on the context's stream;
+ * synchronises to return *ek_out.  Allocates a small device buffer on the
+ * first call. */
+hgks_status hgks_kinetic_energy(hgks_ctx* ctx, const double* cons, double* grad, double* ek_out);
 
 /* Ensembles (no counterpart in the paper): a batch of independent contexts,
  * e.g. instances of uneven sizes, advanced together.  hgks_ensemble_create
@@ -257,7 +302,7 @@ hgks_status hgks_profile_step(hgks_ctx* ctx, double dt, double* ms_out, int ncla
  * that owns all device allocations, a context whose memory footprint must
  * not grow, a path that must not synchronise the device as an allocation
  * may).  No counterpart in the paper: it is the step of hgks_step with its
- * working buffers in one scratch array of fixed size (about 15 MiB) that is
+ * working buffers in one scratch array of fixed size (about 16 MiB) that is
  * part of the library image; every GPU that loads the library holds it until
  * the process exits.  Limits: at most 32 cells on every axis and the
  * constant body force only (larger grids and force_mode 1 return

@@ -25,8 +25,11 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_ensemble_create", "hgks_ensemble_step", "hgks_ensemble_destroy",
            "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape",
            "hgks_turbulence_stats", "hgks_measure_fp_peaks", "hgks_channel_stats",
-           "hgks_set_time", "hgks_count_flops"]
+           "hgks_set_time", "hgks_count_flops", "hgks_channel_compose", "hgks_cell_widths",
+           "hgks_kinetic_energy"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
+CHANNEL_PROFILES = ("rho", "rhoU", "U", "V", "W", "UV", "UU", "T", "y", "y_plus", "U_plus",
+                    "uv_plus", "dUp_dYp", "total_stress_residual")
 
 
 class HgksConfig(ctypes.Structure):
@@ -122,6 +125,9 @@ def load(path: str | None = None):
         L.hgks_channel_stats.argtypes = [vp, pd, ctypes.POINTER(HgksChannel)]
         L.hgks_set_time.argtypes = [vp, d, ctypes.c_longlong]
         L.hgks_count_flops.argtypes = [pcfg, i, pd]
+        L.hgks_channel_compose.argtypes = [pcfg, pd, pd, ctypes.POINTER(HgksChannel)]
+        L.hgks_cell_widths.argtypes = [pcfg, i, pd]
+        L.hgks_kinetic_energy.argtypes = [vp, vp, vp, pd]
         L.hgks_last_error.argtypes = [vp]
         L.hgks_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:

@@ -20,12 +20,18 @@ struct Engine {
   int p[3];
   long long P = 0;  // padded cells per variable
   long long N = 0;  // interior cells
+  // The two padded state buffers swap roles every step: q holds Q^n, the
+  // step writes Q* and then Q^{n+1} into qs, and the host swaps q and qs
+  // (with comp and comp2) after enqueuing the step, so that Q^n survives a
+  // step whose result is non-physical.
   void* q = nullptr;     // padded state Q^n (deviation), 5 * P
-  void* qs = nullptr;    // padded state Q*, 5 * P
+  void* qs = nullptr;    // padded state Q*, then Q^{n+1}, 5 * P
   void* qx = nullptr;    // padded state with x slowest, [5][x][z][y], read by the x sweep
                          // (null: the x sweep reads q with pair loads along x)
   void* inc = nullptr;   // stage-1 increment, 5 * N
-  void* comp = nullptr;  // FP32 compensation, 5 * N (null for FP64)
+  void* comp = nullptr;  // FP32 compensation of Q^n, 5 * N (null for FP64)
+  void* comp2 = nullptr; // FP32 compensation of Q^{n+1}, 5 * N (null for FP64)
+  bool guard = true;     // the step's writes stop once the non-physical flag is set
   void* fd[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction, 10 * faces
   void* w[3] = {nullptr, nullptr, nullptr};   // cell widths incl. ghosts, n + 6
   double* scal = nullptr;                      // [0] dt, [1] t, [2] step
@@ -41,6 +47,7 @@ struct Engine {
   double* turb_part = nullptr;  // turbulence statistics: per-block partials
   double* turb_out = nullptr;   // and the final sums (allocated on first use)
   double* chan_out = nullptr;   // channel statistics: kChanSums sums per y row (first use)
+  double* kin_w = nullptr;      // kinetic-energy functional: FP64 interior widths x, y, z (first use)
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
@@ -126,6 +133,16 @@ int sweep_variant_count(const Engine& e);
 template <class T> cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in,
                                                     double* adj_out);
 cudaError_t enqueue_reset_scalars(const Engine& e);
+// Swap the roles of the two state buffers (and the compensation buffers)
+// after a step has been enqueued: Q^{n+1} is in qs.
+inline void swap_state_buffers(Engine& e) {
+  void* t = e.q;
+  e.q = e.qs;
+  e.qs = t;
+  t = e.comp;
+  e.comp = e.comp2;
+  e.comp2 = t;
+}
 cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed);
 cudaError_t enqueue_advance_time(const Engine& e);
 

@@ -160,6 +160,8 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   ua.qs = static_cast<T*>(e.qs);
   ua.inc = static_cast<T*>(e.inc);
   ua.comp = static_cast<T*>(e.comp);
+  ua.comp_out = static_cast<T*>(e.comp2);
+  ua.flag = e.guard ? e.flag : nullptr;
   ua.fx = static_cast<const T*>(e.fd[0]);
   ua.fy = static_cast<const T*>(e.fd[1]);
   ua.fz = static_cast<const T*>(e.fd[2]);
@@ -171,7 +173,6 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   const bool mass_flux = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX;
   ua.force_x = mass_flux ? T(0) : T(e.cfg.force_x);
   ua.rho_r = T(e.cfg.rho_ref);
-  ua.stash = mass_flux && stage == 2 ? static_cast<T*>(e.qs) : nullptr;
   if (probe) probe->begin(e.stream, KC_UPDATE);
   const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
   if (stage == 1)
@@ -179,13 +180,15 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   else
     k_update<T, 2><<<ugrid, kUpdTX * kUpdTY, 0, e.stream>>>(ua);
   if (mass_flux && stage == 2) {
-    // Sec. 3.3: the force that keeps the volume integral of rho U at its target.
+    // Sec. 3.3: the force that keeps the volume integral of rho U at its
+    // target, on Q~^{n+1} (in qs, compensation in comp2), with rho^n and
+    // (rho U)^n read from Q^n (q).
     const GridDev g = grid_of(e);
     k_massflux_sums<T><<<e.diag_blocks, 256, 0, e.stream>>>(
-        ua.q, ua.stash, ua.comp, g, ua.wx, ua.wy, ua.wz, e.cfg.rho_ref, e.part);
-    k_massflux_force<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, e.cfg.mass_flux, e.scal);
-    k_force_apply<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua.q, ua.stash, ua.comp, g,
-                                                                 e.cfg.rho_ref, e.scal);
+        ua.qs, ua.q, ua.comp_out, g, ua.wx, ua.wy, ua.wz, e.cfg.rho_ref, e.part, ua.flag);
+    k_massflux_force<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, e.cfg.mass_flux, e.scal, ua.flag);
+    k_force_apply<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(ua.qs, ua.q, ua.comp_out, g,
+                                                                 e.cfg.rho_ref, e.scal, ua.flag);
   }
   if (probe) probe->end(e.stream);
   return cudaGetLastError();
@@ -340,8 +343,11 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   T* wL = static_cast<T*>(e.adj_wL);
   T* wdL = static_cast<T*>(e.adj_wdL);
   const size_t accb = 5 * (size_t)e.P * sizeof(T);
-  // Q* = Q^n + dt/2 L + dt^2/8 dL (also fills the ghost cells of Q^n).
-  cudaError_t err = enqueue_rhs_and_update<T>(e, 1);
+  // Q* = Q^n + dt/2 L + dt^2/8 dL (also fills the ghost cells of Q^n); the
+  // step's non-physical guard does not apply here.
+  Engine ea = e;
+  ea.guard = false;
+  cudaError_t err = enqueue_rhs_and_update<T>(ea, 1);
   if (err != cudaSuccess) return err;
   err = enqueue_ghosts<T>(e, e.qs);
   if (err != cudaSuccess) return err;

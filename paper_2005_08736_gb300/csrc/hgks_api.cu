@@ -14,9 +14,17 @@ struct hgks_ctx {
   hgks::Engine e;
   bool own_stream = false;
   std::string err;
-  cudaGraphExec_t graph = nullptr;
-  double graph_dt = 0.0;
+  // The captured step, one graph per assignment of the two state buffers
+  // (graph[0]: q is buf0; graph[1]: q is buf1); the host swaps the
+  // assignment after every step.
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  double graph_dt[2] = {0.0, 0.0};
+  void* buf0 = nullptr;  // the state buffer allocated first
   int device = 0;
+  // Host mirror of the device step counter: steps enqueued since the state
+  // was set (init_steps: the counter when it was set).  Used to find the last
+  // good state after a non-physical one.
+  long long steps_host = 0, init_steps = 0;
 };
 
 namespace {
@@ -101,14 +109,16 @@ cudaError_t upload_widths(hgks::Engine& e, int d, const std::vector<double>& w) 
 }
 
 void free_all(hgks::Engine& e) {
-  void* ptrs[] = {e.q, e.qs, e.qx, e.inc, e.comp, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
+  void* ptrs[] = {e.q, e.qs, e.qx, e.inc, e.comp, e.comp2, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
                   e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out,
-                  e.chan_out};
+                  e.chan_out, e.kin_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
+// One S2O4 step on the context's current buffers; Q^{n+1} ends in e.qs (the
+// caller swaps the buffers after enqueuing).
 cudaError_t enqueue_stage_pair(hgks::Engine& e, double dt_fixed, hgks::Probe* probe = nullptr) {
   cudaError_t err;
   const bool f32 = e.cfg.prec == HGKS_FP32;
@@ -126,11 +136,20 @@ cudaError_t enqueue_stage_pair(hgks::Engine& e, double dt_fixed, hgks::Probe* pr
   return hgks::enqueue_advance_time(e);
 }
 
-hgks_status capture_step(hgks_ctx* c, double dt_fixed) {
+void drop_graphs(hgks_ctx* c) {
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) {
+      cudaGraphExecDestroy(c->graph[k]);
+      c->graph[k] = nullptr;
+    }
+}
+
+// Capture the step for the current buffer assignment (graph[k]).
+hgks_status capture_step(hgks_ctx* c, int k, double dt_fixed) {
   hgks::Engine& e = c->e;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+  if (c->graph[k]) {
+    cudaGraphExecDestroy(c->graph[k]);
+    c->graph[k] = nullptr;
   }
   cudaGraph_t g = nullptr;
   HGKS_CHECK(c, cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal));
@@ -141,10 +160,10 @@ hgks_status capture_step(hgks_ctx* c, double dt_fixed) {
     return cuda_fail(c, err, "capturing the step");
   }
   HGKS_CHECK(c, end);
-  const cudaError_t inst = cudaGraphInstantiate(&c->graph, g, 0);
+  const cudaError_t inst = cudaGraphInstantiate(&c->graph[k], g, 0);
   cudaGraphDestroy(g);
   HGKS_CHECK(c, inst);
-  c->graph_dt = dt_fixed;
+  c->graph_dt[k] = dt_fixed;
   return HGKS_OK;
 }
 
@@ -162,10 +181,75 @@ static __global__ void k_reset_scalars(double* scal, unsigned long long* dtmin, 
   *flag = 0;
 }
 
+static __global__ void k_reset_flag(unsigned long long* dtmin, int* flag) {
+  if (threadIdx.x != 0) return;
+  *dtmin = (unsigned long long)__double_as_longlong(1e300);
+  *flag = 0;
+}
+
 static __global__ void k_set_time(double* scal, double t, double step) {
   if (threadIdx.x != 0) return;
   scal[1] = t;
   scal[2] = step;
+}
+
+// Kinetic-energy functional of an FP64 conservative array [5][nz][ny][nx]:
+// per-block FP64 partial sums of |m|^2 / (2 rho) |Omega_c| over rows of the
+// grid (x over the threads), and, if grad is not null, the gradient
+// d/dQ of scale * |m|^2 / (2 rho) |Omega_c| per cell (zero for rho E).
+static __global__ void __launch_bounds__(256) k_kinetic(const double* __restrict__ cons, GridDev g,
+                                                        const double* __restrict__ w, double scale,
+                                                        double* __restrict__ grad,
+                                                        double* __restrict__ part) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const double* wx = w;
+  const double* wy = w + nx;
+  const double* wz = w + nx + ny;
+  double s = 0.0;
+  const int rows = ny * nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const int y = row % ny, z = row / ny;
+      const long long c = (long long)row * nx + x;
+      const double vol = wx[x] * wy[y] * wz[z];
+      const double rho = cons[c], mx = cons[g.N + c], my = cons[2 * g.N + c], mz = cons[3 * g.N + c];
+      const double inv = 1.0 / rho;
+      const double ke = 0.5 * (mx * mx + my * my + mz * mz) * inv;
+      s += ke * vol;
+      if (grad) {
+        const double f = scale * vol;
+        grad[c] = -ke * inv * f;
+        grad[g.N + c] = mx * inv * f;
+        grad[2 * g.N + c] = my * inv * f;
+        grad[3 * g.N + c] = mz * inv * f;
+        grad[4 * g.N + c] = 0.0;
+      }
+    }
+  __shared__ double sm[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// Deterministic sum of the block partials (one block) times scale into *out.
+static __global__ void __launch_bounds__(256) k_kinetic_final(const double* __restrict__ part, int nblocks,
+                                                              double scale, double* __restrict__ out) {
+  __shared__ double sm[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[b];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *out = v * scale;
+  }
 }
 
 cudaError_t enqueue_reset_scalars(const Engine& e) {
@@ -174,11 +258,11 @@ cudaError_t enqueue_reset_scalars(const Engine& e) {
 }
 
 cudaError_t enqueue_set_dt(const Engine& e, double dt_fixed) {
-  k_set_dt<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.cfg.cfl, dt_fixed);
+  k_set_dt<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.cfg.cfl, dt_fixed, e.guard ? e.flag : nullptr);
   return cudaGetLastError();
 }
 cudaError_t enqueue_advance_time(const Engine& e) {
-  k_advance_time<<<1, 32, 0, e.stream>>>(e.scal);
+  k_advance_time<<<1, 32, 0, e.stream>>>(e.scal, e.guard ? e.flag : nullptr);
   return cudaGetLastError();
 }
 
@@ -251,6 +335,7 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   if (err == cudaSuccess) err = alloc(&e.qx, 5 * e.P * es);
   if (err == cudaSuccess) err = alloc(&e.inc, 5 * e.N * es);
   if (err == cudaSuccess && cfg->prec == HGKS_FP32) err = alloc(&e.comp, 5 * e.N * es);
+  if (err == cudaSuccess && cfg->prec == HGKS_FP32) err = alloc(&e.comp2, 5 * e.N * es);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.fd[d], hgks::face_flux_elems(e, d) * es);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = alloc(&e.w[d], (e.n[d] + 6) * es);
   if (err == cudaSuccess) err = alloc((void**)&e.scal, 4 * sizeof(double));
@@ -270,6 +355,7 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
   err = cudaMemsetAsync(e.q, 0, 5 * e.P * es, e.stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(e.qs, 0, 5 * e.P * es, e.stream);
   if (err == cudaSuccess && e.comp) err = cudaMemsetAsync(e.comp, 0, 5 * e.N * es, e.stream);
+  if (err == cudaSuccess && e.comp2) err = cudaMemsetAsync(e.comp2, 0, 5 * e.N * es, e.stream);
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
     const std::vector<double> w = widths(*cfg, d);
     err = cfg->prec == HGKS_FP32 ? upload_widths<float>(e, d, w) : upload_widths<double>(e, d, w);
@@ -286,6 +372,7 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
     delete c;
     return s;
   }
+  c->buf0 = e.q;
   *out = c;
   return HGKS_OK;
 }
@@ -293,7 +380,7 @@ hgks_status hgks_create(const hgks_config* cfg, void* stream, hgks_ctx** out) {
 hgks_status hgks_destroy(hgks_ctx* c) {
   if (!c) return HGKS_OK;
   cudaStreamSynchronize(c->e.stream);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  drop_graphs(c);
   free_all(c->e);
   if (c->own_stream) cudaStreamDestroy(c->e.stream);
   delete c;
@@ -314,6 +401,7 @@ static hgks_status init_common(hgks_ctx* c, const double* src, int is_host, int 
   if (e.comp) HGKS_CHECK(c, cudaMemsetAsync(e.comp, 0, 5 * e.N * sizeof(float), e.stream));
   hgks::k_reset_scalars<<<1, 32, 0, e.stream>>>(e.scal, e.dtmin, e.flag);
   HGKS_CHECK(c, cudaGetLastError());
+  c->steps_host = c->init_steps = 0;
   if (is_host) HGKS_CHECK(c, cudaStreamSynchronize(e.stream));  // the host buffer is borrowed
   return HGKS_OK;
 }
@@ -329,6 +417,7 @@ hgks_status hgks_set_time(hgks_ctx* c, double t, long long step) {
   if (!c || step < 0) return fail(c, HGKS_E_INVAL, "null context or negative step");
   hgks::k_set_time<<<1, 32, 0, c->e.stream>>>(c->e.scal, t, double(step));
   HGKS_CHECK(c, cudaGetLastError());
+  c->steps_host = c->init_steps = step;
   return HGKS_OK;
 }
 
@@ -350,13 +439,21 @@ hgks_status hgks_step(hgks_ctx* c, int nsteps, double dt, int sync, double* t_ou
   if (nsteps < 0) return fail(c, HGKS_E_INVAL, "nsteps must be non-negative");
   hgks::Engine& e = c->e;
   const double dt_fixed = dt > 0.0 ? dt : 0.0;
-  if (nsteps > 0 && (!c->graph || c->graph_dt != dt_fixed)) {
-    const hgks_status s = capture_step(c, dt_fixed);
-    if (s != HGKS_OK) return s;
+  for (int n = 0; n < nsteps; ++n) {
+    const int k = e.q == c->buf0 ? 0 : 1;
+    if (!c->graph[k] || c->graph_dt[k] != dt_fixed) {
+      const hgks_status s = capture_step(c, k, dt_fixed);
+      if (s != HGKS_OK) return s;
+    }
+    HGKS_CHECK(c, cudaGraphLaunch(c->graph[k], e.stream));
+    hgks::swap_state_buffers(e);
+    ++c->steps_host;
   }
-  for (int n = 0; n < nsteps; ++n) HGKS_CHECK(c, cudaGraphLaunch(c->graph, e.stream));
   if (!sync) return HGKS_OK;
   // Check the state reached: the CFL kernel flags rho <= 0, p <= 0 and NaN.
+  // The flag raised by the CFL kernel of a step stopped that step and every
+  // later one from writing, so the state before the first non-physical one
+  // is still in one of the two buffers.
   const bool f32 = e.cfg.prec == HGKS_FP32;
   HGKS_CHECK(c, f32 ? hgks::enqueue_cfl<float>(e, e.q) : hgks::enqueue_cfl<double>(e, e.q));
   double scal[3];
@@ -364,14 +461,43 @@ hgks_status hgks_step(hgks_ctx* c, int nsteps, double dt, int sync, double* t_ou
   HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
   HGKS_CHECK(c, cudaMemcpyAsync(&flag, e.flag, sizeof(int), cudaMemcpyDeviceToHost, e.stream));
   HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
-  if (t_out) *t_out = scal[1];
-  if (flag) {
-    char buf[128];
-    std::snprintf(buf, sizeof buf, "non-physical state (rho <= 0, p <= 0 or NaN) by step %lld",
-                  (long long)scal[2]);
-    return fail(c, HGKS_E_NONPHYSICAL, buf);
+  if (!flag) {
+    if (t_out) *t_out = scal[1];
+    return HGKS_OK;
   }
-  return HGKS_OK;
+  // scal[2] steps completed, the last of them non-physical (or, if none was
+  // completed since the state was set, the state set was non-physical).
+  const long long done = (long long)scal[2];
+  // The last good state: after done - 1 steps, or, if no step completed since
+  // the state was set (the state set was non-physical), that state.  The
+  // state after s steps is in q if steps_host - s is even, else in qs.
+  const bool rolled = done > c->init_steps;
+  const long long target = rolled ? done - 1 : done;
+  if (((c->steps_host - target) & 1LL) != 0) hgks::swap_state_buffers(e);
+  c->steps_host = target;
+  char buf[160];
+  if (rolled) {
+    const double t_good = scal[1] - scal[0];
+    hgks::k_set_time<<<1, 32, 0, e.stream>>>(e.scal, t_good, double(target));
+    HGKS_CHECK(c, cudaGetLastError());
+    if (t_out) *t_out = t_good;
+    std::snprintf(buf, sizeof buf,
+                  "non-physical state (rho <= 0, p <= 0 or NaN) after step %lld; the state is left "
+                  "at step %lld",
+                  done, target);
+  } else {
+    if (t_out) *t_out = scal[1];
+    std::snprintf(buf, sizeof buf,
+                  "non-physical state (rho <= 0, p <= 0 or NaN) at step %lld, the state set by the "
+                  "caller; no step was taken",
+                  done);
+  }
+  // Clear the flag (and the CFL minimum) so that the caller may continue,
+  // e.g. with a smaller fixed dt.
+  hgks::k_reset_flag<<<1, 32, 0, e.stream>>>(e.dtmin, e.flag);
+  HGKS_CHECK(c, cudaGetLastError());
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  return fail(c, HGKS_E_NONPHYSICAL, buf);
 }
 
 hgks_status hgks_diagnostics(hgks_ctx* c, hgks_diag* out) {
@@ -436,35 +562,28 @@ static double wall_gradient(double w1, double w2, double U1, double U2) {
   return r[0];
 }
 
-hgks_status hgks_channel_stats(hgks_ctx* c, double* profiles, hgks_channel* out) {
-  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
-  hgks::Engine& e = c->e;
-  const hgks_config& cf = e.cfg;
+hgks_status hgks_channel_compose(const hgks_config* cfp, const double* means, double* profiles,
+                                 hgks_channel* out) {
+  if (!cfp || !means || !out) return fail(nullptr, HGKS_E_INVAL, "null argument");
+  const hgks_config& cf = *cfp;
+  const std::string why = hgks::validate_config(cf);
+  if (!why.empty()) return fail(nullptr, HGKS_E_INVAL, why);
   if (cf.bc_y != HGKS_BC_WALL_ISOTHERMAL)
-    return fail(c, HGKS_E_UNSUPPORTED, "channel statistics need the isothermal walls in y");
-  const int ny = e.n[1], NS = hgks::kChanSums;
-  if (!e.chan_out) HGKS_CHECK(c, cudaMalloc((void**)&e.chan_out, sizeof(double) * NS * ny));
-  const bool f32 = cf.prec == HGKS_FP32;
-  HGKS_CHECK(c, f32 ? hgks::enqueue_channel_rows<float>(e) : hgks::enqueue_channel_rows<double>(e));
-  std::vector<double> m(size_t(NS) * ny);
-  double scal[3];
-  HGKS_CHECK(c, cudaMemcpyAsync(m.data(), e.chan_out, m.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                e.stream));
-  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
-  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
-  const double cells = double(e.n[0]) * e.n[2];
-  for (double& v : m) v /= cells;  // plane means
-  if (profiles) std::memcpy(profiles, m.data(), m.size() * sizeof(double));
+    return fail(nullptr, HGKS_E_UNSUPPORTED, "channel statistics need the isothermal walls in y");
+  const int ny = cf.ny, NS = hgks::kChanSums;
+  const double* m = means;
   const std::vector<double> w = widths(cf, 1);  // includes 3 ghosts per side
   auto wy = [&](int j) { return w[j + 3]; };
   const double* rho = &m[0];
   const double* U = &m[2 * ny];
+  const double* V = &m[3 * ny];
+  const double* UV = &m[5 * ny];
   // Wall shear stress (Sec. 3.3): tau_w = mu(T_wall) d<U>/dn at each wall.
   const double a_lo = wall_gradient(wy(0), wy(1), U[0], U[1]);
   const double a_hi = wall_gradient(wy(ny - 1), wy(ny - 2), U[ny - 1], U[ny - 2]);
   const double mu_w = cf.visc == HGKS_VISC_POWER ? cf.mu_ref * std::pow(cf.T_wall / cf.T_ref, cf.visc_exp)
                                                  : cf.mu_ref;
-  out->t = scal[1];
+  out->t = 0.0;
   out->tau_w_lower = mu_w * a_lo;
   out->tau_w_upper = mu_w * a_hi;
   out->tau_w = 0.5 * (out->tau_w_lower + out->tau_w_upper);
@@ -511,6 +630,107 @@ hgks_status hgks_channel_stats(hgks_ctx* c, double* profiles, hgks_channel* out)
   out->Re_c = out->U_c * H / nu;
   out->Re_b = out->U_b * 2.0 * H / nu;
   out->C_f = out->tau_w / (0.5 * out->rho_b * out->U_b * out->U_b);
+  if (!profiles) return HGKS_OK;
+  // Plane means, then the wall-unit profiles of each row j (cell centre y_j):
+  // y+ = rho_w u_tau d_j / mu_w with d_j the distance to the nearer wall,
+  // U+ = <U>/u_tau, <u'v'>+ = (<UV> - <U><V>)/u_tau^2, dU+/dY+ =
+  // mu_w d<U>/dy / (rho_w u_tau^2) (d<U>/dy by the second-order difference
+  // of the row means on the non-uniform centres, one-sided at the first and
+  // last rows), and the total-stress residual of the stationary channel,
+  // dU+/dY+ - <u'v'>+ - (1 - Y+/Re_tau) (Sec. 3.3).
+  std::memcpy(profiles, m, sizeof(double) * NS * ny);
+  double* y = profiles + NS * ny;
+  double* yp = y + ny;
+  double* Up = yp + ny;
+  double* uvp = Up + ny;
+  double* dUp = uvp + ny;
+  double* res = dUp + ny;
+  const double ut = out->u_tau, ut2 = ut * ut;
+  for (int j = 0; j < ny; ++j) {
+    y[j] = 0.5 * (yf[j] + yf[j + 1]);
+    const double dist = std::fmin(y[j] - cf.y0, cf.y0 + cf.ly - y[j]);
+    yp[j] = out->rho_w * ut * dist / mu_w;
+    Up[j] = U[j] / ut;
+    uvp[j] = (UV[j] - U[j] * V[j]) / ut2;
+  }
+  for (int j = 0; j < ny; ++j) {
+    double g;
+    if (j == 0) {
+      g = (U[1] - U[0]) / (y[1] - y[0]);
+    } else if (j == ny - 1) {
+      g = (U[ny - 1] - U[ny - 2]) / (y[ny - 1] - y[ny - 2]);
+    } else {
+      const double hs = y[j] - y[j - 1], hd = y[j + 1] - y[j];
+      g = (hs * hs * U[j + 1] + (hd * hd - hs * hs) * U[j] - hd * hd * U[j - 1]) / (hs * hd * (hd + hs));
+    }
+    dUp[j] = mu_w * g / (out->rho_w * ut2);
+    res[j] = dUp[j] - uvp[j] - (1.0 - yp[j] / out->Re_tau);
+  }
+  return HGKS_OK;
+}
+
+hgks_status hgks_channel_stats(hgks_ctx* c, double* profiles, hgks_channel* out) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  const hgks_config& cf = e.cfg;
+  if (cf.bc_y != HGKS_BC_WALL_ISOTHERMAL)
+    return fail(c, HGKS_E_UNSUPPORTED, "channel statistics need the isothermal walls in y");
+  const int ny = e.n[1], NS = hgks::kChanSums;
+  if (!e.chan_out) HGKS_CHECK(c, cudaMalloc((void**)&e.chan_out, sizeof(double) * NS * ny));
+  const bool f32 = cf.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_channel_rows<float>(e) : hgks::enqueue_channel_rows<double>(e));
+  std::vector<double> m(size_t(NS) * ny);
+  double scal[3];
+  HGKS_CHECK(c, cudaMemcpyAsync(m.data(), e.chan_out, m.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  const double cells = double(e.n[0]) * e.n[2];
+  for (double& v : m) v /= cells;  // plane means
+  const hgks_status st = hgks_channel_compose(&cf, m.data(), profiles, out);
+  if (st != HGKS_OK) return fail(c, st, g_create_error);
+  out->t = scal[1];
+  return HGKS_OK;
+}
+
+hgks_status hgks_kinetic_energy(hgks_ctx* c, const double* cons, double* grad, double* ek_out) {
+  if (!c || !cons || !ek_out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  if (!e.kin_w) {
+    std::vector<double> w;
+    for (int d = 0; d < 3; ++d) {
+      const std::vector<double> wd = widths(e.cfg, d);
+      w.insert(w.end(), wd.begin() + 3, wd.end() - 3);
+    }
+    HGKS_CHECK(c, cudaMalloc((void**)&e.kin_w, w.size() * sizeof(double)));
+    HGKS_CHECK(c, cudaMemcpyAsync(e.kin_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  e.stream));
+    HGKS_CHECK(c, cudaStreamSynchronize(e.stream));  // w is a host temporary
+  }
+  hgks::GridDev g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = e.n[d];
+    g.p[d] = e.p[d];
+  }
+  g.P = e.P;
+  g.N = e.N;
+  const double scale = 1.0 / (e.cfg.rho_ref * e.cfg.lx * e.cfg.ly * e.cfg.lz);
+  hgks::k_kinetic<<<e.diag_blocks, 256, 0, e.stream>>>(cons, g, e.kin_w, scale, grad, e.part);
+  HGKS_CHECK(c, cudaGetLastError());
+  hgks::k_kinetic_final<<<1, 256, 0, e.stream>>>(e.part, e.diag_blocks, scale, e.diag_out);
+  HGKS_CHECK(c, cudaGetLastError());
+  HGKS_CHECK(c, cudaMemcpyAsync(ek_out, e.diag_out, sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  return HGKS_OK;
+}
+
+hgks_status hgks_cell_widths(const hgks_config* cfg, int axis, double* out) {
+  if (!cfg || !out || axis < 0 || axis > 2) return fail(nullptr, HGKS_E_INVAL, "bad argument");
+  const std::string why = hgks::validate_config(*cfg);
+  if (!why.empty()) return fail(nullptr, HGKS_E_INVAL, why);
+  const std::vector<double> w = widths(*cfg, axis);
+  const int n = axis == 0 ? cfg->nx : (axis == 1 ? cfg->ny : cfg->nz);
+  for (int j = 0; j < n; ++j) out[j] = w[j + 3];
   return HGKS_OK;
 }
 
@@ -595,8 +815,15 @@ struct hgks_ensemble {
   std::vector<hgks_ctx*> members;
   cudaStream_t stream = nullptr;  // the first member's stream: fork and join point
   std::vector<cudaEvent_t> events;
-  cudaGraphExec_t graph = nullptr;
-  double graph_dt = -1.0;
+  // Captured batch steps, each for the members' state-buffer assignment at
+  // capture (the members' q pointers); the assignment alternates every step,
+  // so two slots serve a run.
+  struct Slot {
+    cudaGraphExec_t graph = nullptr;
+    double dt = -1.0;
+    std::vector<void*> q;
+  } slot[2];
+  int next_slot = 0;
   std::string err;
 };
 
@@ -630,7 +857,8 @@ hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out) {
 hgks_status hgks_ensemble_destroy(hgks_ensemble* en) {
   if (!en) return HGKS_OK;
   cudaStreamSynchronize(en->stream);
-  if (en->graph) cudaGraphExecDestroy(en->graph);
+  for (auto& sl : en->slot)
+    if (sl.graph) cudaGraphExecDestroy(sl.graph);
   for (auto& ev : en->events)
     if (ev) cudaEventDestroy(ev);
   delete en;
@@ -639,10 +867,10 @@ hgks_status hgks_ensemble_destroy(hgks_ensemble* en) {
 
 // One graph holding every member's step as a parallel branch: fork from the
 // first member's stream, each member's kernels on its own stream, join back.
-static hgks_status capture_ensemble(hgks_ensemble* en, double dt_fixed) {
-  if (en->graph) {
-    cudaGraphExecDestroy(en->graph);
-    en->graph = nullptr;
+static hgks_status capture_ensemble(hgks_ensemble* en, hgks_ensemble::Slot& sl, double dt_fixed) {
+  if (sl.graph) {
+    cudaGraphExecDestroy(sl.graph);
+    sl.graph = nullptr;
   }
   cudaStream_t s0 = en->stream;
   cudaGraph_t g = nullptr;
@@ -664,28 +892,43 @@ static hgks_status capture_ensemble(hgks_ensemble* en, double dt_fixed) {
   }
   const cudaError_t end = cudaStreamEndCapture(s0, &g);
   if (err == cudaSuccess) err = end;
-  if (err == cudaSuccess) err = cudaGraphInstantiate(&en->graph, g, 0);
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&sl.graph, g, 0);
   if (g) cudaGraphDestroy(g);
   if (err != cudaSuccess) {
     en->err = std::string("ensemble capture: ") + cudaGetErrorString(err);
     return err == cudaErrorMemoryAllocation ? HGKS_E_NOMEM : HGKS_E_CUDA;
   }
-  en->graph_dt = dt_fixed;
+  sl.dt = dt_fixed;
+  sl.q.clear();
+  for (hgks_ctx* c : en->members) sl.q.push_back(c->e.q);
   return HGKS_OK;
 }
 
 hgks_status hgks_ensemble_step(hgks_ensemble* en, int nsteps, double dt, int sync) {
   if (!en || nsteps < 0) return HGKS_E_INVAL;
   const double dt_fixed = dt > 0.0 ? dt : 0.0;
-  if (nsteps > 0 && (!en->graph || en->graph_dt != dt_fixed)) {
-    const hgks_status s = capture_ensemble(en, dt_fixed);
-    if (s != HGKS_OK) return s;
-  }
   for (int n = 0; n < nsteps; ++n) {
-    const cudaError_t e = cudaGraphLaunch(en->graph, en->stream);
+    // The slot captured for the members' current buffer assignment, or a new capture.
+    hgks_ensemble::Slot* sl = nullptr;
+    for (auto& cand : en->slot) {
+      bool same = cand.graph && cand.dt == dt_fixed && cand.q.size() == en->members.size();
+      for (size_t i = 0; same && i < en->members.size(); ++i) same = cand.q[i] == en->members[i]->e.q;
+      if (same) sl = &cand;
+    }
+    if (!sl) {
+      sl = &en->slot[en->next_slot];
+      en->next_slot ^= 1;
+      const hgks_status s = capture_ensemble(en, *sl, dt_fixed);
+      if (s != HGKS_OK) return s;
+    }
+    const cudaError_t e = cudaGraphLaunch(sl->graph, en->stream);
     if (e != cudaSuccess) {
       en->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
       return HGKS_E_CUDA;
+    }
+    for (hgks_ctx* c : en->members) {
+      hgks::swap_state_buffers(c->e);
+      ++c->steps_host;
     }
   }
   if (!sync) return HGKS_OK;
@@ -744,10 +987,7 @@ hgks_status hgks_autotune(hgks_ctx* c, int* variant_out, int* chunk_out, double*
   HGKS_CHECK(c, err);
   e.sweep_variant = best_v;
   e.sweep_chunk = best_c;
-  if (c->graph) {  // the captured step holds the old launch shapes
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);  // the captured steps hold the old launch shapes
   if (variant_out) *variant_out = best_v;
   if (chunk_out) *chunk_out = best_c;
   if (ms_out) *ms_out = best / 2.0;
@@ -760,10 +1000,7 @@ hgks_status hgks_set_sweep_shape(hgks_ctx* c, int variant, int chunk) {
     return fail(c, HGKS_E_INVAL, "no such sweep variant");
   c->e.sweep_variant = variant;
   c->e.sweep_chunk = chunk;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);
   return HGKS_OK;
 }
 
@@ -776,6 +1013,10 @@ hgks_status hgks_profile_step(hgks_ctx* c, double dt, double* ms_out, int nclass
     HGKS_CHECK(c, cudaEventCreate(&probe.stop[i]));
   }
   const cudaError_t err = enqueue_stage_pair(e, dt > 0.0 ? dt : 0.0, &probe);
+  if (err == cudaSuccess) {
+    hgks::swap_state_buffers(e);
+    ++c->steps_host;
+  }
   cudaError_t sync = cudaStreamSynchronize(e.stream);
   for (int k = 0; k < nclass; ++k) ms_out[k] = 0.0;
   for (int i = 0; i < probe.n && sync == cudaSuccess; ++i) {

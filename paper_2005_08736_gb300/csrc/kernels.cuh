@@ -166,10 +166,14 @@ __host__ __device__ __forceinline__ int global_var(int d, int i) {
 
 template <class T>
 struct UpdateArgs {
-  T* __restrict__ q;          // Q^n (padded); overwritten with Q^{n+1} in stage 2
-  T* __restrict__ qs;         // Q* (padded), written in stage 1
+  T* __restrict__ q;          // Q^n (padded); read only
+  T* __restrict__ qs;         // Q* (padded), written in stage 1; Q^{n+1} written here in
+                              // stage 2 (Q* is dead by then), so that Q^n stays intact
   T* __restrict__ inc;        // dt L(Q^n) + dt^2/6 dL(Q^n), interior
-  T* __restrict__ comp;       // compensation of the FP32 accumulation (or null)
+  T* __restrict__ comp;       // compensation of the FP32 accumulation of Q^n (or null)
+  T* __restrict__ comp_out;   // stage 2: compensation of Q^{n+1} (or null)
+  const int* __restrict__ flag;  // non-physical flag: nothing is written once it is set
+                                 // (null: no guard)
   const T* __restrict__ fx;
   const T* __restrict__ fy;
   const T* __restrict__ fz;
@@ -180,11 +184,12 @@ struct UpdateArgs {
   GridDev g;
   T force_x;
   T rho_r;
-  T* __restrict__ stash;      // mass-flux force: rho^n, (rho U)^n into planes 0, 1 (or null)
 };
 
 // Stage 1: L, dL of Q^n; Q* = Q^n + dt/2 L + dt^2/8 dL; inc = dt L + dt^2/6 dL.
-// Stage 2: dL of Q*; Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), then the body force.
+// Stage 2: dL of Q*; Q^{n+1} = Q^n + inc + dt^2/3 dL(Q*), then the body force,
+// into the buffer of Q* (qs).  With the non-physical flag set (by the CFL
+// kernel of this step, on Q^n) the kernel writes nothing.
 // One CTA per 32 x 8 cells of an x-y plane.  The x-face fluxes are stored y
 // fastest ([z][x][y]); the CTA stages its 33 x 8 x-faces through shared
 // memory so that both their loads and the per-cell reads are contiguous.
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(kUpdTX * kUpdTY, sizeof(T) == 4 ? 8 : 1) k_upd
   constexpr int NV = STAGE == 1 ? 10 : 5;  // stage 2 needs dF only
   constexpr int V0 = STAGE == 1 ? 0 : 5;
   __shared__ T sfx[NV][kUpdTX + 1][kUpdTY];
+  if (a.flag && *a.flag) return;  // block-uniform: before any barrier
   const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
   const int x0 = blockIdx.x * kUpdTX, y0 = blockIdx.y * kUpdTY, z = blockIdx.z;
   const int tid = threadIdx.x;
@@ -245,10 +251,6 @@ __global__ void __launch_bounds__(kUpdTX * kUpdTY, sizeof(T) == 4 ? 8 : 1) k_upd
       qn[v] = a.q[v * a.g.P + pi];
       dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
     }
-    if (a.stash) {
-      a.stash[pi] = qn[0];
-      a.stash[a.g.P + pi] = qn[1];
-    }
     if (a.force_x != T(0)) {
       // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
       // (rho E) += dt/2 ((rho U)^{n+1} + (rho U)^n) f_x; the reference is at rest.
@@ -262,12 +264,12 @@ __global__ void __launch_bounds__(kUpdTX * kUpdTY, sizeof(T) == 4 ? 8 : 1) k_upd
       for (int v = 0; v < 5; ++v) {
         const T yv = dq[v] - a.comp[v * a.g.N + cell];
         const T t = qn[v] + yv;
-        a.comp[v * a.g.N + cell] = (t - qn[v]) - yv;
-        a.q[v * a.g.P + pi] = t;
+        a.comp_out[v * a.g.N + cell] = (t - qn[v]) - yv;
+        a.qs[v * a.g.P + pi] = t;
       }
     } else {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.q[v * a.g.P + pi] = qn[v] + dq[v];
+      for (int v = 0; v < 5; ++v) a.qs[v * a.g.P + pi] = qn[v] + dq[v];
     }
   }
 }
@@ -354,13 +356,18 @@ __global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
 }
 
 // Scalars: [0] dt, [1] t, [2] steps taken.  dt_fixed > 0 overrides the CFL step.
-static __global__ void k_set_dt(double* scal, unsigned long long* dtmin, double cfl, double dt_fixed) {
+// With the non-physical flag set (flag may be null: no guard) the step's
+// scalars are left as they are.
+static __global__ void k_set_dt(double* scal, unsigned long long* dtmin, double cfl, double dt_fixed,
+                                const int* flag) {
   if (threadIdx.x != 0) return;
+  if (flag && *flag) return;
   scal[0] = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)*dtmin);
   *dtmin = (unsigned long long)__double_as_longlong(1e300);
 }
-static __global__ void k_advance_time(double* scal) {
+static __global__ void k_advance_time(double* scal, const int* flag) {
   if (threadIdx.x != 0) return;
+  if (flag && *flag) return;
   scal[1] += scal[0];
   scal[2] += 1.0;
 }
@@ -452,16 +459,19 @@ static __global__ void k_diag_final(const double* __restrict__ part, int nblocks
 }
 
 // ------------------------------------------------- constant mass flux force ---
-// Sec. 3.3: after the two S2O4 stages (state Q~^{n+1} in q, rho^n and
-// (rho U)^n stashed in planes 0 and 1 of the stash buffer), per-block FP64
-// sums of the cell volume, of (rho U)~ and of (rho^n + rho~)/2, each times
-// the cell volume, into part[3 b + k].  comp (FP32 compensation) may be null.
+// Sec. 3.3: after the two S2O4 stages (state Q~^{n+1} in q; rho^n and
+// (rho U)^n in planes 0 and 1 of `stash`, the buffer of Q^n, which the step
+// leaves intact), per-block FP64 sums of the cell volume, of (rho U)~ and of
+// (rho^n + rho~)/2, each times the cell volume, into part[3 b + k].  comp
+// (FP32 compensation) may be null.
 template <class T>
 __global__ void __launch_bounds__(256) k_massflux_sums(const T* __restrict__ q, const T* __restrict__ stash,
                                                        const T* __restrict__ comp,
                                                        GridDev g, const T* __restrict__ wx,
                                                        const T* __restrict__ wy, const T* __restrict__ wz,
-                                                       double rho_r, double* __restrict__ part) {
+                                                       double rho_r, double* __restrict__ part,
+                                                       const int* __restrict__ flag) {
+  if (flag && *flag) return;
   double s[3] = {0.0, 0.0, 0.0};
   const int nx = g.n[0], ny = g.n[1];
   // Rows (y, z) of the interior spread over the blocks, x over the threads
@@ -502,8 +512,10 @@ __global__ void __launch_bounds__(256) k_massflux_sums(const T* __restrict__ q, 
 // f_x = (mass_flux * volume - int (rho U)~) / (dt * int (rho^n + rho~)/2)
 // into scal[3] (one block of 256; deterministic order).
 static __global__ void __launch_bounds__(256) k_massflux_force(const double* __restrict__ part, int nblocks,
-                                                               double mass_flux, double* __restrict__ scal) {
+                                                               double mass_flux, double* __restrict__ scal,
+                                                               const int* __restrict__ flag) {
   __shared__ double sm[3][8];
+  if (flag && *flag) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double s[3] = {0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
@@ -529,9 +541,11 @@ static __global__ void __launch_bounds__(256) k_massflux_force(const double* __r
 template <class T>
 __global__ void __launch_bounds__(256) k_force_apply(T* __restrict__ q, const T* __restrict__ stash,
                                                      T* __restrict__ comp, GridDev g, double rho_r,
-                                                     const double* __restrict__ scal) {
+                                                     const double* __restrict__ scal,
+                                                     const int* __restrict__ flag) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.N) return;
+  if (flag && *flag) return;
   const int nx = g.n[0], ny = g.n[1];
   const int x = int(c % nx);
   const long long r = c / nx;

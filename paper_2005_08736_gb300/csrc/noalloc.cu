@@ -25,7 +25,7 @@ constexpr size_t kFdBytes = align_up(10ull * (kMaxN + 1) * kMaxN * kMaxN * 8);
 constexpr size_t kWBytes = align_up(kMaxP * 8);
 constexpr size_t kScalBytes = align_up(4 * 8 + 8 + 4);
 constexpr size_t kScratchBytes =
-    2 * kQBytes + 2 * kIncBytes + 3 * kFdBytes + 3 * kWBytes + kScalBytes;  // ~15 MiB
+    2 * kQBytes + 3 * kIncBytes + 3 * kFdBytes + 3 * kWBytes + kScalBytes;  // ~16 MiB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -97,7 +97,11 @@ extern "C" hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_in
   e.qs = take(kQBytes);
   e.inc = take(kIncBytes);
   void* comp = take(kIncBytes);
+  void* comp2 = take(kIncBytes);
   e.comp = cfg->prec == HGKS_FP32 ? comp : nullptr;
+  e.comp2 = cfg->prec == HGKS_FP32 ? comp2 : nullptr;
+  // No non-physical check here: the steps run to the end whatever the state.
+  e.guard = false;
   for (int d = 0; d < 3; ++d) e.fd[d] = take(kFdBytes);
   for (int d = 0; d < 3; ++d) e.w[d] = take(kWBytes);
   unsigned char* sc = static_cast<unsigned char*>(take(kScalBytes));
@@ -135,6 +139,7 @@ extern "C" hgks_status hgks_step_noalloc(const hgks_config* cfg, double* cons_in
       err = f32 ? hgks::enqueue_rhs_and_update<float>(e, stage)
                 : hgks::enqueue_rhs_and_update<double>(e, stage);
     if (err == cudaSuccess) err = hgks::enqueue_advance_time(e);
+    hgks::swap_state_buffers(e);  // Q^{n+1} was written into qs
   }
   if (err == cudaSuccess)
     err = f32 ? hgks::enqueue_to_fp64<float>(e, cons_inout) : hgks::enqueue_to_fp64<double>(e, cons_inout);

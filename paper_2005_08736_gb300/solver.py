@@ -269,34 +269,50 @@ class Simulation:
 
     def channel_stats(self) -> dict:
         """Mean-flow statistics of the wall-bounded channel (Sec. 3.3,
-        hgks_channel_stats): tau_w, u_tau, Re_tau, U_b, U_c, Re_b, Re_c, C_f and
-        the plane-mean profiles per y row, with y+ (distance to the nearer wall
-        in wall units) and U+ = <U>/u_tau, <u'v'>+ = (<UV> - <U><V>)/u_tau^2."""
+        hgks_channel_stats): tau_w, u_tau, Re_tau, U_b, U_c, Re_b, Re_c, C_f,
+        the plane-mean profiles per y row ("profiles"), and the library's
+        wall-unit profiles y, y_plus, U_plus, uv_plus, dUp_dYp and the
+        total-stress residual."""
         out = _lib.HgksChannel()
         ny = self.cfg.ny
-        prof = np.empty((8, ny))
+        prof = np.empty((len(_lib.CHANNEL_PROFILES), ny))
         self._call(self.lib.hgks_channel_stats(
             self.h, prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out)))
         res = {k: getattr(out, k) for k, _ in _lib.HgksChannel._fields_}
-        names = ("rho", "rhoU", "U", "V", "W", "UV", "UU", "T")
-        res["profiles"] = dict(zip(names, prof))
-        faces = self.cfg.y0 + np.concatenate([[0.0], np.cumsum(self._y_widths())])
-        yc = 0.5 * (faces[1:] + faces[:-1])
-        dist = np.minimum(yc - self.cfg.y0, self.cfg.y0 + self.cfg.ly - yc)
-        ut = res["u_tau"]
-        res["y"] = yc
-        res["y_plus"] = res["rho_w"] * ut * dist / res["mu_w"]
-        res["U_plus"] = prof[2] / ut
-        res["uv_plus"] = (prof[5] - prof[2] * prof[3]) / (ut * ut)
+        res["profiles"] = dict(zip(_lib.CHANNEL_PROFILES[:8], prof[:8]))
+        for name, row in zip(_lib.CHANNEL_PROFILES[8:], prof[8:]):
+            res[name] = row
         return res
 
-    def _y_widths(self) -> np.ndarray:
-        c = self.cfg
-        if not c.y_stretch:
-            return np.full(c.ny, c.ly / c.ny)
-        from . import inputs
-        # the mapping's faces span [-1, 1]; the channel spans ly
-        return np.diff(inputs.channel_faces(c.ny, c.stretch_b)) * (0.5 * c.ly)
+    def kinetic_energy(self, q: torch.Tensor, grad: torch.Tensor | None = None) -> float:
+        """E_k of Sec. 3.1 of an FP64 conservative device tensor
+        [5][nz][ny][nx] (hgks_kinetic_energy); with `grad` (same shape) also
+        dE_k/dQ."""
+        for t in (q,) if grad is None else (q, grad):
+            assert t.is_cuda and t.dtype == torch.float64 and tuple(t.shape) == self.cfg.shape
+            assert t.is_contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        ek = ctypes.c_double()
+        self._call(self.lib.hgks_kinetic_energy(
+            self.h, ctypes.c_void_p(q.data_ptr()),
+            ctypes.c_void_p(grad.data_ptr() if grad is not None else None), ctypes.byref(ek)))
+        q.record_stream(self.stream)
+        if grad is not None:
+            grad.record_stream(self.stream)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return ek.value
+
+
+def cell_widths(cfg: Config, axis: int) -> np.ndarray:
+    """Cell widths along axis 0, 1, 2 of the grid cfg describes
+    (hgks_cell_widths: uniform, or the tanh mapping of Sec. 3.3 in y)."""
+    lib = _lib.load()
+    n = (cfg.nx, cfg.ny, cfg.nz)[axis]
+    out = np.empty(n)
+    c = cfg.c_struct()
+    _lib.check(lib.hgks_cell_widths(ctypes.byref(c), int(axis),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 class Ensemble:
@@ -371,29 +387,38 @@ def run_window(q0: torch.Tensor, sim: Simulation, nsteps: int, dt: float, every:
     return StepWindow.apply(q0, sim, nsteps, dt, every)
 
 
-def kinetic_energy(q: torch.Tensor, cfg: Config) -> torch.Tensor:
-    """E_k = (1/(rho_ref |Omega|)) sum rho |U|^2 / 2 |Omega_c| on a uniform grid (Sec. 3.1)."""
-    rho = q[0]
-    ke = 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho
-    return ke.mean() / cfg.rho_ref
+class _KineticEnergy(torch.autograd.Function):
+    """E_k of a device state through hgks_kinetic_energy; its gradient is the
+    library's dE_k/dQ."""
+
+    @staticmethod
+    def forward(ctx, q, sim: "Simulation"):
+        q = q.detach().contiguous()
+        grad = torch.empty_like(q)
+        ek = sim.kinetic_energy(q, grad)
+        ctx.save_for_backward(grad)
+        return torch.tensor(ek, dtype=torch.float64, device=q.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None
+
+
+def kinetic_energy(q: torch.Tensor, sim: "Simulation") -> torch.Tensor:
+    """E_k = (1/(rho_ref |Omega|)) sum rho |U|^2 / 2 |Omega_c| (Sec. 3.1) of a
+    device FP64 conservative state, differentiable (the library computes the
+    value and dE_k/dQ on the device)."""
+    return _KineticEnergy.apply(q, sim)
 
 
 def total_stress_residual(stats: dict) -> tuple[np.ndarray, np.ndarray]:
-    """The stationarity check of the channel (Sec. 3.3): in a statistically
-    steady channel the total stress is linear,
-        dU+/dY+ - <u'v'>+ = 1 - Y+/Re_tau,
-    so the residual dU+/dY+ - <u'v'>+ - (1 - Y+/Re_tau) vanishes.  Evaluated
-    on the lower half of the channel from the statistics of
-    Simulation.channel_stats (dU/dy by second-order differences of the row
-    means on the stretched grid).  Returns (Y+, residual)."""
-    y, U = stats["y"], stats["profiles"]["U"]
+    """The stationarity check of the channel (Sec. 3.3) on the lower half of
+    the channel: (Y+, dU+/dY+ - <u'v'>+ - (1 - Y+/Re_tau)) from the profiles
+    hgks_channel_stats computes (Simulation.channel_stats)."""
+    y = stats["y"]
     lower = y < y[0] + 0.5 * (y[-1] - y[0]) + 1e-12
-    ut, mu, rho = stats["u_tau"], stats["mu_w"], stats["rho_w"]
-    dudy = np.gradient(U, y)
-    dUp_dYp = mu * dudy / (rho * ut * ut)
-    yp = stats["y_plus"]
-    res = dUp_dYp - stats["uv_plus"] - (1.0 - yp / stats["Re_tau"])
-    return yp[lower], res[lower]
+    return stats["y_plus"][lower], stats["total_stress_residual"][lower]
 
 
 def measure_fp_peaks(stream: torch.cuda.Stream | None = None) -> dict:

@@ -7,6 +7,7 @@ entry.  The library calls are replaced by a stand-in that records them.
 """
 import json
 
+import numpy as np
 import pytest
 
 pytest.importorskip("torch")
@@ -53,15 +54,21 @@ def test_choices_are_cached_per_configuration(tmp_path):
 
 
 @pytest.mark.parametrize("ly,stretch", [(2.0, 1), (3.0, 0)])
-def test_y_widths_of_the_statistics_match_the_grid(ly, stretch):
-    # The row positions Simulation.channel_stats reports come from the same
-    # cell widths as the grid: compared with the oracle's widths (the tanh
-    # mapping spans the channel height 2; the library rejects another ly).
+def test_library_cell_widths_match_the_oracle_grid(ly, stretch):
+    # hgks_cell_widths (host function of the library, no device work): the
+    # y widths the statistics and the kinetic-energy functional use, against
+    # the oracle's widths (the tanh mapping spans the channel height 2).
     import oracle
-    from paper_2005_08736_gb300.solver import Config
+    from paper_2005_08736_gb300 import _lib
+    from paper_2005_08736_gb300.solver import Config, cell_widths
+    try:
+        _lib.load()
+    except (RuntimeError, OSError) as e:
+        pytest.skip(str(e))
     cfg = Config(8, 12, 8, ly=ly, y0=-0.5 * ly, y_stretch=stretch, stretch_b=2.0, bc_y=1)
-    got = stand_in(cfg, StandInLib())._y_widths()
+    got = cell_widths(cfg, 1)
     o = oracle.Solver(oracle.Config(8, 12, 8, ly=ly, y0=-0.5 * ly, y_stretch=stretch,
                                     stretch_b=2.0, bc_y=1))
     assert got == pytest.approx(o.widths(1), rel=1e-13)
     assert got.sum() == pytest.approx(ly, rel=1e-14)
+    assert cell_widths(cfg, 0) == pytest.approx(np.full(8, cfg.lx / 8), rel=1e-15)

@@ -176,15 +176,15 @@ def test_autograd_window_with_checkpoints_kinetic_energy():
     cfg, q0 = setup(n, 1, 1)
     sim = Simulation(cfg)
     x = q0.clone().requires_grad_(True)
-    J = kinetic_energy(run_window(x, sim, K, dt, every=2), cfg)
+    J = kinetic_energy(run_window(x, sim, K, dt, every=2), sim)
     (gq,) = torch.autograd.grad(J, x)
     g = torch.Generator(device="cuda").manual_seed(11)
     for _ in range(2):
         v = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
         v *= q0.abs().amax(dim=(1, 2, 3), keepdim=True)
         h = 1e-7
-        jp = kinetic_energy(forward(sim, q0 + h * v, K, dt), cfg).item()
-        jm = kinetic_energy(forward(sim, q0 - h * v, K, dt), cfg).item()
+        jp = kinetic_energy(forward(sim, q0 + h * v, K, dt), sim).item()
+        jm = kinetic_energy(forward(sim, q0 - h * v, K, dt), sim).item()
         fd = (jp - jm) / (2 * h)
         ad = (gq * v).sum().item()
         assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-12, (ad, fd)

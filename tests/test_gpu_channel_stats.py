@@ -42,6 +42,10 @@ def test_channel_statistics_match_oracle(prec, tol):
     # wall units: y+ of the first row and U+ consistent with the scalars
     assert got["y_plus"][0] == pytest.approx(
         ref["rho_w"] * ref["u_tau"] * 0.5 * dy[0] / ref["mu_w"], rel=10 * tol)
+    assert np.allclose(got["U_plus"], prof["U"] / ref["u_tau"], rtol=10 * tol, atol=0)
+    uvp = (prof["UV"] - prof["U"] * prof["V"]) / ref["u_tau"] ** 2
+    assert np.abs(got["uv_plus"] - uvp).max() <= 10 * tol * max(np.abs(uvp).max(), 1.0)
+    assert np.isfinite(got["total_stress_residual"]).all() and len(got["dUp_dYp"]) == n[1]
 
 
 def test_channel_statistics_need_walls():

@@ -328,6 +328,58 @@ def test_nonphysical_state_is_reported():
     assert e.value.status == HGKS_E_NONPHYSICAL
 
 
+def separating_flow():
+    """u = +4 in the middle half of x, -4 outside (rho = p = 1): two
+    rarefactions so strong that the WENO-Z / full-flux step with dt = 0.01
+    is non-physical at step 3 (the oracle: rho_min 0.80 after step 2, NaN
+    after step 3)."""
+    prim = np.zeros((5, 8, 8, 16))
+    prim[0], prim[4] = 1.0, 1.0
+    x = (np.arange(16) + 0.5) / 16 * 2 * math.pi
+    prim[1] = np.where((x > math.pi / 2) & (x < 1.5 * math.pi), 4.0, -4.0)[None, None, :]
+    return prim
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonphysical_step_leaves_the_last_good_state(prec):
+    """E_NONPHYSICAL leaves the state, time and step count at the last good
+    step, whether the steps ran one per call or in one batch of graph
+    replays; stepping can resume afterwards."""
+    cfg = Config(16, 8, 8, prec=0 if prec == "fp64" else 1, recon=2, flux=1, tau_num_C=1.0,
+                 mu_ref=1e-3, p_ref=1.0)
+    prim, dt = separating_flow(), 0.01
+    one = Simulation(cfg)
+    one.init_primitive(prim)
+    failed = None
+    for k in range(1, 7):
+        try:
+            one.step(1, dt)
+        except HgksError as e:
+            assert e.status == HGKS_E_NONPHYSICAL
+            failed = k
+            break
+    assert failed is not None and failed >= 2, failed
+    good = Simulation(cfg)
+    good.init_primitive(prim)
+    good.step(failed - 1, dt)
+    ref, dref = good.state(), good.diagnostics()
+    assert dref["rho_min"] > 0 and dref["p_min"] > 0
+    batch = Simulation(cfg)
+    batch.init_primitive(prim)
+    with pytest.raises(HgksError) as e:
+        batch.step(6, dt)
+    assert e.value.status == HGKS_E_NONPHYSICAL
+    for sim in (one, batch):
+        d = sim.diagnostics()
+        assert np.array_equal(sim.state(), ref)
+        assert d["step"] == failed - 1 and d["t"] == pytest.approx(dref["t"], rel=1e-14)
+    # the flag is cleared: a smaller step from the last good state runs
+    batch.step(1, dt / 100)
+    assert batch.diagnostics()["step"] == failed
+    for sim in (one, good, batch):
+        sim.close()
+
+
 def test_state_round_trip_fp64():
     cfg = taylor_green_config(10, "fp64")
     Q = oracle.conservative(inputs.taylor_green(10), 1.4)

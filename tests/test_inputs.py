@@ -88,15 +88,3 @@ def test_config_presets_carry_the_papers_constants():
     assert iso.mu_ref == pytest.approx(c["mu0"]) and iso.p_ref == pytest.approx(c["p0"])
     assert iso.visc == 1 and iso.visc_exp == 0.76 and iso.prandtl == 0.7
     assert iso.recon == 2 and iso.flux == 1 and iso.tau_num_C == 1.0
-
-
-def test_kinetic_energy_functional_of_the_taylor_green_start():
-    # The functional the autograd window differentiates (Sec. 3.1 E_k), on a
-    # CPU tensor: the Taylor-Green start has E_k = 1/8 (cell-centre samples of
-    # sin^2 cos^2 cos^2 average to 1/8 per component on a periodic grid).
-    import torch
-    from oracle import conservative
-    from paper_2005_08736_gb300.solver import kinetic_energy, taylor_green_config
-    cfg = taylor_green_config(16, "fp64")
-    q = torch.from_numpy(conservative(inputs.taylor_green(16), 1.4))
-    assert float(kinetic_energy(q, cfg)) == pytest.approx(0.125, rel=1e-13)
