@@ -298,9 +298,14 @@ def extra_workloads(steps: int, peak_tflops: float | None = None):
         sim.init_primitive(inputs.isotropic(n, seed))
         sims.append(sim)
         cells += n ** 3
-    ens = Ensemble(sims)
+    ens = Ensemble(sims)  # batched: one launch per phase for all 24 members
     ens.step(2)
     t_ens = timed(lambda: ens.step(steps, sync=False), 1) / steps
+    # The same batch as graph branches (each member's own launches).
+    ensb = Ensemble(sims, batched=False)
+    ensb.step(2)
+    t_br = timed(lambda: ensb.step(steps, sync=False), 1) / steps
+    ensb.close()
     # Sequential runs: each member advanced alone, one after another.
     t_seq = timed(lambda: [s.step(steps, sync=True) for s in sims], 1) / steps
     # Each member's own graph launched on its own stream without waiting (the
@@ -310,6 +315,8 @@ def extra_workloads(steps: int, peak_tflops: float | None = None):
         "instances": 24, "cells": cells, "ensemble_ms_per_step": 1e3 * t_ens,
         "sequential_ms_per_step": 1e3 * t_seq, "speedup": t_seq / t_ens,
         "member_streams_ms_per_step": 1e3 * t_str, "speedup_vs_member_streams": t_str / t_ens,
+        "graph_branches_ms_per_step": 1e3 * t_br, "speedup_vs_graph_branches": t_br / t_ens,
+        "launches_per_step": {"batched": LAUNCHES_PER_STEP, "branches": LAUNCHES_PER_STEP * 24},
         "ensemble_mcups": cells / t_ens / 1e6}
     ens.close()
     for s in sims:

@@ -174,13 +174,45 @@ typedef struct {
   double p_theta;    /* <p theta> (pressure dilatation) */
   double theta_rms, omega_rms;  /* sqrt(<theta^2>), sqrt(<|omega|^2>) */
   double du2[3], du3[3], du4[3];  /* <(d_i U_i)^k>, k = 2, 3, 4 */
+  double eps_zeta;   /* 2 mu_ref zeta / rho0 (Sec. 3.1, the incompressible-limit dissipation
+                        rate; mu_ref is the configured viscosity, the paper's constant mu) */
 } hgks_turbulence;
 
-/* Fill *out from the current state: one ghost fill, one statistics kernel
- * and one final reduction on the context's stream, then a synchronise.
- * Needs a periodic, uniform grid (E_UNSUPPORTED for walls or a stretched y).
- * Allocates its FP64 partial-sum buffers on the first call. */
+/* Fill *out from the current state: one statistics kernel and one final
+ * reduction on the context's stream, then a synchronise.  Needs a periodic,
+ * uniform grid (E_UNSUPPORTED for walls or a stretched y).  Allocates its
+ * FP64 partial-sum buffers on the first call. */
 hgks_status hgks_turbulence_stats(hgks_ctx* ctx, hgks_turbulence* out);
+
+/* Statistics history (Sec. 3.1: the time histories of E_k, eps(E_k),
+ * eps(zeta), eps1..eps3 and the numerical dissipation eps_num).
+ * hgks_history_start records the current state at once and then makes every
+ * step whose step count is a multiple of `every` (> 0) append a record of its
+ * new state, inside the captured step on the device (the statistics kernels
+ * of hgks_turbulence_stats, gated on the step count; no host round trip),
+ * until `capacity` (> 0) records are stored; later records are dropped.  It
+ * clears the records of an earlier start.  Steps with a non-physical state
+ * record nothing.  Needs a periodic, uniform grid (E_UNSUPPORTED otherwise).
+ * Allocates its device buffers on the first call (and when capacity grows).
+ * hgks_history_stop ends the recording (the records stay readable). */
+hgks_status hgks_history_start(hgks_ctx* ctx, int every, int capacity);
+hgks_status hgks_history_stop(hgks_ctx* ctx);
+
+/* One record of the statistics history. */
+typedef struct {
+  hgks_turbulence s;  /* statistics of the recorded state; s.t its time */
+  long long step;     /* step count of the recorded state */
+  double eps_Ek;      /* eps(E_k) = -dE_k/dt (Sec. 3.1), by second-order differences of the
+                         recorded E_k over the recorded times (non-uniform spacing allowed):
+                         central inside, one-sided three-point at both ends; with two
+                         records the one difference; NaN for a single record */
+  double eps_num;     /* the numerical dissipation eps(E_k) - (eps1 + eps2 + eps3) (Sec. 3.1) */
+} hgks_history_rec;
+
+/* Copy the first min(count, capacity) records (HOST array out, may be NULL
+ * if capacity is 0) and write the number recorded to *count.  The
+ * differences are taken over all records stored.  Synchronises. */
+hgks_status hgks_history_read(hgks_ctx* ctx, hgks_history_rec* out, int capacity, int* count);
 
 /* Mean-flow statistics of the wall-bounded channel (Sec. 3.3), from the
  * current state, instantaneous (time averaging is the caller's): plane
@@ -248,15 +280,31 @@ hgks_status hgks_kinetic_energy(hgks_ctx* ctx, const double* cons, double* grad,
  * e.g. instances of uneven sizes, advanced together.  hgks_ensemble_create
  * takes n distinct contexts on the same device, each on its own stream (the
  * handle borrows them; they must outlive it).  hgks_ensemble_step captures,
- * on first use (and again when dt changes), ONE CUDA graph in which every
- * member's S2O4 step is a parallel branch forked from and joined into the
- * first member's stream, and launches it nsteps times: one graph launch per
- * step for the whole batch, the members' kernels running concurrently.
+ * on first use (and again when dt or the members' buffer assignment
+ * changes), ONE CUDA graph holding one S2O4 step of every member, and
+ * launches it nsteps times on the first member's stream (which first waits
+ * for the work already enqueued on the other members' streams; they wait for
+ * the batch afterwards).  Two forms of the graph:
+ *   - batched (the default when the members share precision, reconstruction
+ *     and its variables, flux and sweep tile variant, and have no mass-flux
+ *     force and no statistics history): ONE kernel launch per phase of the
+ *     step (CFL reduction, dt, the ghost fills, the transposed copy, the three
+ *     sweeps and the update of each stage, time) for all members, driven by
+ *     an instance table of up to 32 members per launch (kernel parameter):
+ *     each block finds its instance and its local block and runs that
+ *     instance's part of the phase; ragged grids are fine, no block waits on
+ *     another;
+ *   - graph branches (any members): every member's own launches as a parallel
+ *     branch forked from and joined into the first member's stream.
  * dt > 0 fixes every member's step; dt <= 0 takes each member's own CFL step.
- * With sync != 0 it waits and checks each member as hgks_step does. */
+ * With sync != 0 it waits and checks each member as hgks_step does (a member
+ * with a non-physical state is left at its last good step).
+ * hgks_ensemble_set_batched(ens, 0 or 1) selects the form (E_UNSUPPORTED if
+ * the members cannot share batched launches). */
 typedef struct hgks_ensemble hgks_ensemble;
 hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out);
 hgks_status hgks_ensemble_step(hgks_ensemble* ens, int nsteps, double dt, int sync);
+hgks_status hgks_ensemble_set_batched(hgks_ensemble* ens, int batched);
 hgks_status hgks_ensemble_destroy(hgks_ensemble* ens);
 const char* hgks_ensemble_last_error(const hgks_ensemble* ens);
 

@@ -6,7 +6,10 @@ shares nothing with the CUDA path.
 
 Definitions (Cao, Pan & Xu, arXiv:2005.08736):
   Sec. 3.1: volume-averaged kinetic energy E_k and enstrophy zeta (both scaled
-    by 1/(rho0 Omega)); the three Navier-Stokes dissipation contributions
+    by 1/(rho0 Omega)); eps(zeta) = 2 mu zeta / rho0; eps(E_k) = -dE_k/dt by
+    second-order differences of an E_k history and the numerical dissipation
+    eps_num = eps(E_k) - (eps1 + eps2 + eps3); the three Navier-Stokes
+    dissipation contributions
     eps1 = 2 mu/rho0 <S^d : S^d>, eps2 = mu_b/rho0 <theta^2>,
     eps3 = -1/rho0 <p theta>, with mu_b = 2N/(3(N+3)) mu and every spatial
     derivative taken by the sixth-order central difference.
@@ -29,7 +32,8 @@ import numpy as np
 
 KEYS = ("Ek", "K", "zeta", "eps1", "eps2", "eps3", "rho_mean", "rho_rms", "u_rms",
         "Su", "Fu", "eps_s", "eps_d", "p_theta", "theta_rms", "omega_rms",
-        "du2_x", "du2_y", "du2_z", "du3_x", "du3_y", "du3_z", "du4_x", "du4_y", "du4_z")
+        "du2_x", "du2_y", "du2_z", "du3_x", "du3_y", "du3_z", "du4_x", "du4_y", "du4_z",
+        "eps_zeta")
 
 
 def d6(f: np.ndarray, axis: int, h: float) -> np.ndarray:
@@ -99,4 +103,20 @@ def statistics(cons: np.ndarray, lengths=(2 * np.pi,) * 3, gamma: float = 1.4, r
     for k, m in (("du2", m2), ("du3", m3), ("du4", m4)):
         for i, a in enumerate("xyz"):
             out[f"{k}_{a}"] = m[i]
+    # Sec. 3.1: the incompressible-limit dissipation rate eps(zeta) = 2 mu zeta / rho0
+    # (mu the configured viscosity mu_ref; the paper's case has a constant mu).
+    out["eps_zeta"] = 2.0 * mu_ref * out["zeta"] / rho0
     return out
+
+
+def dissipation_history(t, stats):
+    """Sec. 3.1 from a time history of statistics (`stats[i]` of the state at
+    time t[i]): eps(E_k) = -dE_k/dt by second-order differences of the E_k
+    samples (numpy's gradient with second-order one-sided ends; the times may
+    be unevenly spaced), and the numerical dissipation
+    eps_num = eps(E_k) - (eps1 + eps2 + eps3).  Returns (eps_Ek, eps_num)."""
+    t = np.asarray(t, dtype=np.float64)
+    ek = np.array([s["Ek"] for s in stats])
+    eps_ek = -np.gradient(ek, t, edge_order=2)
+    phys = np.array([s["eps1"] + s["eps2"] + s["eps3"] for s in stats])
+    return eps_ek, eps_ek - phys

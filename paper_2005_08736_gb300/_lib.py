@@ -26,7 +26,8 @@ EXPORTS = ["hgks_default_config", "hgks_create", "hgks_destroy", "hgks_init_stat
            "hgks_ensemble_last_error", "hgks_autotune", "hgks_set_sweep_shape",
            "hgks_turbulence_stats", "hgks_measure_fp_peaks", "hgks_channel_stats",
            "hgks_set_time", "hgks_count_flops", "hgks_channel_compose", "hgks_cell_widths",
-           "hgks_kinetic_energy"]
+           "hgks_kinetic_energy", "hgks_history_start", "hgks_history_stop",
+           "hgks_history_read", "hgks_ensemble_set_batched"]
 KERNEL_CLASSES = ["cfl", "ghost", "face_fields", "flux_stage1", "flux_stage2", "update"]
 CHANNEL_PROFILES = ("rho", "rhoU", "U", "V", "W", "UV", "UU", "T", "y", "y_plus", "U_plus",
                     "uv_plus", "dUp_dYp", "total_stress_residual")
@@ -67,7 +68,13 @@ class HgksTurbulence(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in (
         "t", "Ek", "K", "zeta", "eps1", "eps2", "eps3", "rho_mean", "rho_rms", "u_rms", "Su", "Fu",
         "eps_s", "eps_d", "p_theta", "theta_rms", "omega_rms")] + [
-        ("du2", ctypes.c_double * 3), ("du3", ctypes.c_double * 3), ("du4", ctypes.c_double * 3)]
+        ("du2", ctypes.c_double * 3), ("du3", ctypes.c_double * 3), ("du4", ctypes.c_double * 3),
+        ("eps_zeta", ctypes.c_double)]
+
+
+class HgksHistoryRec(ctypes.Structure):
+    _fields_ = [("s", HgksTurbulence), ("step", ctypes.c_longlong), ("eps_Ek", ctypes.c_double),
+                ("eps_num", ctypes.c_double)]
 
 
 class HgksChannel(ctypes.Structure):
@@ -118,6 +125,7 @@ def load(path: str | None = None):
         L.hgks_ensemble_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
         L.hgks_ensemble_step.argtypes = [vp, i, d, i]
         L.hgks_ensemble_destroy.argtypes = [vp]
+        L.hgks_ensemble_set_batched.argtypes = [vp, i]
         L.hgks_ensemble_last_error.argtypes = [vp]
         L.hgks_ensemble_last_error.restype = ctypes.c_char_p
         L.hgks_step_noalloc.argtypes = [pcfg, vp, i, d, vp]
@@ -128,6 +136,9 @@ def load(path: str | None = None):
         L.hgks_channel_compose.argtypes = [pcfg, pd, pd, ctypes.POINTER(HgksChannel)]
         L.hgks_cell_widths.argtypes = [pcfg, i, pd]
         L.hgks_kinetic_energy.argtypes = [vp, vp, vp, pd]
+        L.hgks_history_start.argtypes = [vp, i, i]
+        L.hgks_history_stop.argtypes = [vp]
+        L.hgks_history_read.argtypes = [vp, ctypes.POINTER(HgksHistoryRec), i, ctypes.POINTER(i)]
         L.hgks_last_error.argtypes = [vp]
         L.hgks_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:

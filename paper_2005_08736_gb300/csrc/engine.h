@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/hgks.h"
 
@@ -48,6 +49,13 @@ struct Engine {
   double* turb_out = nullptr;   // and the final sums (allocated on first use)
   double* chan_out = nullptr;   // channel statistics: kChanSums sums per y row (first use)
   double* kin_w = nullptr;      // kinetic-energy functional: FP64 interior widths x, y, z (first use)
+  // Statistics history (hgks_history_start): when hist_every > 0 the step
+  // appends a record [t, step, kTurbSums sums] of the new state every
+  // hist_every steps, while fewer than hist_cap records are stored.
+  int hist_every = 0;
+  int hist_cap = 0;
+  double* hist = nullptr;
+  int* hist_count = nullptr;
   int diag_blocks = 0;
   int cfl_blocks = 0;
   int sms = 152;  // multiprocessors of the device
@@ -80,6 +88,9 @@ enum TurbSum {
   TS_DU4 = TS_DU3 + 3,
   kTurbSums = TS_DU4 + 3
 };
+
+// A history record: time, step count, then the kTurbSums sums.
+constexpr int kHistStride = kTurbSums + 2;
 
 // Channel statistics (turbulence.cuh, k_channel_rows): plane sums per y row
 // of rho, rho U, U, V, W, U V, U U, T.
@@ -118,6 +129,9 @@ struct Probe {
 // Kernel sequences, implemented per floating type in kernels_f32.cu / kernels_f64.cu.
 template <class T> cudaError_t enqueue_ghosts(const Engine& e, void* qbuf, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_turbulence(const Engine& e);
+// Append a history record of the state in qbuf (gated: only if the step
+// count is a multiple of e.hist_every and the non-physical flag is clear).
+template <class T> cudaError_t enqueue_history_record(const Engine& e, const void* qbuf, bool gated);
 template <class T> cudaError_t enqueue_channel_rows(const Engine& e);
 template <class T> cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe = nullptr);
 template <class T> cudaError_t enqueue_cfl(const Engine& e, const void* qbuf);
@@ -132,6 +146,12 @@ template <class T> cudaError_t enqueue_to_fp64(const Engine& e, double* dst);
 int sweep_variant_count(const Engine& e);
 template <class T> cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in,
                                                     double* adj_out);
+// One S2O4 step of every member with one batched launch per phase (the
+// members share precision, reconstruction, flux and tile variant and have
+// no mass-flux force and no statistics history); Q^{n+1} of each ends in its
+// qs.  On stream s.
+template <class T> cudaError_t enqueue_batched_step(const std::vector<Engine*>& members, double dt_fixed,
+                                                    cudaStream_t s);
 cudaError_t enqueue_reset_scalars(const Engine& e);
 // Swap the roles of the two state buffers (and the compensation buffers)
 // after a step has been enqueued: Q^{n+1} is in qs.

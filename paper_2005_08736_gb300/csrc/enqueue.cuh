@@ -7,8 +7,11 @@
 #include "sweep.cuh"
 #include "adjoint.cuh"
 #include "turbulence.cuh"
+#include "batch.cuh"
 
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 namespace hgks {
 
@@ -75,16 +78,14 @@ template <> struct SweepTile<float, FLUX_FULL> { static constexpr int TP = 16, T
 template <> struct SweepTile<double, FLUX_SMOOTH> { static constexpr int TP = 16, TS = 8, NL = 2; };
 template <> struct SweepTile<double, FLUX_FULL> { static constexpr int TP = 8, TS = 8, NL = 2; };
 
-template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK = false>
-cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
+// Arguments and grid (gx, gy, gz) of the sweep of direction d on the padded
+// state q with a TP x TS tile and NL layers per face-field pass.
+template <class T, int TP, int TS, int NL>
+SweepArgs<T> sweep_args(const Engine& e, const T* q, int d, int& gx, int& gy, int& gz) {
   const GridDev g = grid_of(e);
   SweepArgs<T> a;
-  // The x sweep reads the copy of the state with x slowest, made here.
+  // The x sweep reads the copy of the state with x slowest (k_transpose_x).
   const bool xt = d == 0 && e.qx != nullptr;
-  if (xt) {
-    const dim3 tgrid((g.p[0] + 31) / 32, (g.p[1] + 31) / 32, g.p[2]);
-    k_transpose_x<T><<<tgrid, 256, 0, e.stream>>>(q, static_cast<T*>(e.qx), g);
-  }
   a.q = xt ? static_cast<const T*>(e.qx) : q;
   a.xt = xt ? 1 : 0;
   a.fd = static_cast<T*>(e.fd[d]);
@@ -96,7 +97,8 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   a.d = d;
   a.gas = gas_of<T>(e.cfg);
   const int P = d == 0 ? 1 : 0, S = d == 2 ? 1 : 2;
-  const int gx = (g.n[P] + TP - 1) / TP, gy = (g.n[S] + TS - 1) / TS;
+  gx = (g.n[P] + TP - 1) / TP;
+  gy = (g.n[S] + TS - 1) / TS;
   // Chunk the march along d so that the grid holds several waves of CTAs.
   const int layers = g.n[d] + 1;
   int chunk = e.sweep_chunk;
@@ -107,7 +109,19 @@ cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
   }
   chunk = (chunk + NL - 1) / NL * NL;
   a.chunk = chunk;
-  const int gz = (layers + chunk - 1) / chunk;
+  gz = (layers + chunk - 1) / chunk;
+  return a;
+}
+
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK = false>
+cudaError_t launch_sweep_tile(const Engine& e, const T* q, int d) {
+  const GridDev g = grid_of(e);
+  if (d == 0 && e.qx != nullptr) {
+    const dim3 tgrid((g.p[0] + 31) / 32, (g.p[1] + 31) / 32, g.p[2]);
+    k_transpose_x<T><<<tgrid, 256, 0, e.stream>>>(q, static_cast<T*>(e.qx), g);
+  }
+  int gx, gy, gz;
+  const SweepArgs<T> a = sweep_args<T, TP, TS, NL>(e, q, d, gx, gy, gz);
   constexpr size_t smem = sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL>();
   auto kern = k_sweep<T, MODE, FLUX, STAGE, TP, TS, NL, PK>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -143,18 +157,9 @@ cudaError_t launch_all_directions(const Engine& e, const T* q, int stage, Probe*
   return cudaSuccess;
 }
 
+// Arguments of the update kernel on the context's current buffers.
 template <class T>
-cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
-  T* qin = static_cast<T*>(stage == 1 ? e.q : e.qs);
-  cudaError_t err = enqueue_ghosts<T>(e, qin, probe);
-  if (err != cudaSuccess) return err;
-  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
-#define HGKS_DISPATCH(M, F) \
-  if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe);
-  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0) HGKS_DISPATCH(3, 0) HGKS_DISPATCH(4, 0)
-  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1) HGKS_DISPATCH(3, 1) HGKS_DISPATCH(4, 1)
-#undef HGKS_DISPATCH
-  if (err != cudaSuccess) return err;
+UpdateArgs<T> update_args(const Engine& e) {
   UpdateArgs<T> ua;
   ua.q = static_cast<T*>(e.q);
   ua.qs = static_cast<T*>(e.qs);
@@ -173,6 +178,23 @@ cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
   const bool mass_flux = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX;
   ua.force_x = mass_flux ? T(0) : T(e.cfg.force_x);
   ua.rho_r = T(e.cfg.rho_ref);
+  return ua;
+}
+
+template <class T>
+cudaError_t enqueue_rhs_and_update(const Engine& e, int stage, Probe* probe) {
+  T* qin = static_cast<T*>(stage == 1 ? e.q : e.qs);
+  cudaError_t err = enqueue_ghosts<T>(e, qin, probe);
+  if (err != cudaSuccess) return err;
+  const int mode = sweep_mode(e.cfg), flux = e.cfg.flux;
+#define HGKS_DISPATCH(M, F) \
+  if (mode == M && flux == F) err = launch_all_directions<T, M, F>(e, qin, stage, probe);
+  HGKS_DISPATCH(0, 0) HGKS_DISPATCH(1, 0) HGKS_DISPATCH(2, 0) HGKS_DISPATCH(3, 0) HGKS_DISPATCH(4, 0)
+  HGKS_DISPATCH(0, 1) HGKS_DISPATCH(1, 1) HGKS_DISPATCH(2, 1) HGKS_DISPATCH(3, 1) HGKS_DISPATCH(4, 1)
+#undef HGKS_DISPATCH
+  if (err != cudaSuccess) return err;
+  const UpdateArgs<T> ua = update_args<T>(e);
+  const bool mass_flux = e.cfg.force_mode == HGKS_FORCE_MASS_FLUX;
   if (probe) probe->begin(e.stream, KC_UPDATE);
   const dim3 ugrid((e.n[0] + kUpdTX - 1) / kUpdTX, (e.n[1] + kUpdTY - 1) / kUpdTY, e.n[2]);
   if (stage == 1)
@@ -225,18 +247,12 @@ cudaError_t enqueue_diag(const Engine& e) {
   return cudaGetLastError();
 }
 
-// Turbulence statistics: ghost fill of Q^n, per-block FP64 sums, final sum
-// into e.turb_out (kTurbSums doubles).
-template <class T>
-cudaError_t enqueue_turbulence(const Engine& e) {
-  cudaError_t err = enqueue_ghosts<T>(e, e.q, nullptr);
-  if (err != cudaSuccess) return err;
-  const hgks_config& c = e.cfg;
+inline TurbArgs turb_args(const hgks_config& c, const int n[3]) {
   TurbArgs a;
   const double L[3] = {c.lx, c.ly, c.lz};
   double vol = 1.0;
   for (int d = 0; d < 3; ++d) {
-    const double h = L[d] / e.n[d];
+    const double h = L[d] / n[d];
     a.inv60h[d] = 1.0 / (60.0 * h);
     vol *= h;
   }
@@ -250,8 +266,29 @@ cudaError_t enqueue_turbulence(const Engine& e) {
   a.visc_exp = c.visc_exp;
   const double K = (5.0 - 3.0 * c.gamma) / (c.gamma - 1.0);
   a.mub_ratio = 2.0 * K / (3.0 * (K + 3.0));
-  k_turb<T><<<e.diag_blocks, 256, 0, e.stream>>>(static_cast<const T*>(e.q), grid_of(e), a, e.turb_part);
-  k_turb_final<<<1, 256, 0, e.stream>>>(e.turb_part, e.diag_blocks, e.turb_out);
+  return a;
+}
+
+// Turbulence statistics of Q^n: per-block FP64 sums, final sum into
+// e.turb_out (kTurbSums doubles).
+template <class T>
+cudaError_t enqueue_turbulence(const Engine& e) {
+  const HistGate gate{e.scal, nullptr, 0};
+  k_turb<T><<<e.diag_blocks, 256, 0, e.stream>>>(static_cast<const T*>(e.q), grid_of(e),
+                                                 turb_args(e.cfg, e.n), e.turb_part, gate);
+  const TurbSink sink{e.turb_out, nullptr, nullptr, 0};
+  k_turb_final<<<1, 256, 0, e.stream>>>(e.turb_part, e.diag_blocks, sink, gate);
+  return cudaGetLastError();
+}
+
+// A record of the statistics history from the state in qbuf.
+template <class T>
+cudaError_t enqueue_history_record(const Engine& e, const void* qbuf, bool gated) {
+  const HistGate gate{e.scal, e.flag, gated ? e.hist_every : 0};
+  k_turb<T><<<e.diag_blocks, 256, 0, e.stream>>>(static_cast<const T*>(qbuf), grid_of(e),
+                                                 turb_args(e.cfg, e.n), e.turb_part, gate);
+  const TurbSink sink{nullptr, e.hist, e.hist_count, e.hist_cap};
+  k_turb_final<<<1, 256, 0, e.stream>>>(e.turb_part, e.diag_blocks, sink, gate);
   return cudaGetLastError();
 }
 
@@ -370,6 +407,165 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- batched step ---
+// One S2O4 step of every member (same precision, reconstruction, flux, tile
+// variant; constant or no body force) with one batched launch per phase
+// (batch.cuh) on stream s.  Each member's arguments are those of its own
+// launches: its buffers, grid, chunking and non-physical guard.
+
+// Launch Job over the members (in groups of kBatchMax): job i runs blocks[i] blocks.
+template <class Job>
+cudaError_t launch_batched(const std::vector<Job>& jobs, const std::vector<int>& blocks, size_t smem,
+                           cudaStream_t s) {
+  auto kern = k_batched<Job>;
+  if (smem > 0) {
+    const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  for (size_t i0 = 0; i0 < jobs.size(); i0 += kBatchMax) {
+    BatchTable<Job> t;
+    t.n = (int)std::min<size_t>(kBatchMax, jobs.size() - i0);
+    int acc = 0;
+    for (int m = 0; m < t.n; ++m) {
+      t.start[m] = acc;
+      t.job[m] = jobs[i0 + m];
+      acc += blocks[i0 + m];
+    }
+    t.start[t.n] = acc;
+    if (acc == 0) continue;
+    kern<<<acc, Job::kThreads, smem, s>>>(t);
+    const cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK>
+cudaError_t batched_sweeps(const std::vector<Engine*>& ms, int stage, cudaStream_t s) {
+  for (int d = 0; d < 3; ++d) {
+    if (d == 0) {
+      std::vector<TransposeJob<T>> tj;
+      std::vector<int> tb;
+      for (Engine* e : ms) {
+        if (!e->qx) continue;
+        const GridDev g = grid_of(*e);
+        const int gx = (g.p[0] + 31) / 32, gy = (g.p[1] + 31) / 32;
+        tj.push_back({static_cast<const T*>(stage == 1 ? e->q : e->qs), static_cast<T*>(e->qx), g, gx, gy});
+        tb.push_back(gx * gy * g.p[2]);
+      }
+      const cudaError_t err = launch_batched(tj, tb, 0, s);
+      if (err != cudaSuccess) return err;
+    }
+    using Job = SweepJob<T, MODE, FLUX, STAGE, TP, TS, NL, PK>;
+    std::vector<Job> jobs;
+    std::vector<int> blocks;
+    for (Engine* e : ms) {
+      int gx, gy, gz;
+      Job j;
+      j.a = sweep_args<T, TP, TS, NL>(*e, static_cast<const T*>(stage == 1 ? e->q : e->qs), d, gx, gy, gz);
+      j.gx = gx;
+      j.gy = gy;
+      jobs.push_back(j);
+      blocks.push_back(gx * gy * gz);
+    }
+    const cudaError_t err = launch_batched(jobs, blocks, sweep_smem_bytes<T, MODE, FLUX, TP, TS, NL>(), s);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+template <class T, int MODE, int FLUX, int STAGE>
+cudaError_t batched_sweeps_variant(const std::vector<Engine*>& ms, int stage, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH) {
+    const int v = ms[0]->sweep_variant;
+    if (v == 1) return batched_sweeps<T, MODE, FLUX, STAGE, 32, 8, 2, false>(ms, stage, s);
+    if (v == 2) return batched_sweeps<T, MODE, FLUX, STAGE, 16, 16, 2, false>(ms, stage, s);
+    if (v == 3) return batched_sweeps<T, MODE, FLUX, STAGE, 32, 8, 2, true>(ms, stage, s);
+  }
+  return batched_sweeps<T, MODE, FLUX, STAGE, SweepTile<T, FLUX>::TP, SweepTile<T, FLUX>::TS,
+                        SweepTile<T, FLUX>::NL, false>(ms, stage, s);
+}
+
+template <class T>
+cudaError_t enqueue_batched_step(const std::vector<Engine*>& ms, double dt_fixed, cudaStream_t s) {
+  cudaError_t err;
+  {
+    std::vector<CflJob<T>> jobs;
+    std::vector<int> blocks;
+    for (Engine* e : ms) {
+      jobs.push_back({static_cast<const T*>(e->q), grid_of(*e), static_cast<const T*>(e->w[0]),
+                      static_cast<const T*>(e->w[1]), static_cast<const T*>(e->w[2]), e->cfg.rho_ref,
+                      e->cfg.p_ref, e->cfg.gamma, e->dtmin, e->flag, e->cfl_blocks});
+      blocks.push_back(e->cfl_blocks);
+    }
+    if ((err = launch_batched(jobs, blocks, 0, s)) != cudaSuccess) return err;
+  }
+  {
+    std::vector<SetDtJob> jobs;
+    std::vector<int> blocks;
+    for (Engine* e : ms) {
+      jobs.push_back({e->scal, e->dtmin, e->cfg.cfl, dt_fixed, e->guard ? e->flag : nullptr});
+      blocks.push_back(1);
+    }
+    if ((err = launch_batched(jobs, blocks, 0, s)) != cudaSuccess) return err;
+  }
+  const int mode = sweep_mode(ms[0]->cfg), flux = ms[0]->cfg.flux;
+  for (int stage = 1; stage <= 2; ++stage) {
+    std::vector<GhostXJob<T>> gxj;
+    std::vector<GhostYJob<T>> gyj;
+    std::vector<GhostZJob<T>> gzj;
+    std::vector<int> bx, by, bz;
+    for (Engine* e : ms) {
+      T* q = static_cast<T*>(stage == 1 ? e->q : e->qs);
+      const GridDev g = grid_of(*e);
+      gxj.push_back({q, g});
+      bx.push_back(blocks_for(6LL * g.n[1] * g.n[2], 256));
+      gyj.push_back({q, g, e->cfg.bc_y == HGKS_BC_WALL_ISOTHERMAL ? 1 : 0, gas_of<T>(e->cfg), T(e->cfg.T_wall)});
+      by.push_back(blocks_for(6LL * g.p[0] * g.n[2], 256));
+      gzj.push_back({q, g});
+      bz.push_back(blocks_for(6LL * g.p[0] * g.p[1], 256));
+    }
+    if ((err = launch_batched(gxj, bx, 0, s)) != cudaSuccess) return err;
+    if ((err = launch_batched(gyj, by, 0, s)) != cudaSuccess) return err;
+    if ((err = launch_batched(gzj, bz, 0, s)) != cudaSuccess) return err;
+    err = cudaErrorInvalidValue;
+#define HGKS_BSW(M, F)                                                                           \
+    if (mode == M && flux == F)                                                                  \
+      err = stage == 1 ? batched_sweeps_variant<T, M, F, 1>(ms, stage, s)                        \
+                       : batched_sweeps_variant<T, M, F, 2>(ms, stage, s);
+    HGKS_BSW(0, 0) HGKS_BSW(1, 0) HGKS_BSW(2, 0) HGKS_BSW(3, 0) HGKS_BSW(4, 0)
+    HGKS_BSW(0, 1) HGKS_BSW(1, 1) HGKS_BSW(2, 1) HGKS_BSW(3, 1) HGKS_BSW(4, 1)
+#undef HGKS_BSW
+    if (err != cudaSuccess) return err;
+    std::vector<int> ub;
+    if (stage == 1) {
+      std::vector<UpdateJob<T, 1>> uj;
+      for (Engine* e : ms) {
+        const int gx = (e->n[0] + kUpdTX - 1) / kUpdTX, gy = (e->n[1] + kUpdTY - 1) / kUpdTY;
+        uj.push_back({update_args<T>(*e), gx, gy});
+        ub.push_back(gx * gy * e->n[2]);
+      }
+      err = launch_batched(uj, ub, 0, s);
+    } else {
+      std::vector<UpdateJob<T, 2>> uj;
+      for (Engine* e : ms) {
+        const int gx = (e->n[0] + kUpdTX - 1) / kUpdTX, gy = (e->n[1] + kUpdTY - 1) / kUpdTY;
+        uj.push_back({update_args<T>(*e), gx, gy});
+        ub.push_back(gx * gy * e->n[2]);
+      }
+      err = launch_batched(uj, ub, 0, s);
+    }
+    if (err != cudaSuccess) return err;
+  }
+  std::vector<AdvanceJob> aj;
+  std::vector<int> ab;
+  for (Engine* e : ms) {
+    aj.push_back({e->scal, e->guard ? e->flag : nullptr});
+    ab.push_back(1);
+  }
+  return launch_batched(aj, ab, 0, s);
+}
+
 #define HGKS_INSTANTIATE(T)                                                  \
   template cudaError_t enqueue_ghosts<T>(const Engine&, void*, Probe*);      \
   template cudaError_t enqueue_rhs_and_update<T>(const Engine&, int, Probe*); \
@@ -377,9 +573,11 @@ cudaError_t enqueue_adjoint_step(const Engine& e, const double* adj_in, double* 
   template cudaError_t enqueue_sweep_only<T>(const Engine&, int);            \
   template cudaError_t enqueue_diag<T>(const Engine&);                       \
   template cudaError_t enqueue_turbulence<T>(const Engine&);                 \
+  template cudaError_t enqueue_history_record<T>(const Engine&, const void*, bool); \
   template cudaError_t enqueue_channel_rows<T>(const Engine&);               \
   template cudaError_t enqueue_from_fp64<T>(const Engine&, const double*, int); \
   template cudaError_t enqueue_to_fp64<T>(const Engine&, double*);           \
-  template cudaError_t enqueue_adjoint_step<T>(const Engine&, const double*, double*);
+  template cudaError_t enqueue_adjoint_step<T>(const Engine&, const double*, double*); \
+  template cudaError_t enqueue_batched_step<T>(const std::vector<Engine*>&, double, cudaStream_t);
 
 }  // namespace hgks

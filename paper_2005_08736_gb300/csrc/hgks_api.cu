@@ -112,7 +112,7 @@ void free_all(hgks::Engine& e) {
   void* ptrs[] = {e.q, e.qs, e.qx, e.inc, e.comp, e.comp2, e.fd[0], e.fd[1], e.fd[2], e.w[0], e.w[1],
                   e.w[2], e.scal, e.dtmin, e.flag, e.part, e.diag_out, e.io,
                   e.adj_acc, e.adj_mu, e.adj_wL, e.adj_wdL, e.turb_part, e.turb_out,
-                  e.chan_out, e.kin_w};
+                  e.chan_out, e.kin_w, e.hist, e.hist_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -133,7 +133,11 @@ cudaError_t enqueue_stage_pair(hgks::Engine& e, double dt_fixed, hgks::Probe* pr
               : hgks::enqueue_rhs_and_update<double>(e, stage, probe);
     if (err != cudaSuccess) return err;
   }
-  return hgks::enqueue_advance_time(e);
+  err = hgks::enqueue_advance_time(e);
+  if (err != cudaSuccess || e.hist_every <= 0) return err;
+  // Statistics history: a record of Q^{n+1} (in qs) every hist_every steps.
+  return f32 ? hgks::enqueue_history_record<float>(e, e.qs, true)
+             : hgks::enqueue_history_record<double>(e, e.qs, true);
 }
 
 void drop_graphs(hgks_ctx* c) {
@@ -734,26 +738,12 @@ hgks_status hgks_cell_widths(const hgks_config* cfg, int axis, double* out) {
   return HGKS_OK;
 }
 
-hgks_status hgks_turbulence_stats(hgks_ctx* c, hgks_turbulence* out) {
-  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
-  hgks::Engine& e = c->e;
-  if (e.cfg.bc_y != HGKS_BC_PERIODIC || e.cfg.y_stretch)
-    return fail(c, HGKS_E_UNSUPPORTED, "turbulence statistics need a periodic uniform grid");
-  constexpr int NS = hgks::kTurbSums;
-  if (!e.turb_part) {
-    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_part, sizeof(double) * NS * e.diag_blocks));
-    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_out, sizeof(double) * NS));
-  }
-  const bool f32 = e.cfg.prec == HGKS_FP32;
-  HGKS_CHECK(c, f32 ? hgks::enqueue_turbulence<float>(e) : hgks::enqueue_turbulence<double>(e));
-  double r[NS], scal[3];
-  HGKS_CHECK(c, cudaMemcpyAsync(r, e.turb_out, NS * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
-  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
-  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+// The statistics of include/hgks.h from the kTurbSums raw sums r.
+static void turb_from_sums(const hgks_config& cf, const double* r, double t, hgks_turbulence* out) {
   using namespace hgks;
-  const double V = r[TS_VOL], rho0 = e.cfg.rho_ref;
+  const double V = r[TS_VOL], rho0 = cf.rho_ref;
   auto avg = [&](int k) { return r[k] / V; };
-  out->t = scal[1];
+  out->t = t;
   out->K = avg(TS_KE);
   out->Ek = out->K / rho0;
   out->zeta = avg(TS_ENS) / rho0;
@@ -784,6 +774,119 @@ hgks_status hgks_turbulence_stats(hgks_ctx* c, hgks_turbulence* out) {
   out->p_theta = avg(TS_P_TH);
   out->theta_rms = std::sqrt(avg(TS_TH2));
   out->omega_rms = std::sqrt(avg(TS_W2));
+  // Sec. 3.1: eps(zeta) = 2 mu zeta / rho0 with the reference viscosity mu_ref.
+  out->eps_zeta = 2.0 * cf.mu_ref * out->zeta / rho0;
+}
+
+static bool periodic_uniform(const hgks_config& cf) {
+  return cf.bc_y == HGKS_BC_PERIODIC && !cf.y_stretch;
+}
+
+hgks_status hgks_turbulence_stats(hgks_ctx* c, hgks_turbulence* out) {
+  if (!c || !out) return fail(c, HGKS_E_INVAL, "null argument");
+  hgks::Engine& e = c->e;
+  if (!periodic_uniform(e.cfg))
+    return fail(c, HGKS_E_UNSUPPORTED, "turbulence statistics need a periodic uniform grid");
+  constexpr int NS = hgks::kTurbSums;
+  if (!e.turb_part) {
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_part, sizeof(double) * NS * e.diag_blocks));
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_out, sizeof(double) * NS));
+  }
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_turbulence<float>(e) : hgks::enqueue_turbulence<double>(e));
+  double r[NS], scal[3];
+  HGKS_CHECK(c, cudaMemcpyAsync(r, e.turb_out, NS * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaMemcpyAsync(scal, e.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  turb_from_sums(e.cfg, r, scal[1], out);
+  return HGKS_OK;
+}
+
+hgks_status hgks_history_start(hgks_ctx* c, int every, int capacity) {
+  if (!c || every <= 0 || capacity <= 0) return fail(c, HGKS_E_INVAL, "bad history arguments");
+  hgks::Engine& e = c->e;
+  if (!periodic_uniform(e.cfg))
+    return fail(c, HGKS_E_UNSUPPORTED, "the statistics history needs a periodic uniform grid");
+  if (!e.turb_part) {
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_part, sizeof(double) * hgks::kTurbSums * e.diag_blocks));
+    HGKS_CHECK(c, cudaMalloc((void**)&e.turb_out, sizeof(double) * hgks::kTurbSums));
+  }
+  if (e.hist_cap < capacity) {
+    if (e.hist) cudaFree(e.hist);
+    e.hist = nullptr;
+    e.hist_cap = 0;
+    HGKS_CHECK(c, cudaMalloc((void**)&e.hist, sizeof(double) * hgks::kHistStride * capacity));
+    e.hist_cap = capacity;
+  }
+  e.hist_cap = capacity;
+  if (!e.hist_count) HGKS_CHECK(c, cudaMalloc((void**)&e.hist_count, sizeof(int)));
+  HGKS_CHECK(c, cudaMemsetAsync(e.hist_count, 0, sizeof(int), e.stream));
+  e.hist_every = every;
+  drop_graphs(c);  // the captured steps gain the record
+  // The first record: the current state.
+  const bool f32 = e.cfg.prec == HGKS_FP32;
+  HGKS_CHECK(c, f32 ? hgks::enqueue_history_record<float>(e, e.q, false)
+                    : hgks::enqueue_history_record<double>(e, e.q, false));
+  return HGKS_OK;
+}
+
+hgks_status hgks_history_stop(hgks_ctx* c) {
+  if (!c) return fail(c, HGKS_E_INVAL, "null context");
+  if (c->e.hist_every != 0) {
+    c->e.hist_every = 0;
+    drop_graphs(c);
+  }
+  return HGKS_OK;
+}
+
+hgks_status hgks_history_read(hgks_ctx* c, hgks_history_rec* out, int capacity, int* count) {
+  if (!c || !count || capacity < 0 || (capacity > 0 && !out)) return fail(c, HGKS_E_INVAL, "bad argument");
+  hgks::Engine& e = c->e;
+  int n = 0;
+  if (e.hist_count) {
+    HGKS_CHECK(c, cudaMemcpyAsync(&n, e.hist_count, sizeof(int), cudaMemcpyDeviceToHost, e.stream));
+    HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  }
+  *count = n;
+  const int m = std::min(n, capacity);
+  if (m == 0) return HGKS_OK;
+  std::vector<double> raw(size_t(hgks::kHistStride) * n);
+  HGKS_CHECK(c, cudaMemcpyAsync(raw.data(), e.hist, raw.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                e.stream));
+  HGKS_CHECK(c, cudaStreamSynchronize(e.stream));
+  std::vector<double> t(n), ek(n);
+  std::vector<hgks_history_rec> rec(n);
+  for (int i = 0; i < n; ++i) {
+    const double* r = &raw[size_t(hgks::kHistStride) * i];
+    turb_from_sums(e.cfg, r + 2, r[0], &rec[i].s);
+    rec[i].step = (long long)r[1];
+    t[i] = r[0];
+    ek[i] = rec[i].s.Ek;
+  }
+  // eps(E_k) = -dE_k/dt (Sec. 3.1) by second-order differences of the
+  // recorded history on its (possibly non-uniform) times: the central
+  // formula inside, the one-sided three-point formula at both ends; two
+  // records give the one difference, one record none (NaN).
+  for (int i = 0; i < n; ++i) {
+    double d = std::nan("");
+    if (n >= 3) {
+      if (i == 0 || i == n - 1) {
+        const int a = i == 0 ? 0 : n - 1, s1 = i == 0 ? 1 : -1;
+        const double h1 = t[a + s1] - t[a], h2 = t[a + 2 * s1] - t[a + s1];
+        d = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * ek[a] + (h1 + h2) / (h1 * h2) * ek[a + s1] -
+            h1 / (h2 * (h1 + h2)) * ek[a + 2 * s1];
+      } else {
+        const double hl = t[i] - t[i - 1], hr = t[i + 1] - t[i];
+        d = (hl * hl * ek[i + 1] + (hr * hr - hl * hl) * ek[i] - hr * hr * ek[i - 1]) / (hl * hr * (hl + hr));
+      }
+    } else if (n == 2) {
+      d = (ek[1] - ek[0]) / (t[1] - t[0]);
+    }
+    rec[i].eps_Ek = -d;
+    // Sec. 3.1: the numerical dissipation eps(E_k) - (eps1 + eps2 + eps3).
+    rec[i].eps_num = rec[i].eps_Ek - (rec[i].s.eps1 + rec[i].s.eps2 + rec[i].s.eps3);
+  }
+  std::memcpy(out, rec.data(), sizeof(hgks_history_rec) * m);
   return HGKS_OK;
 }
 
@@ -824,8 +927,24 @@ struct hgks_ensemble {
     std::vector<void*> q;
   } slot[2];
   int next_slot = 0;
+  bool batched = false;  // one batched launch per phase (else graph branches)
   std::string err;
 };
+
+// Whether the members can share batched launches: same precision,
+// reconstruction (and variables), flux and sweep tile variant, no mass-flux
+// force and no statistics history.
+static bool ensemble_batchable(const hgks_ensemble* en) {
+  const hgks::Engine& a = en->members[0]->e;
+  for (hgks_ctx* c : en->members) {
+    const hgks::Engine& e = c->e;
+    if (e.cfg.prec != a.cfg.prec || e.cfg.recon != a.cfg.recon || e.cfg.flux != a.cfg.flux ||
+        e.cfg.recon_vars != a.cfg.recon_vars || e.sweep_variant != a.sweep_variant ||
+        e.cfg.force_mode != HGKS_FORCE_CONSTANT || e.hist_every != 0)
+      return false;
+  }
+  return true;
+}
 
 hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out) {
   if (!ctxs || n <= 0 || !out) return fail(nullptr, HGKS_E_INVAL, "bad ensemble arguments");
@@ -850,7 +969,26 @@ hgks_status hgks_ensemble_create(hgks_ctx** ctxs, int n, hgks_ensemble** out) {
       return cuda_fail(nullptr, e, "cudaEventCreateWithFlags");
     }
   }
+  en->batched = ensemble_batchable(en);
   *out = en;
+  return HGKS_OK;
+}
+
+hgks_status hgks_ensemble_set_batched(hgks_ensemble* en, int batched) {
+  if (!en) return HGKS_E_INVAL;
+  if (batched && !ensemble_batchable(en)) {
+    en->err = "batched launches need members of one precision, scheme and tile variant, without the "
+              "mass-flux force or a statistics history";
+    return HGKS_E_UNSUPPORTED;
+  }
+  if (en->batched != (batched != 0)) {
+    en->batched = batched != 0;
+    for (auto& sl : en->slot)
+      if (sl.graph) {
+        cudaGraphExecDestroy(sl.graph);
+        sl.graph = nullptr;
+      }
+  }
   return HGKS_OK;
 }
 
@@ -879,9 +1017,17 @@ static hgks_status capture_ensemble(hgks_ensemble* en, hgks_ensemble::Slot& sl, 
     en->err = std::string("capture: ") + cudaGetErrorString(err);
     return HGKS_E_CUDA;
   }
-  err = cudaEventRecord(en->events[0], s0);
   const int n = (int)en->members.size();
-  for (int i = 0; i < n && err == cudaSuccess; ++i) {
+  if (en->batched) {
+    // One launch per phase over all members, on the first member's stream.
+    std::vector<hgks::Engine*> ms;
+    for (hgks_ctx* c : en->members) ms.push_back(&c->e);
+    err = en->members[0]->e.cfg.prec == HGKS_FP32 ? hgks::enqueue_batched_step<float>(ms, dt_fixed, s0)
+                                                   : hgks::enqueue_batched_step<double>(ms, dt_fixed, s0);
+  } else {
+    err = cudaEventRecord(en->events[0], s0);
+  }
+  for (int i = 0; i < n && err == cudaSuccess && !en->batched; ++i) {
     hgks::Engine& e = en->members[i]->e;
     if (e.stream != s0) err = cudaStreamWaitEvent(e.stream, en->events[0], 0);
     if (err == cudaSuccess) err = enqueue_stage_pair(e, dt_fixed);
@@ -907,6 +1053,19 @@ static hgks_status capture_ensemble(hgks_ensemble* en, hgks_ensemble::Slot& sl, 
 hgks_status hgks_ensemble_step(hgks_ensemble* en, int nsteps, double dt, int sync) {
   if (!en || nsteps < 0) return HGKS_E_INVAL;
   const double dt_fixed = dt > 0.0 ? dt : 0.0;
+  const int nm = (int)en->members.size();
+  // The batch runs on the first member's stream: it waits for the work
+  // already enqueued on the other members' streams, and they wait for it.
+  if (nsteps > 0) {
+    for (int i = 1; i < nm; ++i) {
+      cudaError_t e = cudaEventRecord(en->events[i + 1], en->members[i]->e.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(en->stream, en->events[i + 1], 0);
+      if (e != cudaSuccess) {
+        en->err = std::string("ordering the member streams: ") + cudaGetErrorString(e);
+        return HGKS_E_CUDA;
+      }
+    }
+  }
   for (int n = 0; n < nsteps; ++n) {
     // The slot captured for the members' current buffer assignment, or a new capture.
     hgks_ensemble::Slot* sl = nullptr;
@@ -929,6 +1088,14 @@ hgks_status hgks_ensemble_step(hgks_ensemble* en, int nsteps, double dt, int syn
     for (hgks_ctx* c : en->members) {
       hgks::swap_state_buffers(c->e);
       ++c->steps_host;
+    }
+  }
+  if (nsteps > 0) {
+    cudaError_t e = cudaEventRecord(en->events[0], en->stream);
+    for (int i = 1; i < nm && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(en->members[i]->e.stream, en->events[0], 0);
+    if (e != cudaSuccess) {
+      en->err = std::string("ordering the member streams: ") + cudaGetErrorString(e);
+      return HGKS_E_CUDA;
     }
   }
   if (!sync) return HGKS_OK;

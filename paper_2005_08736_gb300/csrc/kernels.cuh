@@ -53,10 +53,16 @@ __host__ __device__ __forceinline__ FaceBox face_box(const GridDev& g, int d, in
 
 // ------------------------------------------------------------- ghost cells ---
 
-// x ghosts (periodic) for interior y, z.
+// The ghost fills and the CFL reduction are bodies over explicit block
+// coordinates (device functions) with thin __global__ wrappers; the update,
+// the transposed copy and the sweep keep their bodies in the kernels, as
+// included texts (update_body.inc, transpose_body.inc, sweep_body.inc).  The
+// ensemble's batched launches (batch.cuh) run the same bodies for many
+// instances in one grid.
+
+// x ghosts (periodic) for interior y, z; tid indexes the ghost cells.
 template <class T>
-__global__ void k_ghost_x(T* __restrict__ q, GridDev g) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ghost_x_cells(T* __restrict__ q, const GridDev& g, long long tid) {
   const long long total = 6LL * g.n[1] * g.n[2];
   if (tid >= total) return;
   const int m = int(tid % 6);
@@ -68,13 +74,17 @@ __global__ void k_ghost_x(T* __restrict__ q, GridDev g) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
 }
+template <class T>
+__global__ void k_ghost_x(T* __restrict__ q, GridDev g) {
+  ghost_x_cells(q, g, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
 
 // y ghosts for all x (ghosts included) and interior z: periodic, or the
 // isothermal no-slip wall (Sec. 3.3): the ghost mirrors interior cell m with
 // velocity negated, equal pressure and T_g = 2 T_w - T_m (floored at T_w/2).
 template <class T>
-__global__ void k_ghost_y(T* __restrict__ q, GridDev g, int wall, Gas<T> gas, T T_wall) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ghost_y_cells(T* __restrict__ q, const GridDev& g, int wall,
+                                              const Gas<T>& gas, T T_wall, long long tid) {
   const long long total = 6LL * g.p[0] * g.n[2];
   if (tid >= total) return;
   const int x = int(tid % g.p[0]) - kGhost;
@@ -105,11 +115,14 @@ __global__ void k_ghost_y(T* __restrict__ q, GridDev g, int wall, Gas<T> gas, T 
   q[3 * g.P + dst] = -rg * st.W;
   q[4 * g.P + dst] = st.dp / gas.gm1 + ke;
 }
+template <class T>
+__global__ void k_ghost_y(T* __restrict__ q, GridDev g, int wall, Gas<T> gas, T T_wall) {
+  ghost_y_cells(q, g, wall, gas, T_wall, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
 
 // z ghosts (periodic) for all x, y including ghosts.
 template <class T>
-__global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ghost_z_cells(T* __restrict__ q, const GridDev& g, long long tid) {
   const long long plane = (long long)g.p[0] * g.p[1];
   const long long total = 6LL * plane;
   if (tid >= total) return;
@@ -122,6 +135,10 @@ __global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) q[v * g.P + dst] = q[v * g.P + s];
 }
+template <class T>
+__global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
+  ghost_z_cells(q, g, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
 
 // Copy of the padded state with x slowest, qx[v][x][z][y] = q[v][z][y][x]
 // (padded coordinates, ghosts included), so that the x sweep reads its cells
@@ -132,27 +149,13 @@ __global__ void k_ghost_z(T* __restrict__ q, GridDev g) {
 template <class T>
 __global__ void __launch_bounds__(256) k_transpose_x(const T* __restrict__ q, T* __restrict__ qx,
                                                      GridDev g) {
-  __shared__ T tile[5][32][33];
-  const int p0 = g.p[0], p1 = g.p[1], p2 = g.p[2];
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
-  const T* src = q + (long long)z * p1 * p0;
-  T* dst = qx + (long long)z * p1;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int j = ty; j < 32; j += 8) {
-      const int x = x0 + tx, y = y0 + j;
-      if (x < p0 && y < p1) tile[v][j][tx] = __ldg(src + v * g.P + (long long)y * p0 + x);
-    }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int j = ty; j < 32; j += 8) {
-      const int x = x0 + j, y = y0 + tx;
-      if (x < p0 && y < p1) dst[v * g.P + (long long)x * p2 * p1 + y] = tile[v][tx][j];
-    }
+#define HGKS_TR_BX blockIdx.x
+#define HGKS_TR_BY blockIdx.y
+#define HGKS_TR_BZ blockIdx.z
+#include "transpose_body.inc"
+#undef HGKS_TR_BX
+#undef HGKS_TR_BY
+#undef HGKS_TR_BZ
 }
 
 // Global conservative-variable index of local-frame component i for sweep
@@ -198,80 +201,14 @@ struct UpdateArgs {
 constexpr int kUpdTX = 32, kUpdTY = 8;
 template <class T, int STAGE>
 __global__ void __launch_bounds__(kUpdTX * kUpdTY, sizeof(T) == 4 ? 8 : 1) k_update(UpdateArgs<T> a) {
-  constexpr int NV = STAGE == 1 ? 10 : 5;  // stage 2 needs dF only
-  constexpr int V0 = STAGE == 1 ? 0 : 5;
-  __shared__ T sfx[NV][kUpdTX + 1][kUpdTY];
-  if (a.flag && *a.flag) return;  // block-uniform: before any barrier
-  const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-  const int x0 = blockIdx.x * kUpdTX, y0 = blockIdx.y * kUpdTY, z = blockIdx.z;
-  const int tid = threadIdx.x;
-  const long long SX = (long long)(nx + 1) * ny * nz, SY = (long long)nx * (ny + 1) * nz,
-                  SZ = (long long)nx * ny * (nz + 1);
-  for (int i = tid; i < (kUpdTX + 1) * kUpdTY; i += kUpdTX * kUpdTY) {
-    const int xi = i / kUpdTY, yi = i % kUpdTY;
-    const int x = x0 + xi, y = y0 + yi;
-    const bool ok = x <= nx && y < ny;
-    const long long fi = ((long long)z * (nx + 1) + x) * ny + y;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sfx[v][xi][yi] = ok ? a.fx[(V0 + v) * SX + fi] : T(0);
-  }
-  __syncthreads();
-  const int tx = tid % kUpdTX, ty = tid / kUpdTX;
-  const int x = x0 + tx, y = y0 + ty;
-  if (x >= nx || y >= ny) return;
-  const long long cell = ((long long)z * ny + y) * nx + x;
-  const long long iy = ((long long)z * (ny + 1) + y) * nx + x;
-  const long long iz = ((long long)z * ny + y) * nx + x;
-  const long long sy = nx, sz = (long long)nx * ny;
-  const T ix_w = T(1) / a.wx[x + kGhost], iy_w = T(1) / a.wy[y + kGhost], iz_w = T(1) / a.wz[z + kGhost];
-  const T dt = T(a.scal[0]);
-  const long long pi = pad_index(a.g, x, y, z);
-  T dL[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const int o = 5 + v;
-    dL[v] = -((sfx[o - V0][tx + 1][ty] - sfx[o - V0][tx][ty]) * ix_w +
-              (a.fy[o * SY + iy + sy] - a.fy[o * SY + iy]) * iy_w +
-              (a.fz[o * SZ + iz + sz] - a.fz[o * SZ + iz]) * iz_w);
-  }
-  if (STAGE == 1) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const T L = -((sfx[v][tx + 1][ty] - sfx[v][tx][ty]) * ix_w +
-                    (a.fy[v * SY + iy + sy] - a.fy[v * SY + iy]) * iy_w +
-                    (a.fz[v * SZ + iz + sz] - a.fz[v * SZ + iz]) * iz_w);
-      const T qn = a.q[v * a.g.P + pi];
-      a.qs[v * a.g.P + pi] = qn + T(0.5) * dt * L + T(0.125) * dt * dt * dL[v];
-      a.inc[v * a.g.N + cell] = dt * L + dt * dt / T(6) * dL[v];
-    }
-  } else {
-    T qn[5], dq[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      qn[v] = a.q[v * a.g.P + pi];
-      dq[v] = a.inc[v * a.g.N + cell] + dt * dt / T(3) * dL[v];
-    }
-    if (a.force_x != T(0)) {
-      // Sec. 3.3: (rho U) += dt/2 (rho^{n+1} + rho^n) f_x, then
-      // (rho E) += dt/2 ((rho U)^{n+1} + (rho U)^n) f_x; the reference is at rest.
-      const T rho_n = a.rho_r + qn[0];
-      dq[1] += T(0.5) * dt * (T(2) * rho_n + dq[0]) * a.force_x;
-      dq[4] += T(0.5) * dt * (T(2) * qn[1] + dq[1]) * a.force_x;
-    }
-    if (a.comp) {
-      // Compensated (Kahan) accumulation of Q^{n+1} = Q^n + dq.
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T yv = dq[v] - a.comp[v * a.g.N + cell];
-        const T t = qn[v] + yv;
-        a.comp_out[v * a.g.N + cell] = (t - qn[v]) - yv;
-        a.qs[v * a.g.P + pi] = t;
-      }
-    } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) a.qs[v * a.g.P + pi] = qn[v] + dq[v];
-    }
-  }
+  __shared__ T sfx[STAGE == 1 ? 10 : 5][kUpdTX + 1][kUpdTY];
+#define HGKS_UPD_BX blockIdx.x
+#define HGKS_UPD_BY blockIdx.y
+#define HGKS_UPD_BZ blockIdx.z
+#include "update_body.inc"
+#undef HGKS_UPD_BX
+#undef HGKS_UPD_BY
+#undef HGKS_UPD_BZ
 }
 
 // -------------------------------------------------------------- reductions ---
@@ -292,11 +229,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 // arithmetic runs in T; the minimum is combined in FP64: positive doubles
 // order like their bit patterns, so block minima meet in a 64-bit atomicMin.
 template <class T>
-__global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
-                                             const T* __restrict__ wx, const T* __restrict__ wy,
-                                             const T* __restrict__ wz, double rho_r, double p_r,
-                                             double gamma, unsigned long long* __restrict__ dtmin,
-                                             int* __restrict__ flag) {
+__device__ __forceinline__ void cfl_block(const T* __restrict__ q, const GridDev& g,
+                                          const T* __restrict__ wx, const T* __restrict__ wy,
+                                          const T* __restrict__ wz, double rho_r, double p_r,
+                                          double gamma, unsigned long long* __restrict__ dtmin,
+                                          int* __restrict__ flag, int block, int nblocks) {
   T best = T(1e30);
   int bad = 0;
   const int nx = g.n[0], ny = g.n[1];
@@ -316,7 +253,7 @@ __global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
     b = fmin(b, wz[z + kGhost] / (tabs(mz * inv) + cs));
     if (ok) best = fmin(best, b);
   };
-  for (int row0 = 4 * blockIdx.x; row0 < rows; row0 += 4 * gridDim.x) {
+  for (int row0 = 4 * block; row0 < rows; row0 += 4 * nblocks) {
     for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
       const int x = x0 + threadIdx.x;
       T v[4][5];
@@ -353,6 +290,14 @@ __global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
       if (sbad) atomicOr(flag, 1);
     }
   }
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_cfl(const T* __restrict__ q, GridDev g,
+                                             const T* __restrict__ wx, const T* __restrict__ wy,
+                                             const T* __restrict__ wz, double rho_r, double p_r,
+                                             double gamma, unsigned long long* __restrict__ dtmin,
+                                             int* __restrict__ flag) {
+  cfl_block(q, g, wx, wy, wz, rho_r, p_r, gamma, dtmin, flag, blockIdx.x, gridDim.x);
 }
 
 // Scalars: [0] dt, [1] t, [2] steps taken.  dt_fixed > 0 overrides the CFL step.

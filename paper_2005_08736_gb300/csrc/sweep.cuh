@@ -477,424 +477,13 @@ __host__ __device__ constexpr int sweep_min_blocks() {
 template <class T, int MODE, int FLUX, int STAGE, int TP, int TS, int NL, bool PK = false>
 __global__ void __launch_bounds__(sweep_threads(TP, TS), (PK ? 2 : sweep_min_blocks<T, MODE, FLUX, TP, TS>()))
     k_sweep(SweepArgs<T> a) {
-  constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
-  constexpr int NV = SweepLayout<FLUX>::NV;
-  constexpr int NFF = SweepLayout<FLUX, MODE>::NFF;
-  constexpr int NFACE = TP * TS;
-  constexpr int NT = sweep_threads(TP, TS);  // threads of the CTA
-  constexpr int TPF = NT / NFACE;  // threads per face in phase 3
-  constexpr int GPF = 4 / TPF;      // Gauss points per thread
-  static_assert(TPF * NFACE == NT && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ffb = reinterpret_cast<T*>(smem_raw);  // [NL][NFF][NH]
-  T* tb = ffb + NL * NFF * NH;              // [NT1][NH]
-  T* part = tb + SweepLayout<FLUX>::NT1 * NH;  // [TPF-1][10][NFACE]
-  T* scr = part + (TPF - 1) * 10 * NFACE;      // [60][256] (full flux, TPF = 2)
-
-  const int d = a.d;
-  const SweepAxes ax = sweep_axes(d, a.g, a.xt != 0);
-  const int P = ax.P, S = ax.S;
-  const bool t1P = ax.t1P;
-  const int nP = a.g.n[P], nS = a.g.n[S], nd = a.g.n[d];
-  const int p0 = blockIdx.x * TP, s0 = blockIdx.y * TS;
-  const int f0 = blockIdx.z * a.chunk;
-  const int f1 = min(f0 + a.chunk, nd + 1);
-  const int tid = threadIdx.x;
-
-  // Phase-3 role: one face and GPF Gauss points of it.
-  const int face = tid % NFACE, sub = tid / NFACE;
-  const int ip = face % TP, is = face / TP;
-  const bool f_valid = (p0 + ip < nP) && (s0 + is < nS);
-  const int cP = min(p0 + ip, nP - 1), cS = min(s0 + is, nS - 1);
-  const int ct1 = t1P ? cP : cS, ct2 = t1P ? cS : cP;
-  const T rh1 = T(1) / a.wt1[ct1 + kGhost], rh2 = T(1) / a.wt2[ct2 + kGhost];
-  const int at3 = (is + 2) * HP + (ip + 2);
-  const int st2 = t1P ? HP : 1;
-  const T dt = T(a.scal[0]);
-  const long long FS = (long long)(a.g.n[0] + (d == 0)) * (a.g.n[1] + (d == 1)) * (a.g.n[2] + (d == 2));
-  // Face-flux layout: x fastest for the y and z faces; y fastest ([z][x][y])
-  // for the x faces, so that the tile's threads (running along y) store
-  // contiguously; the update kernel reads them through a shared-memory transpose.
-  long long fout, fstep;
-  if (d == 0) {
-    fout = (long long)cS * (a.g.n[0] + 1) * a.g.n[1] + cP;
-    fstep = a.g.n[1];
-  } else {
-    int c[3];
-    c[d] = 0;
-    c[P] = cP;
-    c[S] = cS;
-    fout = ((long long)c[2] * (a.g.n[1] + (d == 1)) + c[1]) * (a.g.n[0] + (d == 0)) + c[0];
-    fstep = d == 1 ? (long long)a.g.n[0] : (long long)a.g.n[0] * a.g.n[1];
-  }
-
-  for (int fb = f0; fb < f1; fb += NL) {
-    // ---------------- phase 1: face fields of layers fb .. fb+NL-1 ----------------
-    // Items (layer, transverse point of the tile plus a halo of 2).  For d = x
-    // consecutive threads take consecutive layers, so that the loads along x
-    // are coalesced; otherwise consecutive transverse points along P (= x).
-    if (NL == 2 && !is_char_mode<MODE>() && d == 0 && !ax.xt && (a.g.p[0] & 1) == 0) {
-      // x sweep: one item per transverse point for both layers (pair loads
-      // along x; fb is even because chunks and NL are).  Tiles with more
-      // layers per pass keep the per-layer items below (register budget).
-      const int nl = min(NL, f1 - fb);
-      for (int h = tid; h < NH; h += NT) {
-        const int hp = h % HP, hs = h / HP;
-        const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
-        if (Pc <= nP + 1 && Sc <= nS + 1) {
-          face_fields_x_item<T, MODE, FLUX, NH, NL, NFF>(a.q, a.g, ax, a.wn, a.gas, fb, nl, Pc, Sc, h, ffb);
-        } else {
-#pragma unroll 1
-          for (int l = 0; l < NL; ++l)
-#pragma unroll 1
-            for (int k = 0; k < NFF; ++k) ffb[(l * NFF + k) * NH + h] = T(0);
-        }
-#pragma unroll 1
-        for (int l = nl; l < NL; ++l)
-#pragma unroll 1
-          for (int k = 0; k < NFF; ++k) ffb[(l * NFF + k) * NH + h] = T(0);
-      }
-    } else if (PK && !(d == 0 && !ax.xt)) {
-      if constexpr (PK) {
-        // Packed variant: one item per pair of adjacent points along P (the
-        // state is contiguous along P, so both points' cells are neighbours);
-        // pairs that reach past the grid's halo take the per-point path.
-        static_assert(HP % 2 == 0, "point pairs must not straddle a row");
-        constexpr int NH2 = NH / 2;
-        for (int it = tid; it < NL * NH2; it += NT) {
-          const int l = it / NH2, h = 2 * (it % NH2);
-          const int f = fb + l;
-          const int hp = h % HP, hs = h / HP;
-          const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
-          T* ff = ffb + l * NFF * NH;
-          const bool ok0 = f < f1 && Pc <= nP + 1 && Sc <= nS + 1;
-          const bool ok1 = ok0 && Pc + 1 <= nP + 1;
-          if (ok1) {
-            // Cell f-3 along d at (Pc, Sc): P = y, S = z for d = x; P = x otherwise.
-            const int cx = d == 0 ? f - 3 : Pc;
-            const int cy = d == 0 ? Pc : (d == 1 ? f - 3 : Sc);
-            const int cz = d == 2 ? f - 3 : Sc;
-            const long long cb = ax.index(a.g, cx, cy, cz);
-            float2 qk[5][6];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              const T* qv = a.q + ax.gv[i] * a.g.P + cb;
-#pragma unroll
-              for (int k = 0; k < 6; ++k) qk[i][k] = make_float2(__ldg(qv + k * ax.sd), __ldg(qv + k * ax.sd + 1));
-            }
-            float2 Q0[5], D0[5];
-            face_fields_smooth_linear_x2(qk, a.wn[f - 1 + kGhost], a.wn[f + kGhost], a.gas, Q0, D0);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              *reinterpret_cast<float2*>(ff + i * NH + h) = Q0[i];
-              *reinterpret_cast<float2*>(ff + (5 + i) * NH + h) = D0[i];
-            }
-          } else {
-#pragma unroll 1
-            for (int e2 = 0; e2 < 2; ++e2) {
-              const bool ok = e2 == 0 ? ok0 : (f < f1 && Pc + 1 <= nP + 1 && Sc <= nS + 1);
-              if (ok) {
-                face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc + e2, Sc, h + e2, ff);
-              } else {
-#pragma unroll 1
-                for (int k = 0; k < NFF; ++k) ff[k * NH + h + e2] = T(0);
-              }
-            }
-          }
-        }
-      }
-    } else
-    for (int it = tid; it < NL * NH; it += NT) {
-      // Consecutive threads: consecutive layers for the x sweep reading q
-      // (cells along x are contiguous), else consecutive points along P.
-      const bool by_layer = d == 0 && !ax.xt;
-      const int l = by_layer ? it % NL : it / NH;
-      const int h = by_layer ? it / NL : it % NH;
-      const int f = fb + l;
-      const int hp = h % HP, hs = h / HP;
-      const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
-      T* ff = ffb + l * NFF * NH;
-      if (f < f1 && Pc <= nP + 1 && Sc <= nS + 1) {
-        face_fields_item<T, MODE, FLUX, NH>(a.q, a.g, ax, a.wn, a.gas, f, Pc, Sc, h, ff);
-      } else {
-#pragma unroll 1
-        for (int k = 0; k < NFF; ++k) ff[k * NH + h] = T(0);
-      }
-    }
-    __syncthreads();
-
-#pragma unroll 1
-  for (int l = 0; l < NL && fb + l < f1; ++l) {
-    const int f = fb + l;
-    const T* ff = ffb + l * NFF * NH;
-    // ---------------- phase 2: tangential pass along t1 ----------------
-    // Points of the tile with a halo of 2 along t2.  Conservative variables:
-    // the (group of five fields, point) pairs are spread evenly over the CTA;
-    // characteristic variables: one point (all fields) per item.
-    if constexpr (is_char_mode<MODE>()) {
-      const int items = t1P ? TP * HS : HP * TS;
-      const int st1 = t1P ? 1 : HP;
-      for (int it = tid; it < items; it += NT) {
-        const int hp2 = t1P ? 2 + it % TP : it % HP;
-        const int hs2 = t1P ? it / TP : 2 + it / HP;
-        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1, a.gas);
-      }
-    } else if (t1P) {
-      constexpr int ITEMS = TP * HS;
-#pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
-        const int grp = it / ITEMS, pt = it % ITEMS;
-        if constexpr (PK) t1_pass_group_x2<MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
-        else t1_pass_group<T, MODE, NV, NH>(ff, tb, (pt / TP) * HP + 2 + pt % TP, 1, grp);
-      }
-    } else {
-      constexpr int ITEMS = HP * TS;
-#pragma unroll 1
-      for (int it = tid; it < ITEMS * 2 * NV / 5; it += NT) {
-        const int grp = it / ITEMS, pt = it % ITEMS;
-        if constexpr (PK) t1_pass_group_x2<MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
-        else t1_pass_group<T, MODE, NV, NH>(ff, tb, (2 + pt / HP) * HP + pt % HP, HP, grp);
-      }
-    }
-    __syncthreads();
-
-    // ---------------- phase 3: tangential pass along t2 and flux ----------------
-    // Characteristic modes: the basis of Qm at this thread's face.
-    CharBasis<T> cbs{};
-    if constexpr (is_char_mode<MODE>()) {
-      T qm[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) qm[i] = ff[(SweepLayout<FLUX, MODE>::QM + i) * NH + at3];
-      cbs = char_basis(qm, a.gas);
-    }
-    T Fs[10];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) Fs[i] = T(0);
-    if constexpr (PK) {
-      // Both t1 abscissae at once, as the halves of packed pairs: one pass
-      // along t2 per field gives both t2 abscissae; the flux at (., m2) is
-      // evaluated for the two t1 abscissae together.
-      static_assert(std::is_same<T, float>::value && MODE == RECON_LINEAR && FLUX == FLUX_SMOOTH &&
-                        TPF == 1, "packed phase 3: FP32, linear weights, smooth flux, one thread per face");
-      const float2* tb2 = reinterpret_cast<const float2*>(tb);
-      PointStateX2 st[2];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        const float2* sv = tb2 + (2 * i) * NH + at3;
-        const float2* sdv = tb2 + (2 * i + 1) * NH + at3;
-        const float2* ss = tb2 + (2 * NV + i) * NH + at3;
-        float2 v[2], dd[2], vd[2], vs[2];
-        tangential_linear_x2(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-        tangential_linear_val_x2(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
-        tangential_linear_val_x2(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
-#pragma unroll
-        for (int m2 = 0; m2 < 2; ++m2) {
-          st[m2].q[i] = v[m2];
-          st[m2].dq[0][i] = vs[m2];
-          st[m2].dq[1][i] = mul2(vd[m2], bc2(rh1));
-          st[m2].dq[2][i] = mul2(dd[m2], bc2(rh2));
-        }
-      }
-      flux_smooth_x2<STAGE == 1>(st[0], a.gas, Fs);
-      flux_smooth_x2<STAGE == 1>(st[1], a.gas, Fs);
-    } else if constexpr (FLUX == FLUX_SMOOTH && TPF <= 2) {
-      // One pass along t2 gives both t2 abscissae: each thread takes one (or
-      // both) t1 abscissae m1 and evaluates the flux at (m1, 0) and (m1, 1).
-#pragma unroll 1
-      for (int m1 = (TPF == 2 ? sub : 0); m1 < (TPF == 2 ? sub + 1 : 2); ++m1) {
-        PointState<T> st[2];
-        if constexpr (is_char_mode<MODE>()) {
-          T val[2][5], d2[2][5], d1[2][5], dn[2][5];
-          t2_group<T, MODE, NV, NH>(tb, 0, m1, at3, st2, cbs, val, d2, d1, dn);
-#pragma unroll
-          for (int m2 = 0; m2 < 2; ++m2)
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              st[m2].q[i] = val[m2][i];
-              st[m2].dq[0][i] = dn[m2][i];
-              st[m2].dq[1][i] = d1[m2][i] * rh1;
-              st[m2].dq[2][i] = d2[m2][i] * rh2;
-            }
-        } else {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          const T* sv = tb + (4 * i + m1) * NH + at3;
-          const T* sdv = tb + (4 * i + 2 + m1) * NH + at3;
-          const T* ss = tb + (4 * NV + 2 * i + m1) * NH + at3;
-          T v[2], dd[2], vd[2], vs[2];
-          tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-          tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
-          tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
-#pragma unroll
-          for (int m2 = 0; m2 < 2; ++m2) {
-            st[m2].q[i] = v[m2];
-            st[m2].dq[0][i] = vs[m2];
-            st[m2].dq[1][i] = vd[m2] * rh1;
-            st[m2].dq[2][i] = dd[m2] * rh2;
-          }
-        }
-        }
-#pragma unroll
-        for (int m2 = 0; m2 < 2; ++m2) {
-          T F[5], dF[5];
-          flux_smooth(st[m2], a.gas, STAGE == 1, F, dF);
-#pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            if (STAGE == 1) Fs[i] += F[i];
-            Fs[5 + i] += dF[i];
-          }
-        }
-      }
-    } else if constexpr (FLUX == FLUX_FULL && TPF == 2) {
-      // Full flux, two threads per face: thread `sub` takes the t1 abscissa
-      // m1 = sub; one pass along t2 per field gives both t2 abscissae.  The
-      // point states of m2 = 1 wait in the thread's shared-memory slots
-      // (index ((s*4 + c)*5 + i)*256 + tid, c = 0 value, 1..3 derivatives
-      // along n, t1, t2) while the flux at m2 = 0 is evaluated.
-      static_assert(NT == 256, "the shared-memory slots are laid out for 256 threads");
-      const int m1 = sub;
-      PointState<T> st[3];
-      // One state group per iteration (the loop body once in the code): the
-      // group's m2 = 0 states go to st[s] through constant indices.
-#pragma unroll 1
-      for (int s = 0; s < 3; ++s) {
-        PointState<T> g0;
-        if constexpr (is_char_mode<MODE>()) {
-          T val[2][5], d2[2][5], d1[2][5], dn[2][5];
-          t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
-#pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            g0.q[i] = val[0][i];
-            g0.dq[0][i] = dn[0][i];
-            g0.dq[1][i] = d1[0][i] * rh1;
-            g0.dq[2][i] = d2[0][i] * rh2;
-            scr[((s * 4 + 0) * 5 + i) * 256 + tid] = val[1][i];
-            scr[((s * 4 + 1) * 5 + i) * 256 + tid] = dn[1][i];
-            scr[((s * 4 + 2) * 5 + i) * 256 + tid] = d1[1][i] * rh1;
-            scr[((s * 4 + 3) * 5 + i) * 256 + tid] = d2[1][i] * rh2;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            const int k = 5 * s + i;
-            const T* sv = tb + (4 * k + m1) * NH + at3;
-            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-            T v[2], dd[2], vd[2], vs[2];
-            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], vd);
-            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], vs);
-            g0.q[i] = v[0];
-            g0.dq[0][i] = vs[0];
-            g0.dq[1][i] = vd[0] * rh1;
-            g0.dq[2][i] = dd[0] * rh2;
-            scr[((s * 4 + 0) * 5 + i) * 256 + tid] = v[1];
-            scr[((s * 4 + 1) * 5 + i) * 256 + tid] = vs[1];
-            scr[((s * 4 + 2) * 5 + i) * 256 + tid] = vd[1] * rh1;
-            scr[((s * 4 + 3) * 5 + i) * 256 + tid] = dd[1] * rh2;
-          }
-        }
-        if (s == 0) st[0] = g0;
-        else if (s == 1) st[1] = g0;
-        else st[2] = g0;
-      }
-#pragma unroll 1
-      for (int m2 = 0; m2 < 2; ++m2) {
-        if (m2 == 1) {
-#pragma unroll
-          for (int s = 0; s < 3; ++s)
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              st[s].q[i] = scr[((s * 4 + 0) * 5 + i) * 256 + tid];
-              st[s].dq[0][i] = scr[((s * 4 + 1) * 5 + i) * 256 + tid];
-              st[s].dq[1][i] = scr[((s * 4 + 2) * 5 + i) * 256 + tid];
-              st[s].dq[2][i] = scr[((s * 4 + 3) * 5 + i) * 256 + tid];
-            }
-        }
-        T F[5], dF[5];
-        flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          if (STAGE == 1) Fs[i] += F[i];
-          Fs[5 + i] += dF[i];
-        }
-      }
-    } else {
-#pragma unroll 1
-      for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
-        const int m1 = g & 1, m2 = g >> 1;
-        constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
-        PointState<T> st[NS];
-        // One state group per iteration (the body once in the code); the
-        // group's states go to st[s] through constant indices.
-#pragma unroll 1
-        for (int s = 0; s < NS; ++s) {
-          PointState<T> g0;
-          if constexpr (is_char_mode<MODE>()) {
-            T val[2][5], d2[2][5], d1[2][5], dn[2][5];
-            t2_group<T, MODE, NV, NH>(tb, s, m1, at3, st2, cbs, val, d2, d1, dn);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              g0.q[i] = val[m2][i];
-              g0.dq[0][i] = dn[m2][i];
-              g0.dq[1][i] = d1[m2][i] * rh1;
-              g0.dq[2][i] = d2[m2][i] * rh2;
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              const int k = 5 * s + i;
-              const T* sv = tb + (4 * k + m1) * NH + at3;
-              const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-              const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-              T v[2], dd[2];
-              tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-              g0.q[i] = v[m2];
-              g0.dq[2][i] = dd[m2] * rh2;
-              tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
-              g0.dq[1][i] = v[m2] * rh1;
-              tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
-              g0.dq[0][i] = v[m2];
-            }
-          }
-          if (s == 0) st[0] = g0;
-          else if (NS > 1 && s == 1) st[NS > 1 ? 1 : 0] = g0;
-          else if (NS > 2) st[NS > 2 ? 2 : 0] = g0;
-        }
-        T F[5], dF[5];
-        if constexpr (FLUX == FLUX_SMOOTH) {
-          flux_smooth(st[0], a.gas, STAGE == 1, F, dF);
-        } else {
-          flux_full(st[0], st[1], st[2], a.gas, dt, F, dF);
-        }
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          if (STAGE == 1) Fs[i] += F[i];
-          Fs[5 + i] += dF[i];
-        }
-      }
-    }
-    if (TPF > 1 && sub > 0) {
-#pragma unroll
-      for (int i = 0; i < 10; ++i) part[((sub - 1) * 10 + i) * NFACE + face] = Fs[i];
-    }
-    if (TPF > 1) __syncthreads();
-    if (sub == 0 && f_valid) {
-#pragma unroll
-      for (int r = 1; r < TPF; ++r)
-#pragma unroll
-        for (int i = 0; i < 10; ++i) Fs[i] += part[((r - 1) * 10 + i) * NFACE + face];
-      const long long o = fout + (long long)f * fstep;
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        // The second stage needs dF only (Eq. (6)); its F planes are not written.
-        if (STAGE == 1) a.fd[ax.gv[i] * FS + o] = T(0.25) * Fs[i];
-        a.fd[(5 + ax.gv[i]) * FS + o] = T(0.25) * Fs[5 + i];
-      }
-    }
-    __syncthreads();
-  }
-  }
+#define HGKS_SW_BX blockIdx.x
+#define HGKS_SW_BY blockIdx.y
+#define HGKS_SW_BZ blockIdx.z
+#include "sweep_body.inc"
+#undef HGKS_SW_BX
+#undef HGKS_SW_BY
+#undef HGKS_SW_BZ
 }
 
 }  // namespace hgks

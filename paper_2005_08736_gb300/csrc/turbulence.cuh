@@ -3,10 +3,12 @@
 // contributions eps1..eps3, rho_rms, K, the skewness / flatness moments of
 // the velocity slopes, the solenoidal and dilatational dissipation rates and
 // the pressure dilatation.  Velocity gradients use the sixth-order central
-// difference (Sec. 3.1) on the ghost-filled padded state (periodic, uniform
-// grids).  Every sum is FP64; the per-cell arithmetic is FP64 whatever the
-// storage type.  Output: kTurbSums raw volume-weighted sums, composed into
-// the ABI's statistics on the host.
+// difference (Sec. 3.1) on the periodic, uniform grid, the neighbours taken
+// by periodic wrap of the interior indices (no ghost fill needed).  Every
+// sum is FP64; the per-cell arithmetic is FP64 whatever the storage type.
+// Output: kTurbSums raw volume-weighted sums, composed into the ABI's
+// statistics on the host -- on demand, or appended to the statistics
+// history by the step itself (gated on the step count).
 #pragma once
 
 #include "engine.h"
@@ -32,19 +34,32 @@ __device__ __forceinline__ void velocity_at(const T* __restrict__ q, long long P
   u[2] = double(q[3 * P + i]) * inv;
 }
 
+// Gate of the history record: with every > 0 the kernels run only when the
+// step count scal[2] is a multiple of every and the non-physical flag is
+// clear; every = 0 always runs.
+struct HistGate {
+  const double* scal;
+  const int* flag;
+  int every;
+  __device__ __forceinline__ bool skip() const {
+    return every > 0 && ((flag && *flag) || ((long long)scal[2]) % every != 0);
+  }
+};
+
 template <class T>
 __global__ void __launch_bounds__(256) k_turb(const T* __restrict__ q, GridDev g, TurbArgs a,
-                                              double* __restrict__ part) {
+                                              double* __restrict__ part, HistGate gate) {
+  if (gate.skip()) return;
   double s[kTurbSums];
 #pragma unroll
   for (int k = 0; k < kTurbSums; ++k) s[k] = 0.0;
   const int nx = g.n[0], ny = g.n[1];
-  const long long stride[3] = {1, g.p[0], (long long)g.p[0] * g.p[1]};
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
        c += (long long)gridDim.x * blockDim.x) {
     const int x = int(c % nx);
     const long long r = c / nx;
     const int y = int(r % ny), z = int(r / ny);
+    const int cc[3] = {x, y, z};
     const long long pi = pad_index(g, x, y, z);
     const double drho = double(q[pi]);
     const double rho = a.rho_r + drho;
@@ -61,9 +76,12 @@ __global__ void __launch_bounds__(256) k_turb(const T* __restrict__ q, GridDev g
 #pragma unroll
       for (int k = 1; k <= 3; ++k) {
         const double ck = k == 1 ? 45.0 : (k == 2 ? -9.0 : 1.0);
+        int cp[3] = {cc[0], cc[1], cc[2]}, cm[3] = {cc[0], cc[1], cc[2]};
+        cp[j] = cc[j] + k < g.n[j] ? cc[j] + k : cc[j] + k - g.n[j];  // periodic wrap
+        cm[j] = cc[j] - k >= 0 ? cc[j] - k : cc[j] - k + g.n[j];
         double up[3], um[3];
-        velocity_at(q, g.P, pi + k * stride[j], a.rho_r, up);
-        velocity_at(q, g.P, pi - k * stride[j], a.rho_r, um);
+        velocity_at(q, g.P, pad_index(g, cp[0], cp[1], cp[2]), a.rho_r, up);
+        velocity_at(q, g.P, pad_index(g, cm[0], cm[1], cm[2]), a.rho_r, um);
 #pragma unroll
         for (int i = 0; i < 3; ++i) acc[i] += ck * (up[i] - um[i]);
       }
@@ -125,10 +143,27 @@ __global__ void __launch_bounds__(256) k_turb(const T* __restrict__ q, GridDev g
   }
 }
 
+// Where the final sums go: out (on demand), or the next record of the
+// history (hist != null): [t, step, sums], then the count is advanced;
+// records beyond cap are dropped.
+struct TurbSink {
+  double* out;
+  double* hist;
+  int* count;
+  int cap;
+};
+
 // Deterministic final sum of the per-block partials (one block of 256).
 static __global__ void __launch_bounds__(256) k_turb_final(const double* __restrict__ part, int nblocks,
-                                                           double* __restrict__ out) {
+                                                           TurbSink sink, HistGate gate) {
   __shared__ double sm[kTurbSums][8];
+  if (gate.skip()) return;
+  double* out = sink.out;
+  if (sink.hist) {
+    const int idx = *sink.count;  // one block: read before any thread advances it
+    if (idx >= sink.cap) return;
+    out = sink.hist + (long long)idx * kHistStride + 2;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < kTurbSums; ++k) {
     double t = 0.0;
@@ -143,6 +178,12 @@ static __global__ void __launch_bounds__(256) k_turb_final(const double* __restr
       double t = lane < nw ? sm[k][lane] : 0.0;
       t = warp_sum(t);
       if (lane == 0) out[k] = t;
+    }
+    if (sink.hist && lane == 0) {
+      out[-2] = gate.scal[1];
+      out[-1] = gate.scal[2];
+      __threadfence();
+      *sink.count = *sink.count + 1;
     }
   }
 }

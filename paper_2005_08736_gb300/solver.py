@@ -261,11 +261,26 @@ class Simulation:
         eps_d, <p theta> and the per-axis moments du{2,3,4}_{x,y,z}."""
         d = _lib.HgksTurbulence()
         self._call(self.lib.hgks_turbulence_stats(self.h, ctypes.byref(d)))
-        out = {k: getattr(d, k) for k, _ in d._fields_ if not k.startswith("du")}
-        for k in ("du2", "du3", "du4"):
-            for i, a in enumerate("xyz"):
-                out[f"{k}_{a}"] = getattr(d, k)[i]
-        return out
+        return _turb_dict(d)
+
+    def history_start(self, every: int, capacity: int = 4096) -> None:
+        """Record the statistics of the current state and, every `every`
+        steps, of the stepped state (on the device, inside the step)."""
+        self._call(self.lib.hgks_history_start(self.h, int(every), int(capacity)))
+
+    def history_stop(self) -> None:
+        self._call(self.lib.hgks_history_stop(self.h))
+
+    def history(self) -> list:
+        """The recorded statistics, oldest first: each a dict of the
+        turbulence statistics with step, eps_Ek = -dE_k/dt and
+        eps_num = eps_Ek - (eps1 + eps2 + eps3) (Sec. 3.1)."""
+        n = ctypes.c_int()
+        self._call(self.lib.hgks_history_read(self.h, None, 0, ctypes.byref(n)))
+        recs = (_lib.HgksHistoryRec * max(n.value, 1))()
+        self._call(self.lib.hgks_history_read(self.h, recs, n.value, ctypes.byref(n)))
+        return [dict(_turb_dict(r.s), step=r.step, eps_Ek=r.eps_Ek, eps_num=r.eps_num)
+                for r in recs[:n.value]]
 
     def channel_stats(self) -> dict:
         """Mean-flow statistics of the wall-bounded channel (Sec. 3.3,
@@ -303,6 +318,14 @@ class Simulation:
         return ek.value
 
 
+def _turb_dict(d) -> dict:
+    out = {k: getattr(d, k) for k, _ in d._fields_ if not k.startswith("du")}
+    for k in ("du2", "du3", "du4"):
+        for i, a in enumerate("xyz"):
+            out[f"{k}_{a}"] = getattr(d, k)[i]
+    return out
+
+
 def cell_widths(cfg: Config, axis: int) -> np.ndarray:
     """Cell widths along axis 0, 1, 2 of the grid cfg describes
     (hgks_cell_widths: uniform, or the tanh mapping of Sec. 3.3 in y)."""
@@ -316,15 +339,24 @@ def cell_widths(cfg: Config, axis: int) -> np.ndarray:
 
 
 class Ensemble:
-    """Independent simulations advanced by one CUDA graph launch per step."""
+    """Independent simulations advanced by one CUDA graph launch per step:
+    one batched kernel launch per phase for all members when they share a
+    scheme (the default then), else every member's launches as parallel graph
+    branches.  batched=False forces the branches; batched=True requires the
+    batched form."""
 
-    def __init__(self, sims: list):
+    def __init__(self, sims: list, batched: bool | None = None):
         self.lib = _lib.load()
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(sims))(*[s.h.value for s in sims])
         h = ctypes.c_void_p()
         _lib.check(self.lib.hgks_ensemble_create(arr, len(sims), ctypes.byref(h)))
         self.h = h
+        if batched is not None:
+            status = self.lib.hgks_ensemble_set_batched(self.h, int(bool(batched)))
+            if status != _lib.HGKS_OK:
+                msg = self.lib.hgks_ensemble_last_error(self.h)
+                raise _lib.HgksError(status, msg.decode() if msg else "")
 
     def step(self, nsteps: int = 1, dt: float = 0.0, sync: bool = True) -> None:
         status = self.lib.hgks_ensemble_step(self.h, int(nsteps), float(dt), int(sync))

@@ -106,3 +106,46 @@ def test_rejects_walls():
         sim.turbulence()
     sim.close()
     assert ei.value.status == HGKS_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_history_matches_the_oracle_run(prec):
+    """The device statistics history (hgks_history_start / _read) of a
+    Taylor-Green run with CFL steps (uneven times): every record against
+    the oracle's statistics of the oracle's state at the same step, and
+    eps(E_k), eps_num against the oracle's second-order differences
+    (Sec. 3.1).  FP32: the records at the FP32 state tolerance (the
+    differences of FP32 E_k samples are not compared)."""
+    import oracle
+    from oracle.turbulence import dissipation_history
+    n, every, steps = 24, 2, 10
+    cfg = taylor_green_config(n, prec)
+    cfg64 = taylor_green_config(n, "fp64")
+    prim = inputs.taylor_green(n)
+    sim = Simulation(cfg)
+    sim.init_primitive(prim)
+    sim.history_start(every, capacity=5)   # steps 0, 2, 4, 6, 8 fit; step 10 is dropped
+    sim.step(steps)
+    recs = sim.history()
+    sim.history_stop()
+    sim.step(2)
+    assert len(sim.history()) == 5         # no recording after the stop
+    sim.close()
+    o = oracle.Solver(oracle.Config(n, n, n, recon=0, flux=0, prandtl=cfg.prandtl, mu_ref=cfg.mu_ref,
+                                    cfl=cfg.cfl))
+    o.set_state(oracle.conservative(prim, 1.4))
+    times, stats = [], []
+    for k in range(0, 9, every):
+        if k:
+            o.step(every)
+        times.append(o.t)
+        stats.append(oracle_stats(cfg64, o.state()))
+    eps_ek, eps_num = dissipation_history(times, stats)
+    assert [r["step"] for r in recs] == [0, 2, 4, 6, 8]
+    tol = TOL if prec == "fp64" else 2e-5
+    for r, t, ref, e, en in zip(recs, times, stats, eps_ek, eps_num):
+        assert r["t"] == pytest.approx(t, rel=1e-13 if prec == "fp64" else 1e-6, abs=1e-300)
+        compare(r, ref, tol)
+        if prec == "fp64":
+            assert r["eps_Ek"] == pytest.approx(e, rel=1e-6)
+            assert abs(r["eps_num"] - en) <= 1e-6 * abs(e)

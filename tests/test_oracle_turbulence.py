@@ -171,3 +171,55 @@ def test_reference_density_divides_the_normalised_quantities():
         assert abs(a[k]) > 0 and b[k] == pytest.approx(a[k] / 2, rel=1e-14), k
     for k in ("K", "eps_s", "eps_d", "p_theta"):
         assert abs(a[k]) > 0 and b[k] == pytest.approx(a[k], rel=1e-14), k
+
+
+def test_eps_zeta_of_the_taylor_green_start():
+    # zeta = <rho |omega|^2 / 2> / rho0 = (3/8) g^2 for rho = rho0, so
+    # eps(zeta) = 2 mu zeta / rho0 = 2 mu (3/8) g^2 / rho0
+    n, mu, rho0 = 16, 1.0 / 1600.0, 1.3
+    cons = conservative(inputs.taylor_green(n, rho0=rho0), GAMMA)
+    s = statistics(cons, gamma=GAMMA, rho0=rho0, mu_ref=mu)
+    g = symbol(1, 2 * math.pi / n)
+    assert s["zeta"] == pytest.approx(0.375 * g * g, rel=1e-12)
+    assert s["eps_zeta"] == pytest.approx(2 * mu * 0.375 * g * g / rho0, rel=1e-12)
+
+
+def test_dissipation_rate_of_a_quadratic_history_is_exact():
+    # second-order differences are exact on a quadratic, on uneven times
+    from oracle.turbulence import dissipation_history
+    t = np.array([0.0, 0.1, 0.25, 0.3, 0.45, 0.7])
+    a, b, c = 0.125, -0.02, 0.003
+    stats = [{"Ek": a + b * x + c * x * x, "eps1": 0.01, "eps2": 0.002, "eps3": -0.001} for x in t]
+    eps_ek, eps_num = dissipation_history(t, stats)
+    assert np.allclose(eps_ek, -(b + 2 * c * t), rtol=0, atol=1e-14)
+    assert np.allclose(eps_num, eps_ek - 0.011, rtol=0, atol=1e-14)
+
+
+def test_decaying_shear_wave_has_no_numerical_dissipation():
+    """u = U0 sin(y) e^{-nu t}, v = w = 0, uniform rho and p: an exact solution
+    of the incompressible Navier-Stokes equations with E_k = U0^2/4 e^{-2 nu t}.
+    Sampled exactly at uneven times, eps(E_k) = 2 nu E_k up to the O(dt^2)
+    time differences, eps1 = 2 nu g^2 E_k and eps(zeta) = 2 nu g^2 E_k (g the
+    sixth-order difference symbol), eps2 = eps3 = 0; so the numerical
+    dissipation eps(E_k) - (eps1 + eps2 + eps3) = 2 nu E_k (1 - g^2) + O(dt^2)
+    is tiny against eps(E_k)."""
+    from oracle.turbulence import dissipation_history
+    n, U0, nu = 32, 0.7, 0.01
+    y = inputs.centres(n, 2 * math.pi)
+    times = np.array([0.0, 0.05, 0.09, 0.15, 0.2])
+    stats = []
+    for t in times:
+        prim = np.zeros((5, n, n, n))
+        prim[0], prim[4] = 1.0, 10.0
+        prim[1] = (U0 * math.exp(-nu * t) * np.sin(y))[None, :, None]
+        stats.append(statistics(conservative(prim, GAMMA), gamma=GAMMA, rho0=1.0, mu_ref=nu))
+    eps_ek, eps_num = dissipation_history(times, stats)
+    g2 = symbol(1, 2 * math.pi / n) ** 2
+    for t, s, e, en in zip(times, stats, eps_ek, eps_num):
+        ek = 0.25 * U0 * U0 * math.exp(-2 * nu * t)
+        assert s["Ek"] == pytest.approx(ek, rel=1e-13)
+        assert s["eps1"] == pytest.approx(2 * nu * g2 * ek, rel=1e-12)
+        assert s["eps_zeta"] == pytest.approx(2 * nu * g2 * ek, rel=1e-12)
+        assert abs(s["eps2"]) < 1e-20 and abs(s["eps3"]) < 1e-12
+        assert e == pytest.approx(2 * nu * ek, rel=1e-5)
+        assert abs(en) < 1e-5 * e
