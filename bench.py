@@ -326,12 +326,12 @@ def extra_workloads(steps: int, peak_tflops: float | None = None):
 
 def run_history(args):
     """Taylor-Green to t = 10 (Sec. 3.1) in FP32 and FP64 with the same fixed
-    dt: kinetic energy E_k every 10 steps, the dissipation rate
-    eps(E_k) = -dE_k/dt by second-order central differences, and the FP32
-    errors against the FP64 path (itself checked against the oracle).
-    --grid 128 by default; --t-end-fp64 stops the FP64 run earlier (the FP32
-    errors are then taken over the common interval, the density error at its
-    end)."""
+    dt: the library's statistics history (recorded on the device every 10
+    steps) -- E_k, eps(E_k) = -dE_k/dt by second-order differences, eps(zeta),
+    eps1..eps3 and the numerical dissipation eps_num -- and the FP32 errors
+    against the FP64 path (itself checked against the oracle).  --grid 128 by
+    default; --t-end-fp64 stops the FP64 run earlier (the FP32 errors are then
+    taken over the common interval, the density error at its end)."""
     import numpy as np
     from paper_2005_08736_gb300 import inputs
     from paper_2005_08736_gb300.solver import Simulation, taylor_green_config
@@ -341,36 +341,60 @@ def run_history(args):
     nsteps = int(round(t_end / dt))
     t64 = min(t_end, args.t_end_fp64) if args.t_end_fp64 else t_end
     nsteps64 = min(int(round(t64 / dt / every)) * every, nsteps // every * every)
+    keys = ("t", "Ek", "zeta", "eps1", "eps2", "eps3", "eps_zeta", "eps_Ek", "eps_num")
     hist, finals, times = {}, {}, {}
     for prec in ("fp64", "fp32"):
         sim = Simulation(taylor_green_config(n, prec))
         sim.init_primitive(prim)
-        ek = [sim.diagnostics()["Ek"]]
         total = nsteps64 if prec == "fp64" else nsteps
+        sim.history_start(every, capacity=total // every + 2)
         t0 = time.perf_counter()
-        for k in range(0, total, every):
-            sim.step(min(every, total - k), dt, sync=False)
-            ek.append(sim.diagnostics()["Ek"])
-            if min(k + every, total) == nsteps64:
+        done = 0
+        while done < total:
+            k = min(500, total - done)
+            if done < nsteps64 <= done + k:
+                k = nsteps64 - done
+            sim.step(k, dt, sync=False)
+            done += k
+            if done == nsteps64:
                 finals[prec] = sim.state()
+        sim.step(0, dt)  # synchronise and check
         times[prec] = time.perf_counter() - t0
-        hist[prec] = np.array(ek)
+        recs = sim.history()
+        hist[prec] = {key: np.array([r[key] for r in recs]) for key in keys}
         sim.close()
-    m = len(hist["fp64"])
-    t = np.arange(len(hist["fp32"])) * every * dt
-    eps = {k: -np.gradient(v, t[:len(v)]) for k, v in hist.items()}
-    ek_err = np.abs(hist["fp32"][:m] - hist["fp64"]) / hist["fp64"]
-    eps_err = np.abs(eps["fp32"][1:m - 1] - eps["fp64"][1:m - 1]).max() / np.abs(eps["fp64"]).max()
+    h32, h64 = hist["fp32"], hist["fp64"]
+    m = len(h64["t"])
+    assert np.allclose(h32["t"][:m], h64["t"], rtol=1e-12, atol=0)
+
+    def rel(key, scale_by_peak):
+        a, b = h32[key][:m], h64[key]
+        if not scale_by_peak:
+            return float(np.max(np.abs(a - b) / np.abs(b)))
+        # the differences of the FP32 E_k samples at the ends of a shortened
+        # FP64 run are one-sided: compare the interior
+        lo, hi = (1, m - 1) if m < len(h32["t"]) else (0, m)
+        return float(np.max(np.abs(a[lo:hi] - b[lo:hi])) / np.max(np.abs(b)))
     a, b = finals["fp32"], finals["fp64"]
     rho_err = float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max())
+    ipk = int(np.argmax(h32["eps_Ek"]))
+    sub = slice(None, None, 10)
     out = {"workload": f"taylor-green-{n}^3 to t={t_end} (FP64 to t={nsteps64 * dt:.3f})",
-           "steps": nsteps, "steps_fp64": nsteps64, "dt": dt,
-           "Ek_rel_err_max": float(ek_err.max()), "Ek_rel_err_final": float(ek_err[-1]),
-           "eps_rel_err_max": float(eps_err), "rho_rel_linf_at_fp64_end": rho_err,
-           "Ek_final_fp32": float(hist["fp32"][-1]), "eps_peak_fp32": float(eps["fp32"].max()),
-           "t_eps_peak_fp32": float(t[int(np.argmax(eps["fp32"]))]),
-           "wall_s": times, "samples_every_steps": every,
-           "Ek_fp32_every_100_steps": [float(x) for x in hist["fp32"][::10]]}
+           "steps": nsteps, "steps_fp64": nsteps64, "dt": dt, "samples_every_steps": every,
+           "fp32_vs_fp64": {
+               "Ek_rel_err_max": rel("Ek", False),
+               "eps_Ek_err_max_of_peak": rel("eps_Ek", True),
+               "eps_zeta_err_max_of_peak": rel("eps_zeta", True),
+               "eps_num_err_max_of_peak_eps": float(
+                   np.max(np.abs(h32["eps_num"][1:m - 1] - h64["eps_num"][1:m - 1])) / np.max(np.abs(h64["eps_Ek"]))),
+               "rho_rel_linf_at_fp64_end": rho_err},
+           "fp32": {"Ek_final": float(h32["Ek"][-1]), "eps_Ek_peak": float(h32["eps_Ek"][ipk]),
+                    "t_eps_Ek_peak": float(h32["t"][ipk]), "eps_zeta_peak": float(h32["eps_zeta"].max()),
+                    "eps_num_at_eps_peak": float(h32["eps_num"][ipk]),
+                    "eps1_at_eps_peak": float(h32["eps1"][ipk])},
+           "wall_s": times,
+           "history_fp32_every_100_steps": {key: [float(x) for x in h32[key][sub]] for key in keys},
+           "history_fp64_every_100_steps": {key: [float(x) for x in h64[key][sub]] for key in keys}}
     print(json.dumps(out), flush=True)
 
 

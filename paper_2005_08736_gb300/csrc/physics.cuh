@@ -464,31 +464,42 @@ HGKS_HD T collision_time_full(T mu0, T p0, T pl, T pr, const Gas<T>& g, T dt) {
   return mu0 / p0 + g.tau_num_C * tabs((pl - pr) / (pl + pr)) * dt;
 }
 
-// Full second-order flux (Eq. (5)) with the Heaviside factor H(u) on g_l and
-// 1 - H(u) on g_r, integrated over [0, dt] and [0, dt/2] and fitted linearly
-// (Eq. (7)).  Returns F - E(Q_ref) and dF.
+// The parts of the full flux gathered for one Gauss point: the equilibrium
+// part, the sum of the two half-space parts and the pressures of the l and r
+// states (the full flux evaluated part by part, state by state).
 template <class T>
-HGKS_HD void flux_full(const PointState<T>& stl, const PointState<T>& str,
-                                          const PointState<T>& st0, const Gas<T>& g, T dt,
-                                          T F[5], T dF[5]) {
-  T V[6][5];
+struct FullParts {
   FullEq<T> e;
-  flux_full_eq(st0, g, e);
+  T Vs[3][5];  // half-space parts, side l then + side r
+  T pl, pr;
+};
+
+// Add the half-space part of side `side` (0: l, assigns; 1: r, adds) of the
+// state st to the parts.
+template <class T>
+HGKS_HD void flux_full_add_side(const PointState<T>& st, const Gas<T>& g, int side, FullParts<T>& a) {
+  FullSide<T> h;
+  flux_full_side(st, g, side, h);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int i = 0; i < 5; ++i) V[k][i] = e.V[k][i];
-  T pl, pr;
-#pragma unroll 1  // one copy of the half-space code for both sides
-  for (int side = 0; side < 2; ++side) {
-    FullSide<T> h;
-    flux_full_side(side == 0 ? stl : str, g, side, h);
+    for (int i = 0; i < 5; ++i) a.Vs[k][i] = side == 0 ? h.V[k][i] : a.Vs[k][i] + h.V[k][i];
+  if (side == 0) a.pl = h.p; else a.pr = h.p;
+}
+
+// The full flux from its parts: tau, the fit of Eq. (7), the Prandtl fix.
+template <class T>
+HGKS_HD void flux_full_combine(const FullParts<T>& a, const Gas<T>& g, T dt, T F[5], T dF[5]) {
+  const FullEq<T>& e = a.e;
+  T V[6][5];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int i = 0; i < 5; ++i) V[3 + k][i] = side == 0 ? h.V[k][i] : V[3 + k][i] + h.V[k][i];
-    if (side == 0) pl = h.p; else pr = h.p;
-  }
+    for (int i = 0; i < 5; ++i) {
+      V[k][i] = e.V[k][i];
+      V[3 + k][i] = a.Vs[k][i];
+    }
+  const T pl = a.pl, pr = a.pr;
   V[3][1] -= g.p_r;  // the half-space sum minus the reference Euler flux
   const T tau = collision_time_full(e.mu, e.p, pl, pr, g, dt);
   T Fq[6], dFq[6];
@@ -507,6 +518,20 @@ HGKS_HD void flux_full(const PointState<T>& stl, const PointState<T>& str,
   // Prandtl fix: (1/Pr - 1) times the heat flux -tau rho0 <h (a.u + A)> =
   // -tau p0 c_p dT/dn of the equilibrium part (tau includes the numerical term).
   F[4] -= g.pr_fix * tau * e.p * (T(0.5) * (g.K + T(5))) * e.dT;
+}
+
+// Full second-order flux (Eq. (5)) with the Heaviside factor H(u) on g_l and
+// 1 - H(u) on g_r, integrated over [0, dt] and [0, dt/2] and fitted linearly
+// (Eq. (7)).  Returns F - E(Q_ref) and dF.
+template <class T>
+HGKS_HD void flux_full(const PointState<T>& stl, const PointState<T>& str,
+                                          const PointState<T>& st0, const Gas<T>& g, T dt,
+                                          T F[5], T dF[5]) {
+  FullParts<T> a;
+  flux_full_eq(st0, g, a.e);
+#pragma unroll 1  // one copy of the half-space code for both sides
+  for (int side = 0; side < 2; ++side) flux_full_add_side(side == 0 ? stl : str, g, side, a);
+  flux_full_combine(a, g, dt, F, dF);
 }
 
 // Equilibrium state of the compatibility condition, Q0 = int_{u>0} psi g_l +
