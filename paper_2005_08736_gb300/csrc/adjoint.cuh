@@ -17,14 +17,14 @@
 // The WENO5 end values and the tangential polynomials are transposed in
 // reverse mode (closed-form derivatives of the nonlinear weights); the flux's
 // slope inputs through the transposes of the linear maps that consume them;
-// the flux's values and the compatibility state by forward-mode dual numbers
-// through the same device functions as the forward sweep, one input direction
-// at a time (for the full flux, through the one part each value enters).
+// the flux's values in reverse mode through each part of the flux
+// (flux_rev.cuh), and the compatibility state's sign moments likewise.
 // Ghost cells collect cotangents like interior cells; k_fold_ghosts returns
 // them to their periodic images afterwards.
 #pragma once
 
 #include "dual.cuh"
+#include "flux_rev.cuh"
 #include "sweep.cuh"
 
 namespace hgks {
@@ -154,29 +154,20 @@ __device__ __forceinline__ void tangential_vjp(const T f[5], const T gv[2], cons
 
 // (cl, cr) += J^T g0 for the compatibility state Q0(Q_l, Q_r) =
 // (Q_l + Q_r)/2 + (S(Q_l) - S(Q_r))/2 (compat_dev): the identity part
-// directly, S of each state by one dual-number pass per component.
+// directly, S of each state by one reverse-mode pass (flux_rev.cuh).
 template <class T>
 __device__ __forceinline__ void compat_vjp(const T ql[5], const T qr[5], const T g0[5],
                                            const Gas<T>& gas, T cl[5], T cr[5]) {
-  const Gas<Dual<T>> gd = dual_gas(gas);
+  T hp[5], hm[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     cl[i] += T(0.5) * g0[i];
     cr[i] += T(0.5) * g0[i];
+    hp[i] = T(0.5) * g0[i];
+    hm[i] = -T(0.5) * g0[i];
   }
-#pragma unroll 1
-  for (int j = 0; j < 10; ++j) {
-    const T* q = j < 5 ? ql : qr;
-    const int c = j < 5 ? j : j - 5;
-    Dual<T> x[5], S[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) x[k] = Dual<T>(q[k], T(k == c ? 1 : 0));
-    sign_moments(x, gd, S);
-    T s = T(0);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) s += g0[i] * S[i].d;
-    if (j < 5) cl[c] += T(0.5) * s; else cr[c] -= T(0.5) * s;
-  }
+  sign_moments_rev(ql, gas, hp, cl);
+  sign_moments_rev(qr, gas, hm, cr);
 }
 
 // ---- transposed linear maps: both fluxes are affine in the slopes dq of
@@ -345,8 +336,8 @@ __device__ __forceinline__ void flux_full_dq_vjp(const PointState<T>* st, const 
 // weight of term V_k and phi_tau the sensitivity to tau (fit coefficients
 // and the Prandtl term), each value enters through one part only: q0 the
 // equilibrium part (and tau through mu0/p0), q_l and q_r their half-space
-// part (and tau through p_l, p_r).  One forward-mode pass of that part per
-// value component, instead of a pass of the whole flux.
+// part (and tau through p_l, p_r).  One reverse-mode pass of each part
+// (flux_rev.cuh) gives the cotangents of all five values of its state.
 template <class T>
 __device__ __forceinline__ void flux_full_value_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
                                                     const T gF[5], const T gdF[5], PointState<T>* cot) {
@@ -377,50 +368,31 @@ __device__ __forceinline__ void flux_full_value_vjp(const PointState<T>* st, con
                                          Dual<T>(hr.p), gd, Dual<T>(dt)).d;
   const T dtau_dpr = collision_time_full(Dual<T>(e.mu), Dual<T>(e.p), Dual<T>(hl.p),
                                          Dual<T>(hr.p, T(1)), gd, Dual<T>(dt)).d;
-  // Equilibrium state q0.
-#pragma unroll 1
-  for (int c = 0; c < 5; ++c) {
-    PointState<Dual<T>> x;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      x.q[i] = Dual<T>(st[2].q[i], T(i == c ? 1 : 0));
-#pragma unroll
-      for (int d = 0; d < 3; ++d) x.dq[d][i] = Dual<T>(st[2].dq[d][i], T(0));
-    }
-    FullEq<Dual<T>> de;
-    flux_full_eq(x, gd, de);
-    T sdot = T(0);
+  // Equilibrium state q0: the part's outputs V0..V2, mu0, p0 and dT0 carry
+  // the cotangents G_k, phi_tau dtau/dmu0, phi_tau dtau/dp0 - (Prandtl term)
+  // and -(Prandtl term); one reverse pass (flux_rev.cuh).
+  {
+    T gV[3][5];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int i = 0; i < 5; ++i) sdot += G[k][i] * de.V[k][i].d;
-    const T dtau = (de.mu.d * e.p - e.mu * de.p.d) / (e.p * e.p);
-    sdot += phi_tau * dtau - wpr * tau * (de.p.d * e.dT + e.p * de.dT.d);
-    cot[2].q[c] += sdot;
+      for (int i = 0; i < 5; ++i) gV[k][i] = G[k][i];
+    const T gmu = phi_tau / e.p;
+    const T gp = -phi_tau * e.mu / (e.p * e.p) - wpr * tau * e.dT;
+    const T gdT = -wpr * tau * e.p;
+    flux_full_eq_value_rev(st[2], gas, gV, gmu, gp, gdT, cot[2].q);
   }
-  // Left and right states.
+  // Left and right states: V3..V5 with G_3..G_5, the pressure with
+  // phi_tau dtau/dp; one reverse pass each.
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const T dtau_dp = side == 0 ? dtau_dpl : dtau_dpr;
-#pragma unroll 1
-    for (int c = 0; c < 5; ++c) {
-      PointState<Dual<T>> x;
+    T gV[3][5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        x.q[i] = Dual<T>(st[side].q[i], T(i == c ? 1 : 0));
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) x.dq[d][i] = Dual<T>(st[side].dq[d][i], T(0));
-      }
-      FullSide<Dual<T>> dh;
-      flux_full_side(x, gd, side, dh);
-      T sdot = T(0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int i = 0; i < 5; ++i) sdot += G[3 + k][i] * dh.V[k][i].d;
-      sdot += phi_tau * dtau_dp * dh.p.d;
-      cot[side].q[c] += sdot;
-    }
+      for (int i = 0; i < 5; ++i) gV[k][i] = G[3 + k][i];
+    flux_full_side_value_rev(st[side], gas, side, gV, phi_tau * (side == 0 ? dtau_dpl : dtau_dpr),
+                             cot[side].q);
   }
 }
 
@@ -430,44 +402,14 @@ template <class T, int FLUX>
 __device__ __forceinline__ void flux_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
                                          bool want_F, const T gF[5], const T gdF[5],
                                          PointState<T>* cot) {
-  constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
   if constexpr (FLUX == FLUX_FULL) {
     flux_full_value_vjp(st, gas, dt, gF, gdF, cot);
     flux_full_dq_vjp(st, gas, dt, gF, gdF, cot);
-    return;
-  }
-  const Gas<Dual<T>> gd = dual_gas(gas);
-  // Values q: one forward-mode (dual-number) pass per component.
-#pragma unroll 1
-  for (int j = 0; j < 5 * NS; ++j) {
-    PointState<Dual<T>> x[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        x[s].q[i] = Dual<T>(st[s].q[i], T(j == 5 * s + i ? 1 : 0));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) x[s].dq[c][i] = Dual<T>(st[s].dq[c][i], T(0));
-      }
-    Dual<T> F[5], dF[5];
-    if constexpr (FLUX == FLUX_SMOOTH) {
-      flux_smooth(x[0], gd, want_F, F, dF);
-      if (!want_F)
-#pragma unroll
-        for (int i = 0; i < 5; ++i) F[i] = Dual<T>(T(0));
-    } else {
-      flux_full(x[0], x[NS > 1 ? 1 : 0], x[NS > 2 ? 2 : 0], gd, Dual<T>(dt), F, dF);
-    }
-    T sdot = T(0);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) sdot += gF[i] * F[i].d + gdF[i] * dF[i].d;
-    cot[j / 5].q[j % 5] += sdot;
-  }
-  // Slopes dq: the fluxes are linear in them, one transposed pass.
-  if constexpr (FLUX == FLUX_SMOOTH) {
-    flux_smooth_dq_vjp(st[0], gas, want_F, gF, gdF, cot[0].dq);
   } else {
-    flux_full_dq_vjp(st, gas, dt, gF, gdF, cot);
+    // Values q: one reverse-mode pass (flux_rev.cuh); slopes dq: the flux is
+    // linear in them, one transposed pass.
+    flux_smooth_value_rev(st[0], gas, want_F, gF, gdF, cot[0].q);
+    flux_smooth_dq_vjp(st[0], gas, want_F, gF, gdF, cot[0].dq);
   }
 }
 
