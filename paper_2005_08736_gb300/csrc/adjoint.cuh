@@ -435,6 +435,40 @@ constexpr size_t adj_smem_bytes() {
   return sizeof(T) * 2 * (SweepLayout<FLUX>::NFF + SweepLayout<FLUX>::NT1) * NH;
 }
 
+// Rows of the t1-pass buffer read by the t2 pass for call c = 3 i + r of
+// state group s (i the component, r = 0: the value field, which also gives
+// the t2-derivative; 1: its t1-derivative; 2: its normal slope) at the t1
+// abscissa m1.
+template <int NV>
+__device__ __forceinline__ int t2_row(int s, int c, int m1) {
+  const int k = 5 * s + c / 3, r = c % 3;
+  return r == 0 ? 4 * k + m1 : (r == 1 ? 4 * k + 2 + m1 : 4 * NV + 2 * k + m1);
+}
+
+// The point-state entries of call c (compile-time) from the tangential
+// value v and derivative dv at this thread's t2 abscissa.
+template <class T>
+__device__ __forceinline__ void t2_assign(PointState<T>& p, int c, T v, T dv, T rh1, T rh2) {
+  const int i = c / 3, r = c % 3;
+  if (r == 0) {
+    p.q[i] = v;
+    p.dq[2][i] = dv * rh2;
+  } else if (r == 1) {
+    p.dq[1][i] = v * rh1;
+  } else {
+    p.dq[0][i] = v;
+  }
+}
+
+// Cotangents of the tangential value and derivative of call c (the
+// transpose of t2_assign).
+template <class T>
+__device__ __forceinline__ void t2_cot(const PointState<T>& p, int c, T rh1, T rh2, T& gv, T& gd) {
+  const int i = c / 3, r = c % 3;
+  gv = r == 0 ? p.q[i] : (r == 1 ? p.dq[1][i] * rh1 : p.dq[0][i]);
+  gd = r == 0 ? p.dq[2][i] * rh2 : T(0);
+}
+
 template <class T, int MODE, int FLUX, int TP, int TS, int NT>
 __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
   constexpr int HP = TP + 4, HS = TS + 4, NH = HP * HS;
@@ -444,8 +478,8 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
   constexpr int NS = FLUX == FLUX_FULL ? 3 : 1;
   constexpr int NFACE = TP * TS;
   constexpr int TPF = NT / NFACE;
-  constexpr int GPF = 4 / TPF;
-  static_assert(TPF * NFACE == NT && GPF * TPF == 4, "tile must give 1, 2 or 4 threads per face");
+  static_assert(TPF * NFACE == NT && (TPF == 2 || TPF == 4), "tile must give 2 or 4 threads per face");
+  constexpr unsigned kAll = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ff = reinterpret_cast<T*>(smem_raw);  // [NFF][NH] face fields
   T* tb = ff + NFF * NH;                   // [NT1][NH] t1 pass
@@ -463,7 +497,12 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
   const int tid = threadIdx.x;
   const T dt = T(a.scal[0]);
 
-  const int face = tid % NFACE, sub = tid / NFACE;
+  // TPF consecutive threads per face.  Thread tid takes the t2 abscissa
+  // m2 = tid & 1 and its neighbour tid ^ 1 (same warp, same face) the other:
+  // each tangential reconstruction gives both abscissae, so the pair splits
+  // the t2 pass and its transpose between them and swaps halves by shuffles.
+  const int face = tid / TPF, sub = tid % TPF;
+  const int m2 = sub & 1;
   const int ip = face % TP, is = face / TP;
   const bool f_valid = (p0 + ip < nP) && (s0 + is < nS);
   const int cP = min(p0 + ip, nP - 1), cS = min(s0 + is, nS - 1);
@@ -472,6 +511,7 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
   const int at3 = (is + 2) * HP + (ip + 2);
   const int st2 = t1P ? HP : 1;
   const int st1 = t1P ? 1 : HP;
+  const int items = t1P ? TP * HS : HP * TS;  // points of the t1 pass
 
   for (int f = f0; f < f1; ++f) {
     // ---------------- forward: face fields, t1 pass ----------------
@@ -489,18 +529,19 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
     }
     for (int i = tid; i < NT1 * NH; i += NT) tbc[i] = T(0);
     __syncthreads();
-    {
-      const int items = t1P ? TP * HS : HP * TS;
-      for (int it = tid; it < items; it += NT) {
-        const int hp2 = t1P ? 2 + it % TP : it % HP;
-        const int hs2 = t1P ? it / TP : 2 + it / HP;
-        t1_pass_item<T, MODE, FLUX, NH>(ff, tb, hs2 * HP + hp2, st1, a.gas);
-      }
+    // One group of five fields per work item (2 NV / 5 groups per point).
+    for (int u = tid; u < items * (2 * NV / 5); u += NT) {
+      const int it = u % items, grp = u / items;
+      const int hp2 = t1P ? 2 + it % TP : it % HP;
+      const int hs2 = t1P ? it / TP : 2 + it / HP;
+      t1_pass_group<T, MODE, NV, NH>(ff, tb, hs2 * HP + hp2, st1, grp);
     }
     __syncthreads();
 
     // ---------------- R3: flux VJP and transposed t2 pass ----------------
-    if (f_valid) {
+    // Every thread takes part (the pair shuffles); a face outside the grid
+    // computes on the tile's padding and adds nothing.
+    {
       // Face-flux cotangents from L_c = -(F_{c+1/2} - F_{c-1/2}) / h_c: the face
       // f is the right face of cell f-1 and the left face of cell f.
       T gF[5], gdF[5];
@@ -531,28 +572,27 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
         }
       }
 #pragma unroll 1
-      for (int g = sub * GPF; g < (sub + 1) * GPF; ++g) {
-        const int m1 = g & 1, m2 = g >> 1;
+      for (int m1 = sub >> 1; m1 < 2; m1 += TPF / 2) {
         PointState<T> st[NS], ct[NS];
-        // Forward t2 pass, one state group per iteration (the body once in
-        // the code); the group's states go to st[s] through constant indices.
+        // Forward t2 pass, one state group per iteration: the 15 calls of a
+        // group (5 components x value field, t1-derivative, normal slope) in
+        // pairs, the first of each pair on the m2 = 0 thread and the second
+        // on its partner; each keeps its own abscissa's result and sends the
+        // other's.  The odd last call runs on both.
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
           PointState<T> g0;
 #pragma unroll
-          for (int i = 0; i < 5; ++i) {
-            const int k = 5 * s + i;
-            const T* sv = tb + (4 * k + m1) * NH + at3;
-            const T* sdv = tb + (4 * k + 2 + m1) * NH + at3;
-            const T* ss = tb + (4 * NV + 2 * k + m1) * NH + at3;
-            T v[2], dd[2];
-            tangential<MODE>(sv[-2 * st2], sv[-st2], sv[0], sv[st2], sv[2 * st2], v, dd);
-            g0.q[i] = v[m2];
-            g0.dq[2][i] = dd[m2] * rh2;
-            tangential_val<MODE>(sdv[-2 * st2], sdv[-st2], sdv[0], sdv[st2], sdv[2 * st2], v);
-            g0.dq[1][i] = v[m2] * rh1;
-            tangential_val<MODE>(ss[-2 * st2], ss[-st2], ss[0], ss[st2], ss[2 * st2], v);
-            g0.dq[0][i] = v[m2];
+          for (int j = 0; j < 8; ++j) {
+            const int c0 = 2 * j, c1 = 2 * j + 1 < 15 ? 2 * j + 1 : 2 * j;
+            const T* src = tb + t2_row<NV>(s, m2 ? c1 : c0, m1) * NH + at3;
+            T v[2], dv[2];
+            tangential<MODE>(src[-2 * st2], src[-st2], src[0], src[st2], src[2 * st2], v, dv);
+            const T ov = m2 ? v[1] : v[0], od = m2 ? dv[1] : dv[0];
+            const T rv = __shfl_xor_sync(kAll, m2 ? v[0] : v[1], 1);
+            const T rd = __shfl_xor_sync(kAll, m2 ? dv[0] : dv[1], 1);
+            t2_assign(g0, c0, m2 ? rv : ov, m2 ? rd : od, rh1, rh2);
+            if (c1 != c0) t2_assign(g0, c1, m2 ? ov : rv, m2 ? od : rd, rh1, rh2);
           }
           if (s == 0) st[0] = g0;
           else if (NS > 1 && s == 1) st[NS > 1 ? 1 : 0] = g0;
@@ -567,128 +607,165 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
             for (int c = 0; c < 3; ++c) ct[s].dq[c][i] = T(0);
           }
         flux_vjp<T, FLUX>(st, a.gas, dt, a.wL != nullptr, gF, gdF, ct);
-        // Transposed t2 pass into the t1-pass cotangents.
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
+        // Transposed t2 pass into the t1-pass cotangents, in the same pairs:
+        // the thread that owns a call receives its partner's cotangent of it
+        // and transposes the reconstruction for both abscissae at once.
 #pragma unroll 1
-          for (int i = 0; i < 5; ++i) {
-            const int k = 5 * s + i;
-            const int rows[3] = {4 * k + m1, 4 * k + 2 + m1, 4 * NV + 2 * k + m1};
-            T gvv[3][2] = {{0, 0}, {0, 0}, {0, 0}}, gdd[2] = {0, 0};
-            gvv[0][m2] = ct[s].q[i];
-            gdd[m2] = ct[s].dq[2][i] * rh2;
-            gvv[1][m2] = ct[s].dq[1][i] * rh1;
-            gvv[2][m2] = ct[s].dq[0][i];
+        for (int s = 0; s < NS; ++s) {
+          PointState<T> cs = ct[0];
+          if (NS > 1 && s == 1) cs = ct[NS > 1 ? 1 : 0];
+          if (NS > 2 && s == 2) cs = ct[NS > 2 ? 2 : 0];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              const T* src = tb + rows[r] * NH + at3;
+          for (int j = 0; j < 8; ++j) {
+            const int c0 = 2 * j, c1 = 2 * j + 1 < 15 ? 2 * j + 1 : 2 * j;
+            T v0, d0, v1, d1;
+            t2_cot(cs, c0, rh1, rh2, v0, d0);
+            t2_cot(cs, c1, rh1, rh2, v1, d1);
+            const T rv = __shfl_xor_sync(kAll, m2 ? v0 : v1, 1);
+            const T rd = __shfl_xor_sync(kAll, m2 ? d0 : d1, 1);
+            const T ov = m2 ? v1 : v0, od = m2 ? d1 : d0;
+            const T gv[2] = {m2 ? rv : ov, m2 ? ov : rv};
+            const T gd[2] = {m2 ? rd : od, m2 ? od : rd};
+            const bool owner = c1 != c0 || m2 == 0;
+            if (f_valid && owner && (gv[0] != T(0) || gv[1] != T(0) || gd[0] != T(0) || gd[1] != T(0))) {
+              const int row = t2_row<NV>(s, m2 ? c1 : c0, m1);
+              const T* src = tb + row * NH + at3;
               const T fv[5] = {src[-2 * st2], src[-st2], src[0], src[st2], src[2 * st2]};
               T cot[5] = {0, 0, 0, 0, 0};
-              const T zero2[2] = {0, 0};
-              tangential_vjp<MODE>(fv, gvv[r], r == 0 ? gdd : zero2, cot);
-              T* dst = tbc + rows[r] * NH + at3;
+              tangential_vjp<MODE>(fv, gv, gd, cot);
+              T* dst = tbc + row * NH + at3;
 #pragma unroll
-              for (int j = 0; j < 5; ++j) atomicAdd(dst + (j - 2) * st2, cot[j]);
+              for (int jj = 0; jj < 5; ++jj) atomicAdd(dst + (jj - 2) * st2, cot[jj]);
             }
           }
+        }
       }
     }
     __syncthreads();
 
     // ---------------- R2: transposed t1 pass ----------------
-    {
-      const int items = t1P ? TP * HS : HP * TS;
-      for (int it = tid; it < items; it += NT) {
-        const int hp2 = t1P ? 2 + it % TP : it % HP;
-        const int hs2 = t1P ? it / TP : 2 + it / HP;
-        const int at = hs2 * HP + hp2;
-#pragma unroll 1
-        for (int k = 0; k < 2 * NV; ++k) {
-          const bool value_field = k < NV;
-          const T* src = ff + k * NH + at;
-          const T fv[5] = {src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1]};
-          T gv2[2], gd2[2];
-          if (value_field) {
-            gv2[0] = tbc[(4 * k + 0) * NH + at];
-            gv2[1] = tbc[(4 * k + 1) * NH + at];
-            gd2[0] = tbc[(4 * k + 2) * NH + at];
-            gd2[1] = tbc[(4 * k + 3) * NH + at];
-          } else {
-            gv2[0] = tbc[(4 * NV + 2 * (k - NV) + 0) * NH + at];
-            gv2[1] = tbc[(4 * NV + 2 * (k - NV) + 1) * NH + at];
-            gd2[0] = gd2[1] = T(0);
-          }
-          if (gv2[0] == T(0) && gv2[1] == T(0) && gd2[0] == T(0) && gd2[1] == T(0)) continue;
-          T cot[5] = {0, 0, 0, 0, 0};
-          tangential_vjp<MODE>(fv, gv2, gd2, cot);
-          T* dst = ffc + k * NH + at;
-#pragma unroll
-          for (int j = 0; j < 5; ++j) atomicAdd(dst + (j - 2) * st1, cot[j]);
-        }
+    // One field of one point per work item.
+    for (int u = tid; u < items * 2 * NV; u += NT) {
+      const int it = u % items, k = u / items;
+      const int hp2 = t1P ? 2 + it % TP : it % HP;
+      const int hs2 = t1P ? it / TP : 2 + it / HP;
+      const int at = hs2 * HP + hp2;
+      const bool value_field = k < NV;
+      T gv2[2], gd2[2];
+      if (value_field) {
+        gv2[0] = tbc[(4 * k + 0) * NH + at];
+        gv2[1] = tbc[(4 * k + 1) * NH + at];
+        gd2[0] = tbc[(4 * k + 2) * NH + at];
+        gd2[1] = tbc[(4 * k + 3) * NH + at];
+      } else {
+        gv2[0] = tbc[(4 * NV + 2 * (k - NV) + 0) * NH + at];
+        gv2[1] = tbc[(4 * NV + 2 * (k - NV) + 1) * NH + at];
+        gd2[0] = gd2[1] = T(0);
       }
+      if (gv2[0] == T(0) && gv2[1] == T(0) && gd2[0] == T(0) && gd2[1] == T(0)) continue;
+      const T* src = ff + k * NH + at;
+      const T fv[5] = {src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1]};
+      T cot[5] = {0, 0, 0, 0, 0};
+      tangential_vjp<MODE>(fv, gv2, gd2, cot);
+      T* dst = ffc + k * NH + at;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) atomicAdd(dst + (j - 2) * st1, cot[j]);
     }
     __syncthreads();
 
     // ---------------- R1: face fields -> cells ----------------
+    // R1a, per point: the compatibility state's cotangent onto those of Q_l
+    // and Q_r (full flux: added to their face-field cotangents; smooth flux:
+    // written to rows 0-9 of the t1 cotangent buffer, free by now).
+    T* gql = FLUX == FLUX_FULL ? ffc : tbc;
     for (int h = tid; h < NH; h += NT) {
       const int hp = h % HP, hs = h / HP;
       const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
       if (Pc > nP + 1 || Sc > nS + 1) continue;
-      T gQl[5], gQr[5], gQ0[5], gDl[5], gDr[5], gD0[5];
+      T g0[5], cl[5], cr[5];
       bool any = false;
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        if constexpr (FLUX == FLUX_SMOOTH) {
-          gQl[i] = gQr[i] = gDl[i] = gDr[i] = T(0);
-          gQ0[i] = ffc[i * NH + h];
-          gD0[i] = ffc[(5 + i) * NH + h];
-        } else {
-          gQl[i] = ffc[i * NH + h];
-          gQr[i] = ffc[(5 + i) * NH + h];
-          gQ0[i] = ffc[(10 + i) * NH + h];
-          gDl[i] = ffc[(15 + i) * NH + h];
-          gDr[i] = ffc[(20 + i) * NH + h];
-          gD0[i] = ffc[(25 + i) * NH + h];
-        }
-        any = any || gQl[i] != T(0) || gQr[i] != T(0) || gQ0[i] != T(0) || gDl[i] != T(0) ||
-              gDr[i] != T(0) || gD0[i] != T(0);
+        g0[i] = ffc[((FLUX == FLUX_FULL ? 10 : 0) + i) * NH + h];
+        any = any || g0[i] != T(0);
+        cl[i] = FLUX == FLUX_FULL ? ffc[i * NH + h] : T(0);
+        cr[i] = FLUX == FLUX_FULL ? ffc[(5 + i) * NH + h] : T(0);
       }
-      if (!any) continue;
-      int c[3];
-      c[d] = f - 3;
-      c[P] = Pc;
-      c[S] = Sc;
-      const long long cb = pad_index(a.g, c[0], c[1], c[2]);
+      if (any) {
+        T Ql[5], Qr[5];
+        if constexpr (FLUX == FLUX_FULL) {
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            Ql[i] = ff[i * NH + h];
+            Qr[i] = ff[(5 + i) * NH + h];
+          }
+        } else {
+          int c[3];
+          c[d] = f - 3;
+          c[P] = Pc;
+          c[S] = Sc;
+          const long long cb = pad_index(a.g, c[0], c[1], c[2]);
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            const T* qv = a.q + ax.gv[i] * a.g.P + cb;
+            T qc[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) qc[k] = qv[k * ax.sd];
+            T Li, Ri, Lr, Rr;
+            weno5_pair<MODE>(qc[0], qc[1], qc[2], qc[3], qc[4], Li, Ri);
+            weno5_pair<MODE>(qc[1], qc[2], qc[3], qc[4], qc[5], Lr, Rr);
+            Ql[i] = Ri;
+            Qr[i] = Lr;
+          }
+        }
+        compat_vjp(Ql, Qr, g0, a.gas, cl, cr);
+      }
+      if (any || FLUX != FLUX_FULL) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          gql[i * NH + h] = cl[i];
+          gql[(5 + i) * NH + h] = cr[i];
+        }
+      }
+    }
+    __syncthreads();
+    // R1b, per point and component: the normal slopes and the WENO5 pairs
+    // transposed, scattered into the cells f-3 .. f+2.
+    {
       const T hl = a.wn[f - 1 + kGhost], hr = a.wn[f + kGhost];
       const T rhl = T(1) / hl, rhr = T(1) / hr, r6 = T(1) / (T(6) * (hl + hr));
-      T qc[5][6], Ql[5], Qr[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
+      for (int u = tid; u < 5 * NH; u += NT) {
+        const int h = u % NH, i = u / NH;
+        const int hp = h % HP, hs = h / HP;
+        const int Pc = p0 - 2 + hp, Sc = s0 - 2 + hs;
+        if (Pc > nP + 1 || Sc > nS + 1) continue;
+        const T gQl = gql[i * NH + h], gQr = gql[(5 + i) * NH + h];
+        const T gDl = FLUX == FLUX_FULL ? ffc[(15 + i) * NH + h] : T(0);
+        const T gDr = FLUX == FLUX_FULL ? ffc[(20 + i) * NH + h] : T(0);
+        const T gD0 = ffc[((FLUX == FLUX_FULL ? 25 : 5) + i) * NH + h];
+        if (gQl == T(0) && gQr == T(0) && gDl == T(0) && gDr == T(0) && gD0 == T(0)) continue;
+        int c[3];
+        c[d] = f - 3;
+        c[P] = Pc;
+        c[S] = Sc;
+        const long long cb = pad_index(a.g, c[0], c[1], c[2]);
         const T* qv = a.q + ax.gv[i] * a.g.P + cb;
+        T qc[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) qc[i][k] = qv[k * ax.sd];
-        T Li, Ri, Lr, Rr;
-        weno5_pair<MODE>(qc[i][0], qc[i][1], qc[i][2], qc[i][3], qc[i][4], Li, Ri);
-        weno5_pair<MODE>(qc[i][1], qc[i][2], qc[i][3], qc[i][4], qc[i][5], Lr, Rr);
-        Ql[i] = Ri;
-        Qr[i] = Lr;
-      }
-      compat_vjp(Ql, Qr, gQ0, a.gas, gQl, gQr);
-#pragma unroll 1
-      for (int i = 0; i < 5; ++i) {
+        for (int k = 0; k < 6; ++k) qc[k] = qv[k * ax.sd];
         T gq[6] = {0, 0, 0, 0, 0, 0};
         // Slopes: Dl = (4 Ri + 2 Li - 6 q2)/hl, Dr = -(4 Lr + 2 Rr - 6 q3)/hr,
         // D0 = (q1 - 15 q2 + 15 q3 - q4) / (6 (hl + hr)).
-        const T gRi = gQl[i] + T(4) * rhl * gDl[i], gLi = T(2) * rhl * gDl[i];
-        const T gLr = gQr[i] - T(4) * rhr * gDr[i], gRr = -T(2) * rhr * gDr[i];
-        gq[2] -= T(6) * rhl * gDl[i];
-        gq[3] += T(6) * rhr * gDr[i];
-        gq[1] += r6 * gD0[i];
-        gq[2] -= T(15) * r6 * gD0[i];
-        gq[3] += T(15) * r6 * gD0[i];
-        gq[4] -= r6 * gD0[i];
-        weno5_pair_vjp<MODE>(&qc[i][0], gLi, gRi, &gq[0]);
-        weno5_pair_vjp<MODE>(&qc[i][1], gLr, gRr, &gq[1]);
+        const T gRi = gQl + T(4) * rhl * gDl, gLi = T(2) * rhl * gDl;
+        const T gLr = gQr - T(4) * rhr * gDr, gRr = -T(2) * rhr * gDr;
+        gq[2] -= T(6) * rhl * gDl;
+        gq[3] += T(6) * rhr * gDr;
+        gq[1] += r6 * gD0;
+        gq[2] -= T(15) * r6 * gD0;
+        gq[3] += T(15) * r6 * gD0;
+        gq[4] -= r6 * gD0;
+        weno5_pair_vjp<MODE>(&qc[0], gLi, gRi, &gq[0]);
+        weno5_pair_vjp<MODE>(&qc[1], gLr, gRr, &gq[1]);
         T* accv = a.acc + ax.gv[i] * a.g.P + cb;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
