@@ -170,247 +170,14 @@ __device__ __forceinline__ void compat_vjp(const T ql[5], const T qr[5], const T
   sign_moments_rev(qr, gas, hm, cr);
 }
 
-// ---- transposed linear maps: both fluxes are affine in the slopes dq of
-// each state for fixed values q, so the slope cotangents come from one pass
-// through the transposes of the linear maps that consume dq.
-
-// out = J_J(Q)^T v, the transpose of euler_jvp<J> (H = rho E + p).
-template <int J, class T>
-__device__ __forceinline__ void euler_vjp(const Prim<T>& s, T H, const T v[5], const Gas<T>& g,
-                                          T out[5]) {
-  const T inv = s.inv_rho;
-  const T U[3] = {s.U, s.V, s.W};
-  const T mJ = s.rho * U[J];
-  const T c1J = v[0] + v[1] * U[0] + v[2] * U[1] + v[3] * U[2];  // direct dQ[1+J] terms
-  T wdu[3];                                                     // cotangents of du_i
-#pragma unroll
-  for (int i = 0; i < 3; ++i) wdu[i] = mJ * v[1 + i];
-  wdu[J] += H * v[4];
-  const T wdp = v[1 + J] + U[J] * v[4];  // cotangent of dp
-  const T gd = g.gm1 * wdp;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) out[1 + i] = wdu[i] * inv - gd * U[i];
-  out[1 + J] += c1J;
-  out[0] = -(wdu[0] * U[0] + wdu[1] * U[1] + wdu[2] * U[2]) * inv +
-           gd * T(0.5) * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-  out[4] = U[J] * v[4] + gd;
-}
-
-// c0 += cotangent of dq along n from tb, the cotangent of the temperature
-// slope dT0 = (dp0 - theta dq[0])/rho, dp0 = (gamma-1)(dq[4] - U.dm + |U|^2/2 dq[0]).
-template <class T>
-__device__ __forceinline__ void temperature_slope_vjp(const Prim<T>& s, const Gas<T>& g, T tb,
-                                                      T c0[5]) {
-  const T inv = s.inv_rho;
-  const T dpb = tb * inv * g.gm1;
-  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
-  c0[0] += -s.theta * tb * inv + T(0.5) * q2 * dpb;
-  c0[1] -= s.U * dpb;
-  c0[2] -= s.V * dpb;
-  c0[3] -= s.W * dpb;
-  c0[4] += dpb;
-}
-
-// cd += (d Fv / d dq)^T w for ns_viscous_flux (linear in dq).
-template <class T>
-__device__ __forceinline__ void ns_viscous_vjp(const Prim<T>& s, const Gas<T>& g, T mu, T heat_scale,
-                                               const T w[5], T cd[3][5]) {
-  const T inv = s.inv_rho;
-  const T U[3] = {s.U, s.V, s.W};
-  const T s00 = -w[1] - w[4] * U[0], s01 = -w[2] - w[4] * U[1], s02 = -w[3] - w[4] * U[2];
-  const T divb = -mu * T(2) / (g.K + T(3)) * s00;
-  const T du0b[3] = {T(2) * mu * s00 + divb, mu * s01, mu * s02};
-  const T du10 = mu * s01, du20 = mu * s02, du11 = divb, du22 = divb;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    cd[0][1 + i] += du0b[i] * inv;
-    cd[0][0] -= U[i] * du0b[i] * inv;
-  }
-  cd[1][1] += du10 * inv;
-  cd[1][2] += du11 * inv;
-  cd[1][0] -= (U[0] * du10 + U[1] * du11) * inv;
-  cd[2][1] += du20 * inv;
-  cd[2][3] += du22 * inv;
-  cd[2][0] -= (U[0] * du20 + U[2] * du22) * inv;
-  temperature_slope_vjp(s, g, -w[4] * heat_scale * mu * T(0.5) * (g.K + T(5)), cd[0]);
-}
-
-// cd[d] += cotangent of dq[d] through Q_t = -sum_d J_d dq[d], given qtb = cotangent of Q_t.
-template <class T>
-__device__ __forceinline__ void time_derivative_vjp(const Prim<T>& s, T H, const T qtb[5],
-                                                    const Gas<T>& g, T cd[3][5]) {
-  T t[5];
-  euler_vjp<0>(s, H, qtb, g, t);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) cd[0][i] -= t[i];
-  euler_vjp<1>(s, H, qtb, g, t);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) cd[1][i] -= t[i];
-  euler_vjp<2>(s, H, qtb, g, t);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) cd[2][i] -= t[i];
-}
-
-// Slope cotangents of the smooth flux: dF = J_n Q_t; F = Euler + viscous flux.
-template <class T>
-__device__ __forceinline__ void flux_smooth_dq_vjp(const PointState<T>& st0, const Gas<T>& g,
-                                                   bool want_F, const T gF[5], const T gdF[5],
-                                                   T cd[3][5]) {
-  const Prim<T> s = prim_of(st0.q, g);
-  const T H = g.h_r + st0.q[4] + s.dp;
-  T qtb[5];
-  euler_vjp<0>(s, H, gdF, g, qtb);
-  time_derivative_vjp(s, H, qtb, g, cd);
-  if (want_F) ns_viscous_vjp(s, g, viscosity(s, g), g.pr_fix + T(1), gF, cd);
-}
-
-// Slope cotangents of the full flux (flux_full): the equilibrium terms V1, V2
-// and the Prandtl fix depend on dq0; the half-space terms V4, V5 on dq_l, dq_r
-// through the slopes a_d = M^{-1} dq_d / rho and A = M^{-1} Q_t / rho (the
-// moment matrix M is symmetric, so its inverse is its own transpose) and the
-// symmetric half-space moment matrices.
-template <class T>
-__device__ __forceinline__ void flux_full_dq_vjp(const PointState<T>* st, const Gas<T>& g, T dt,
-                                                 const T gF[5], const T gdF[5], PointState<T>* cot) {
-  const Prim<T> s0 = prim_of(st[2].q, g);
-  const Prim<T> sl = prim_of(st[0].q, g), sr = prim_of(st[1].q, g);
-  T tau = viscosity(s0, g) / s0.p;
-  tau += g.tau_num_C * tabs((sl.p - sr.p) / (sl.p + sr.p)) * dt;
-  T Fq[6], dFq[6];
-  fit_coefficients(tau, dt, Fq, dFq);
-  // Equilibrium part: V1 = -Fv(mu = p, Pr = 1) - V2, V2 = J_n Q_t0.
-  {
-    const T H0 = g.h_r + st[2].q[4] + s0.dp;
-    T w2[5], wv[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const T G1 = gF[i] * Fq[1] + gdF[i] * dFq[1], G2 = gF[i] * Fq[2] + gdF[i] * dFq[2];
-      w2[i] = G2 - G1;
-      wv[i] = -G1;
-    }
-    T qtb[5];
-    euler_vjp<0>(s0, H0, w2, g, qtb);
-    time_derivative_vjp(s0, H0, qtb, g, cot[2].dq);
-    ns_viscous_vjp(s0, g, s0.p, T(1), wv, cot[2].dq);
-    // Prandtl fix: F[4] -= pr_fix tau p0 c_p dT0.
-    temperature_slope_vjp(s0, g, -gF[4] * g.pr_fix * tau * s0.p * (T(0.5) * (g.K + T(5))),
-                          cot[2].dq[0]);
-  }
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    const PointState<T>& sst = st[side];
-    const Prim<T> s = side == 0 ? sl : sr;
-    Mom<T> mh;
-    moments(s, g, side == 0 ? +1 : -1, mh);
-    T g4[5], g5[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      g4[i] = s.rho * (gF[i] * Fq[4] + gdF[i] * dFq[4]);
-      g5[i] = s.rho * (gF[i] * Fq[5] + gdF[i] * dFq[5]);
-    }
-    T M[15];
-    // V5 = rho <u psi psi^T> A: A_bar = M_u g5; Q_t_bar = M^{-1} A_bar / rho.
-    T Ab[5] = {0, 0, 0, 0, 0}, qtb[5];
-    mom_psipsi<1, 0, 0>(mh, M);
-    sym5_matvec_add(M, g5, Ab);
-    slope_solve(s, g, Ab, qtb);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) qtb[i] *= s.inv_rho;
-    time_derivative_vjp(s, g.h_r + sst.q[4] + s.dp, qtb, g, cot[side].dq);
-    // V4 = rho sum_d <u u_d psi psi^T> a_d: a_bar_d = M_d g4; dq_bar_d = M^{-1} a_bar_d / rho.
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T ab[5] = {0, 0, 0, 0, 0}, bb[5];
-      if (d == 0) mom_psipsi<2, 0, 0>(mh, M);
-      else if (d == 1) mom_psipsi<1, 1, 0>(mh, M);
-      else mom_psipsi<1, 0, 1>(mh, M);
-      sym5_matvec_add(M, g4, ab);
-      slope_solve(s, g, ab, bb);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) cot[side].dq[d][i] += bb[i] * s.inv_rho;
-    }
-  }
-}
-
-// Value cotangents of the full flux.  With G_k = gF Fq_k + gdF dFq_k the
-// weight of term V_k and phi_tau the sensitivity to tau (fit coefficients
-// and the Prandtl term), each value enters through one part only: q0 the
-// equilibrium part (and tau through mu0/p0), q_l and q_r their half-space
-// part (and tau through p_l, p_r).  One reverse-mode pass of each part
-// (flux_rev.cuh) gives the cotangents of all five values of its state.
-template <class T>
-__device__ __forceinline__ void flux_full_value_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
-                                                    const T gF[5], const T gdF[5], PointState<T>* cot) {
-  const Gas<Dual<T>> gd = dual_gas(gas);
-  const T cp = T(0.5) * (gas.K + T(5));
-  FullEq<T> e;
-  flux_full_eq(st[2], gas, e);
-  FullSide<T> hl, hr;
-  flux_full_side(st[0], gas, 0, hl);
-  flux_full_side(st[1], gas, 1, hr);
-  const T tau = collision_time_full(e.mu, e.p, hl.p, hr.p, gas, dt);
-  Dual<T> Fq[6], dFq[6];
-  fit_coefficients(Dual<T>(tau, T(1)), Dual<T>(dt), Fq, dFq);
-  T G[6][5];
-  T phi_tau = T(0);
-#pragma unroll
-  for (int k = 0; k < 6; ++k)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      G[k][i] = gF[i] * Fq[k].v + gdF[i] * dFq[k].v;
-      T Vki = k < 3 ? e.V[k][i] : hl.V[k - 3][i] + hr.V[k - 3][i];
-      if (k == 3 && i == 1) Vki -= gas.p_r;
-      phi_tau += (gF[i] * Fq[k].d + gdF[i] * dFq[k].d) * Vki;
-    }
-  const T wpr = gF[4] * gas.pr_fix * cp;  // F[4] -= pr_fix tau p0 c_p dT0
-  phi_tau -= wpr * e.p * e.dT;
-  const T dtau_dpl = collision_time_full(Dual<T>(e.mu), Dual<T>(e.p), Dual<T>(hl.p, T(1)),
-                                         Dual<T>(hr.p), gd, Dual<T>(dt)).d;
-  const T dtau_dpr = collision_time_full(Dual<T>(e.mu), Dual<T>(e.p), Dual<T>(hl.p),
-                                         Dual<T>(hr.p, T(1)), gd, Dual<T>(dt)).d;
-  // Equilibrium state q0: the part's outputs V0..V2, mu0, p0 and dT0 carry
-  // the cotangents G_k, phi_tau dtau/dmu0, phi_tau dtau/dp0 - (Prandtl term)
-  // and -(Prandtl term); one reverse pass (flux_rev.cuh).
-  {
-    T gV[3][5];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gV[k][i] = G[k][i];
-    const T gmu = phi_tau / e.p;
-    const T gp = -phi_tau * e.mu / (e.p * e.p) - wpr * tau * e.dT;
-    const T gdT = -wpr * tau * e.p;
-    flux_full_eq_value_rev(st[2], gas, gV, gmu, gp, gdT, cot[2].q);
-  }
-  // Left and right states: V3..V5 with G_3..G_5, the pressure with
-  // phi_tau dtau/dp; one reverse pass each.
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    T gV[3][5];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gV[k][i] = G[3 + k][i];
-    flux_full_side_value_rev(st[side], gas, side, gV, phi_tau * (side == 0 ? dtau_dpl : dtau_dpr),
-                             cot[side].q);
-  }
-}
-
 // Cotangents of the reconstructed Gauss-point states (value and the three
 // derivatives of each of NS states) from the flux cotangents (gF, gdF).
 template <class T, int FLUX>
 __device__ __forceinline__ void flux_vjp(const PointState<T>* st, const Gas<T>& gas, T dt,
                                          bool want_F, const T gF[5], const T gdF[5],
                                          PointState<T>* cot) {
-  if constexpr (FLUX == FLUX_FULL) {
-    flux_full_value_vjp(st, gas, dt, gF, gdF, cot);
-    flux_full_dq_vjp(st, gas, dt, gF, gdF, cot);
-  } else {
-    // Values q: one reverse-mode pass (flux_rev.cuh); slopes dq: the flux is
-    // linear in them, one transposed pass.
-    flux_smooth_value_rev(st[0], gas, want_F, gF, gdF, cot[0].q);
-    flux_smooth_dq_vjp(st[0], gas, want_F, gF, gdF, cot[0].dq);
-  }
+  if constexpr (FLUX == FLUX_FULL) flux_full_vjp(st, gas, dt, gF, gdF, cot);
+  else flux_smooth_rev(st[0], gas, want_F, gF, gdF, cot[0]);
 }
 
 template <class T>

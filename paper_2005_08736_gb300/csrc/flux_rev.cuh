@@ -1,15 +1,17 @@
-// Reverse-mode derivatives of the two parts of the full flux (physics.cuh)
-// with respect to the VALUES q of their state, the slopes dq held fixed:
-// the half-space part (flux_full_side) given cotangents gV of its three
-// moment vectors and gp of its pressure, and the equilibrium part
-// (flux_full_eq) given cotangents of its moment vectors, viscosity, pressure
-// and normal temperature slope -- the cotangent of q in one backward pass
-// each (instead of one forward-mode pass per component of q).  Every
-// function below is the transpose of the forward function it names, line by
-// line, with the forward intermediates recomputed.  No counterpart in the
-// paper.
+// Reverse-mode derivatives (vector-Jacobian products) of the fluxes at one
+// Gauss point with respect to their input states, values q and slopes dq
+// together, in one backward pass per part: the half-space parts of the full
+// flux (flux_full_side), its equilibrium part (flux_full_eq), the full flux
+// assembled from them with the collision time and the fit of Eq. (7)
+// (flux_full_vjp), the smooth flux (flux_smooth_rev) and the sign moments of
+// the compatibility state.  Every function is the transpose of the forward
+// function it names, with the forward intermediates recomputed; the
+// slopes enter each part linearly, through the same intermediates as the
+// values, so their cotangents come out of the same pass.  No counterpart in
+// the paper.
 #pragma once
 
+#include "dual.cuh"
 #include "physics.cuh"
 
 namespace hgks {
@@ -301,101 +303,6 @@ HGKS_HD void moments_rev(const Prim<T>& s, const Gas<T>& g, int half, const Mom<
   sb.theta += thb;
 }
 
-// Cotangent of the VALUES q of the state of flux_full_side (side 0: u > 0,
-// side 1: u < 0), the slopes held fixed, given the cotangents gV[3][5] of its
-// moment vectors V and gp of its pressure; added to qb.
-template <class T>
-HGKS_HD void flux_full_side_value_rev(const PointState<T>& st, const Gas<T>& g, int side, const T gV[3][5],
-                                      T gp, T qb[5]) {
-  const Prim<T> s = prim_of(st.q, g);
-  const T inv = s.inv_rho;
-  // forward: slopes a_d = slope_solve(s, dq_d inv), Q_t, A = slope_solve(s, Q_t inv)
-  T bd[3][5], a[3][5];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) bd[d][i] = st.dq[d][i] * inv;
-    slope_solve(s, g, bd[d], a[d]);
-  }
-  const T H = g.h_r + st.q[4] + s.dp;
-  T Qt[5];
-  state_time_derivative(s, H, st.dq, g, Qt);
-  T bA[5], A[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) bA[i] = Qt[i] * inv;
-  slope_solve(s, g, bA, A);
-  Mom<T> mh;
-  moments(s, g, side == 0 ? +1 : -1, mh);
-  // forward values needed by the transposes: ua, uA, and the four matrices
-  T M1[15], M2[15], M3[15], M4[15];
-  mom_psipsi<1, 0, 0>(mh, M1);
-  mom_psipsi<2, 0, 0>(mh, M2);
-  mom_psipsi<1, 1, 0>(mh, M3);
-  mom_psipsi<1, 0, 1>(mh, M4);
-  T ua[5] = {0, 0, 0, 0, 0}, uA[5] = {0, 0, 0, 0, 0};
-  sym5_matvec_add(M1, A, uA);
-  sym5_matvec_add(M2, a[0], ua);
-  sym5_matvec_add(M3, a[1], ua);
-  sym5_matvec_add(M4, a[2], ua);
-  // backward: V0 = rho M1[0..4], V1 = rho ua, V2 = rho uA, p = s.p
-  PrimBar<T> sb;
-  prim_bar_zero(sb);
-  sb.p += gp;
-  T M1b[15], M2b[15], M3b[15], M4b[15];
-#pragma unroll
-  for (int k = 0; k < 15; ++k) M1b[k] = M2b[k] = M3b[k] = M4b[k] = T(0);
-  T uab[5], uAb[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    sb.rho += gV[0][i] * M1[i] + gV[1][i] * ua[i] + gV[2][i] * uA[i];
-    M1b[i] += s.rho * gV[0][i];
-    uab[i] = s.rho * gV[1][i];
-    uAb[i] = s.rho * gV[2][i];
-  }
-  T Ab[5] = {0, 0, 0, 0, 0}, ab[3][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-  sym5_matvec_rev(M1, A, uAb, M1b, Ab);
-  sym5_matvec_rev(M2, a[0], uab, M2b, ab[0]);
-  sym5_matvec_rev(M3, a[1], uab, M3b, ab[1]);
-  sym5_matvec_rev(M4, a[2], uab, M4b, ab[2]);
-  MomBar<T> mb;
-#pragma unroll
-  for (int n = 0; n < 7; ++n) mb.u[n] = mb.v[n] = mb.w[n] = T(0);
-  mb.xi1 = mb.xi2 = T(0);
-  mom_psipsi_rev<1, 0, 0>(mh, M1b, mb);
-  mom_psipsi_rev<2, 0, 0>(mh, M2b, mb);
-  mom_psipsi_rev<1, 1, 0>(mh, M3b, mb);
-  mom_psipsi_rev<1, 0, 1>(mh, M4b, mb);
-  moments_rev(s, g, side == 0 ? +1 : -1, mh, mb, sb);
-  // A = slope_solve(s, Q_t inv), Q_t = -sum_d J_d(Q) dq_d
-  T bAb[5] = {0, 0, 0, 0, 0};
-  slope_solve_rev(s, g, bA, Ab, sb, bAb);
-  T Qtb[5], Hb = T(0);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    Qtb[i] = bAb[i] * inv;
-    sb.inv += bAb[i] * Qt[i];
-  }
-  // Q_t = -(J_0 dq_0 + J_1 dq_1 + J_2 dq_2)
-  T nQtb[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) nQtb[i] = -Qtb[i];
-  euler_jvp_rev_state<0>(s, H, st.dq[0], g, nQtb, sb, Hb);
-  euler_jvp_rev_state<1>(s, H, st.dq[1], g, nQtb, sb, Hb);
-  euler_jvp_rev_state<2>(s, H, st.dq[2], g, nQtb, sb, Hb);
-  // H = h_r + q4 + dp
-  qb[4] += Hb;
-  sb.dp += Hb;
-  // a_d = slope_solve(s, dq_d inv)
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    T bdb[5] = {0, 0, 0, 0, 0};
-    slope_solve_rev(s, g, bd[d], ab[d], sb, bdb);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) sb.inv += bdb[i] * st.dq[d][i];
-  }
-  prim_of_rev(st.q, s, g, sb, qb);
-}
-
 // euler_jvp<J> transposed in dQ (the state held fixed): adds J_J(Q)^T ob to dQb.
 template <int J, class T>
 HGKS_HD void euler_jvp_rev_dq(const Prim<T>& s, T H, const Gas<T>& g, const T ob[5], T dQb[5]) {
@@ -426,6 +333,152 @@ HGKS_HD void euler_jvp_rev_dq(const Prim<T>& s, T H, const Gas<T>& g, const T ob
     dQb[1 + i] += dub[i] * inv;
     dQb[0] += -dub[i] * U[i] * inv;
   }
+}
+
+// Cotangents of the values q and slopes dq of the state of flux_full_side
+// (side 0: u > 0, side 1: u < 0) as it enters the full flux through the
+// fit weights w_k = Fq[k] (F) and dFq[k] (dF) of its three moment vectors V_k
+// (flux_full_combine), given the flux cotangents gF, gdF; added to cot.  The
+// weights are dual numbers carrying d/dtau; returns the part's share of
+// gF . dF/dtau + gdF . d(dF)/dtau.  The cotangent of its pressure (through
+// tau) is applied by pressure_viscosity_rev.  The four moment matrices are
+// formed one at a time, forward and again backward, to keep few values live.
+template <class T>
+HGKS_HD T flux_full_side_rev(const PointState<T>& st, const Gas<T>& g, int side, const T gF[5],
+                             const T gdF[5], const Dual<T> Fq[3], const Dual<T> dFq[3], PointState<T>& cot) {
+  const Prim<T> s = prim_of(st.q, g);
+  const T inv = s.inv_rho;
+  // forward: slopes a_d = slope_solve(s, dq_d inv), Q_t, A = slope_solve(s, Q_t inv)
+  T a[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T bd[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) bd[i] = st.dq[d][i] * inv;
+    slope_solve(s, g, bd, a[d]);
+  }
+  const T H = g.h_r + st.q[4] + s.dp;
+  T Qt[5];
+  state_time_derivative(s, H, st.dq, g, Qt);
+  T bA[5], A[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) bA[i] = Qt[i] * inv;
+  slope_solve(s, g, bA, A);
+  const int half = side == 0 ? +1 : -1;
+  Mom<T> mh;
+  moments(s, g, half, mh);
+  // V0 = rho <u psi> (the first column of M1), V1 = rho ua, V2 = rho uA with
+  // M1 = <u psi psi^T>, uA = M1 A, ua = sum_d <u u_d psi psi^T> a_d.
+  T m1[5], ua[5] = {0, 0, 0, 0, 0}, uA[5] = {0, 0, 0, 0, 0};
+  {
+    T M[15];
+    mom_psipsi<1, 0, 0>(mh, M);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) m1[i] = M[i];
+    sym5_matvec_add(M, A, uA);
+  }
+  {
+    T M[15];
+    mom_psipsi<2, 0, 0>(mh, M);
+    sym5_matvec_add(M, a[0], ua);
+  }
+  {
+    T M[15];
+    mom_psipsi<1, 1, 0>(mh, M);
+    sym5_matvec_add(M, a[1], ua);
+  }
+  {
+    T M[15];
+    mom_psipsi<1, 0, 1>(mh, M);
+    sym5_matvec_add(M, a[2], ua);
+  }
+  // backward: the cotangents of V_k are gV_k = gF w_k + gdF dw_k
+  PrimBar<T> sb;
+  prim_bar_zero(sb);
+  T phi = T(0), uab[5], uAb[5], m1b[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T gv0 = gF[i] * Fq[0].v + gdF[i] * dFq[0].v, gt0 = gF[i] * Fq[0].d + gdF[i] * dFq[0].d;
+    const T gv1 = gF[i] * Fq[1].v + gdF[i] * dFq[1].v, gt1 = gF[i] * Fq[1].d + gdF[i] * dFq[1].d;
+    const T gv2 = gF[i] * Fq[2].v + gdF[i] * dFq[2].v, gt2 = gF[i] * Fq[2].d + gdF[i] * dFq[2].d;
+    phi += s.rho * (gt0 * m1[i] + gt1 * ua[i] + gt2 * uA[i]);
+    sb.rho += gv0 * m1[i] + gv1 * ua[i] + gv2 * uA[i];
+    m1b[i] = s.rho * gv0;
+    uab[i] = s.rho * gv1;
+    uAb[i] = s.rho * gv2;
+  }
+  MomBar<T> mb;
+#pragma unroll
+  for (int n = 0; n < 7; ++n) mb.u[n] = mb.v[n] = mb.w[n] = T(0);
+  mb.xi1 = mb.xi2 = T(0);
+  T Ab[5] = {0, 0, 0, 0, 0}, ab[3][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+  {
+    T M[15], Mb[15];
+    mom_psipsi<1, 0, 0>(mh, M);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Mb[k] = k < 5 ? m1b[k] : T(0);
+    sym5_matvec_rev(M, A, uAb, Mb, Ab);
+    mom_psipsi_rev<1, 0, 0>(mh, Mb, mb);
+  }
+  {
+    T M[15], Mb[15];
+    mom_psipsi<2, 0, 0>(mh, M);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Mb[k] = T(0);
+    sym5_matvec_rev(M, a[0], uab, Mb, ab[0]);
+    mom_psipsi_rev<2, 0, 0>(mh, Mb, mb);
+  }
+  {
+    T M[15], Mb[15];
+    mom_psipsi<1, 1, 0>(mh, M);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Mb[k] = T(0);
+    sym5_matvec_rev(M, a[1], uab, Mb, ab[1]);
+    mom_psipsi_rev<1, 1, 0>(mh, Mb, mb);
+  }
+  {
+    T M[15], Mb[15];
+    mom_psipsi<1, 0, 1>(mh, M);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Mb[k] = T(0);
+    sym5_matvec_rev(M, a[2], uab, Mb, ab[2]);
+    mom_psipsi_rev<1, 0, 1>(mh, Mb, mb);
+  }
+  moments_rev(s, g, half, mh, mb, sb);
+  // A = slope_solve(s, Q_t inv), Q_t = -sum_d J_d(Q) dq_d
+  T bAb[5] = {0, 0, 0, 0, 0};
+  slope_solve_rev(s, g, bA, Ab, sb, bAb);
+  T nQtb[5], Hb = T(0);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    nQtb[i] = -bAb[i] * inv;
+    sb.inv += bAb[i] * Qt[i];
+  }
+  // Q_t = -(J_0 dq_0 + J_1 dq_1 + J_2 dq_2): both the state and the slopes
+  euler_jvp_rev_state<0>(s, H, st.dq[0], g, nQtb, sb, Hb);
+  euler_jvp_rev_state<1>(s, H, st.dq[1], g, nQtb, sb, Hb);
+  euler_jvp_rev_state<2>(s, H, st.dq[2], g, nQtb, sb, Hb);
+  euler_jvp_rev_dq<0>(s, H, g, nQtb, cot.dq[0]);
+  euler_jvp_rev_dq<1>(s, H, g, nQtb, cot.dq[1]);
+  euler_jvp_rev_dq<2>(s, H, g, nQtb, cot.dq[2]);
+  // H = h_r + q4 + dp
+  cot.q[4] += Hb;
+  sb.dp += Hb;
+  // a_d = slope_solve(s, dq_d inv)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T bd[5], bdb[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) bd[i] = st.dq[d][i] * inv;
+    slope_solve_rev(s, g, bd, ab[d], sb, bdb);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      sb.inv += bdb[i] * st.dq[d][i];
+      cot.dq[d][i] += bdb[i] * inv;
+    }
+  }
+  prim_of_rev(st.q, s, g, sb, cot.q);
+  return phi;
 }
 
 // ns_viscous_flux transposed in the state and the viscosity (dq held fixed):
@@ -547,12 +600,50 @@ HGKS_HD void sign_moments_rev(const T dq[5], const Gas<T>& g, const T gS[5], T q
   prim_of_rev(dq, s, g, sb, qb);
 }
 
-// Cotangent of the VALUES q of the state of the smooth flux (flux_smooth),
-// the slopes held fixed, given the cotangents gF of F (if want_F) and gdF of
-// dF; added to qb.
+// c0 += cotangent of dq along n from tb, the cotangent of the temperature
+// slope dT0 = (dp0 - theta dq[0])/rho, dp0 = (gamma-1)(dq[4] - U.dm + |U|^2/2 dq[0]).
 template <class T>
-HGKS_HD void flux_smooth_value_rev(const PointState<T>& st0, const Gas<T>& g, bool want_F, const T gF[5],
-                                   const T gdF[5], T qb[5]) {
+HGKS_HD void temperature_slope_vjp(const Prim<T>& s, const Gas<T>& g, T tb, T c0[5]) {
+  const T inv = s.inv_rho;
+  const T dpb = tb * inv * g.gm1;
+  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+  c0[0] += -s.theta * tb * inv + T(0.5) * q2 * dpb;
+  c0[1] -= s.U * dpb;
+  c0[2] -= s.V * dpb;
+  c0[3] -= s.W * dpb;
+  c0[4] += dpb;
+}
+
+// cd += (d Fv / d dq)^T w for ns_viscous_flux (linear in dq).
+template <class T>
+HGKS_HD void ns_viscous_vjp(const Prim<T>& s, const Gas<T>& g, T mu, T heat_scale, const T w[5],
+                           T cd[3][5]) {
+  const T inv = s.inv_rho;
+  const T U[3] = {s.U, s.V, s.W};
+  const T s00 = -w[1] - w[4] * U[0], s01 = -w[2] - w[4] * U[1], s02 = -w[3] - w[4] * U[2];
+  const T divb = -mu * T(2) / (g.K + T(3)) * s00;
+  const T du0b[3] = {T(2) * mu * s00 + divb, mu * s01, mu * s02};
+  const T du10 = mu * s01, du20 = mu * s02, du11 = divb, du22 = divb;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cd[0][1 + i] += du0b[i] * inv;
+    cd[0][0] -= U[i] * du0b[i] * inv;
+  }
+  cd[1][1] += du10 * inv;
+  cd[1][2] += du11 * inv;
+  cd[1][0] -= (U[0] * du10 + U[1] * du11) * inv;
+  cd[2][1] += du20 * inv;
+  cd[2][3] += du22 * inv;
+  cd[2][0] -= (U[0] * du20 + U[2] * du22) * inv;
+  temperature_slope_vjp(s, g, -w[4] * heat_scale * mu * T(0.5) * (g.K + T(5)), cd[0]);
+}
+
+// Cotangents of the values q and slopes dq of the state of the smooth flux
+// (flux_smooth) given the cotangents gF of F (if want_F) and gdF of dF;
+// added to cot.
+template <class T>
+HGKS_HD void flux_smooth_rev(const PointState<T>& st0, const Gas<T>& g, bool want_F, const T gF[5],
+                             const T gdF[5], PointState<T>& cot) {
   const T* q = st0.q;
   const Prim<T> s = prim_of(q, g);
   const T H = g.h_r + q[4] + s.dp;
@@ -571,59 +662,80 @@ HGKS_HD void flux_smooth_value_rev(const PointState<T>& st0, const Gas<T>& g, bo
   euler_jvp_rev_state<0>(s, H, st0.dq[0], g, nQtb, sb, Hb);
   euler_jvp_rev_state<1>(s, H, st0.dq[1], g, nQtb, sb, Hb);
   euler_jvp_rev_state<2>(s, H, st0.dq[2], g, nQtb, sb, Hb);
+  euler_jvp_rev_dq<0>(s, H, g, nQtb, cot.dq[0]);
+  euler_jvp_rev_dq<1>(s, H, g, nQtb, cot.dq[1]);
+  euler_jvp_rev_dq<2>(s, H, g, nQtb, cot.dq[2]);
   if (want_F) {
     // F = Euler flux + viscous flux (mu = viscosity(s), heat flux scaled by 1/Pr)
-    euler_flux_dev_rev(s, q, g, gF, sb, qb);
+    euler_flux_dev_rev(s, q, g, gF, sb, cot.q);
     const T mu = viscosity(s, g);
     T mub = T(0);
     ns_viscous_flux_rev(s, st0.dq, g, mu, g.pr_fix + T(1), gF, sb, mub);
     if (g.visc_law == 1) sb.theta += mub * mu * g.visc_exp / s.theta;
+    ns_viscous_vjp(s, g, mu, g.pr_fix + T(1), gF, cot.dq);
   }
-  qb[4] += Hb;
+  cot.q[4] += Hb;
   sb.dp += Hb;
-  prim_of_rev(q, s, g, sb, qb);
+  prim_of_rev(q, s, g, sb, cot.q);
 }
 
-// Cotangent of the VALUES q of the equilibrium state of flux_full_eq, the
-// slopes held fixed, given the cotangents gV[3][5] of its moment vectors and
-// gmu, gp, gdT of its viscosity, pressure and normal temperature slope;
-// added to qb.
+// Cotangents of the values q and slopes dq of the equilibrium state of
+// flux_full_eq as it enters the full flux (flux_full_combine): its three
+// moment vectors V_k with the fit weights Fq[k] (F) and dFq[k] (dF), dual
+// numbers carrying d/dtau, and the Prandtl fix -wpr tau p0 dT0 of F[4]
+// (wpr = gF[4] pr_fix c_p), given the flux cotangents gF, gdF and the
+// collision time tau; added to cot.  Returns the part's share of
+// gF . dF/dtau + gdF . d(dF)/dtau.  The cotangents of mu0 and p0 through tau
+// are applied by pressure_viscosity_rev.
 template <class T>
-HGKS_HD void flux_full_eq_value_rev(const PointState<T>& st0, const Gas<T>& g, const T gV[3][5], T gmu,
-                                    T gp, T gdT, T qb[5]) {
+HGKS_HD T flux_full_eq_rev(const PointState<T>& st0, const Gas<T>& g, const T gF[5], const T gdF[5],
+                           const Dual<T> Fq[3], const Dual<T> dFq[3], T wpr, T tau, PointState<T>& cot) {
   const T* q = st0.q;
+  const T* d0 = st0.dq[0];
   const Prim<T> s = prim_of(q, g);
   const T H = g.h_r + q[4] + s.dp;
   T Qt[5];
   state_time_derivative(s, H, st0.dq, g, Qt);
+  // forward: V0 = Euler flux, V2 = J_n Q_t, V1 = -Fv(mu = p, Pr = 1) - V2, dT0
+  T V0[5], V2[5], Fv[5];
+  euler_flux_dev(s, q, g, V0);
+  euler_jvp<0>(s, H, Qt, g, V2);
+  ns_viscous_flux(s, st0.dq, g, s.p, T(1), Fv);
+  const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
+  const T dp0 = g.gm1 * (d0[4] - s.U * d0[1] - s.V * d0[2] - s.W * d0[3] + T(0.5) * q2 * d0[0]);
+  const T dT = (dp0 - s.theta * d0[0]) * s.inv_rho;
+  T phi = -wpr * s.p * dT;
+  T gV0[5], Fvb[5], V2b[5];  // cotangents of V0, of Fv and of V2 (V1 = -Fv - V2)
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const T gt0 = gF[i] * Fq[0].d + gdF[i] * dFq[0].d, gt1 = gF[i] * Fq[1].d + gdF[i] * dFq[1].d;
+    const T gt2 = gF[i] * Fq[2].d + gdF[i] * dFq[2].d;
+    phi += gt0 * V0[i] + gt1 * (-Fv[i] - V2[i]) + gt2 * V2[i];
+    const T gv1 = gF[i] * Fq[1].v + gdF[i] * dFq[1].v, gv2 = gF[i] * Fq[2].v + gdF[i] * dFq[2].v;
+    gV0[i] = gF[i] * Fq[0].v + gdF[i] * dFq[0].v;
+    Fvb[i] = -gv1;
+    V2b[i] = gv2 - gv1;
+  }
+  // backward; the Prandtl fix gives p0 and dT0 the cotangents -wpr tau dT0
+  // and -wpr tau p0
+  const T gdT = -wpr * tau * s.p;
   PrimBar<T> sb;
   prim_bar_zero(sb);
   T Hb = T(0);
-  // dT = (dp0 - theta dq00) inv, dp0 = gm1 (dq0[4] - U.dq0m + |U|^2/2 dq00)
   {
-    const T* d0 = st0.dq[0];
-    const T q2 = s.U * s.U + s.V * s.V + s.W * s.W;
-    const T dp0 = g.gm1 * (d0[4] - s.U * d0[1] - s.V * d0[2] - s.W * d0[3] + T(0.5) * q2 * d0[0]);
     const T dp0b = gdT * s.inv_rho;
     sb.theta += -gdT * d0[0] * s.inv_rho;
     sb.inv += gdT * (dp0 - s.theta * d0[0]);
     sb.U += dp0b * g.gm1 * (s.U * d0[0] - d0[1]);
     sb.V += dp0b * g.gm1 * (s.V * d0[0] - d0[2]);
     sb.W += dp0b * g.gm1 * (s.W * d0[0] - d0[3]);
+    temperature_slope_vjp(s, g, gdT, cot.dq[0]);
   }
-  // p = s.p; mu = viscosity(s)
-  sb.p += gp;
-  if (g.visc_law == 1) sb.theta += gmu * viscosity(s, g) * g.visc_exp / s.theta;
-  // V1 = -Fv - V2 with Fv = ns_viscous_flux(s, dq, mu = p, 1); V2 = J_n(Q) Q_t
-  T Fvb[5], V2b[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    Fvb[i] = -gV[1][i];
-    V2b[i] = gV[2][i] - gV[1][i];
-  }
+  sb.p += -wpr * tau * dT;
   T mub = T(0);
   ns_viscous_flux_rev(s, st0.dq, g, s.p, T(1), Fvb, sb, mub);
   sb.p += mub;
+  ns_viscous_vjp(s, g, s.p, T(1), Fvb, cot.dq);
   euler_jvp_rev_state<0>(s, H, Qt, g, V2b, sb, Hb);
   T Qtb[5] = {0, 0, 0, 0, 0};
   euler_jvp_rev_dq<0>(s, H, g, V2b, Qtb);
@@ -634,11 +746,87 @@ HGKS_HD void flux_full_eq_value_rev(const PointState<T>& st0, const Gas<T>& g, c
   euler_jvp_rev_state<0>(s, H, st0.dq[0], g, nQtb, sb, Hb);
   euler_jvp_rev_state<1>(s, H, st0.dq[1], g, nQtb, sb, Hb);
   euler_jvp_rev_state<2>(s, H, st0.dq[2], g, nQtb, sb, Hb);
-  euler_flux_dev_rev(s, q, g, gV[0], sb, qb);
+  euler_jvp_rev_dq<0>(s, H, g, nQtb, cot.dq[0]);
+  euler_jvp_rev_dq<1>(s, H, g, nQtb, cot.dq[1]);
+  euler_jvp_rev_dq<2>(s, H, g, nQtb, cot.dq[2]);
+  euler_flux_dev_rev(s, q, g, gV0, sb, cot.q);
   // H = h_r + q4 + dp
-  qb[4] += Hb;
+  cot.q[4] += Hb;
   sb.dp += Hb;
+  prim_of_rev(q, s, g, sb, cot.q);
+  return phi;
+}
+
+// Adds to qb the cotangent of the values q through the pressure (gp) and the
+// viscosity (gmu) of their state.
+template <class T>
+HGKS_HD void pressure_viscosity_rev(const T q[5], const Gas<T>& g, T gp, T gmu, T qb[5]) {
+  const Prim<T> s = prim_of(q, g);
+  PrimBar<T> sb;
+  prim_bar_zero(sb);
+  sb.p += gp;
+  if (g.visc_law == 1) sb.theta += gmu * viscosity(s, g) * g.visc_exp / s.theta;
   prim_of_rev(q, s, g, sb, qb);
+}
+
+// Cotangents of the three states (st[0] = l, st[1] = r, st[2] = the
+// compatibility state; values and slopes) of the full flux (flux_full) given
+// the cotangents gF of F and gdF of dF; added to cot.  The fit weights
+// Fq_k, dFq_k of Eq. (7) are formed as dual numbers in tau; each part runs
+// one reverse pass with the cotangents gF Fq_k + gdF dFq_k of its moment
+// vectors and returns its share of phi = gF . dF/dtau + gdF . d(dF)/dtau;
+// phi then reaches the states through tau = mu0/p0 + C |p_l - p_r|/(p_l +
+// p_r) dt.
+template <class T>
+HGKS_HD void flux_full_vjp(const PointState<T>* st, const Gas<T>& g, T dt, const T gF[5], const T gdF[5],
+                           PointState<T>* cot) {
+  T mu0, p0, pl, pr;
+  {
+    const Prim<T> s0 = prim_of(st[2].q, g);
+    mu0 = viscosity(s0, g);
+    p0 = s0.p;
+    pl = prim_of(st[0].q, g).p;
+    pr = prim_of(st[1].q, g).p;
+  }
+  const T tau = collision_time_full(mu0, p0, pl, pr, g, dt);
+  Dual<T> Fq[6], dFq[6];
+  fit_coefficients(Dual<T>(tau, T(1)), Dual<T>(dt), Fq, dFq);
+  const T wpr = gF[4] * g.pr_fix * (T(0.5) * (g.K + T(5)));
+  T phi = flux_full_eq_rev(st[2], g, gF, gdF, Fq, dFq, wpr, tau, cot[2]);
+  // V_3 is the half-space sum minus the reference Euler flux (p_r in component 1).
+  phi -= (gF[1] * Fq[3].d + gdF[1] * dFq[3].d) * g.p_r;
+  // One copy of the half-space code for both sides: the side's state in and
+  // its cotangent out through selects.
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const PointState<T> x = side == 0 ? st[0] : st[1];
+    PointState<T> c;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      c.q[i] = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) c.dq[d][i] = T(0);
+    }
+    phi += flux_full_side_rev(x, g, side, gF, gdF, Fq + 3, dFq + 3, c);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (side == 0) cot[0].q[i] += c.q[i];
+      else cot[1].q[i] += c.q[i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (side == 0) cot[0].dq[d][i] += c.dq[d][i];
+        else cot[1].dq[d][i] += c.dq[d][i];
+      }
+    }
+  }
+  const Gas<Dual<T>> gd = dual_gas(g);
+  const T dtau_dpl =
+      collision_time_full(Dual<T>(mu0), Dual<T>(p0), Dual<T>(pl, T(1)), Dual<T>(pr), gd, Dual<T>(dt)).d;
+  const T dtau_dpr =
+      collision_time_full(Dual<T>(mu0), Dual<T>(p0), Dual<T>(pl), Dual<T>(pr, T(1)), gd, Dual<T>(dt)).d;
+  pressure_viscosity_rev(st[2].q, g, -phi * mu0 / (p0 * p0), phi / p0, cot[2].q);
+  pressure_viscosity_rev(st[0].q, g, phi * dtau_dpl, T(0), cot[0].q);
+  pressure_viscosity_rev(st[1].q, g, phi * dtau_dpr, T(0), cot[1].q);
 }
 
 }  // namespace hgks
