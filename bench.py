@@ -219,6 +219,56 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_ratio(prec: int, flux: int, reps: int = 5) -> dict:
+    """Adjoint step / forward step at 64^3 (isotropic, kappa0 = 4, Ma_t 0.5,
+    WENO-Z, power-law viscosity, numerical collision time), dt fixed."""
+    import torch
+    from paper_2005_08736_gb300 import inputs
+    from paper_2005_08736_gb300.solver import Config, Simulation
+
+    c = inputs.isotropic_constants(k0=4.0, mach_t=0.5)
+    cfg = Config(64, 64, 64, prec=prec, recon=2, flux=flux, tau_num_C=1.0, prandtl=0.7, visc=1,
+                 mu_ref=c["mu0"], T_ref=c["T0"], visc_exp=0.76, p_ref=c["p0"], rho_ref=1.0)
+    sim = Simulation(cfg)
+    sim.init_primitive(inputs.isotropic(64, 0, k0=4.0))
+    dt = 2e-3  # a fixed step (the timing does not depend on its size)
+
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n
+
+    sim.step(2, dt)
+    fwd = timed(lambda: sim.step(1, dt, sync=False), 2 * reps)
+    lam = torch.randn(cfg.shape, dtype=torch.float64, device="cuda")
+    o = torch.empty_like(lam)
+    sim.adjoint_step(dt, lam, o)
+    adj = timed(lambda: sim.adjoint_step(dt, lam, o), reps)
+    sim.close()
+    return {"forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj, "adjoint_over_forward": adj / fwd}
+
+
+def run_adjoint(args):
+    """--adjoint: the 64^3 adjoint / forward ratios (full and smooth flux, FP32
+    and FP64); with --quick only --precision and --flux, one adjoint step
+    after one warm-up (for profiling)."""
+    from paper_2005_08736_gb300 import build
+    build.build()
+    if args.quick:
+        prec = 1 if args.precision == "fp32" else 0
+        flux = 1 if args.flux == "full" else 0
+        print(json.dumps({f"adjoint_64_wenoz_{args.flux}_{args.precision}": adjoint_ratio(prec, flux, 1)}))
+        return
+    out = {}
+    for flux, fname in ((1, "full"), (0, "smooth")):
+        for prec, pname in ((1, "fp32"), (0, "fp64")):
+            out[f"adjoint_64_wenoz_{fname}_{pname}"] = adjoint_ratio(prec, flux)
+    print(json.dumps(out, indent=1))
+
+
 def extra_workloads(steps: int, peak_tflops: float | None = None):
     """The other measured configurations: isotropic turbulence 256^3 (WENO-Z +
     full flux, FP32), the stretched wall-bounded channel 128 x 128 x 96 (FP32),
@@ -279,17 +329,7 @@ def extra_workloads(steps: int, peak_tflops: float | None = None):
     sim.close()
     # Adjoint / forward time ratio at 64^3.
     for prec, name in ((0, "fp64"), (1, "fp32")):
-        acfg = iso_cfg(64, prec, k0=4.0)
-        sim = Simulation(acfg)
-        sim.init_primitive(inputs.isotropic(64, 0, k0=4.0))
-        dt = 2e-3  # a fixed step (the timing does not depend on its size)
-        fwd = timed(lambda: sim.step(1, dt, sync=False), 5)
-        lam = torch.randn(acfg.shape, dtype=torch.float64, device="cuda")
-        o = torch.empty_like(lam)
-        adj = timed(lambda: sim.adjoint_step(dt, lam, o), 3)
-        out[f"adjoint_64_wenoz_full_{name}"] = {"forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj,
-                                                "adjoint_over_forward": adj / fwd}
-        sim.close()
+        out[f"adjoint_64_wenoz_full_{name}"] = adjoint_ratio(prec, 1)
     # Ensemble of 24 isotropic instances, grids {32, 48, 64, 96}^3 by seed, FP32.
     sims, cells = [], 0
     for seed in range(24):
@@ -789,6 +829,8 @@ def main():
                     help="--gradcheck: C of the numerical collision time (default 1)")
     ap.add_argument("--gradcheck", action="store_true",
                     help="adjoint gradient of E_k(50) at 64^3 against central differences")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="adjoint / forward step time at 64^3 (full and smooth flux, FP32 and FP64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the isotropic, channel, adjoint and ensemble measurements")
     ap.add_argument("--quick", action="store_true",
@@ -802,6 +844,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.gradcheck:
         run_gradcheck(args)
+    elif args.adjoint:
+        run_adjoint(args)
     elif args.history:
         run_history(args)
     elif args.errors:
