@@ -535,7 +535,11 @@ def run_gradcheck(args):
         fsim.step(K, dt)
         return kinetic_energy(fsim.state(device=True), fsim).item()
 
-    h0 = 1e-6 * u0.norm().item()
+    unorm = u0.norm().item()
+    h0 = 1e-6 * unorm
+    # --fd-scales: the step sizes h / |u0| of the central differences along
+    # every direction (default: 1e-6, and 1e-7 along the first four).
+    scales = [float(x) for x in args.fd_scales.split(",")] if args.fd_scales else None
     rows = []
     for k, seed in enumerate(range(100, 116)):
         gen = torch.Generator(device="cuda").manual_seed(seed)
@@ -543,12 +547,20 @@ def run_gradcheck(args):
         v /= v.norm()
         ad64, ad32 = (g64 * v).sum().item(), (g32 * v).sum().item()
         row = {"seed": seed, "adjoint_fp64": ad64, "adjoint_fp32": ad32}
-        for h in ((h0, h0 / 10) if k < 4 else (h0,)):
+        hs = [sc * unorm for sc in scales] if scales else ((h0, h0 / 10) if k < 4 else (h0,))
+        for h in hs:
             fd = (J_of(u0 + h * v) - J_of(u0 - h * v)) / (2 * h)
             row[f"fd_h{h:.1e}"] = fd
             row[f"rel_fp64_h{h:.1e}"] = abs(ad64 - fd) / abs(fd)
         rows.append(row)
     out["directions"] = rows
+    if scales:
+        h0 = scales[0] * unorm
+        out["fd_rel_err_fp64_by_h"] = []
+        for sc in scales:
+            rel = [r[f"rel_fp64_h{sc * unorm:.1e}"] for r in rows]
+            out["fd_rel_err_fp64_by_h"].append({"h_over_norm": sc, "h": sc * unorm, "max": max(rel),
+                                                "median": float(np.median(rel))})
     rel = [r[f"rel_fp64_h{h0:.1e}"] for r in rows]
     out["fd_rel_err_fp64"] = {"h": h0, "max": max(rel), "median": float(np.median(rel))}
     out["fd_rel_err_fp32_adjoint"] = float(np.median(
@@ -829,6 +841,8 @@ def main():
                     help="--gradcheck: C of the numerical collision time (default 1)")
     ap.add_argument("--gradcheck", action="store_true",
                     help="adjoint gradient of E_k(50) at 64^3 against central differences")
+    ap.add_argument("--fd-scales", default="",
+                    help="--gradcheck: comma-separated step sizes h / |u0| of the differences")
     ap.add_argument("--adjoint", action="store_true",
                     help="adjoint / forward step time at 64^3 (full and smooth flux, FP32 and FP64)")
     ap.add_argument("--no-extras", action="store_true",
