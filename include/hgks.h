@@ -62,7 +62,7 @@ typedef enum { HGKS_FP64 = 0, HGKS_FP32 = 1 } hgks_prec;
 typedef enum { HGKS_FORCE_CONSTANT = 0, HGKS_FORCE_MASS_FLUX = 1 } hgks_force;
 
 typedef struct {
-  int nx, ny, nz;                  /* interior cells; >= 6 on every axis */
+  int nx, ny, nz;                  /* interior cells; 6 .. 65529 on every axis */
   double x0, lx, y0, ly, z0, lz;   /* origin and extent of the box */
   int y_stretch;                   /* 0 uniform y; 1 tanh mapping of Sec. 3.3 (ly = 2, else E_INVAL) */
   double stretch_b;                /* b_g of the mapping */

@@ -303,15 +303,20 @@ cudaError_t enqueue_channel_rows(const Engine& e) {
 
 template <class T>
 cudaError_t enqueue_from_fp64(const Engine& e, const double* src, int conservative) {
-  k_from_prim<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
-      src, static_cast<T*>(e.q), grid_of(e), e.cfg.rho_ref, e.cfg.p_ref, e.cfg.gamma, conservative);
+  const GridDev g = grid_of(e);
+  const dim3 grid((g.n[0] + 255) / 256, g.n[1], g.n[2]);
+  const double inv_gm1 = 1.0 / (e.cfg.gamma - 1.0);
+  k_from_prim<T><<<grid, 256, 0, e.stream>>>(src, static_cast<T*>(e.q), g, e.cfg.rho_ref,
+                                              e.cfg.p_ref / (e.cfg.gamma - 1.0), inv_gm1, conservative);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t enqueue_to_fp64(const Engine& e, double* dst) {
-  k_to_cons<T><<<blocks_for(e.N, 256), 256, 0, e.stream>>>(
-      static_cast<const T*>(e.q), dst, grid_of(e), e.cfg.rho_ref, e.cfg.p_ref, e.cfg.gamma);
+  const GridDev g = grid_of(e);
+  const dim3 grid((g.n[0] + 255) / 256, g.n[1], g.n[2]);
+  k_to_cons<T><<<grid, 256, 0, e.stream>>>(static_cast<const T*>(e.q), dst, g, e.cfg.rho_ref,
+                                            e.cfg.p_ref / (e.cfg.gamma - 1.0));
   return cudaGetLastError();
 }
 

@@ -53,6 +53,8 @@ size_t elem_size(const hgks_config& c) { return c.prec == HGKS_FP32 ? 4 : 8; }
 
 std::string hgks::validate_config(const hgks_config& c) {
   if (c.nx < 6 || c.ny < 6 || c.nz < 6) return "every axis needs at least 6 cells";
+  // Kernels launch one grid row per padded y and z index (grid dimensions <= 65535).
+  if (c.nx > 65529 || c.ny > 65529 || c.nz > 65529) return "every axis has at most 65529 cells";
   if (!(c.gamma > 1.0)) return "gamma must exceed 1";
   if (!(c.prandtl > 0.0)) return "Prandtl number must be positive";
   if (!(c.cfl > 0.0)) return "cfl must be positive";

@@ -521,15 +521,17 @@ __global__ void __launch_bounds__(256) k_force_apply(T* __restrict__ q, const T*
 // ----------------------------------------------------------- state in/out ---
 
 // FP64 primitive (rho, u, v, w, p) [5][N] -> deviation conservative (padded interior).
+// FP64 state in / out, one thread per cell of an x row: grid (ceil(nx /
+// 256), ny, nz), so that the cell's coordinates come without integer
+// division; inv_gm1 = 1 / (gamma - 1) and E_r = p_r / (gamma - 1) are formed
+// on the host.
 template <class T>
 __global__ void k_from_prim(const double* __restrict__ prim, T* __restrict__ q, GridDev g,
-                            double rho_r, double p_r, double gamma, int conservative) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  const int nx = g.n[0], ny = g.n[1];
-  const int x = int(c % nx);
-  const long long r = c / nx;
-  const int y = int(r % ny), z = int(r / ny);
+                            double rho_r, double E_r, double inv_gm1, int conservative) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.n[0]) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long c = ((long long)z * g.n[1] + y) * g.n[0] + x;
   const long long pi = pad_index(g, x, y, z);
   double Q[5];
   if (conservative) {
@@ -542,30 +544,28 @@ __global__ void k_from_prim(const double* __restrict__ prim, T* __restrict__ q, 
     Q[1] = rho * u;
     Q[2] = rho * v;
     Q[3] = rho * w;
-    Q[4] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+    Q[4] = p * inv_gm1 + 0.5 * rho * (u * u + v * v + w * w);
   }
   q[pi] = T(Q[0] - rho_r);
   q[g.P + pi] = T(Q[1]);
   q[2 * g.P + pi] = T(Q[2]);
   q[3 * g.P + pi] = T(Q[3]);
-  q[4 * g.P + pi] = T(Q[4] - p_r / (gamma - 1.0));
+  q[4 * g.P + pi] = T(Q[4] - E_r);
 }
 
 template <class T>
-__global__ void k_to_cons(const T* __restrict__ q, double* __restrict__ out, GridDev g,
-                          double rho_r, double p_r, double gamma) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  const int nx = g.n[0], ny = g.n[1];
-  const int x = int(c % nx);
-  const long long r = c / nx;
-  const int y = int(r % ny), z = int(r / ny);
+__global__ void k_to_cons(const T* __restrict__ q, double* __restrict__ out, GridDev g, double rho_r,
+                          double E_r) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.n[0]) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long c = ((long long)z * g.n[1] + y) * g.n[0] + x;
   const long long pi = pad_index(g, x, y, z);
   out[c] = rho_r + double(q[pi]);
   out[g.N + c] = double(q[g.P + pi]);
   out[2 * g.N + c] = double(q[2 * g.P + pi]);
   out[3 * g.N + c] = double(q[3 * g.P + pi]);
-  out[4 * g.N + c] = p_r / (gamma - 1.0) + double(q[4 * g.P + pi]);
+  out[4 * g.N + c] = E_r + double(q[4 * g.P + pi]);
 }
 
 }  // namespace hgks

@@ -69,7 +69,7 @@ int main(void) {
                     ctypes.sizeof(_lib.HgksChannel), _lib.HgksChannel.C_f.offset]
 
 
-@pytest.mark.parametrize("field,value", [("nx", 5), ("gamma", 1.0), ("prandtl", 0.0), ("cfl", -1.0),
+@pytest.mark.parametrize("field,value", [("nx", 5), ("nz", 65530), ("gamma", 1.0), ("prandtl", 0.0), ("cfl", -1.0),
                                          ("recon", 7), ("flux", 2), ("prec", 3), ("p_ref", 0.0),
                                          ("bc_y", 4), ("y_stretch", 1)])
 def test_invalid_configurations_are_rejected_before_any_device_work(lib, field, value):
