@@ -42,84 +42,84 @@ __device__ __forceinline__ void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5
   // Candidate polynomials: d pR_k / dq and d pL_k / dq (times 6).
   const T dR[3][5] = {{2, -7, 11, 0, 0}, {0, -1, 5, 2, 0}, {0, 0, 2, 5, -1}};
   const T dL[3][5] = {{0, 0, 11, -7, 2}, {0, 2, 5, -1, 0}, {-1, 5, 2, 0, 0}};
-  if (MODE == RECON_LINEAR) {
+  if constexpr (MODE == RECON_LINEAR) {
     const T w[3] = {T(0.1), T(0.6), T(0.3)};
 #pragma unroll
     for (int j = 0; j < 5; ++j)
 #pragma unroll
       for (int k = 0; k < 3; ++k) cot[j] += (gR * w[k] * dR[k][j] + gL * w[k] * dL[k][j]) * c6;
-    return;
-  }
-  T pR[3], pL[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    pR[k] = T(0);
-    pL[k] = T(0);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      pR[k] += dR[k][j] * q[j];
-      pL[k] += dL[k][j] * q[j];
-    }
-    pR[k] *= c6;
-    pL[k] *= c6;
-  }
-  const T sv[3] = {q[0] - T(2) * q[1] + q[2], q[1] - T(2) * q[2] + q[3], q[2] - T(2) * q[3] + q[4]};
-  const T tv[3] = {q[0] - T(4) * q[1] + T(3) * q[2], q[1] - q[3], T(3) * q[2] - T(4) * q[3] + q[4]};
-  const T c13 = T(13) / T(12);
-  T bt[3], f[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) bt[k] = c13 * sv[k] * sv[k] + T(0.25) * tv[k] * tv[k];
-  T tau5 = T(0), sg = T(0);
-  if (MODE == RECON_WENO_JS) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f[k] = T(1) / ((T(1e-6) + bt[k]) * (T(1e-6) + bt[k]));
   } else {
-    const T d02 = bt[0] - bt[2];
-    tau5 = tabs(d02);
-    sg = d02 > T(0) ? T(1) : (d02 < T(0) ? T(-1) : T(0));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f[k] = T(1) + tau5 / (bt[k] + T(1e-20));
-  }
-  const T aR[3] = {T(0.1) * f[0], T(0.6) * f[1], T(0.3) * f[2]};
-  const T aL[3] = {T(0.1) * f[2], T(0.6) * f[1], T(0.3) * f[0]};
-  const T iSR = T(1) / (aR[0] + aR[1] + aR[2]), iSL = T(1) / (aL[0] + aL[1] + aL[2]);
-  const T qR = (aR[0] * pR[0] + aR[1] * pR[1] + aR[2] * pR[2]) * iSR;
-  const T qL = (aL[0] * pL[0] + aL[1] * pL[1] + aL[2] * pL[2]) * iSL;
-  T gaR[3], gaL[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gaR[k] = gR * (pR[k] - qR) * iSR;
-    gaL[k] = gL * (pL[k] - qL) * iSL;
-  }
-  const T gf[3] = {T(0.1) * gaR[0] + T(0.3) * gaL[2], T(0.6) * (gaR[1] + gaL[1]),
-                   T(0.3) * gaR[2] + T(0.1) * gaL[0]};
-  T gb[3];
-  if (MODE == RECON_WENO_JS) {
-#pragma unroll
+    T pR[3], pL[3];
+  #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const T e = T(1e-6) + bt[k];
-      gb[k] = gf[k] * T(-2) / (e * e * e);
+      pR[k] = T(0);
+      pL[k] = T(0);
+  #pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        pR[k] += dR[k][j] * q[j];
+        pL[k] += dL[k][j] * q[j];
+      }
+      pR[k] *= c6;
+      pL[k] *= c6;
     }
-  } else {
-    T gtau = T(0);
-#pragma unroll
+    const T sv[3] = {q[0] - T(2) * q[1] + q[2], q[1] - T(2) * q[2] + q[3], q[2] - T(2) * q[3] + q[4]};
+    const T tv[3] = {q[0] - T(4) * q[1] + T(3) * q[2], q[1] - q[3], T(3) * q[2] - T(4) * q[3] + q[4]};
+    const T c13 = T(13) / T(12);
+    T bt[3], f[3];
+  #pragma unroll
+    for (int k = 0; k < 3; ++k) bt[k] = c13 * sv[k] * sv[k] + T(0.25) * tv[k] * tv[k];
+    T tau5 = T(0), sg = T(0);
+    if (MODE == RECON_WENO_JS) {
+  #pragma unroll
+      for (int k = 0; k < 3; ++k) f[k] = T(1) / ((T(1e-6) + bt[k]) * (T(1e-6) + bt[k]));
+    } else {
+      const T d02 = bt[0] - bt[2];
+      tau5 = tabs(d02);
+      sg = d02 > T(0) ? T(1) : (d02 < T(0) ? T(-1) : T(0));
+  #pragma unroll
+      for (int k = 0; k < 3; ++k) f[k] = T(1) + tau5 / (bt[k] + T(1e-20));
+    }
+    const T aR[3] = {T(0.1) * f[0], T(0.6) * f[1], T(0.3) * f[2]};
+    const T aL[3] = {T(0.1) * f[2], T(0.6) * f[1], T(0.3) * f[0]};
+    const T iSR = T(1) / (aR[0] + aR[1] + aR[2]), iSL = T(1) / (aL[0] + aL[1] + aL[2]);
+    const T qR = (aR[0] * pR[0] + aR[1] * pR[1] + aR[2] * pR[2]) * iSR;
+    const T qL = (aL[0] * pL[0] + aL[1] * pL[1] + aL[2] * pL[2]) * iSL;
+    T gaR[3], gaL[3];
+  #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const T ie = T(1) / (bt[k] + T(1e-20));
-      gb[k] = -gf[k] * tau5 * ie * ie;
-      gtau += gf[k] * ie;
+      gaR[k] = gR * (pR[k] - qR) * iSR;
+      gaL[k] = gL * (pL[k] - qL) * iSL;
     }
-    gb[0] += gtau * sg;
-    gb[2] -= gtau * sg;
-  }
-  // beta_k = 13/12 s_k^2 + t_k^2 / 4, s_k and t_k linear in q.
-  const T ds[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
-  const T dt[3][5] = {{1, -4, 3, 0, 0}, {0, 1, 0, -1, 0}, {0, 0, 3, -4, 1}};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const T gs = gb[k] * T(2) * c13 * sv[k], gt = gb[k] * T(0.5) * tv[k];
-    const T gpR = gR * aR[k] * iSR * c6, gpL = gL * aL[k] * iSL * c6;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) cot[j] += gs * ds[k][j] + gt * dt[k][j] + gpR * dR[k][j] + gpL * dL[k][j];
+    const T gf[3] = {T(0.1) * gaR[0] + T(0.3) * gaL[2], T(0.6) * (gaR[1] + gaL[1]),
+                     T(0.3) * gaR[2] + T(0.1) * gaL[0]};
+    T gb[3];
+    if (MODE == RECON_WENO_JS) {
+  #pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T e = T(1e-6) + bt[k];
+        gb[k] = gf[k] * T(-2) / (e * e * e);
+      }
+    } else {
+      T gtau = T(0);
+  #pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T ie = T(1) / (bt[k] + T(1e-20));
+        gb[k] = -gf[k] * tau5 * ie * ie;
+        gtau += gf[k] * ie;
+      }
+      gb[0] += gtau * sg;
+      gb[2] -= gtau * sg;
+    }
+    // beta_k = 13/12 s_k^2 + t_k^2 / 4, s_k and t_k linear in q.
+    const T ds[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
+    const T dt[3][5] = {{1, -4, 3, 0, 0}, {0, 1, 0, -1, 0}, {0, 0, 3, -4, 1}};
+  #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T gs = gb[k] * T(2) * c13 * sv[k], gt = gb[k] * T(0.5) * tv[k];
+      const T gpR = gR * aR[k] * iSR * c6, gpL = gL * aL[k] * iSL * c6;
+  #pragma unroll
+      for (int j = 0; j < 5; ++j) cot[j] += gs * ds[k][j] + gt * dt[k][j] + gpR * dR[k][j] + gpL * dL[k][j];
+    }
   }
 }
 
