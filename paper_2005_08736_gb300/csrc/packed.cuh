@@ -13,6 +13,7 @@
 #pragma once
 
 #include "physics.cuh"
+#include "recon.cuh"
 
 namespace hgks {
 
@@ -153,6 +154,70 @@ __device__ __forceinline__ void flux_smooth_x2(const PointStateX2& st, const Gas
 #pragma unroll
     for (int i = 0; i < 5; ++i) Fs[i] += F[i].x + F[i].y;
   }
+}
+
+// WENO5 end values with nonlinear weights (weno5_pair, WENO-JS or WENO-Z) of
+// two columns at once: the candidate polynomials, smoothness indicators,
+// weights and combinations in pair arithmetic; |beta0 - beta2| and the
+// reciprocals per half.
+template <int MODE>
+__device__ __forceinline__ void weno5_pair_x2(float2 q0, float2 q1, float2 q2, float2 q3, float2 q4,
+                                              float2& qL, float2& qR) {
+  const float2 c6 = bc2(1.f / 6.f);
+  const float2 pR0 = mul2(fma2(bc2(2.f), q0, fma2(bc2(-7.f), q1, mul2(bc2(11.f), q2))), c6);
+  const float2 pR1 = mul2(fma2(bc2(-1.f), q1, fma2(bc2(5.f), q2, mul2(bc2(2.f), q3))), c6);
+  const float2 pR2 = mul2(fma2(bc2(2.f), q2, fma2(bc2(5.f), q3, mul2(bc2(-1.f), q4))), c6);
+  const float2 pL0 = mul2(fma2(bc2(2.f), q4, fma2(bc2(-7.f), q3, mul2(bc2(11.f), q2))), c6);
+  const float2 pL1 = mul2(fma2(bc2(-1.f), q3, fma2(bc2(5.f), q2, mul2(bc2(2.f), q1))), c6);
+  const float2 pL2 = mul2(fma2(bc2(2.f), q2, fma2(bc2(5.f), q1, mul2(bc2(-1.f), q0))), c6);
+  const float2 s0 = fma2(bc2(-2.f), q1, add2(q0, q2)), t0 = fma2(bc2(-4.f), q1, fma2(bc2(3.f), q2, q0));
+  const float2 s1 = fma2(bc2(-2.f), q2, add2(q1, q3)), t1 = sub2(q1, q3);
+  const float2 s2 = fma2(bc2(-2.f), q3, add2(q2, q4)), t2 = fma2(bc2(3.f), q2, fma2(bc2(-4.f), q3, q4));
+  const float2 c13 = bc2(13.f / 12.f), qt = bc2(0.25f);
+  const float2 b0 = fma2(mul2(c13, s0), s0, mul2(mul2(qt, t0), t0));
+  const float2 b1 = fma2(mul2(c13, s1), s1, mul2(mul2(qt, t1), t1));
+  const float2 b2 = fma2(mul2(c13, s2), s2, mul2(mul2(qt, t2), t2));
+  float2 f0, f1, f2;  // weight factors of beta0, beta1, beta2
+  if constexpr (MODE == RECON_WENO_JS) {
+    const float2 e = bc2(1e-6f);
+    const float2 e0 = add2(e, b0), e1 = add2(e, b1), e2 = add2(e, b2);
+    f0 = rcp2(mul2(e0, e0));
+    f1 = rcp2(mul2(e1, e1));
+    f2 = rcp2(mul2(e2, e2));
+  } else {
+    const float2 e = bc2(1e-20f);
+    const float2 d02 = sub2(b0, b2);
+    const float2 tau5 = make_float2(fabsf(d02.x), fabsf(d02.y));
+    f0 = fma2(tau5, rcp2(add2(b0, e)), bc2(1.f));
+    f1 = fma2(tau5, rcp2(add2(b1, e)), bc2(1.f));
+    f2 = fma2(tau5, rcp2(add2(b2, e)), bc2(1.f));
+  }
+  {
+    const float2 a0 = mul2(bc2(0.1f), f0), a1 = mul2(bc2(0.6f), f1), a2 = mul2(bc2(0.3f), f2);
+    qR = mul2(fma2(a0, pR0, fma2(a1, pR1, mul2(a2, pR2))), rcp2(add2(add2(a0, a1), a2)));
+  }
+  {
+    const float2 a0 = mul2(bc2(0.1f), f2), a1 = mul2(bc2(0.6f), f1), a2 = mul2(bc2(0.3f), f0);
+    qL = mul2(fma2(a0, pL0, fma2(a1, pL1, mul2(a2, pL2))), rcp2(add2(add2(a0, a1), a2)));
+  }
+}
+
+// Tangential reconstruction with nonlinear weights (tangential, WENO modes)
+// of two columns at once: values v[m] and derivatives d[m] at the two Gauss
+// abscissae from the quadratic through the WENO5 end values and the average.
+template <int MODE>
+__device__ __forceinline__ void tangential_weno_x2(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4,
+                                                   float2 v[2], float2 d[2]) {
+  float2 qL, qR;
+  weno5_pair_x2<MODE>(f0, f1, f2, f3, f4, qL, qR);
+  const float2 gs = bc2(0.5f / 1.7320508075688772f);
+  const float2 b = sub2(qR, qL);
+  const float2 c = fma2(bc2(3.f), add2(qL, qR), mul2(bc2(-6.f), f2));
+  v[0] = fma2(mul2(b, bc2(-1.f)), gs, f2);
+  v[1] = fma2(b, gs, f2);
+  const float2 c2 = mul2(mul2(bc2(2.f), c), gs);
+  d[0] = sub2(b, c2);
+  d[1] = add2(b, c2);
 }
 
 }  // namespace hgks
