@@ -423,6 +423,58 @@ HGKS_HD void t1_pass_group(const T* ff, T* tb, int at, int st1, int grp) {
   }
 }
 
+// t1_pass_group in FP32 with nonlinear weights: the five fields of the
+// group two at a time in packed FP32 pairs (fields 0 and 1, 2 and 3), the
+// fifth alone; the same outputs and layout.
+template <int MODE, int NV, int NH>
+__device__ __forceinline__ void t1_pass_group_wx2(const float* ff, float* tb, int at, int st1, int grp) {
+  const bool state = grp < NV / 5;
+  // first field of the group in ff
+  const int kf = state ? 5 * grp : NV + 5 * (grp - NV / 5);
+#pragma unroll
+  for (int i = 0; i < 4; i += 2) {
+    const float* sa = ff + (kf + i) * NH + at;
+    const float* sb = sa + NH;
+    float2 f[5], v[2], dd[2];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) f[j] = make_float2(sa[(j - 2) * st1], sb[(j - 2) * st1]);
+    tangential_weno_x2<MODE>(f[0], f[1], f[2], f[3], f[4], v, dd);
+    if (state) {
+      const int k = kf + i;
+      tb[(4 * k + 0) * NH + at] = v[0].x;
+      tb[(4 * k + 1) * NH + at] = v[1].x;
+      tb[(4 * k + 2) * NH + at] = dd[0].x;
+      tb[(4 * k + 3) * NH + at] = dd[1].x;
+      tb[(4 * k + 4) * NH + at] = v[0].y;
+      tb[(4 * k + 5) * NH + at] = v[1].y;
+      tb[(4 * k + 6) * NH + at] = dd[0].y;
+      tb[(4 * k + 7) * NH + at] = dd[1].y;
+    } else {
+      const int j = kf - NV + i;  // state field whose normal slope this is
+      tb[(4 * NV + 2 * j + 0) * NH + at] = v[0].x;
+      tb[(4 * NV + 2 * j + 1) * NH + at] = v[1].x;
+      tb[(4 * NV + 2 * j + 2) * NH + at] = v[0].y;
+      tb[(4 * NV + 2 * j + 3) * NH + at] = v[1].y;
+    }
+  }
+  {
+    const float* src = ff + (kf + 4) * NH + at;
+    float v[2], dd[2];
+    tangential<MODE>(src[-2 * st1], src[-st1], src[0], src[st1], src[2 * st1], v, dd);
+    if (state) {
+      const int k = kf + 4;
+      tb[(4 * k + 0) * NH + at] = v[0];
+      tb[(4 * k + 1) * NH + at] = v[1];
+      tb[(4 * k + 2) * NH + at] = dd[0];
+      tb[(4 * k + 3) * NH + at] = dd[1];
+    } else {
+      const int j = kf - NV + 4;
+      tb[(4 * NV + 2 * j + 0) * NH + at] = v[0];
+      tb[(4 * NV + 2 * j + 1) * NH + at] = v[1];
+    }
+  }
+}
+
 // t1_pass_group with the packed layout of the last phase (FP32, linear
 // weights): the outputs at the two t1 abscissae are stored side by side as a
 // float2 -- state field k: pair plane 2k (values), 2k+1 (t1-derivatives);
