@@ -179,8 +179,24 @@ HGKS_HD void face_fields_cells(const T qa[5][6], T hl, T hr, const Gas<T>& gas,
   for (int i = 0; i < 5; ++i) {
     const T q0 = qa[i][0], q1 = qa[i][1], q2 = qa[i][2], q3 = qa[i][3], q4 = qa[i][4], q5 = qa[i][5];
     T Li, Ri, Lr, Rr;
-    weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
-    weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+    bool packed = false;
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR) {
+      // Both cells' WENO5 pairs in the halves of packed FP32 pairs.
+      float2 L2, R2;
+      weno5_pair_x2<recon_of<MODE>()>(make_float2(q0, q1), make_float2(q1, q2), make_float2(q2, q3),
+                                      make_float2(q3, q4), make_float2(q4, q5), L2, R2);
+      Li = L2.x;
+      Ri = R2.x;
+      Lr = L2.y;
+      Rr = R2.y;
+      packed = true;
+    }
+#endif
+    if (!packed) {
+      weno5_pair<MODE>(q0, q1, q2, q3, q4, Li, Ri);
+      weno5_pair<MODE>(q1, q2, q3, q4, q5, Lr, Rr);
+    }
     Ql[i] = Ri;
     Qr[i] = Lr;
     Dl[i] = (T(4) * Ri + T(2) * Li - T(6) * q2) * rhl;
