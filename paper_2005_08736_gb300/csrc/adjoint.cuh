@@ -25,6 +25,7 @@
 
 #include "dual.cuh"
 #include "flux_rev.cuh"
+#include "packed.cuh"
 #include "sweep.cuh"
 
 namespace hgks {
@@ -121,6 +122,109 @@ __device__ __forceinline__ void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5
       for (int j = 0; j < 5; ++j) cot[j] += gs * ds[k][j] + gt * dt[k][j] + gpR * dR[k][j] + gpL * dL[k][j];
     }
   }
+}
+
+// weno5_pair_vjp (nonlinear weights) for two stencils at once, in the
+// halves of packed FP32 pairs: the forward quantities and the reverse pass
+// of the scalar function, pairwise; |beta0 - beta2|, its sign and the
+// reciprocals per half.
+template <int MODE>
+__device__ __forceinline__ void weno5_pair_vjp_x2(const float2 q[5], float2 gL, float2 gR, float2 cot[5]) {
+  const float c6 = 1.f / 6.f;
+  const float dR[3][5] = {{2, -7, 11, 0, 0}, {0, -1, 5, 2, 0}, {0, 0, 2, 5, -1}};
+  const float dL[3][5] = {{0, 0, 11, -7, 2}, {0, 2, 5, -1, 0}, {-1, 5, 2, 0, 0}};
+  float2 pR[3], pL[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    pR[k] = bc2(0.f);
+    pL[k] = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      if (dR[k][j] != 0.f) pR[k] = fma2(bc2(dR[k][j]), q[j], pR[k]);
+      if (dL[k][j] != 0.f) pL[k] = fma2(bc2(dL[k][j]), q[j], pL[k]);
+    }
+    pR[k] = mul2(pR[k], bc2(c6));
+    pL[k] = mul2(pL[k], bc2(c6));
+  }
+  const float2 sv[3] = {fma2(bc2(-2.f), q[1], add2(q[0], q[2])), fma2(bc2(-2.f), q[2], add2(q[1], q[3])),
+                        fma2(bc2(-2.f), q[3], add2(q[2], q[4]))};
+  const float2 tv[3] = {fma2(bc2(-4.f), q[1], fma2(bc2(3.f), q[2], q[0])), sub2(q[1], q[3]),
+                        fma2(bc2(3.f), q[2], fma2(bc2(-4.f), q[3], q[4]))};
+  const float c13 = 13.f / 12.f;
+  float2 bt[3], f[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) bt[k] = fma2(mul2(bc2(c13), sv[k]), sv[k], mul2(mul2(bc2(0.25f), tv[k]), tv[k]));
+  float2 tau5 = bc2(0.f), sg = bc2(0.f);
+  if constexpr (MODE == RECON_WENO_JS) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 e = add2(bc2(1e-6f), bt[k]);
+      f[k] = rcp2(mul2(e, e));
+    }
+  } else {
+    const float2 d02 = sub2(bt[0], bt[2]);
+    tau5 = make_float2(fabsf(d02.x), fabsf(d02.y));
+    sg = make_float2(d02.x > 0.f ? 1.f : (d02.x < 0.f ? -1.f : 0.f), d02.y > 0.f ? 1.f : (d02.y < 0.f ? -1.f : 0.f));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = fma2(tau5, rcp2(add2(bt[k], bc2(1e-20f))), bc2(1.f));
+  }
+  const float2 aR[3] = {mul2(bc2(0.1f), f[0]), mul2(bc2(0.6f), f[1]), mul2(bc2(0.3f), f[2])};
+  const float2 aL[3] = {mul2(bc2(0.1f), f[2]), mul2(bc2(0.6f), f[1]), mul2(bc2(0.3f), f[0])};
+  const float2 iSR = rcp2(add2(add2(aR[0], aR[1]), aR[2])), iSL = rcp2(add2(add2(aL[0], aL[1]), aL[2]));
+  const float2 qR = mul2(fma2(aR[0], pR[0], fma2(aR[1], pR[1], mul2(aR[2], pR[2]))), iSR);
+  const float2 qL = mul2(fma2(aL[0], pL[0], fma2(aL[1], pL[1], mul2(aL[2], pL[2]))), iSL);
+  float2 gaR[3], gaL[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gaR[k] = mul2(mul2(gR, sub2(pR[k], qR)), iSR);
+    gaL[k] = mul2(mul2(gL, sub2(pL[k], qL)), iSL);
+  }
+  const float2 gf[3] = {fma2(bc2(0.1f), gaR[0], mul2(bc2(0.3f), gaL[2])), mul2(bc2(0.6f), add2(gaR[1], gaL[1])),
+                        fma2(bc2(0.3f), gaR[2], mul2(bc2(0.1f), gaL[0]))};
+  float2 gb[3];
+  if constexpr (MODE == RECON_WENO_JS) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 e = add2(bc2(1e-6f), bt[k]);
+      gb[k] = mul2(mul2(gf[k], bc2(-2.f)), rcp2(mul2(mul2(e, e), e)));
+    }
+  } else {
+    float2 gtau = bc2(0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 ie = rcp2(add2(bt[k], bc2(1e-20f)));
+      gb[k] = mul2(mul2(mul2(gf[k], bc2(-1.f)), tau5), mul2(ie, ie));
+      gtau = fma2(gf[k], ie, gtau);
+    }
+    gb[0] = fma2(gtau, sg, gb[0]);
+    gb[2] = fma2(mul2(gtau, bc2(-1.f)), sg, gb[2]);
+  }
+  // beta_k = 13/12 s_k^2 + t_k^2 / 4, s_k and t_k linear in q.
+  const float ds[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
+  const float dt[3][5] = {{1, -4, 3, 0, 0}, {0, 1, 0, -1, 0}, {0, 0, 3, -4, 1}};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 gs = mul2(gb[k], mul2(bc2(2.f * c13), sv[k])), gt = mul2(gb[k], mul2(bc2(0.5f), tv[k]));
+    const float2 gpR = mul2(mul2(gR, aR[k]), mul2(iSR, bc2(c6))), gpL = mul2(mul2(gL, aL[k]), mul2(iSL, bc2(c6)));
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      if (ds[k][j] != 0.f) cot[j] = fma2(gs, bc2(ds[k][j]), cot[j]);
+      if (dt[k][j] != 0.f) cot[j] = fma2(gt, bc2(dt[k][j]), cot[j]);
+      if (dR[k][j] != 0.f) cot[j] = fma2(gpR, bc2(dR[k][j]), cot[j]);
+      if (dL[k][j] != 0.f) cot[j] = fma2(gpL, bc2(dL[k][j]), cot[j]);
+    }
+  }
+}
+
+// tangential_vjp (nonlinear weights) of two five-point stencils at once.
+template <int MODE>
+__device__ __forceinline__ void tangential_vjp_x2(const float2 f[5], const float2 gv[2], const float2 gd[2],
+                                                  float2 cot[5]) {
+  const float gs = 0.5f / 1.7320508075688772f;
+  const float2 gb = fma2(bc2(gs), sub2(gv[1], gv[0]), add2(gd[0], gd[1]));
+  const float2 gc = mul2(bc2(2.f * gs), sub2(gd[1], gd[0]));
+  cot[2] = add2(cot[2], fma2(bc2(-6.f), gc, add2(gv[0], gv[1])));
+  weno5_pair_vjp_x2<MODE>(f, fma2(bc2(3.f), gc, mul2(gb, bc2(-1.f))), fma2(bc2(3.f), gc, gb), cot);
 }
 
 // cot[j] += sum_m gv[m] dv[m]/df_j + gd[m] dd[m]/df_j for the tangential
@@ -301,7 +405,10 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
       const int it = u % items, grp = u / items;
       const int hp2 = t1P ? 2 + it % TP : it % HP;
       const int hs2 = t1P ? it / TP : 2 + it / HP;
-      t1_pass_group<T, MODE, NV, NH>(ff, tb, hs2 * HP + hp2, st1, grp);
+      if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR)
+        t1_pass_group_wx2<recon_of<MODE>(), NV, NH>(ff, tb, hs2 * HP + hp2, st1, grp);
+      else
+        t1_pass_group<T, MODE, NV, NH>(ff, tb, hs2 * HP + hp2, st1, grp);
     }
     __syncthreads();
 
@@ -411,7 +518,52 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
     __syncthreads();
 
     // ---------------- R2: transposed t1 pass ----------------
-    // One field of one point per work item.
+    // One field of one point per work item; FP32 with nonlinear weights: a
+    // pair of fields per item, transposed in packed FP32 pairs.
+    if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR) {
+      for (int u = tid; u < items * NV; u += NT) {
+        const int it = u % items, kp = u / items;
+        const int hp2 = t1P ? 2 + it % TP : it % HP;
+        const int hs2 = t1P ? it / TP : 2 + it / HP;
+        const int at = hs2 * HP + hp2;
+        float gvs[2][2], gds[2][2];  // [field of the pair][abscissa]
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int k = 2 * kp + e2;
+          if (k < NV) {
+            gvs[e2][0] = tbc[(4 * k + 0) * NH + at];
+            gvs[e2][1] = tbc[(4 * k + 1) * NH + at];
+            gds[e2][0] = tbc[(4 * k + 2) * NH + at];
+            gds[e2][1] = tbc[(4 * k + 3) * NH + at];
+          } else {
+            gvs[e2][0] = tbc[(4 * NV + 2 * (k - NV) + 0) * NH + at];
+            gvs[e2][1] = tbc[(4 * NV + 2 * (k - NV) + 1) * NH + at];
+            gds[e2][0] = gds[e2][1] = 0.f;
+          }
+        }
+        if (gvs[0][0] == 0.f && gvs[0][1] == 0.f && gds[0][0] == 0.f && gds[0][1] == 0.f &&
+            gvs[1][0] == 0.f && gvs[1][1] == 0.f && gds[1][0] == 0.f && gds[1][1] == 0.f)
+          continue;
+        const float2 gv2[2] = {make_float2(gvs[0][0], gvs[1][0]), make_float2(gvs[0][1], gvs[1][1])};
+        const float2 gd2[2] = {make_float2(gds[0][0], gds[1][0]), make_float2(gds[0][1], gds[1][1])};
+        const T* src0 = ff + (2 * kp) * NH + at;
+        const T* src1 = src0 + NH;
+        float2 fv[5], cot[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          fv[j] = make_float2(src0[(j - 2) * st1], src1[(j - 2) * st1]);
+          cot[j] = make_float2(0.f, 0.f);
+        }
+        tangential_vjp_x2<recon_of<MODE>()>(fv, gv2, gd2, cot);
+        T* dst0 = ffc + (2 * kp) * NH + at;
+        T* dst1 = dst0 + NH;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          atomicAdd(dst0 + (j - 2) * st1, cot[j].x);
+          atomicAdd(dst1 + (j - 2) * st1, cot[j].y);
+        }
+      }
+    } else
     for (int u = tid; u < items * 2 * NV; u += NT) {
       const int it = u % items, k = u / items;
       const int hp2 = t1P ? 2 + it % TP : it % HP;
@@ -531,8 +683,24 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
         gq[2] -= T(15) * r6 * gD0;
         gq[3] += T(15) * r6 * gD0;
         gq[4] -= r6 * gD0;
-        weno5_pair_vjp<MODE>(&qc[0], gLi, gRi, &gq[0]);
-        weno5_pair_vjp<MODE>(&qc[1], gLr, gRr, &gq[1]);
+        if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR) {
+          // both cells' pairs in the halves of packed FP32 pairs
+          float2 q2[5], c2[5];
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            q2[j] = make_float2(qc[j], qc[j + 1]);
+            c2[j] = make_float2(0.f, 0.f);
+          }
+          weno5_pair_vjp_x2<recon_of<MODE>()>(q2, make_float2(gLi, gLr), make_float2(gRi, gRr), c2);
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            gq[j] += c2[j].x;
+            gq[j + 1] += c2[j].y;
+          }
+        } else {
+          weno5_pair_vjp<MODE>(&qc[0], gLi, gRi, &gq[0]);
+          weno5_pair_vjp<MODE>(&qc[1], gLr, gRr, &gq[1]);
+        }
         T* accv = a.acc + ax.gv[i] * a.g.P + cb;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
