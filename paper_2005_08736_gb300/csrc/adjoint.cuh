@@ -456,6 +456,37 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
           PointState<T> g0;
+          if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR &&
+                        FLUX == FLUX_FULL) {
+            // FP32 with nonlinear weights, full flux: the thread's calls of
+            // pairs j and j + 4 in the halves of one packed evaluation (the
+            // smooth-flux tile keeps its two CTAs per SM on the scalar form).
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int a0 = 2 * jj, a1 = 2 * jj + 1;
+              const int b0 = 2 * jj + 8, b1 = 2 * jj + 9 < 15 ? 2 * jj + 9 : 2 * jj + 8;
+              const T* sa = tb + t2_row<NV>(s, m2 ? a1 : a0, m1) * NH + at3;
+              const T* sb = tb + t2_row<NV>(s, m2 ? b1 : b0, m1) * NH + at3;
+              float2 f[5], v[2], dv[2];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) f[k] = make_float2(sa[(k - 2) * st2], sb[(k - 2) * st2]);
+              tangential_weno_x2<recon_of<MODE>()>(f[0], f[1], f[2], f[3], f[4], v, dv);
+              {
+                const T ov = m2 ? v[1].x : v[0].x, od = m2 ? dv[1].x : dv[0].x;
+                const T rv = __shfl_xor_sync(kAll, m2 ? v[0].x : v[1].x, 1);
+                const T rd = __shfl_xor_sync(kAll, m2 ? dv[0].x : dv[1].x, 1);
+                t2_assign(g0, a0, m2 ? rv : ov, m2 ? rd : od, rh1, rh2);
+                t2_assign(g0, a1, m2 ? ov : rv, m2 ? od : rd, rh1, rh2);
+              }
+              {
+                const T ov = m2 ? v[1].y : v[0].y, od = m2 ? dv[1].y : dv[0].y;
+                const T rv = __shfl_xor_sync(kAll, m2 ? v[0].y : v[1].y, 1);
+                const T rd = __shfl_xor_sync(kAll, m2 ? dv[0].y : dv[1].y, 1);
+                t2_assign(g0, b0, m2 ? rv : ov, m2 ? rd : od, rh1, rh2);
+                if (b1 != b0) t2_assign(g0, b1, m2 ? ov : rv, m2 ? od : rd, rh1, rh2);
+              }
+            }
+          } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int c0 = 2 * j, c1 = 2 * j + 1 < 15 ? 2 * j + 1 : 2 * j;
@@ -467,6 +498,7 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
             const T rd = __shfl_xor_sync(kAll, m2 ? dv[0] : dv[1], 1);
             t2_assign(g0, c0, m2 ? rv : ov, m2 ? rd : od, rh1, rh2);
             if (c1 != c0) t2_assign(g0, c1, m2 ? ov : rv, m2 ? od : rd, rh1, rh2);
+          }
           }
           if (s == 0) st[0] = g0;
           else if (NS > 1 && s == 1) st[NS > 1 ? 1 : 0] = g0;
@@ -489,6 +521,68 @@ __global__ void __launch_bounds__(NT) k_sweep_adj(AdjArgs<T> a) {
           PointState<T> cs = ct[0];
           if (NS > 1 && s == 1) cs = ct[NS > 1 ? 1 : 0];
           if (NS > 2 && s == 2) cs = ct[NS > 2 ? 2 : 0];
+          if constexpr (std::is_same<T, float>::value && recon_of<MODE>() != RECON_LINEAR &&
+                        FLUX == FLUX_FULL) {
+            // The same pairs j and j + 4 as the forward pass, transposed in
+            // one packed evaluation.
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int a0 = 2 * jj, a1 = 2 * jj + 1;
+              const int b0 = 2 * jj + 8, b1 = 2 * jj + 9 < 15 ? 2 * jj + 9 : 2 * jj + 8;
+              T gva[2], gda[2], gvb[2], gdb[2];
+              {
+                T v0, d0, v1, d1;
+                t2_cot(cs, a0, rh1, rh2, v0, d0);
+                t2_cot(cs, a1, rh1, rh2, v1, d1);
+                const T rv = __shfl_xor_sync(kAll, m2 ? v0 : v1, 1);
+                const T rd = __shfl_xor_sync(kAll, m2 ? d0 : d1, 1);
+                const T ov = m2 ? v1 : v0, od = m2 ? d1 : d0;
+                gva[0] = m2 ? rv : ov;
+                gva[1] = m2 ? ov : rv;
+                gda[0] = m2 ? rd : od;
+                gda[1] = m2 ? od : rd;
+              }
+              {
+                T v0, d0, v1, d1;
+                t2_cot(cs, b0, rh1, rh2, v0, d0);
+                t2_cot(cs, b1, rh1, rh2, v1, d1);
+                const T rv = __shfl_xor_sync(kAll, m2 ? v0 : v1, 1);
+                const T rd = __shfl_xor_sync(kAll, m2 ? d0 : d1, 1);
+                const T ov = m2 ? v1 : v0, od = m2 ? d1 : d0;
+                const bool owner = b1 != b0 || m2 == 0;  // the odd last call: one thread
+                gvb[0] = owner ? (m2 ? rv : ov) : T(0);
+                gvb[1] = owner ? (m2 ? ov : rv) : T(0);
+                gdb[0] = owner ? (m2 ? rd : od) : T(0);
+                gdb[1] = owner ? (m2 ? od : rd) : T(0);
+              }
+              const bool anya = gva[0] != T(0) || gva[1] != T(0) || gda[0] != T(0) || gda[1] != T(0);
+              const bool anyb = gvb[0] != T(0) || gvb[1] != T(0) || gdb[0] != T(0) || gdb[1] != T(0);
+              if (f_valid && (anya || anyb)) {
+                const int rowa = t2_row<NV>(s, m2 ? a1 : a0, m1), rowb = t2_row<NV>(s, m2 ? b1 : b0, m1);
+                const T* sa = tb + rowa * NH + at3;
+                const T* sb = tb + rowb * NH + at3;
+                float2 f[5], cot[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                  f[k] = make_float2(sa[(k - 2) * st2], sb[(k - 2) * st2]);
+                  cot[k] = make_float2(0.f, 0.f);
+                }
+                const float2 gv2[2] = {make_float2(gva[0], gvb[0]), make_float2(gva[1], gvb[1])};
+                const float2 gd2[2] = {make_float2(gda[0], gdb[0]), make_float2(gda[1], gdb[1])};
+                tangential_vjp_x2<recon_of<MODE>()>(f, gv2, gd2, cot);
+                if (anya) {
+                  T* dst = tbc + rowa * NH + at3;
+#pragma unroll
+                  for (int k = 0; k < 5; ++k) atomicAdd(dst + (k - 2) * st2, cot[k].x);
+                }
+                if (anyb) {
+                  T* dst = tbc + rowb * NH + at3;
+#pragma unroll
+                  for (int k = 0; k < 5; ++k) atomicAdd(dst + (k - 2) * st2, cot[k].y);
+                }
+              }
+            }
+          } else
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int c0 = 2 * j, c1 = 2 * j + 1 < 15 ? 2 * j + 1 : 2 * j;

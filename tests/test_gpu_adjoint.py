@@ -190,18 +190,22 @@ def test_autograd_window_with_checkpoints_kinetic_energy():
         assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-12, (ad, fd)
 
 
-def test_fp32_adjoint_agrees_with_fp64():
+@pytest.mark.parametrize("recon,flux", [(1, 1), (2, 1), (2, 0)])
+def test_fp32_adjoint_agrees_with_fp64(recon, flux):
+    # The FP32 sweep evaluates the WENO reconstructions and their transposes
+    # two at a time in packed pairs; against FP64 it agrees to FP32 rounding
+    # propagated through two steps (measured ~1e-6).
     n, K, dt = (12, 10, 9), 2, 0.05
     out = []
     for prec in (0, 1):
-        cfg, q0 = setup(n, 1, 1, prec)
+        cfg, q0 = setup(n, recon, flux, prec)
         sim = Simulation(cfg)
         g = torch.Generator(device="cuda").manual_seed(5)
         r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
         out.append(adjoint_gradient(sim, q0, K, dt, r))
     err = ((out[1] - out[0]).abs().amax() / out[0].abs().amax()).item()
-    print(f"FP32 adjoint vs FP64 adjoint: relative L-inf {err:.3e}")
-    assert err < 1e-3, err
+    print(f"FP32 adjoint vs FP64 adjoint (recon {recon}, flux {flux}): relative L-inf {err:.3e}")
+    assert err < 1e-4, err
 
 
 def test_adjoint_rejects_walls():
