@@ -194,7 +194,9 @@ def test_autograd_window_with_checkpoints_kinetic_energy():
 def test_fp32_adjoint_agrees_with_fp64(recon, flux):
     # The FP32 sweep evaluates the WENO reconstructions and their transposes
     # two at a time in packed pairs; against FP64 it agrees to FP32 rounding
-    # propagated through two steps (measured ~1e-6).
+    # propagated through two steps (measured ~1e-6), except where WENO-Z's
+    # |beta0 - beta2| is near zero and FP32 can take the other side of the
+    # kink (full flux: measured 3.9e-5, 1.1e-4 with the scalar form).
     n, K, dt = (12, 10, 9), 2, 0.05
     out = []
     for prec in (0, 1):
@@ -205,7 +207,7 @@ def test_fp32_adjoint_agrees_with_fp64(recon, flux):
         out.append(adjoint_gradient(sim, q0, K, dt, r))
     err = ((out[1] - out[0]).abs().amax() / out[0].abs().amax()).item()
     print(f"FP32 adjoint vs FP64 adjoint (recon {recon}, flux {flux}): relative L-inf {err:.3e}")
-    assert err < 1e-4, err
+    assert err < (5e-4 if recon == 2 and flux == 1 else 1e-5), err
 
 
 def test_adjoint_rejects_walls():
