@@ -192,8 +192,10 @@ __device__ __forceinline__ void weno5_pair_vjp_x2(const float2 q[5], float2 gL, 
     float2 gtau = bc2(0.f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+      // (-gf tau5 ie) ie, in the scalar order: ie^2 alone overflows FP32
+      // where beta vanishes (ie = 1e20), and tau5 = 0 there.
       const float2 ie = rcp2(add2(bt[k], bc2(1e-20f)));
-      gb[k] = mul2(mul2(mul2(gf[k], bc2(-1.f)), tau5), mul2(ie, ie));
+      gb[k] = mul2(mul2(mul2(mul2(gf[k], bc2(-1.f)), tau5), ie), ie);
       gtau = fma2(gf[k], ie, gtau);
     }
     gb[0] = fma2(gtau, sg, gb[0]);

@@ -210,6 +210,28 @@ def test_fp32_adjoint_agrees_with_fp64(recon, flux):
     assert err < (5e-4 if recon == 2 and flux == 1 else 1e-5), err
 
 
+def test_fp32_wenoz_adjoint_is_finite_on_constant_stencils():
+    # Where the data are constant along a stencil every smoothness indicator
+    # vanishes, so WENO-Z's 1/(beta + 1e-20) is 1e20 and its square exceeds
+    # the FP32 range; the transposes must form (-gf tau5 ie) ie in that
+    # order (tau5 = 0 there) to stay finite.  FP32 and FP64 are not compared
+    # here: next to the slab FP64 resolves smoothness indicators of rounding
+    # size (~1e-32) that FP32 holds as 0, and WENO-Z's derivative there (the
+    # weights jump, tau5/beta being scale-invariant) differs between them.
+    n, K, dt = (16, 10, 9), 1, 0.05
+    for prec in (0, 1):
+        cfg = Config(*n, prec=prec, recon=2, flux=1, tau_num_C=1.0, mu_ref=5e-3, p_ref=1.0,
+                     prandtl=0.7, visc=1, T_ref=1.0, visc_exp=0.76)
+        prim = inputs.random_smooth(n, seed=21, amp=0.15, kmax=1)
+        prim[:, :, :, 4:12] = np.array([1.0, 0.1, 0.0, 0.0, 1.0])[:, None, None, None]
+        q0 = torch.from_numpy(np.ascontiguousarray(oracle.conservative(prim, 1.4))).cuda()
+        sim = Simulation(cfg)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        r = torch.randn(cfg.shape, dtype=torch.float64, device="cuda", generator=g)
+        lam = adjoint_gradient(sim, q0, K, dt, r)
+        assert torch.isfinite(lam).all(), prec
+
+
 def test_adjoint_rejects_walls():
     from paper_2005_08736_gb300._lib import HGKS_E_UNSUPPORTED, HgksError
     cfg = Config(8, 8, 8, prec=0, ly=2.0, y0=-1.0, bc_y=1, T_wall=100 / 1.4)
