@@ -37,7 +37,7 @@ namespace hgks {
 // f = (eps + beta)^-2; WENO-Z: f = 1 + tau5/(beta + eps), tau5 = |beta0 -
 // beta2|, d|x|/dx = sign(x) with sign(0) = 0), each a quadratic form of q.
 template <int MODE_, class T>
-__device__ __forceinline__ void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5]) {
+HGKS_HD void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5]) {
   constexpr int MODE = recon_of<MODE_>();
   const T c6 = T(1) / T(6);
   // Candidate polynomials: d pR_k / dq and d pL_k / dq (times 6).
@@ -129,7 +129,7 @@ __device__ __forceinline__ void weno5_pair_vjp(const T q[5], T gL, T gR, T cot[5
 // of the scalar function, pairwise; |beta0 - beta2|, its sign and the
 // reciprocals per half.
 template <int MODE>
-__device__ __forceinline__ void weno5_pair_vjp_x2(const float2 q[5], float2 gL, float2 gR, float2 cot[5]) {
+HGKS_HD void weno5_pair_vjp_x2(const float2 q[5], float2 gL, float2 gR, float2 cot[5]) {
   const float c6 = 1.f / 6.f;
   const float dR[3][5] = {{2, -7, 11, 0, 0}, {0, -1, 5, 2, 0}, {0, 0, 2, 5, -1}};
   const float dL[3][5] = {{0, 0, 11, -7, 2}, {0, 2, 5, -1, 0}, {-1, 5, 2, 0, 0}};
@@ -220,7 +220,7 @@ __device__ __forceinline__ void weno5_pair_vjp_x2(const float2 q[5], float2 gL, 
 
 // tangential_vjp (nonlinear weights) of two five-point stencils at once.
 template <int MODE>
-__device__ __forceinline__ void tangential_vjp_x2(const float2 f[5], const float2 gv[2], const float2 gd[2],
+HGKS_HD void tangential_vjp_x2(const float2 f[5], const float2 gv[2], const float2 gd[2],
                                                   float2 cot[5]) {
   const float gs = 0.5f / 1.7320508075688772f;
   const float2 gb = fma2(bc2(gs), sub2(gv[1], gv[0]), add2(gd[0], gd[1]));
@@ -232,7 +232,7 @@ __device__ __forceinline__ void tangential_vjp_x2(const float2 f[5], const float
 // cot[j] += sum_m gv[m] dv[m]/df_j + gd[m] dd[m]/df_j for the tangential
 // polynomial of the five averages f (the transpose of tangential()).
 template <int MODE_, class T>
-__device__ __forceinline__ void tangential_vjp(const T f[5], const T gv[2], const T gd[2],
+HGKS_HD void tangential_vjp(const T f[5], const T gv[2], const T gd[2],
                                                T cot[5]) {
   constexpr int MODE = recon_of<MODE_>();
   const T sq3 = T(1.7320508075688772);

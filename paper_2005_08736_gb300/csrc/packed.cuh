@@ -12,18 +12,40 @@
 // rounding of the fused operations can differ from the scalar code.
 #pragma once
 
+#include <cmath>
+
 #include "physics.cuh"
 #include "recon.cuh"
 
 namespace hgks {
 
-__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// On the host (the checks of tests/support) each pair operation is the two
+// scalar operations it stands for.
+HGKS_HD float2 bc2(float s) { return make_float2(s, s); }
+HGKS_HD float2 add2(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+HGKS_HD float2 mul2(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+HGKS_HD float2 fma2(float2 a, float2 b, float2 c) {
+#if defined(__CUDA_ARCH__)
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
+#endif
+}
 // a - b
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
-__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.f / a.x, 1.f / a.y); }
+HGKS_HD float2 sub2(float2 a, float2 b) { return fma2(b, bc2(-1.f), a); }
+HGKS_HD float2 rcp2(float2 a) { return make_float2(1.f / a.x, 1.f / a.y); }
 
 // Linear-weight tangential reconstruction (the quartic through five face
 // averages) of two columns at once: values v[m] and derivatives d[m] (per
@@ -32,7 +54,7 @@ __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.f / a.x,
 //   E = 719/720 f2 + (f1+f3)/1080 - (f0+f4)/4320,
 //   O = sqrt3 (7/432 (f0-f4) + 25/216 (f3-f1)),
 //   A = (f0-f4)/12 + 2(f3-f1)/3,  B = sqrt3/54 (13 (f1+f3) - 24 f2 - (f0+f4)).
-__device__ __forceinline__ void tangential_linear_x2(float2 f0, float2 f1, float2 f2, float2 f3,
+HGKS_HD void tangential_linear_x2(float2 f0, float2 f1, float2 f2, float2 f3,
                                                      float2 f4, float2 v[2], float2 d[2]) {
   const float sq3 = 1.7320508075688772f;
   const float2 s13 = add2(f1, f3), s04 = add2(f0, f4);
@@ -48,7 +70,7 @@ __device__ __forceinline__ void tangential_linear_x2(float2 f0, float2 f1, float
   d[1] = add2(A, B);
 }
 
-__device__ __forceinline__ void tangential_linear_val_x2(float2 f0, float2 f1, float2 f2, float2 f3,
+HGKS_HD void tangential_linear_val_x2(float2 f0, float2 f1, float2 f2, float2 f3,
                                                          float2 f4, float2 v[2]) {
   const float sq3 = 1.7320508075688772f;
   const float2 s13 = add2(f1, f3), s04 = add2(f0, f4);
@@ -161,7 +183,7 @@ __device__ __forceinline__ void flux_smooth_x2(const PointStateX2& st, const Gas
 // weights and combinations in pair arithmetic; |beta0 - beta2| and the
 // reciprocals per half.
 template <int MODE>
-__device__ __forceinline__ void weno5_pair_x2(float2 q0, float2 q1, float2 q2, float2 q3, float2 q4,
+HGKS_HD void weno5_pair_x2(float2 q0, float2 q1, float2 q2, float2 q3, float2 q4,
                                               float2& qL, float2& qR) {
   const float2 c6 = bc2(1.f / 6.f);
   const float2 pR0 = mul2(fma2(bc2(2.f), q0, fma2(bc2(-7.f), q1, mul2(bc2(11.f), q2))), c6);
@@ -206,7 +228,7 @@ __device__ __forceinline__ void weno5_pair_x2(float2 q0, float2 q1, float2 q2, f
 // of two columns at once: values v[m] and derivatives d[m] at the two Gauss
 // abscissae from the quadratic through the WENO5 end values and the average.
 template <int MODE>
-__device__ __forceinline__ void tangential_weno_x2(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4,
+HGKS_HD void tangential_weno_x2(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4,
                                                    float2 v[2], float2 d[2]) {
   float2 qL, qR;
   weno5_pair_x2<MODE>(f0, f1, f2, f3, f4, qL, qR);
